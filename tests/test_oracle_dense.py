@@ -1,0 +1,91 @@
+"""Pins for the conventional (dense) BIEM: exact disk solutions and energy balance."""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+from oracle import dense, geometry, mie
+from paper_2603_09381_gb300 import workloads as wl
+
+ANG = math.radians(30.0)
+
+
+def _mie_error(prob, angle=ANG):
+    phi = dense.solve(prob, [angle])[:, 0]
+    k0 = prob["k_out"]
+    inc0 = prob["inclusions"][0]
+    k1, a = inc0["k_in"], inc0["prm"][0]
+    cents = [(i["cx"], i["cy"]) for i in prob["inclusions"]]
+    U, Q, M = mie.disks_solution(cents, a, k0, k1, (k1 / k0) ** 2, angle)
+    err, ref = [], []
+    for j, (q, u) in enumerate(dense.split(prob, phi)):
+        theta = geometry.nodes(prob["inclusions"][j])["t"]
+        ue, qe = mie.boundary_values(U[j], Q[j], theta, M)
+        err.append(np.concatenate([q - qe, u - ue]))
+        ref.append(np.concatenate([qe, ue]))
+    return np.linalg.norm(np.concatenate(err)) / np.linalg.norm(np.concatenate(ref))
+
+
+def test_graf_addition_theorem():
+    k = 2 * math.pi
+    ci, cj = np.array([1.0, 0.3]), np.array([-0.2, 0.1])
+    M = 40
+    W = mie.translation_matrix(ci, cj, k, M)
+    ms = np.arange(-M, M + 1)
+    x = ci + 0.35 * np.array([math.cos(2.0), math.sin(2.0)])
+    dj, di = x - cj, x - ci
+    for m in [0, 1, -3, 7]:
+        lhs = sp.hankel1(m, k * np.hypot(*dj)) * np.exp(1j * m * math.atan2(dj[1], dj[0]))
+        rhs = np.sum(W[:, m + M] * sp.jv(ms, k * np.hypot(*di)) * np.exp(1j * ms * math.atan2(di[1], di[0])))
+        assert abs(lhs - rhs) < 1e-12
+
+
+def test_single_disk_mie():
+    assert _mie_error(wl.circle_grid(1, 1, n=64)) < 1e-12
+
+
+def test_single_lossy_disk_mie():
+    assert _mie_error(wl.circle_grid(1, 1, n=64, k_in=4 * math.pi * (1 + 0.05j))) < 1e-12
+
+
+def test_two_disks_multipole():
+    # the plain trapezoid rule of the off-diagonal blocks (gap 0.2) limits n = 64 to ~2e-10
+    assert _mie_error(wl.circle_grid(2, 1, n=64)) < 3e-10
+    assert _mie_error(wl.circle_grid(2, 1, n=80)) < 1e-10
+
+
+def test_two_by_two_grid_multipole():
+    assert _mie_error(wl.circle_grid(2, 2, n=64)) < 6e-10
+    assert _mie_error(wl.circle_grid(2, 2, n=96), angle=1.1) < 1e-10
+
+
+@pytest.mark.parametrize("lossy", [False, True])
+def test_energy_balance(lossy):
+    k_in = 15.707963267948966 * ((1 + 0.05j) if lossy else 1)
+    # spacing 1.6: the off-diagonal trapezoid rule is then accurate, so the discrete
+    # solution satisfies the exact identity to near machine precision
+    prob = wl.star_grid(2, 2, n=128, seed=5, spacing=1.6)
+    for inc in prob["inclusions"]:
+        inc["k_in"] = k_in
+    phi = dense.solve(prob, [0.4])[:, 0]
+    eps = (k_in / prob["k_out"]) ** 2
+    for j, (q, u) in enumerate(dense.split(prob, phi)):
+        w = geometry.nodes(prob["inclusions"][j])["w"]
+        flux = np.sum(w * np.conj(u) * q) * eps
+        scale = np.sum(w * np.abs(u) * np.abs(q)) * abs(eps)
+        if lossy:
+            assert flux.imag < -1e-3 * scale
+        else:
+            assert abs(flux.imag) < 1e-9 * scale
+
+
+def test_omit_and_all_agree_to_discretisation_error():
+    prob = wl.circle_grid(2, 2, n=96)
+    a = dense.solve(prob, [ANG], "omit")[:, 0]
+    b = dense.solve(prob, [ANG], "all")[:, 0]
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-9
+    # and the interior off-diagonal potentials applied to the solution nearly vanish
+    A_all = dense.assemble(prob, "all")
+    A_omit = dense.assemble(prob, "omit")
+    assert np.linalg.norm((A_all - A_omit) @ a) < 1e-9 * np.linalg.norm(A_omit @ a)

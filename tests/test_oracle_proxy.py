@@ -1,0 +1,53 @@
+"""Pins for the proxy/ID fast direct solver: agreement with the dense solve."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, proxy
+from paper_2603_09381_gb300 import workloads as wl
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_small_circle_grid_matches_dense():
+    prob, opts, angs = wl.config_fp64_small()
+    fac = proxy.factor(prob, opts)
+    F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
+    assert _rel(proxy.solve(fac, F), dense.solve(prob, angs)) < 1e-11
+    assert fac["L"] == 1 and fac["stats"]["K"] <= 512
+
+
+def test_single_inclusion_degenerates_to_dense():
+    prob = wl.star_grid(1, 1, n=64)
+    fac = proxy.factor(prob, {"tol": 1e-10})
+    assert fac["L"] == 0
+    f = dense.plane_wave(prob, 0.7)
+    assert _rel(proxy.solve(fac, f), dense.solve(prob, [0.7])[:, 0]) < 1e-13
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_star_grid_matches_dense_within_tolerance(tol):
+    prob = wl.star_grid(4, 4, n=64, seed=1)
+    fac = proxy.factor(prob, {"tol": tol, "proxy_factor": 1.5})
+    phi = proxy.solve(fac, dense.plane_wave(prob, 0.3))
+    ref = dense.solve(prob, [0.3])[:, 0]
+    assert _rel(phi, ref) < 30 * tol
+    assert fac["stats"]["K"] < fac["N"]
+
+
+def test_ranks_shrink_with_looser_tolerance():
+    prob = wl.star_grid(4, 4, n=64, seed=1)
+    k_tight = proxy.factor(prob, {"tol": 1e-10})["stats"]["K"]
+    k_loose = proxy.factor(prob, {"tol": 1e-4})["stats"]["K"]
+    assert k_loose < k_tight
+
+
+def test_ragged_grid_and_multi_rhs():
+    prob = wl.circle_grid(3, 2, n=48)
+    fac = proxy.factor(prob, {"tol": 1e-10})
+    angs = [0.1, 2.0, 4.0]
+    F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
+    assert _rel(proxy.solve(fac, F), dense.solve(prob, angs)) < 1e-8
