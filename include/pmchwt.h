@@ -1,0 +1,166 @@
+/*
+ * pmchwt.h -- C ABI of the GB300 proxy fast direct solver for 2-D Helmholtz
+ * transmission scattering by many disjoint inclusions in the PMCHWT (Omit)
+ * formulation (Y. Matsumoto, arXiv 2603.09381).
+ *
+ * Conventions
+ *  - Every call returns pm_status; PM_OK == 0.  On any other status the call
+ *    has produced no partial output, and pm_last_error() returns a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Complex numbers are pm_c64 {re, im}, layout-compatible with complex128.
+ *  - Unknowns and equations are ordered per inclusion, in input order.
+ *    Inclusion j with n_j nodes owns 2 n_j consecutive entries:
+ *      unknowns  phi_j = [q_j (n_j); u_j (n_j)]          (paper Sec. 2.2, phi_i)
+ *      equations       = [u-equation rows; q-equation rows],
+ *      plane-wave RHS f_j = [-u^I_j; -q^I_j]             (paper Sec. 2.2, f_i)
+ *    where u is the total field on the boundary and q = (1/eps) du/dn its
+ *    scaled normal derivative (paper Sec. 2.1, eqs. pressure and flux),
+ *    N = sum_j 2 n_j.  Matrices and multi-RHS blocks are column-major.
+ *  - Handles are owned by the library and released with the *_free calls
+ *    (NULL-safe).  Factor handles are immutable after pm_factor.
+ *  - All compute runs on the current CUDA device; there is no CPU fallback.
+ *    If no CUDA device is present the calls fail with PM_ERR_CUDA.
+ */
+#ifndef PMCHWT_H
+#define PMCHWT_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PM_OK = 0,
+  PM_ERR_INVALID_ARG = 1,   /* bad pointer, size, shape or option */
+  PM_ERR_OOM = 2,           /* device or host allocation failed */
+  PM_ERR_CUDA = 3,          /* CUDA runtime error (message names the call) */
+  PM_ERR_SINGULAR = 4,      /* exactly singular pivot in an LU, or R A^{-1} L singular */
+  PM_ERR_NOT_CONVERGED = 5, /* reserved for iterative refinement */
+  PM_ERR_TIMEOUT = 6,       /* reserved for bounded device waits */
+  PM_ERR_GEOMETRY = 7,      /* inclusions not on a grid, two in one cell, ... */
+  PM_ERR_UNSUPPORTED = 8    /* valid input the library does not handle yet */
+} pm_status;
+
+typedef struct { double re, im; } pm_c64;
+
+enum { PM_CIRCLE = 0, PM_ELLIPSE = 1, PM_STAR = 2, PM_FOURIER = 3 };
+enum { PM_FP64 = 0 };
+
+/* One inclusion (paper Sec. 2.1: Omega_j with smooth boundary Gamma_j).
+ * Boundary x(t) = (cx, cy) + Rot(rot) rho(t), t in [0, 2 pi), counter-clockwise:
+ *   PM_CIRCLE : prm[0] = a;                     rho = a (cos t, sin t)
+ *   PM_ELLIPSE: prm[0] = a, prm[1] = b;         rho = (a cos t, b sin t)
+ *   PM_STAR   : prm[0] = r0, prm[1] = e, prm[2] = p;  r(t) = r0 (1 + e cos(p t))
+ *   PM_FOURIER: prm[0] = r0, prm[1..5] = a_2..a_6, prm[6..10] = phi_2..phi_6;
+ *               r(t) = r0 (1 + sum_m a_m cos(m t + phi_m)),  rho = r(t) (cos t, sin t)
+ * n_nodes: Nystrom nodes t_l = 2 pi l / n (paper Sec. 2.2), even, 16..4096.
+ * k_in: interior wavenumber k^- (eps^- = (k^-/k^+)^2, eps^+ = 1).  Only real
+ * k_in is supported by this build (complex -> PM_ERR_UNSUPPORTED). */
+typedef struct {
+  int32_t shape;
+  double cx, cy, rot;
+  double prm[16];
+  int32_t n_nodes;
+  pm_c64 k_in;
+} pm_inclusion;
+
+/* m inclusions on a grid of spacing `spacing` (paper Sec. 4: inclusions on a
+ * regular grid, each one a leaf cell).  k_out = k^+ = omega (eps^+ = 1). */
+typedef struct {
+  int32_t m;
+  const pm_inclusion* inc;
+  double k_out;
+  int32_t grid_nx, grid_ny;
+  double spacing;
+} pm_problem;
+
+typedef struct pm_geometry pm_geometry;
+typedef struct pm_factor pm_factor;
+
+/* Factorization options.
+ * tol: CPQR threshold epsilon; a column is kept while |R_jj| > tol |R_11|
+ *      (paper Sec. 3, adaptive rank).  Must be in (0, 1).
+ * proxy_factor: proxy circle radius / cell radius (> 1; default 1.5).
+ * proxy_points: points on every proxy circle; 0 selects
+ *      p = max(32, 8 ceil((2 k^+ R_p + ceil(ln(1/tol)/ln(proxy_factor)))/8)).
+ * precision: PM_FP64.
+ * stream: cudaStream_t to run on, or NULL for the default stream. */
+typedef struct {
+  double tol;
+  double proxy_factor;
+  int32_t proxy_points;
+  int32_t precision;
+  void* stream;
+  uint32_t flags;
+} pm_factor_opts;
+
+/* Statistics of a factorization (filled by pm_factor_stats). */
+typedef struct {
+  int32_t levels;           /* compressed levels L (0: a single inclusion, dense) */
+  int32_t N;                /* unknowns 2 sum n_j */
+  int32_t K;                /* size of the top-level dense system */
+  int32_t skeleton[16];     /* sum of box ranks per level, index = level (1..L) */
+  double ms_assemble, ms_id, ms_schur, ms_top, ms_total;   /* factor phase times */
+} pm_stats;
+
+/* Build node geometry on the device (paper Sec. 2.2) and the quadtree
+ * (paper Sec. 3 / Sec. 4: each inclusion a leaf cell, Morton order).
+ * The problem struct and its inclusion array are copied; the caller keeps
+ * ownership.  Errors: PM_ERR_INVALID_ARG (m < 1, bad shape, odd n_nodes ...),
+ * PM_ERR_GEOMETRY (two inclusions rounding to one grid cell),
+ * PM_ERR_UNSUPPORTED (complex k_in). */
+pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out);
+
+/* Number of unknowns N = 2 sum n_j. */
+pm_status pm_geometry_size(const pm_geometry* g, int32_t* N, int32_t* total_nodes);
+
+/* Copy node data to caller buffers (host): xy (2 x total_nodes, interleaved x,y),
+ * nrm (interleaved unit outward normals), w (trapezoid weights (2 pi/n)|x'|).
+ * Any pointer may be NULL. */
+pm_status pm_geometry_nodes(const pm_geometry* g, double* xy, double* nrm, double* w);
+
+/* Plane-wave right-hand sides (paper Sec. 4: u^I = exp(i k^+ d.x)), one column
+ * per angle: rhs is N x nrhs column-major, on the device if on_device = 1
+ * (caller-owned, e.g. a torch tensor's data_ptr), else on the host. */
+pm_status pm_plane_wave_rhs(const pm_geometry* g, const double* angles, int32_t nrhs, pm_c64* rhs,
+                            int32_t on_device);
+
+/* Factor the PMCHWT (Omit) system (paper Sec. 2.2, eq. pmchwt_omit_bie) with
+ * the multilevel proxy / interpolative-decomposition fast direct solver
+ * (paper Sec. 3): self blocks, proxy IDs per cell (exterior kernel only),
+ * compressed blocks A~_i = (R_i A_ii^{-1} L_i)^{-1}, recursive merge, top LU.
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_SINGULAR. */
+pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_factor** out);
+
+/* Solve A phi = rhs for nrhs right-hand sides (paper Sec. 3: eq. compressed and
+ * the recovery formula).  rhs and phi are N x nrhs column-major, device
+ * pointers if on_device = 1, else host pointers; they may alias. */
+pm_status pm_solve(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device);
+
+pm_status pm_factor_stats(const pm_factor* f, pm_stats* out);
+
+/* Skeleton (selected) global row / column indices of one box, for inspection.
+ * level in 1..L, box in Morton order of that level; rows/cols receive up to
+ * cap entries each; *k receives the box rank. */
+pm_status pm_factor_skeleton(const pm_factor* f, int32_t level, int32_t box, int32_t* rows, int32_t* cols,
+                             int32_t cap, int32_t* k);
+
+/* Entries of the PMCHWT (Omit) matrix between inclusions (trapezoid rule,
+ * exterior kernel only, paper Sec. 2.2): out[i + j M] = A(rows[i], cols[j])
+ * for global indices on different inclusions (same-inclusion pairs give 0).
+ * Host arrays; M x N complex output. */
+pm_status pm_matrix_entries(const pm_geometry* g, const int32_t* rows, int32_t M, const int32_t* cols,
+                            int32_t Ncols, pm_c64* out);
+
+/* The self block A_jj (2 n_j x 2 n_j, column-major) of inclusion j
+ * (paper Sec. 2.2: Kress log-split quadrature for S, D, D*; Maue's form of N). */
+pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out);
+
+void pm_factor_free(pm_factor* f);
+void pm_geometry_free(pm_geometry* g);
+const char* pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,318 @@
+// Node geometry, plane-wave right-hand sides, self blocks (Kress log split +
+// Maue) and gathered off-diagonal entries of the PMCHWT (Omit) system.
+//
+// Kernel normalisation G = (i/4) H0(k r); with d = x - y, r = |d|:
+//   S = (i/4) H0,  D = (ik/4) H1 (n_y.d)/r,  D* = -(ik/4) H1 (n_x.d)/r,
+//   N = (ik/4) [k H0 (n_x.d)(n_y.d)/r^2 + H1/r (n_x.n_y - 2 (n_x.d)(n_y.d)/r^2)]
+// (paper Sec. 2.1, eqs. slp, dlp, d_slp, d_dlp).  Bessel values for real
+// arguments come from CUDA's j0/j1/y0/y1 (FP64) or j0f/j1f/y0f/y1f (FP32).
+#include "assemble.cuh"
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double EULER_C = 0.57721566490153286061;
+
+__device__ __forceinline__ void polar_r(const InclDev& c, double t, double& r, double& dr, double& ddr) {
+  if (c.shape == 0) { r = c.prm[0]; dr = 0; ddr = 0; return; }
+  if (c.shape == 2) {
+    double r0 = c.prm[0], e = c.prm[1], p = c.prm[2];
+    double cs, sn; sincos(p * t, &sn, &cs);
+    r = r0 * (1 + e * cs); dr = -r0 * e * p * sn; ddr = -r0 * e * p * p * cs; return;
+  }
+  // fourier: r0 (1 + sum_{m=2..6} a_m cos(m t + phi_m))
+  double r0 = c.prm[0];
+  double a = 1, b = 0, d = 0;
+  for (int i = 0; i < 5; ++i) {
+    double m = 2 + i, am = c.prm[1 + i], ph = c.prm[6 + i];
+    double cs, sn; sincos(m * t + ph, &sn, &cs);
+    a += am * cs; b -= am * m * sn; d -= am * m * m * cs;
+  }
+  r = r0 * a; dr = r0 * b; ddr = r0 * d;
+}
+
+__global__ void k_geom_nodes(const InclDev* __restrict__ inc, NodesDev nd, int total) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int j = nd.incl[g];
+  const InclDev c = inc[j];
+  const int l = g - c.node_off;
+  const int n = c.n;
+  const double t = 2 * PI * l / n;
+  double ct, st; sincos(t, &st, &ct);
+  double lx, ly, dx, dy, ddx, ddy;
+  if (c.shape == 1) {
+    double a = c.prm[0], b = c.prm[1];
+    lx = a * ct; ly = b * st; dx = -a * st; dy = b * ct; ddx = -a * ct; ddy = -b * st;
+  } else {
+    double r, dr, ddr; polar_r(c, t, r, dr, ddr);
+    lx = r * ct; ly = r * st;
+    dx = dr * ct - r * st; dy = dr * st + r * ct;
+    ddx = ddr * ct - 2 * dr * st - r * ct; ddy = ddr * st + 2 * dr * ct - r * st;
+  }
+  double cr, sr; sincos(c.rot, &sr, &cr);
+  double X = c.cx + cr * lx - sr * ly, Y = c.cy + sr * lx + cr * ly;
+  double DX = cr * dx - sr * dy, DY = sr * dx + cr * dy;
+  double DDX = cr * ddx - sr * ddy, DDY = sr * ddx + cr * ddy;
+  double sp = sqrt(DX * DX + DY * DY);
+  double nx = DY / sp, ny = -DX / sp;
+  nd.x[g] = X; nd.y[g] = Y; nd.nx[g] = nx; nd.ny[g] = ny;
+  nd.speed[g] = sp; nd.w[g] = 2 * PI / n * sp;
+  nd.curv[g] = (nx * DDX + ny * DDY) / sp;
+  // Kress weight R_n(s), s = 2 pi l / n:
+  //   -(4 pi/n) sum_{m=1}^{n/2-1} cos(m s)/m - (4 pi/n^2) cos(n s/2)
+  double acc = 0;
+  for (int m = 1; m < n / 2; ++m) acc += cos(2 * PI * (double)((long long)m * l % n) / n) / m;
+  nd.kress[g] = -(4 * PI / n) * acc - (4 * PI / ((double)n * n)) * ((l & 1) ? -1.0 : 1.0);
+}
+
+__global__ void k_points_from_nodes(NodesDev nd, PointsDev p, int total) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  p.x[g] = nd.x[g]; p.y[g] = nd.y[g]; p.nx[g] = nd.nx[g]; p.ny[g] = nd.ny[g]; p.w[g] = nd.w[g];
+}
+
+__global__ void k_proxy_points(const ProxyBoxDev* __restrict__ box, int nbox, PointsDev p, int total, int off) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = nbox;
+  while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (box[mid].point_off <= g) lo = mid; else hi = mid; }
+  const ProxyBoxDev b = box[lo];
+  int s = g - b.point_off;
+  double th = 2 * PI * s / b.p;
+  double c, sn; sincos(th, &sn, &c);
+  int q = off + g;
+  p.x[q] = b.cx + b.R * c; p.y[q] = b.cy + b.R * sn;
+  p.nx[q] = c; p.ny[q] = sn; p.w[q] = 2 * PI * b.R / b.p;
+}
+
+template <typename C>
+__global__ void k_plane_wave(const InclDev* __restrict__ inc, NodesDev nd, int total, double k0,
+                             const double* __restrict__ ang, int nrhs, C* F, int ldf) {
+  typedef typename real_of<C>::type R;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (g >= total || r >= nrhs) return;
+  const InclDev c = inc[nd.incl[g]];
+  const int l = g - c.node_off;
+  double ca, sa; sincos(ang[r], &sa, &ca);
+  double ph = k0 * (ca * nd.x[g] + sa * nd.y[g]);
+  double cp, sp; sincos(ph, &sp, &cp);
+  double dn = k0 * (ca * nd.nx[g] + sa * nd.ny[g]);
+  // f = [-u^I; -q^I], q^I = (1/eps+) i k0 (d.n) u^I with eps+ = 1
+  F[c.row_off + l + (size_t)r * ldf] = mk((R)(-cp), (R)(-sp));
+  F[c.row_off + c.n + l + (size_t)r * ldf] = mk((R)(dn * sp), (R)(-dn * cp));
+}
+
+// Bessel J0, Y0, J1, Y1 of a positive real argument.
+__device__ __forceinline__ void bessel4(double z, double& j0v, double& y0v, double& j1v, double& y1v) {
+  j0v = j0(z); y0v = y0(z); j1v = j1(z); y1v = y1(z);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_self_pointwise(const InclDev* __restrict__ inc, NodesDev nd, double k0,
+                                                        C* const* __restrict__ Aptr, const int* __restrict__ ldA,
+                                                        C* const* __restrict__ Cptr) {
+  typedef typename real_of<C>::type R;
+  const int j = blockIdx.y;
+  const InclDev c = inc[j];
+  const int n = c.n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int i = e % n, l = e / n;   // target node i, source node l
+  const int gi = c.node_off + i, gl = c.node_off + l;
+  const double h = 2 * PI / n;
+  const double spl = nd.speed[gl], spi = nd.speed[gi];
+  const double nxi = nd.nx[gi], nyi = nd.ny[gi], nxl = nd.nx[gl], nyl = nd.ny[gl];
+  const double nn = nxi * nxl + nyi * nyl;
+  const double ks[2] = {k0, c.k_in_re};
+  const double eps_in = c.eps_in_re;
+  double Sre[2], Sim[2], Dre[2], Dim[2], Tre[2], Tim[2];
+  const int d = (i - l + n) % n;
+  const double Rw = nd.kress[c.node_off + d];
+  if (i == l) {
+    for (int q = 0; q < 2; ++q) {
+      double k = ks[q];
+      double M1 = -spi / (4 * PI);
+      double M2re = (-EULER_C / (2 * PI) - log(k * spi / 2) / (2 * PI)) * spi, M2im = 0.25 * spi;
+      Sre[q] = Rw * M1 + h * M2re; Sim[q] = h * M2im;
+      double L2 = nd.curv[gi] / (4 * PI);
+      Dre[q] = h * L2; Dim[q] = 0; Tre[q] = h * L2; Tim[q] = 0;
+    }
+  } else {
+    const double dx = nd.x[gi] - nd.x[gl], dy = nd.y[gi] - nd.y[gl];
+    const double r = sqrt(dx * dx + dy * dy);
+    const double ndy = (nxl * dx + nyl * dy) / r, ndx = (nxi * dx + nyi * dy) / r;
+    double sn = sin(PI * (double)(i - l) / n);
+    const double logsin = log(4 * sn * sn);
+    for (int q = 0; q < 2; ++q) {
+      double k = ks[q];
+      double J0, Y0, J1, Y1;
+      bessel4(k * r, J0, Y0, J1, Y1);
+      // single layer: M = (i/4) H0 |x'|, M1 = -(1/4pi) J0 |x'|
+      double Mre = -0.25 * Y0 * spl, Mim = 0.25 * J0 * spl;
+      double M1 = -J0 * spl / (4 * PI);
+      Sre[q] = Rw * M1 + h * (Mre - M1 * logsin); Sim[q] = h * Mim;
+      // double layer: L = (ik/4) H1 (n_y.d)/r |x'|, L1 = -(k/4pi) J1 (n_y.d)/r |x'|
+      double Lre = -0.25 * k * Y1 * ndy * spl, Lim = 0.25 * k * J1 * ndy * spl;
+      double L1 = -k * J1 * ndy * spl / (4 * PI);
+      Dre[q] = Rw * L1 + h * (Lre - L1 * logsin); Dim[q] = h * Lim;
+      // adjoint: L* = -(ik/4) H1 (n_x.d)/r |x'|, L1* = (k/4pi) J1 (n_x.d)/r |x'|
+      double Tre_ = 0.25 * k * Y1 * ndx * spl, Tim_ = -0.25 * k * J1 * ndx * spl;
+      double T1 = k * J1 * ndx * spl / (4 * PI);
+      Tre[q] = Rw * T1 + h * (Tre_ - T1 * logsin); Tim[q] = h * Tim_;
+    }
+  }
+  C* A = Aptr[j];
+  const size_t lda = ldA[j];
+  // [[-(e+ S+ + e- S-), D+ + D-], [-(D*+ + D*-), k+^2/e+ S+ o nn + k-^2/e- S- o nn (+ Maue part)]]
+  A[i + (size_t)l * lda] = mk((R)(-(Sre[0] + eps_in * Sre[1])), (R)(-(Sim[0] + eps_in * Sim[1])));
+  A[i + (size_t)(n + l) * lda] = mk((R)(Dre[0] + Dre[1]), (R)(Dim[0] + Dim[1]));
+  A[n + i + (size_t)l * lda] = mk((R)(-(Tre[0] + Tre[1])), (R)(-(Tim[0] + Tim[1])));
+  const double a0 = k0 * k0 * nn, a1 = ks[1] * ks[1] / eps_in * nn;
+  A[n + i + (size_t)(n + l) * lda] = mk((R)(a0 * Sre[0] + a1 * Sre[1]), (R)(a0 * Sim[0] + a1 * Sim[1]));
+  // Maue middle factor: S0+/e+ + S0-/e-, S0 = S / |x'(tau)|
+  C* Cm = Cptr[j];
+  Cm[i + (size_t)l * n] = mk((R)((Sre[0] + Sre[1] / eps_in) / spl), (R)((Sim[0] + Sim[1] / eps_in) / spl));
+}
+
+template <typename C>
+__global__ void k_diff_matrix(int n, C* Dt) {
+  typedef typename real_of<C>::type R;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  int i = e % n, j = e / n;
+  double v = 0;
+  if (i != j) {
+    int d = i - j;
+    v = 0.5 * ((d & 1) ? -1.0 : 1.0) / tan(PI * (double)d / n);
+  }
+  Dt[e] = mk((R)v, (R)0);
+}
+
+template <typename C>
+__global__ void k_scaled_diff(const InclDev* __restrict__ inc, NodesDev nd, C* const* __restrict__ out) {
+  typedef typename real_of<C>::type R;
+  const int j = blockIdx.y;
+  const InclDev c = inc[j];
+  const int n = c.n;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  int i = e % n, l = e / n;
+  double v = 0;
+  if (i != l) {
+    int d = i - l;
+    v = 0.5 * ((d & 1) ? -1.0 : 1.0) / tan(PI * (double)d / n) / nd.speed[c.node_off + i];
+  }
+  out[j][e] = mk((R)v, (R)0);
+}
+
+// Omit off-diagonal entry between a target (row group rg) and a source (column group cg).
+template <typename C>
+__device__ __forceinline__ C omit_entry(const PointsDev& P, int t, int s, double k) {
+  typedef typename real_of<C>::type R;
+  const int pt = t >> 1, rg = t & 1, ps = s >> 1, cg = s & 1;
+  const double dx = P.x[pt] - P.x[ps], dy = P.y[pt] - P.y[ps];
+  const double r2 = dx * dx + dy * dy;
+  if (!(r2 > 0)) return czero<C>();
+  const double r = sqrt(r2);
+  const double z = k * r;
+  const double w = P.w[ps];
+  if (rg == 0 && cg == 0) {         // -eps+ S = -(i/4) H0 w
+    double J0 = j0(z), Y0 = y0(z);
+    return mk((R)(0.25 * Y0 * w), (R)(-0.25 * J0 * w));
+  }
+  const double J1 = j1(z), Y1 = y1(z);
+  if (rg == 0) {                    // D = (ik/4) H1 (n_y.d)/r w
+    double g = (P.nx[ps] * dx + P.ny[ps] * dy) / r * 0.25 * k * w;
+    return mk((R)(-Y1 * g), (R)(J1 * g));
+  }
+  if (cg == 0) {                    // -D* = (ik/4) H1 (n_x.d)/r w
+    double g = (P.nx[pt] * dx + P.ny[pt] * dy) / r * 0.25 * k * w;
+    return mk((R)(-Y1 * g), (R)(J1 * g));
+  }
+  // N/eps+ = (ik/4) [k H0 a b + H1/r (nn - 2 a b)] w,  a = n_x.d/r, b = n_y.d/r
+  const double J0 = j0(z), Y0 = y0(z);
+  const double a = (P.nx[pt] * dx + P.ny[pt] * dy) / r, b = (P.nx[ps] * dx + P.ny[ps] * dy) / r;
+  const double nn = P.nx[pt] * P.nx[ps] + P.ny[pt] * P.ny[ps];
+  const double c0 = k * a * b, c1 = (nn - 2 * a * b) / r;
+  const double Hre = c0 * J0 + c1 * J1, Him = c0 * Y0 + c1 * Y1;   // k H0 ab + H1/r (...)
+  const double f = 0.25 * k * w;
+  return mk((R)(-Him * f), (R)(Hre * f));
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_gather(const GatherProb<C>* __restrict__ prob, const int* __restrict__ tile_off,
+                                                int nprob, PointsDev P, double k) {
+  int t = blockIdx.x;
+  int lo = 0, hi = nprob;
+  while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (tile_off[mid] <= t) lo = mid; else hi = mid; }
+  const GatherProb<C> g = prob[lo];
+  int local = t - tile_off[lo];
+  int tiles_m = (g.M + 31) / 32;
+  int i = (local % tiles_m) * 32 + (threadIdx.x & 31);
+  int j = (local / tiles_m) * 8 + (threadIdx.x >> 5);
+  if (i >= g.M || j >= g.N) return;
+  int tc = g.trans ? g.tgt[j] : g.tgt[i];
+  int sc = g.trans ? g.src[i] : g.src[j];
+  g.out[i + (size_t)j * g.ld] = omit_entry<C>(P, tc, sc, k);
+}
+
+}  // namespace
+
+void geom_nodes(const InclDev* d_inc, NodesDev nodes, int total, const InclDev*, cudaStream_t st) {
+  if (total <= 0) return;
+  k_geom_nodes<<<(total + 127) / 128, 128, 0, st>>>(d_inc, nodes, total);
+}
+
+void geom_points_from_nodes(NodesDev nodes, PointsDev pts, int total, cudaStream_t st) {
+  if (total <= 0) return;
+  k_points_from_nodes<<<(total + 255) / 256, 256, 0, st>>>(nodes, pts, total);
+}
+
+void geom_proxy_points(const ProxyBoxDev* d_box, int nbox, PointsDev pts, int total, int off, cudaStream_t st) {
+  if (total <= 0 || nbox <= 0) return;
+  k_proxy_points<<<(total + 255) / 256, 256, 0, st>>>(d_box, nbox, pts, total, off);
+}
+
+template <typename C>
+void plane_wave_rhs(const InclDev* d_inc, NodesDev nodes, int total, double k0, const double* d_ang, int nrhs,
+                    C* F, int ldf, cudaStream_t st) {
+  if (total <= 0 || nrhs <= 0) return;
+  dim3 g((total + 255) / 256, nrhs);
+  k_plane_wave<C><<<g, 256, 0, st>>>(d_inc, nodes, total, k0, d_ang, nrhs, F, ldf);
+}
+
+template <typename C>
+void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, double k0, C* const* d_A,
+                    const int* d_lda, C* const* d_Cm, cudaStream_t st) {
+  if (m <= 0) return;
+  dim3 g((maxn * maxn + 255) / 256, m);
+  k_self_pointwise<C><<<g, 256, 0, st>>>(d_inc, nodes, k0, d_A, d_lda, d_Cm);
+}
+
+template <typename C>
+void diff_matrices(int n, C* Dt, cudaStream_t st) {
+  k_diff_matrix<C><<<(n * n + 255) / 256, 256, 0, st>>>(n, Dt);
+}
+
+template <typename C>
+void scaled_diff(const InclDev* d_inc, int m, int maxn, NodesDev nodes, C* const* d_DtS, cudaStream_t st) {
+  if (m <= 0) return;
+  dim3 g((maxn * maxn + 255) / 256, m);
+  k_scaled_diff<C><<<g, 256, 0, st>>>(d_inc, nodes, d_DtS);
+}
+
+template <typename C>
+void gather_assemble(const GatherProb<C>* d_prob, const int* d_tile_off, int nprob, int total_tiles,
+                     PointsDev pts, double k0, cudaStream_t st) {
+  if (nprob <= 0 || total_tiles <= 0) return;
+  k_gather<C><<<total_tiles, 256, 0, st>>>(d_prob, d_tile_off, nprob, pts, k0);
+}
+
+template void plane_wave_rhs<double2>(const InclDev*, NodesDev, int, double, const double*, int, double2*, int, cudaStream_t);
+template void self_pointwise<double2>(const InclDev*, int, int, NodesDev, double, double2* const*, const int*,
+                                      double2* const*, cudaStream_t);
+template void diff_matrices<double2>(int, double2*, cudaStream_t);
+template void scaled_diff<double2>(const InclDev*, int, int, NodesDev, double2* const*, cudaStream_t);
+template void gather_assemble<double2>(const GatherProb<double2>*, const int*, int, int, PointsDev, double, cudaStream_t);

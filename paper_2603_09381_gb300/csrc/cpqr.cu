@@ -1,0 +1,233 @@
+// Column-pivoted Householder QR, one launch per elimination step.
+//
+// Each CTA owns up to 32 columns of one matrix.  At step s every CTA of the
+// matrix reads the same squared trailing norms, picks the same pivot
+// (largest norm; norms within a factor 1 - 1e-12 of the largest count as
+// tied and the lowest column index wins), forms the Householder reflector of
+// the pivot column (LAPACK zlarfg phase convention) and applies H^H to its
+// own columns, recomputing their trailing norms from scratch for step s+1.
+// The pivot column itself is left in place; R_ss goes to rdiag[s].  Because
+// consecutive steps are consecutive launches no grid-wide barrier is needed.
+// Work per entry and step: ~10 real FMAs on 48 bytes, so the FP64 pipe, not
+// HBM, bounds it on GB300.
+#include "cpqr.cuh"
+
+namespace {
+
+constexpr double TIE = 1e-12;
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_init_norms(const CpqrProb<C>* __restrict__ P, const CpqrChunk* __restrict__ chunks) {
+  typedef typename real_of<C>::type R;
+  const CpqrChunk ch = chunks[blockIdx.x];
+  const CpqrProb<C> p = P[ch.id];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = ch.c0 + warp; c < ch.c1; c += 8) {
+    const C* col = p.Z + (size_t)c * p.ld;
+    R acc = 0;
+    for (int r = lane; r < p.W; r += 32) acc += abs2(col[r]);
+    acc = warp_sum(acc);
+    if (lane == 0) p.norm2[c] = (double)acc;
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict__ P, const CpqrChunk* __restrict__ chunks, int t) {
+  typedef typename real_of<C>::type R;
+  const CpqrChunk ch = chunks[blockIdx.x];
+  const CpqrProb<C> p = P[ch.id];
+  const int s = p.base + t;
+  if (s >= p.target) return;
+  if (p.mode == CPQR_FIND_RANK && *p.rank >= 0) return;
+  const int n = p.n;
+  const double* cur = p.norm2 + (s & 1) * n;
+  double* nxt = p.norm2 + ((s + 1) & 1) * n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ double red[8];
+  __shared__ int redi[8];
+  __shared__ double s_mx;
+  __shared__ int s_q;
+  // pass 1: largest squared norm among unpivoted columns
+  double mx = -1.0;
+  for (int c = tid; c < n; c += 256) mx = fmax(mx, cur[c]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = red[0];
+    for (int w = 1; w < 8; ++w) m2 = fmax(m2, red[w]);
+    s_mx = m2;
+  }
+  __syncthreads();
+  mx = s_mx;
+  // pass 2: lowest index within the tie band
+  const double band = (1.0 - TIE) * mx;
+  int qi = n;
+  for (int c = tid; c < n; c += 256) if (cur[c] >= 0 && cur[c] >= band) { qi = c; break; }
+  for (int o = 16; o > 0; o >>= 1) qi = min(qi, __shfl_xor_sync(0xffffffffu, qi, o));
+  if (lane == 0) redi[warp] = qi;
+  __syncthreads();
+  if (tid == 0) {
+    int q2 = redi[0];
+    for (int w = 1; w < 8; ++w) q2 = min(q2, redi[w]);
+    s_q = q2;
+  }
+  __syncthreads();
+  const int q = s_q;
+  if (mx < 0 || q >= n) return;  // no unpivoted column left
+  if (p.mode == CPQR_FIND_RANK) {
+    double ref = (s == 0) ? sqrt(mx) : *p.ref;
+    if (s == 0 && ch.first && tid == 0) *p.ref = ref;
+    if (!(sqrt(mx) > p.tol * ref)) {
+      if (ch.first && tid == 0) *p.rank = s;
+      return;
+    }
+  }
+  const C* xq = p.Z + (size_t)q * p.ld;
+  const C alpha = xq[s];
+  const R xnorm = (R)sqrt(cur[q]);
+  const R beta = -copysign(xnorm, alpha.x);
+  C tau = czero<C>(), sc = czero<C>();
+  const bool reflect = xnorm > 0;
+  if (reflect) {
+    C bm = mk(beta, (R)0);
+    tau = cdiv(bm - alpha, bm);
+    sc = cdiv(mk((R)1, (R)0), alpha - bm);
+  }
+  const C ctau = conj(tau), csc = conj(sc);
+  for (int c = ch.c0 + warp; c < ch.c1; c += 8) {
+    if (cur[c] < 0 || c == q) { if (lane == 0) nxt[c] = -1.0; continue; }
+    C* col = p.Z + (size_t)c * p.ld;
+    if (!reflect) {
+      R acc = 0;
+      for (int r = s + 1 + lane; r < p.W; r += 32) acc += abs2(col[r]);
+      acc = warp_sum(acc);
+      if (lane == 0) nxt[c] = (double)acc;
+      continue;
+    }
+    C dot = czero<C>();
+    for (int r = s + 1 + lane; r < p.W; r += 32) cfma_conj(dot, __ldg(&xq[r]), col[r]);
+    dot.x = warp_sum(dot.x); dot.y = warp_sum(dot.y);
+    const C a_s = col[s];
+    dot = a_s + csc * dot;          // v^H a with v = [1; x/(alpha - beta)]
+    const C f = ctau * dot;         // H^H a = a - conj(tau) v (v^H a)
+    const C fs = f * sc;
+    if (lane == 0) col[s] = a_s - f;
+    R acc = 0;
+    for (int r = s + 1 + lane; r < p.W; r += 32) {
+      C v = col[r];
+      cfms(v, fs, __ldg(&xq[r]));
+      col[r] = v;
+      acc += abs2(v);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) nxt[c] = (double)acc;
+  }
+  if (tid == 0 && q >= ch.c0 && q < ch.c1) {
+    p.rdiag[s] = mk(beta, (R)0);
+    p.perm[s] = q;
+  }
+}
+
+template <typename C>
+__global__ void k_interp(const InterpProb<C>* __restrict__ P) {
+  const InterpProb<C> p = P[blockIdx.y];
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = p.k;
+  if (cc >= p.n - k || k <= 0) return;
+  const C* r12 = p.Z + (size_t)p.perm[k + cc] * p.ld;
+  C* t = p.T + (size_t)cc * p.ldt;
+  for (int i = k - 1; i >= 0; --i) {
+    C acc = r12[i];
+    for (int j = i + 1; j < k; ++j) cfms(acc, p.Z[i + (size_t)p.perm[j] * p.ld], t[j]);
+    t[i] = cdiv(acc, p.rdiag[i]);
+  }
+}
+
+template <typename C>
+__global__ void k_scatter(const ScatterProb<C>* __restrict__ P) {
+  typedef typename real_of<C>::type R;
+  const ScatterProb<C> p = P[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.k * p.ng) return;
+  const int j = e % p.k, c = e / p.k;
+  C v;
+  if (c < p.k) {
+    if (c != j) return;
+    v = mk((R)1, (R)0);
+  } else {
+    v = p.T[j + (size_t)(c - p.k) * p.ldt];
+  }
+  const int row = p.pos[p.perm[c]];
+  if (p.isL) p.out[row + (size_t)(p.off + j) * p.ld] = v;
+  else p.out[(p.off + j) + (size_t)row * p.ld] = v;
+}
+
+template <typename C>
+__global__ void k_copy(const CopyProb<C>* __restrict__ P) {
+  const CopyProb<C> p = P[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.m * p.n) return;
+  const int i = e % p.m, j = e / p.m;
+  p.dst[i + (size_t)j * p.ldd] = p.src[i + (size_t)j * p.lds];
+}
+
+// Completes a permutation: after `done` pivot steps, the remaining columns in
+// ascending order (one CTA per matrix).
+__global__ void k_complete_perm(const PermFill* __restrict__ P) {
+  extern __shared__ unsigned char used[];
+  const PermFill p = P[blockIdx.x];
+  for (int c = threadIdx.x; c < p.n; c += blockDim.x) used[c] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < p.done; s += blockDim.x) used[p.perm[s]] = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = p.done;
+    for (int c = 0; c < p.n; ++c) if (!used[c]) p.perm[o++] = c;
+  }
+}
+
+}  // namespace
+
+void complete_perm(const PermFill* d_prob, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_complete_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    attr = true;
+  }
+  k_complete_perm<<<nprob, 256, 65536, st>>>(d_prob);
+}
+
+template <typename C>
+void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, cudaStream_t st) {
+  if (nchunk > 0) k_init_norms<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk);
+}
+template <typename C>
+void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, cudaStream_t st) {
+  if (nchunk > 0) k_cpqr_step<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk, t);
+}
+template <typename C>
+void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st) {
+  if (nprob <= 0 || max_cols <= 0) return;
+  dim3 g((max_cols + 63) / 64, nprob);
+  k_interp<C><<<g, 64, 0, st>>>(d_prob);
+}
+template <typename C>
+void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {
+  if (nprob <= 0 || max_elems <= 0) return;
+  dim3 g((max_elems + 255) / 256, nprob);
+  k_scatter<C><<<g, 256, 0, st>>>(d_prob);
+}
+template <typename C>
+void copy_batched(const CopyProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {
+  if (nprob <= 0 || max_elems <= 0) return;
+  dim3 g((max_elems + 255) / 256, nprob);
+  k_copy<C><<<g, 256, 0, st>>>(d_prob);
+}
+
+template void cpqr_init_norms<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, cudaStream_t);
+template void cpqr_step<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, int, cudaStream_t);
+template void interp_solve<double2>(const InterpProb<double2>*, int, int, cudaStream_t);
+template void scatter_interp<double2>(const ScatterProb<double2>*, int, int, cudaStream_t);
+template void copy_batched<double2>(const CopyProb<double2>*, int, int, cudaStream_t);

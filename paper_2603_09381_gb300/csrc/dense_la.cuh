@@ -1,0 +1,42 @@
+// Batched complex dense linear algebra used by the factorization: GEMM,
+// partial-pivot LU and LU solves for many variable-size matrices at once.
+// All matrices are column-major with interleaved complex entries.
+#pragma once
+#include <cuda_runtime.h>
+#include "pm_common.cuh"
+
+template <typename C>
+struct GemmDesc {      // Cm = alpha * A(m x k) * B(k x n) + beta * Cm
+  int m, n, k;
+  const C* A; int lda;
+  const C* B; int ldb;
+  C* Cm; int ldc;
+  C alpha, beta;
+  int beta_zero;       // 1: Cm is write-only (beta ignored)
+};
+
+template <typename C>
+struct LuProb {        // in-place LU of the leading m x m block of A
+  C* A; int m; int ld;
+  int* ipiv;           // m entries, 0-based row interchanged with row i at step i
+  int* info;           // set to (first zero-pivot column + 1); 0 if none
+};
+
+template <typename C>
+struct SolveProb {     // B (m x nrhs) <- A^{-1} B using the LU of A
+  const C* A; int m; int ld;
+  const int* ipiv;
+  C* B; int ldb; int nrhs;
+};
+
+// Host launchers (dense_la.cu).  Descriptors live in device memory.
+template <typename C>
+void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob, int total_tiles,
+                     cudaStream_t st);
+template <typename C>
+void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, cudaStream_t st);
+template <typename C>
+void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, cudaStream_t st);
+
+// tiles of a GEMM problem for the 32 x 32 output tiling
+inline int gemm_tiles(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }

@@ -1,0 +1,1093 @@
+// Host runtime of the PMCHWT (Omit) proxy fast direct solver: C ABI entry
+// points, quadtree planner, level scheduler and device memory arenas.
+// Every numerical step runs in the CUDA kernels of assemble.cu, cpqr.cu and
+// dense_la.cu; this file only plans index lists and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/pmchwt.h"
+#include "assemble.cuh"
+#include "cpqr.cuh"
+#include "dense_la.cuh"
+
+typedef double2 Cd;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct PmError {
+  pm_status st;
+  std::string msg;
+};
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    pm_status s = (e == cudaErrorMemoryAllocation) ? PM_ERR_OOM : PM_ERR_CUDA;
+    cudaGetLastError();
+    throw PmError{s, std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+#define CK(x) ck((x), #x)
+
+void fail(pm_status s, const std::string& m) { throw PmError{s, m}; }
+
+// Bump allocator over large cudaMalloc blocks; reset() keeps the blocks for reuse.
+struct Arena {
+  struct Blk { char* p; size_t size; };
+  std::vector<Blk> blks;
+  size_t cur = 0, off = 0;
+  size_t min_block = (size_t)64 << 20;
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    while (cur < blks.size() && off + bytes > blks[cur].size) { ++cur; off = 0; }
+    if (cur == blks.size()) {
+      size_t sz = std::max(bytes, min_block);
+      void* p = nullptr;
+      CK(cudaMalloc(&p, sz));
+      blks.push_back({(char*)p, sz});
+      off = 0;
+    }
+    void* r = blks[cur].p + off;
+    off += bytes;
+    return r;
+  }
+  template <class T> T* get(size_t n) { return (T*)alloc(n * sizeof(T)); }
+  void reset() { cur = 0; off = 0; }
+  void release() {
+    for (auto& b : blks) cudaFree(b.p);
+    blks.clear();
+    cur = off = 0;
+  }
+  ~Arena() { release(); }
+};
+
+template <class T>
+T* upload(Arena& a, const std::vector<T>& v, cudaStream_t st) {
+  T* d = a.get<T>(std::max<size_t>(v.size(), 1));
+  if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+__global__ void k_identity(Cd* A, int m, int ld) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  int i = e % m, j = e / m;
+  A[i + (size_t)j * ld] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+}
+
+uint64_t morton(uint32_t x, uint32_t y) {
+  uint64_t c = 0;
+  for (int b = 0; b < 32; ++b) {
+    c |= (uint64_t)((x >> b) & 1) << (2 * b);
+    c |= (uint64_t)((y >> b) & 1) << (2 * b + 1);
+  }
+  return c;
+}
+
+struct Box {
+  int bx, by;
+  std::vector<int> leaves;    // inclusion ids
+  std::vector<int> children;  // indices into the level below
+  double cx = 0, cy = 0, r_cell = 0, R_p = 0;
+  int p = 0;
+  std::vector<int> near;
+};
+
+}  // namespace
+
+struct pm_geometry {
+  int m = 0;
+  double k0 = 0, spacing = 1;
+  int gnx = 0, gny = 0;
+  std::vector<pm_inclusion> inc;
+  std::vector<int> node_off, row_off;
+  int total_nodes = 0, N = 0, maxn = 0;
+  std::vector<double> hx, hy, hnx, hny, hw;
+  std::vector<InclDev> hinc;
+  Arena arena;
+  InclDev* d_inc = nullptr;
+  NodesDev nodes{};
+  // quadtree (paper Sec. 3; grid cells padded to 2^L x 2^L, Morton order)
+  int L = 0;
+  double ox = 0, oy = 0;
+  std::vector<std::vector<Box>> levels;  // levels[l], l = 0..L
+
+  // global index -> packed point code (node * 2 + group)
+  int code_of(int g) const {
+    int j = int(std::upper_bound(row_off.begin(), row_off.end(), g) - row_off.begin()) - 1;
+    int loc = g - row_off[j];
+    int n = inc[j].n_nodes;
+    return (node_off[j] + loc % n) * 2 + (loc >= n ? 1 : 0);
+  }
+};
+
+namespace {
+
+struct BoxF {
+  std::vector<int> rows, rgrp, cols, cgrp;
+  int mb = 0, kb = 0, kg[2] = {0, 0};
+  Cd *D = nullptr, *X = nullptr, *Rm = nullptr, *At = nullptr;
+  int* ipiv = nullptr;
+  std::vector<int> srows, scols;
+  std::vector<int> srgrp, scgrp;
+  std::vector<int> child_off;  // offsets of the children's blocks in rows/cols
+};
+
+}  // namespace
+
+struct pm_factor {
+  const pm_geometry* g = nullptr;
+  pm_factor_opts opts{};
+  cudaStream_t st = nullptr;
+  int L = 0;
+  std::vector<std::vector<BoxF>> lev;
+  BoxF root;
+  Arena arena, scratch;
+  pm_stats stats{};
+  std::vector<std::vector<Box>> tree;  // the geometry's quadtree with this factorization's proxies
+};
+
+namespace {
+
+void build_tree(pm_geometry* g, const pm_factor_opts* o) {
+  // grid indices
+  double ox = 1e300, oy = 1e300;
+  for (auto& c : g->inc) { ox = std::min(ox, c.cx); oy = std::min(oy, c.cy); }
+  g->ox = ox; g->oy = oy;
+  const double s = g->spacing;
+  std::vector<int> ix(g->m), iy(g->m);
+  int side = 1;
+  std::map<std::pair<int, int>, int> seen;
+  for (int j = 0; j < g->m; ++j) {
+    ix[j] = (int)std::lround((g->inc[j].cx - ox) / s);
+    iy[j] = (int)std::lround((g->inc[j].cy - oy) / s);
+    if (ix[j] < 0 || iy[j] < 0 || ix[j] > (1 << 20) || iy[j] > (1 << 20)) fail(PM_ERR_GEOMETRY, "grid index out of range");
+    if (!seen.emplace(std::make_pair(ix[j], iy[j]), j).second) fail(PM_ERR_GEOMETRY, "two inclusions share a grid cell");
+    side = std::max(side, std::max(ix[j], iy[j]) + 1);
+  }
+  int L = 0;
+  while ((1 << L) < side) ++L;
+  g->L = L;
+  g->levels.assign(L + 1, {});
+  std::vector<int> order(g->m);
+  for (int j = 0; j < g->m; ++j) order[j] = j;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return morton(ix[a], iy[a]) < morton(ix[b], iy[b]); });
+  for (int j : order) {
+    Box b; b.bx = ix[j]; b.by = iy[j]; b.leaves = {j};
+    g->levels[L].push_back(b);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    auto& ch = g->levels[l + 1];
+    std::vector<Box> par;
+    for (int c = 0; c < (int)ch.size(); ++c) {
+      int px = ch[c].bx >> 1, py = ch[c].by >> 1;
+      if (par.empty() || par.back().bx != px || par.back().by != py) {
+        Box b; b.bx = px; b.by = py;
+        par.push_back(b);
+      }
+      par.back().children.push_back(c);
+      for (int j : ch[c].leaves) par.back().leaves.push_back(j);
+    }
+    g->levels[l] = par;  // children of a Morton-ordered level are contiguous and ordered
+  }
+  (void)o;
+}
+
+// Proxy circles and near lists (depend on the tolerance and the proxy options).
+void plan_proxies(const pm_geometry* g, std::vector<std::vector<Box>>& levels, const pm_factor_opts* o) {
+  const double f = o->proxy_factor > 0 ? o->proxy_factor : 1.5;
+  const int ctol = (int)std::ceil(std::log(1.0 / o->tol) / std::log(f));
+  const double s = g->spacing;
+  for (int l = 0; l <= g->L; ++l) {
+    const double scale = std::ldexp(1.0, g->L - l);
+    auto& boxes = levels[l];
+    for (auto& b : boxes) {
+      b.cx = g->ox + s * (b.bx * scale + (scale - 1) / 2.0);
+      b.cy = g->oy + s * (b.by * scale + (scale - 1) / 2.0);
+      double r = 0;
+      for (int j : b.leaves)
+        for (int q = g->node_off[j]; q < g->node_off[j + 1]; ++q)
+          r = std::max(r, std::hypot(g->hx[q] - b.cx, g->hy[q] - b.cy));
+      b.r_cell = r;
+      b.R_p = f * r;
+      int p = o->proxy_points;
+      if (p <= 0) p = std::max(32, 8 * (int)std::ceil((2 * g->k0 * b.R_p + ctol) / 8.0));
+      b.p = p;
+    }
+    for (int i = 0; i < (int)boxes.size(); ++i) {
+      auto& b = boxes[i];
+      b.near.clear();
+      for (int j = 0; j < (int)boxes.size(); ++j) {
+        if (j == i) continue;
+        const auto& o2 = boxes[j];
+        int dk = std::abs(o2.bx - b.bx) + std::abs(o2.by - b.by);
+        if (dk == 1) { b.near.push_back(j); continue; }
+        if (std::hypot(o2.cx - b.cx, o2.cy - b.cy) - o2.r_cell >= b.R_p) continue;
+        bool inside = false;
+        for (int jj : o2.leaves) {
+          for (int q = g->node_off[jj]; q < g->node_off[jj + 1] && !inside; ++q)
+            if (std::hypot(g->hx[q] - b.cx, g->hy[q] - b.cy) < b.R_p) inside = true;
+          if (inside) break;
+        }
+        if (inside) b.near.push_back(j);
+      }
+    }
+  }
+}
+
+void upload_inclusions(pm_geometry* g) {
+  g->hinc.resize(g->m);
+  for (int j = 0; j < g->m; ++j) {
+    const pm_inclusion& c = g->inc[j];
+    InclDev d{};
+    d.shape = c.shape; d.n = c.n_nodes; d.node_off = g->node_off[j]; d.row_off = g->row_off[j];
+    d.cx = c.cx; d.cy = c.cy; d.rot = c.rot;
+    for (int i = 0; i < 16; ++i) d.prm[i] = c.prm[i];
+    d.k_in_re = c.k_in.re; d.k_in_im = c.k_in.im;
+    double r = c.k_in.re / g->k0;
+    d.eps_in_re = r * r; d.eps_in_im = 0;
+    g->hinc[j] = d;
+  }
+}
+
+// Self blocks A_jj of the listed inclusions into A[i] (leading dims lda[i]).
+void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std::vector<Cd*>& A,
+                   const std::vector<int>& lda, Arena& scr, cudaStream_t st) {
+  const int m = (int)incl.size();
+  if (m == 0) return;
+  std::vector<InclDev> sub(m);
+  int maxn = 0;
+  std::map<int, Cd*> dts;
+  std::vector<Cd*> Cm(m), DtS(m), E(m);
+  for (int i = 0; i < m; ++i) {
+    sub[i] = g->hinc[incl[i]];
+    int n = sub[i].n;
+    maxn = std::max(maxn, n);
+    Cm[i] = scr.get<Cd>((size_t)n * n);
+    DtS[i] = scr.get<Cd>((size_t)n * n);
+    E[i] = scr.get<Cd>((size_t)n * n);
+    if (!dts.count(n)) {
+      Cd* d = scr.get<Cd>((size_t)n * n);
+      diff_matrices<Cd>(n, d, st);
+      dts[n] = d;
+    }
+  }
+  InclDev* d_sub = upload(scr, sub, st);
+  Cd** dA = upload(scr, A, st);
+  int* dlda = upload(scr, lda, st);
+  Cd** dC = upload(scr, Cm, st);
+  Cd** dD = upload(scr, DtS, st);
+  self_pointwise<Cd>(d_sub, m, maxn, g->nodes, g->k0, dA, dlda, dC, st);
+  scaled_diff<Cd>(d_sub, m, maxn, g->nodes, dD, st);
+  CK(cudaGetLastError());
+  // Maue: N-block += diag(1/|x'|) Dt (S0+/e+ + S0-/e-) Dt
+  std::vector<GemmDesc<Cd>> d1(m), d2(m);
+  std::vector<int> off1(m + 1, 0), off2(m + 1, 0);
+  for (int i = 0; i < m; ++i) {
+    int n = sub[i].n;
+    d1[i] = GemmDesc<Cd>{n, n, n, Cm[i], n, dts[n], n, E[i], n, make_double2(1, 0), make_double2(0, 0), 1};
+    d2[i] = GemmDesc<Cd>{n, n, n, DtS[i], n, E[i], n, A[i] + n + (size_t)n * lda[i], lda[i], make_double2(1, 0),
+                         make_double2(1, 0), 0};
+    off1[i + 1] = off1[i] + gemm_tiles(n, n);
+    off2[i + 1] = off2[i] + gemm_tiles(n, n);
+  }
+  auto* dd1 = upload(scr, d1, st); auto* do1 = upload(scr, off1, st);
+  la_gemm_batched<Cd>(dd1, do1, m, off1[m], st);
+  auto* dd2 = upload(scr, d2, st); auto* do2 = upload(scr, off2, st);
+  la_gemm_batched<Cd>(dd2, do2, m, off2[m], st);
+  CK(cudaGetLastError());
+}
+
+struct GatherBatch {
+  std::vector<GatherProb<Cd>> probs;
+  std::vector<int> tile_off{0};
+  std::vector<int> codes;                 // all target / source lists
+  std::vector<std::pair<size_t, size_t>> lists;  // (tgt offset, src offset) per prob
+  void add(Cd* out, int ld, int M, int N, const std::vector<int>& tgt, const std::vector<int>& src, int trans) {
+    if (M <= 0 || N <= 0) return;
+    size_t to = codes.size();
+    codes.insert(codes.end(), tgt.begin(), tgt.end());
+    size_t so = codes.size();
+    codes.insert(codes.end(), src.begin(), src.end());
+    probs.push_back(GatherProb<Cd>{out, ld, M, N, nullptr, nullptr, trans});
+    lists.push_back({to, so});
+    tile_off.push_back(tile_off.back() + gather_tiles(M, N));
+  }
+  void run(Arena& scr, PointsDev pts, double k0, cudaStream_t st) {
+    if (probs.empty()) return;
+    int* dcodes = upload(scr, codes, st);
+    for (size_t i = 0; i < probs.size(); ++i) {
+      probs[i].tgt = dcodes + lists[i].first;
+      probs[i].src = dcodes + lists[i].second;
+    }
+    auto* dp = upload(scr, probs, st);
+    int* dt = upload(scr, tile_off, st);
+    gather_assemble<Cd>(dp, dt, (int)probs.size(), tile_off.back(), pts, k0, st);
+    CK(cudaGetLastError());
+  }
+};
+
+struct GemmBatch {
+  std::vector<GemmDesc<Cd>> d;
+  std::vector<int> off{0};
+  void add(int m, int n, int k, const Cd* A, int lda, const Cd* B, int ldb, Cd* C, int ldc, Cd alpha, Cd beta,
+           int beta_zero) {
+    if (m <= 0 || n <= 0) return;
+    if (k <= 0) {
+      if (beta_zero) k = 0; else return;
+    }
+    d.push_back(GemmDesc<Cd>{m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, beta_zero});
+    off.push_back(off.back() + gemm_tiles(m, n));
+  }
+  void run(Arena& scr, cudaStream_t st) {
+    if (d.empty()) return;
+    auto* dd = upload(scr, d, st);
+    int* dof = upload(scr, off, st);
+    la_gemm_batched<Cd>(dd, dof, (int)d.size(), off.back(), st);
+    CK(cudaGetLastError());
+  }
+};
+
+struct CopyBatch {
+  std::vector<CopyProb<Cd>> p;
+  int maxe = 0;
+  void add(const Cd* src, int lds, Cd* dst, int ldd, int m, int n) {
+    if (m <= 0 || n <= 0) return;
+    p.push_back(CopyProb<Cd>{src, lds, dst, ldd, m, n});
+    maxe = std::max(maxe, m * n);
+  }
+  void run(Arena& scr, cudaStream_t st) {
+    if (p.empty()) return;
+    auto* dp = upload(scr, p, st);
+    copy_batched<Cd>(dp, (int)p.size(), maxe, st);
+    CK(cudaGetLastError());
+  }
+};
+
+void lu_batch(std::vector<LuProb<Cd>>& probs, Arena& scr, cudaStream_t st, const char* what) {
+  if (probs.empty()) return;
+  int n = (int)probs.size();
+  int* info = scr.get<int>(n);
+  CK(cudaMemsetAsync(info, 0, n * sizeof(int), st));
+  int maxm = 0;
+  for (int i = 0; i < n; ++i) { probs[i].info = info + i; maxm = std::max(maxm, probs[i].m); }
+  auto* dp = upload(scr, probs, st);
+  la_getrf_batched<Cd>(dp, n, maxm, st);
+  CK(cudaGetLastError());
+  std::vector<int> h(n);
+  CK(cudaMemcpyAsync(h.data(), info, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i)
+    if (h[i] != 0) fail(PM_ERR_SINGULAR, std::string(what) + ": exactly singular pivot in LU");
+}
+
+void solve_batch(std::vector<SolveProb<Cd>>& probs, Arena& scr, cudaStream_t st) {
+  if (probs.empty()) return;
+  int maxm = 0, maxr = 0;
+  for (auto& p : probs) { maxm = std::max(maxm, p.m); maxr = std::max(maxr, p.nrhs); }
+  auto* dp = upload(scr, probs, st);
+  la_getrs_batched<Cd>(dp, (int)probs.size(), maxm, maxr, st);
+  CK(cudaGetLastError());
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) { cudaEventCreate(&a); cudaEventCreate(&b); cudaEventRecord(a, st); }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a); cudaEventDestroy(b);
+    return ms;
+  }
+};
+
+// Active sets and D_b of a parent (or the root) from its children's compressed blocks.
+void merge_children(pm_factor* F, int lev, const Box& box, BoxF& bf, GatherBatch& gb, CopyBatch& cb) {
+  auto& kids = F->lev[lev + 1];
+  bf.rows.clear(); bf.rgrp.clear(); bf.cols.clear(); bf.cgrp.clear(); bf.child_off.clear();
+  for (int c : box.children) {
+    bf.child_off.push_back((int)bf.rows.size());
+    const BoxF& k = kids[c];
+    bf.rows.insert(bf.rows.end(), k.srows.begin(), k.srows.end());
+    bf.rgrp.insert(bf.rgrp.end(), k.srgrp.begin(), k.srgrp.end());
+    bf.cols.insert(bf.cols.end(), k.scols.begin(), k.scols.end());
+    bf.cgrp.insert(bf.cgrp.end(), k.scgrp.begin(), k.scgrp.end());
+  }
+  bf.mb = (int)bf.rows.size();
+  bf.D = F->arena.get<Cd>((size_t)std::max(bf.mb, 1) * std::max(bf.mb, 1));
+  const pm_geometry* g = F->g;
+  for (size_t a = 0; a < box.children.size(); ++a) {
+    const BoxF& ka = kids[box.children[a]];
+    std::vector<int> tcodes(ka.srows.size());
+    for (size_t i = 0; i < ka.srows.size(); ++i) tcodes[i] = g->code_of(ka.srows[i]);
+    for (size_t b = 0; b < box.children.size(); ++b) {
+      const BoxF& kb = kids[box.children[b]];
+      Cd* dst = bf.D + bf.child_off[a] + (size_t)bf.child_off[b] * bf.mb;
+      if (a == b) {
+        cb.add(ka.At, ka.kb, dst, bf.mb, ka.kb, ka.kb);
+      } else {
+        std::vector<int> scodes(kb.scols.size());
+        for (size_t i = 0; i < kb.scols.size(); ++i) scodes[i] = g->code_of(kb.scols[i]);
+        gb.add(dst, bf.mb, ka.kb, kb.kb, tcodes, scodes, 0);
+      }
+    }
+  }
+}
+
+PointsDev make_points(const pm_geometry* g, const std::vector<Box>& boxes, Arena& scr, cudaStream_t st,
+                      std::vector<int>& proxy_off) {
+  int total_proxy = 0;
+  proxy_off.assign(boxes.size(), 0);
+  std::vector<ProxyBoxDev> pb(boxes.size());
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    proxy_off[b] = total_proxy;
+    pb[b] = ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, total_proxy};
+    total_proxy += boxes[b].p;
+  }
+  const size_t np = (size_t)g->total_nodes + total_proxy;
+  PointsDev P;
+  P.x = scr.get<double>(np); P.y = scr.get<double>(np); P.nx = scr.get<double>(np);
+  P.ny = scr.get<double>(np); P.w = scr.get<double>(np);
+  geom_points_from_nodes(g->nodes, P, g->total_nodes, st);
+  auto* dpb = upload(scr, pb, st);
+  geom_proxy_points(dpb, (int)boxes.size(), P, total_proxy, g->total_nodes, st);
+  CK(cudaGetLastError());
+  return P;
+}
+
+void process_level(pm_factor* F, int lev) {
+  const pm_geometry* g = F->g;
+  cudaStream_t st = F->st;
+  Arena& scr = F->scratch;
+  scr.reset();
+  const auto& boxes = F->tree[lev];
+  auto& BF = F->lev[lev];
+  const int nb = (int)boxes.size();
+  BF.assign(nb, BoxF());
+  Timer t_asm(st);
+  // 1. active sets and diagonal blocks
+  if (lev == F->L) {
+    std::vector<int> incl(nb), lda(nb);
+    std::vector<Cd*> A(nb);
+    for (int b = 0; b < nb; ++b) {
+      int j = boxes[b].leaves[0];
+      int n = g->inc[j].n_nodes;
+      BoxF& bf = BF[b];
+      bf.mb = 2 * n;
+      for (int i = 0; i < 2 * n; ++i) {
+        bf.rows.push_back(g->row_off[j] + i);
+        bf.rgrp.push_back(i >= n);
+      }
+      bf.cols = bf.rows; bf.cgrp = bf.rgrp;
+      bf.D = F->arena.get<Cd>((size_t)bf.mb * bf.mb);
+      incl[b] = j; A[b] = bf.D; lda[b] = bf.mb;
+    }
+    assemble_self(g, incl, A, lda, scr, st);
+  } else {
+    GatherBatch gb; CopyBatch cb;
+    for (int b = 0; b < nb; ++b) merge_children(F, lev, boxes[b], BF[b], gb, cb);
+    std::vector<int> dummy;
+    PointsDev P0 = make_points(g, {}, scr, st, dummy);
+    gb.run(scr, P0, g->k0, st);
+    cb.run(scr, st);
+  }
+  // 2. proxy points and ID inputs: per box 4 IDs (row u-eq, row q-eq, col q, col u)
+  std::vector<int> poff;
+  PointsDev P = make_points(g, boxes, scr, st, poff);
+  const int nid = 4 * nb;
+  std::vector<int> W(nid), nn(nid);
+  std::vector<Cd*> Z(nid);
+  std::vector<std::vector<int>> pos(nid);
+  GatherBatch gb;
+  for (int b = 0; b < nb; ++b) {
+    const Box& box = boxes[b];
+    const BoxF& bf = BF[b];
+    std::vector<int> ncols, nrows;
+    for (int o : box.near) {
+      for (int c : BF[o].cols) ncols.push_back(g->code_of(c));
+      for (int r : BF[o].rows) nrows.push_back(g->code_of(r));
+    }
+    const int pbase = g->total_nodes + poff[b];
+    std::vector<int> pcols, prows;
+    for (int grp = 0; grp < 2; ++grp)
+      for (int s = 0; s < box.p; ++s) { pcols.push_back((pbase + s) * 2 + grp); prows.push_back((pbase + s) * 2 + grp); }
+    for (int grp = 0; grp < 2; ++grp) {
+      // row ID of group grp: Z[w, c] = A(row c, source w), sources = near columns + proxy
+      int id = 4 * b + grp;
+      std::vector<int> tgt;
+      for (int i = 0; i < bf.mb; ++i) if (bf.rgrp[i] == grp) { pos[id].push_back(i); tgt.push_back(g->code_of(bf.rows[i])); }
+      std::vector<int> src = ncols;
+      src.insert(src.end(), pcols.begin(), pcols.end());
+      W[id] = (int)src.size(); nn[id] = (int)tgt.size();
+      Z[id] = scr.get<Cd>((size_t)W[id] * std::max(nn[id], 1));
+      gb.add(Z[id], W[id], W[id], nn[id], tgt, src, 1);
+      // column ID of group grp: Z[w, c] = A(target w, column c), targets = near rows + proxy
+      id = 4 * b + 2 + grp;
+      std::vector<int> srcc;
+      for (int i = 0; i < bf.mb; ++i) if (bf.cgrp[i] == grp) { pos[id].push_back(i); srcc.push_back(g->code_of(bf.cols[i])); }
+      std::vector<int> tg = nrows;
+      tg.insert(tg.end(), prows.begin(), prows.end());
+      W[id] = (int)tg.size(); nn[id] = (int)srcc.size();
+      Z[id] = scr.get<Cd>((size_t)W[id] * std::max(nn[id], 1));
+      gb.add(Z[id], W[id], W[id], nn[id], tg, srcc, 0);
+    }
+  }
+  gb.run(scr, P, g->k0, st);
+  F->stats.ms_assemble += t_asm.stop();
+  Timer t_id(st);
+  // 3. CPQR with rank detection
+  int total_n = 0;
+  std::vector<int> noff(nid + 1, 0);
+  for (int i = 0; i < nid; ++i) noff[i + 1] = noff[i] + nn[i];
+  total_n = noff[nid];
+  double* norm2 = scr.get<double>(2 * (size_t)std::max(total_n, 1));
+  int* perm = scr.get<int>(std::max(total_n, 1));
+  Cd* rdiag = scr.get<Cd>(std::max(total_n, 1));
+  int* rank = scr.get<int>(nid);
+  double* ref = scr.get<double>(nid);
+  CK(cudaMemsetAsync(rank, 0xff, nid * sizeof(int), st));
+  CK(cudaMemsetAsync(perm, 0, std::max(total_n, 1) * sizeof(int), st));
+  std::vector<CpqrProb<Cd>> cp(nid);
+  std::vector<CpqrChunk> chunks;
+  int maxT = 0;
+  for (int i = 0; i < nid; ++i) {
+    int tgt = std::min(W[i], nn[i]);
+    cp[i] = CpqrProb<Cd>{Z[i], W[i], W[i], nn[i], F->opts.tol, CPQR_FIND_RANK, 0, tgt,
+                         norm2 + 2 * (size_t)noff[i], perm + noff[i], rdiag + noff[i], rank + i, ref + i};
+    maxT = std::max(maxT, tgt);
+    for (int c0 = 0; c0 < nn[i]; c0 += CPQR_CB) chunks.push_back(CpqrChunk{i, c0, std::min(c0 + CPQR_CB, nn[i]), c0 == 0});
+  }
+  auto* dcp = upload(scr, cp, st);
+  auto* dch = upload(scr, chunks, st);
+  const int nch = (int)chunks.size();
+  cpqr_init_norms<Cd>(dcp, dch, nch, st);
+  std::vector<int> hr(nid);
+  for (int t = 0; t < maxT; ++t) {
+    cpqr_step<Cd>(dcp, dch, nch, t, st);
+    if ((t % 16 == 15) || t == maxT - 1) {
+      CK(cudaMemcpyAsync(hr.data(), rank, nid * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      bool all = true;
+      for (int i = 0; i < nid; ++i) if (hr[i] < 0 && t + 1 < cp[i].target) { all = false; break; }
+      if (all) break;
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(hr.data(), rank, nid * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int> r(nid);
+  for (int i = 0; i < nid; ++i) r[i] = hr[i] >= 0 ? hr[i] : cp[i].target;
+  // 4. pair ranks k_g = max(row rank, column rank); extend the shorter factorization
+  std::vector<int> kk(nid);
+  int maxExt = 0;
+  for (int b = 0; b < nb; ++b)
+    for (int grp = 0; grp < 2; ++grp) {
+      int ir = 4 * b + grp, ic = 4 * b + 2 + grp;
+      int k = std::min(std::max(r[ir], r[ic]), std::min(cp[ir].target, cp[ic].target));
+      kk[ir] = kk[ic] = k;
+      BF[b].kg[grp] = k;
+    }
+  for (int i = 0; i < nid; ++i) {
+    cp[i].mode = CPQR_EXTEND;
+    cp[i].base = r[i];
+    cp[i].target = std::max(kk[i], r[i]);
+    maxExt = std::max(maxExt, cp[i].target - cp[i].base);
+  }
+  if (maxExt > 0) {
+    dcp = upload(scr, cp, st);
+    for (int t = 0; t < maxExt; ++t) cpqr_step<Cd>(dcp, dch, nch, t, st);
+    CK(cudaGetLastError());
+  }
+  {
+    // the unchosen columns follow the pivots, ascending (defines the column order of T)
+    std::vector<PermFill> pf;
+    for (int i = 0; i < nid; ++i) {
+      if (nn[i] > 65536) fail(PM_ERR_UNSUPPORTED, "ID with more than 65536 candidate indices");
+      pf.push_back(PermFill{perm + noff[i], nn[i], std::max(r[i], kk[i])});
+    }
+    auto* dpf = upload(scr, pf, st);
+    complete_perm(dpf, nid, st);
+    CK(cudaGetLastError());
+  }
+  std::vector<int> hperm(std::max(total_n, 1));
+  CK(cudaMemcpyAsync(hperm.data(), perm, std::max(total_n, 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // 5. interpolation matrices T = R11^{-1} R12
+  std::vector<InterpProb<Cd>> ip;
+  std::vector<Cd*> T(nid, nullptr);
+  int maxcols = 0;
+  for (int i = 0; i < nid; ++i) {
+    int k = kk[i], n = nn[i];
+    if (k <= 0 || n - k <= 0) continue;
+    T[i] = scr.get<Cd>((size_t)k * (n - k));
+    ip.push_back(InterpProb<Cd>{Z[i], W[i], n, k, perm + noff[i], rdiag + noff[i], T[i], k});
+    maxcols = std::max(maxcols, n - k);
+  }
+  if (!ip.empty()) {
+    auto* dip = upload(scr, ip, st);
+    interp_solve<Cd>(dip, (int)ip.size(), maxcols, st);
+    CK(cudaGetLastError());
+  }
+  F->stats.ms_id += t_id.stop();
+  Timer t_sc(st);
+  // 6. skeleton lists, L (into X) and R
+  std::vector<ScatterProb<Cd>> sp;
+  std::vector<int> posall;
+  std::vector<std::pair<size_t, size_t>> posref;  // (offset into posall) per scatter
+  int maxe = 0;
+  for (int b = 0; b < nb; ++b) {
+    BoxF& bf = BF[b];
+    bf.kb = bf.kg[0] + bf.kg[1];
+    bf.X = F->arena.get<Cd>((size_t)std::max(bf.mb, 1) * std::max(bf.kb, 1));
+    bf.Rm = F->arena.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.mb, 1));
+    bf.At = F->arena.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
+    bf.ipiv = F->arena.get<int>(std::max(bf.mb, 1));
+    CK(cudaMemsetAsync(bf.X, 0, sizeof(Cd) * (size_t)bf.mb * bf.kb, st));
+    CK(cudaMemsetAsync(bf.Rm, 0, sizeof(Cd) * (size_t)bf.mb * bf.kb, st));
+    int off = 0;
+    for (int grp = 0; grp < 2; ++grp) {
+      int k = bf.kg[grp];
+      int ir = 4 * b + grp, ic = 4 * b + 2 + grp;
+      for (int j = 0; j < k; ++j) {
+        int pr = pos[ir][hperm[noff[ir] + j]];
+        bf.srows.push_back(bf.rows[pr]); bf.srgrp.push_back(grp);
+        int pc = pos[ic][hperm[noff[ic] + j]];
+        bf.scols.push_back(bf.cols[pc]); bf.scgrp.push_back(grp);
+      }
+      for (int side = 0; side < 2; ++side) {
+        int id = side == 0 ? ir : ic;
+        size_t po = posall.size();
+        posall.insert(posall.end(), pos[id].begin(), pos[id].end());
+        ScatterProb<Cd> s{side == 0 ? bf.X : bf.Rm, side == 0 ? bf.mb : bf.kb, off, side == 0,
+                          nullptr, perm + noff[id], k, nn[id], T[id], k};
+        sp.push_back(s);
+        posref.push_back({po, 0});
+        maxe = std::max(maxe, k * nn[id]);
+      }
+      off += k;
+    }
+  }
+  if (!sp.empty()) {
+    int* dpos = upload(scr, posall, st);
+    for (size_t i = 0; i < sp.size(); ++i) sp[i].pos = dpos + posref[i].first;
+    auto* dsp = upload(scr, sp, st);
+    scatter_interp<Cd>(dsp, (int)sp.size(), maxe, st);
+    CK(cudaGetLastError());
+  }
+  // 7. LU of D_b, X = D_b^{-1} L_b, Y = R_b X, A~_b = Y^{-1}
+  std::vector<LuProb<Cd>> lu;
+  for (int b = 0; b < nb; ++b) lu.push_back(LuProb<Cd>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, nullptr});
+  lu_batch(lu, scr, st, "diagonal block");
+  std::vector<SolveProb<Cd>> sv;
+  for (int b = 0; b < nb; ++b) sv.push_back(SolveProb<Cd>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, BF[b].X, BF[b].mb, BF[b].kb});
+  solve_batch(sv, scr, st);
+  GemmBatch gy;
+  std::vector<Cd*> Y(nb);
+  std::vector<int*> ypiv(nb);
+  for (int b = 0; b < nb; ++b) {
+    BoxF& bf = BF[b];
+    Y[b] = scr.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
+    ypiv[b] = scr.get<int>(std::max(bf.kb, 1));
+    gy.add(bf.kb, bf.kb, bf.mb, bf.Rm, bf.kb, bf.X, bf.mb, Y[b], bf.kb, make_double2(1, 0), make_double2(0, 0), 1);
+    if (bf.kb > 0) k_identity<<<(bf.kb * bf.kb + 255) / 256, 256, 0, st>>>(bf.At, bf.kb, bf.kb);
+  }
+  gy.run(scr, st);
+  std::vector<LuProb<Cd>> luy;
+  std::vector<SolveProb<Cd>> svy;
+  for (int b = 0; b < nb; ++b) {
+    if (BF[b].kb <= 0) continue;
+    luy.push_back(LuProb<Cd>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], nullptr});
+    svy.push_back(SolveProb<Cd>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], BF[b].At, BF[b].kb, BF[b].kb});
+  }
+  lu_batch(luy, scr, st, "R A^-1 L (compressed block)");
+  solve_batch(svy, scr, st);
+  F->stats.ms_schur += t_sc.stop();
+  int sk = 0;
+  for (auto& bf : BF) sk += bf.kb;
+  if (lev < 16) F->stats.skeleton[lev] = sk;
+}
+
+void factor_top(pm_factor* F) {
+  const pm_geometry* g = F->g;
+  cudaStream_t st = F->st;
+  Arena& scr = F->scratch;
+  scr.reset();
+  Timer t(st);
+  BoxF& rt = F->root;
+  if (F->L == 0) {
+    int j = F->tree[0][0].leaves[0];
+    int n = g->inc[j].n_nodes;
+    rt.mb = 2 * n;
+    for (int i = 0; i < 2 * n; ++i) { rt.rows.push_back(g->row_off[j] + i); rt.rgrp.push_back(i >= n); }
+    rt.cols = rt.rows; rt.cgrp = rt.rgrp;
+    rt.D = F->arena.get<Cd>((size_t)rt.mb * rt.mb);
+    assemble_self(g, {j}, {rt.D}, {rt.mb}, scr, st);
+  } else {
+    GatherBatch gb; CopyBatch cb;
+    merge_children(F, 0, F->tree[0][0], rt, gb, cb);
+    std::vector<int> dummy;
+    PointsDev P0 = make_points(g, {}, scr, st, dummy);
+    gb.run(scr, P0, g->k0, st);
+    cb.run(scr, st);
+  }
+  rt.ipiv = F->arena.get<int>(std::max(rt.mb, 1));
+  std::vector<LuProb<Cd>> lu{LuProb<Cd>{rt.D, rt.mb, rt.mb, rt.ipiv, nullptr}};
+  lu_batch(lu, scr, st, "top-level system");
+  F->stats.K = rt.mb;
+  F->stats.ms_top += t.stop();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Solve (paper Sec. 3): upward RHS compression, top solve, downward recovery.
+namespace {
+
+void solve_device(const pm_factor* Fc, const Cd* rhs, int nrhs, Cd* phi, Arena& ws, cudaStream_t st) {
+  pm_factor* F = const_cast<pm_factor*>(Fc);
+  const pm_geometry* g = F->g;
+  const int N = g->N;
+  const int L = F->L;
+  if (L == 0) {
+    CopyBatch cb;
+    cb.add(rhs, N, phi, N, N, nrhs);
+    cb.run(ws, st);
+    std::vector<SolveProb<Cd>> sv{SolveProb<Cd>{F->root.D, F->root.mb, F->root.mb, F->root.ipiv, phi, N, nrhs}};
+    solve_batch(sv, ws, st);
+    return;
+  }
+  // per-level buffers: fin (m_b x nrhs, becomes g_b then x_b), ft (k_b x nrhs)
+  std::vector<std::vector<Cd*>> fin(L + 1), ft(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    auto& BF = F->lev[l];
+    fin[l].resize(BF.size()); ft[l].resize(BF.size());
+    for (size_t b = 0; b < BF.size(); ++b) {
+      fin[l][b] = ws.get<Cd>((size_t)std::max(BF[b].mb, 1) * nrhs);
+      ft[l][b] = ws.get<Cd>((size_t)std::max(BF[b].kb, 1) * nrhs);
+    }
+  }
+  BoxF& rt = F->root;
+  Cd* froot = ws.get<Cd>((size_t)std::max(rt.mb, 1) * nrhs);
+  const Cd one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
+  // leaves: gather the right-hand side (contiguous per inclusion)
+  {
+    CopyBatch cb;
+    auto& BF = F->lev[L];
+    for (size_t b = 0; b < BF.size(); ++b) cb.add(rhs + BF[b].rows[0], N, fin[L][b], BF[b].mb, BF[b].mb, nrhs);
+    cb.run(ws, st);
+  }
+  for (int l = L; l >= 1; --l) {
+    auto& BF = F->lev[l];
+    const auto& boxes = F->tree[l];
+    std::vector<SolveProb<Cd>> sv;
+    for (size_t b = 0; b < BF.size(); ++b)
+      sv.push_back(SolveProb<Cd>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, fin[l][b], BF[b].mb, nrhs});
+    solve_batch(sv, ws, st);  // g_b = D_b^{-1} f_b
+    Cd* tmp = ws.get<Cd>(1);
+    (void)tmp;
+    std::vector<Cd*> t(BF.size());
+    GemmBatch g1, g2;
+    for (size_t b = 0; b < BF.size(); ++b) {
+      t[b] = ws.get<Cd>((size_t)std::max(BF[b].kb, 1) * nrhs);
+      g1.add(BF[b].kb, nrhs, BF[b].mb, BF[b].Rm, BF[b].kb, fin[l][b], BF[b].mb, t[b], BF[b].kb, one, zero, 1);
+      g2.add(BF[b].kb, nrhs, BF[b].kb, BF[b].At, BF[b].kb, t[b], BF[b].kb, ft[l][b], BF[b].kb, one, zero, 1);
+    }
+    g1.run(ws, st);
+    g2.run(ws, st);
+    // f~ of every child into its parent's right-hand side
+    CopyBatch cb;
+    const auto& parents = F->tree[l - 1];
+    for (size_t pidx = 0; pidx < parents.size(); ++pidx) {
+      const BoxF& pb = (l - 1 == 0) ? F->root : F->lev[l - 1][pidx];
+      Cd* pf = (l - 1 == 0) ? froot : fin[l - 1][pidx];
+      for (size_t a = 0; a < parents[pidx].children.size(); ++a) {
+        int c = parents[pidx].children[a];
+        cb.add(ft[l][c], BF[c].kb, pf + pb.child_off[a], pb.mb, BF[c].kb, nrhs);
+      }
+    }
+    cb.run(ws, st);
+    (void)boxes;
+  }
+  {
+    std::vector<SolveProb<Cd>> sv{SolveProb<Cd>{rt.D, rt.mb, rt.mb, rt.ipiv, froot, rt.mb, nrhs}};
+    solve_batch(sv, ws, st);
+  }
+  for (int l = 1; l <= L; ++l) {
+    auto& BF = F->lev[l];
+    const auto& parents = F->tree[l - 1];
+    GemmBatch g1, g2;
+    for (size_t pidx = 0; pidx < parents.size(); ++pidx) {
+      const BoxF& pb = (l - 1 == 0) ? F->root : F->lev[l - 1][pidx];
+      const Cd* px = (l - 1 == 0) ? froot : fin[l - 1][pidx];
+      for (size_t a = 0; a < parents[pidx].children.size(); ++a) {
+        int c = parents[pidx].children[a];
+        const Cd* y = px + pb.child_off[a];
+        // f~ - A~ y, then x = g - X (f~ - A~ y)
+        g1.add(BF[c].kb, nrhs, BF[c].kb, BF[c].At, BF[c].kb, y, pb.mb, ft[l][c], BF[c].kb, mone, one, 0);
+        g2.add(BF[c].mb, nrhs, BF[c].kb, BF[c].X, BF[c].mb, ft[l][c], BF[c].kb, fin[l][c], BF[c].mb, mone, one, 0);
+      }
+    }
+    g1.run(ws, st);
+    g2.run(ws, st);
+  }
+  CopyBatch cb;
+  auto& BF = F->lev[L];
+  for (size_t b = 0; b < BF.size(); ++b) cb.add(fin[L][b], BF[b].mb, phi + BF[b].cols[0], N, BF[b].mb, nrhs);
+  cb.run(ws, st);
+}
+
+pm_status run_guarded(const char* where, const std::function<void()>& fn);
+
+}  // namespace
+
+namespace {
+pm_status run_guarded(const char* where, const std::function<void()>& fn) {
+  try {
+    fn();
+    return PM_OK;
+  } catch (const PmError& e) {
+    g_err = std::string(where) + ": " + e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    g_err = std::string(where) + ": host allocation failed";
+    return PM_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = std::string(where) + ": " + e.what();
+    return PM_ERR_INVALID_ARG;
+  }
+}
+
+void check_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    fail(PM_ERR_CUDA, "no CUDA device available (this library has no CPU fallback)");
+  }
+}
+}  // namespace
+
+extern "C" {
+
+const char* pm_last_error(void) { return g_err.c_str(); }
+
+pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out) {
+  if (!prob || !out) { g_err = "pm_build_geometry: NULL argument"; return PM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  pm_geometry* g = nullptr;
+  pm_status s = run_guarded("pm_build_geometry", [&] {
+    if (prob->m < 1 || !prob->inc) fail(PM_ERR_INVALID_ARG, "need m >= 1 inclusions");
+    if (!(prob->k_out > 0) || !std::isfinite(prob->k_out)) fail(PM_ERR_INVALID_ARG, "k_out must be positive");
+    if (!(prob->spacing > 0)) fail(PM_ERR_INVALID_ARG, "spacing must be positive");
+    for (int j = 0; j < prob->m; ++j) {
+      const pm_inclusion& c = prob->inc[j];
+      if (c.shape < 0 || c.shape > 3) fail(PM_ERR_INVALID_ARG, "unknown shape");
+      if (c.n_nodes < 16 || c.n_nodes > 4096 || (c.n_nodes & 1)) fail(PM_ERR_INVALID_ARG, "n_nodes must be even in [16, 4096]");
+      if (!std::isfinite(c.cx) || !std::isfinite(c.cy) || !std::isfinite(c.rot)) fail(PM_ERR_INVALID_ARG, "non-finite centre");
+      for (int i = 0; i < 16; ++i) if (!std::isfinite(c.prm[i])) fail(PM_ERR_INVALID_ARG, "non-finite shape parameter");
+      if (!(c.prm[0] > 0)) fail(PM_ERR_INVALID_ARG, "shape size must be positive");
+      if (!(c.k_in.re > 0)) fail(PM_ERR_INVALID_ARG, "k_in must have positive real part");
+      if (c.k_in.im != 0) fail(PM_ERR_UNSUPPORTED, "complex interior wavenumber not supported by this build");
+    }
+    check_device();
+    g = new pm_geometry();
+    g->m = prob->m; g->k0 = prob->k_out; g->spacing = prob->spacing;
+    g->gnx = prob->grid_nx; g->gny = prob->grid_ny;
+    g->inc.assign(prob->inc, prob->inc + prob->m);
+    g->node_off.assign(g->m + 1, 0); g->row_off.assign(g->m + 1, 0);
+    for (int j = 0; j < g->m; ++j) {
+      g->node_off[j + 1] = g->node_off[j] + g->inc[j].n_nodes;
+      g->row_off[j + 1] = 2 * g->node_off[j + 1];
+      g->maxn = std::max(g->maxn, g->inc[j].n_nodes);
+    }
+    g->total_nodes = g->node_off[g->m];
+    g->N = 2 * g->total_nodes;
+    upload_inclusions(g);
+    cudaStream_t st = 0;
+    g->d_inc = upload(g->arena, g->hinc, st);
+    const size_t T = g->total_nodes;
+    NodesDev& nd = g->nodes;
+    nd.x = g->arena.get<double>(T); nd.y = g->arena.get<double>(T); nd.nx = g->arena.get<double>(T);
+    nd.ny = g->arena.get<double>(T); nd.speed = g->arena.get<double>(T); nd.w = g->arena.get<double>(T);
+    nd.curv = g->arena.get<double>(T); nd.kress = g->arena.get<double>(T);
+    std::vector<int> incl(T);
+    for (int j = 0; j < g->m; ++j) for (int q = g->node_off[j]; q < g->node_off[j + 1]; ++q) incl[q] = j;
+    nd.incl = upload(g->arena, incl, st);
+    geom_nodes(g->d_inc, nd, (int)T, g->hinc.data(), st);
+    CK(cudaGetLastError());
+    g->hx.resize(T); g->hy.resize(T); g->hnx.resize(T); g->hny.resize(T); g->hw.resize(T);
+    CK(cudaMemcpy(g->hx.data(), nd.x, T * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(g->hy.data(), nd.y, T * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(g->hnx.data(), nd.nx, T * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(g->hny.data(), nd.ny, T * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(g->hw.data(), nd.w, T * 8, cudaMemcpyDeviceToHost));
+    build_tree(g, nullptr);
+  });
+  if (s != PM_OK) { delete g; return s; }
+  *out = g;
+  return PM_OK;
+}
+
+pm_status pm_geometry_size(const pm_geometry* g, int32_t* N, int32_t* total_nodes) {
+  if (!g) { g_err = "pm_geometry_size: NULL geometry"; return PM_ERR_INVALID_ARG; }
+  if (N) *N = g->N;
+  if (total_nodes) *total_nodes = g->total_nodes;
+  return PM_OK;
+}
+
+pm_status pm_geometry_nodes(const pm_geometry* g, double* xy, double* nrm, double* w) {
+  if (!g) { g_err = "pm_geometry_nodes: NULL geometry"; return PM_ERR_INVALID_ARG; }
+  for (int q = 0; q < g->total_nodes; ++q) {
+    if (xy) { xy[2 * q] = g->hx[q]; xy[2 * q + 1] = g->hy[q]; }
+    if (nrm) { nrm[2 * q] = g->hnx[q]; nrm[2 * q + 1] = g->hny[q]; }
+    if (w) w[q] = g->hw[q];
+  }
+  return PM_OK;
+}
+
+pm_status pm_plane_wave_rhs(const pm_geometry* g, const double* angles, int32_t nrhs, pm_c64* rhs, int32_t on_device) {
+  if (!g || !angles || !rhs || nrhs < 1) { g_err = "pm_plane_wave_rhs: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_plane_wave_rhs", [&] {
+    Arena ws;
+    ws.min_block = 1 << 20;
+    cudaStream_t st = 0;
+    std::vector<double> a(angles, angles + nrhs);
+    double* da = upload(ws, a, st);
+    Cd* F = on_device ? (Cd*)rhs : ws.get<Cd>((size_t)g->N * nrhs);
+    plane_wave_rhs<Cd>(g->d_inc, g->nodes, g->total_nodes, g->k0, da, nrhs, F, g->N, st);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpy(rhs, F, sizeof(Cd) * (size_t)g->N * nrhs, cudaMemcpyDeviceToHost));
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_factor** out) {
+  if (!g || !opts || !out) { g_err = "pm_factorize: NULL argument"; return PM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!(opts->tol > 0 && opts->tol < 1)) { g_err = "pm_factorize: tol must be in (0, 1)"; return PM_ERR_INVALID_ARG; }
+  if (opts->proxy_factor != 0 && !(opts->proxy_factor > 1)) { g_err = "pm_factorize: proxy_factor must be > 1"; return PM_ERR_INVALID_ARG; }
+  if (opts->proxy_points < 0 || opts->proxy_points > 100000) { g_err = "pm_factorize: bad proxy_points"; return PM_ERR_INVALID_ARG; }
+  if (opts->precision != PM_FP64) { g_err = "pm_factorize: unsupported precision"; return PM_ERR_UNSUPPORTED; }
+  pm_factor* F = new pm_factor();
+  pm_status s = run_guarded("pm_factorize", [&] {
+    F->g = g;
+    F->opts = *opts;
+    if (F->opts.proxy_factor == 0) F->opts.proxy_factor = 1.5;
+    F->st = (cudaStream_t)opts->stream;
+    F->L = g->L;
+    F->tree = g->levels;
+    plan_proxies(g, F->tree, &F->opts);
+    F->stats.levels = F->L;
+    F->stats.N = g->N;
+    F->lev.assign(F->L + 1, {});
+    Timer tt(F->st);
+    for (int l = F->L; l >= 1; --l) process_level(F, l);
+    factor_top(F);
+    F->scratch.release();
+    F->stats.ms_total = tt.stop();
+  });
+  if (s != PM_OK) { delete F; return s; }
+  *out = F;
+  return PM_OK;
+}
+
+pm_status pm_solve(const pm_factor* F, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device) {
+  if (!F || !rhs || !phi || nrhs < 1) { g_err = "pm_solve: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_solve", [&] {
+    Arena ws;
+    cudaStream_t st = F->st;
+    const size_t bytes = sizeof(Cd) * (size_t)F->g->N * nrhs;
+    const Cd* drhs = (const Cd*)rhs;
+    Cd* dphi = (Cd*)phi;
+    if (!on_device) {
+      Cd* a = ws.get<Cd>((size_t)F->g->N * nrhs);
+      CK(cudaMemcpyAsync(a, rhs, bytes, cudaMemcpyHostToDevice, st));
+      drhs = a;
+      dphi = ws.get<Cd>((size_t)F->g->N * nrhs);
+    } else if ((const void*)rhs == (const void*)phi) {
+      Cd* a = ws.get<Cd>((size_t)F->g->N * nrhs);
+      CK(cudaMemcpyAsync(a, rhs, bytes, cudaMemcpyDeviceToDevice, st));
+      drhs = a;
+    }
+    solve_device(F, drhs, nrhs, dphi, ws, st);
+    if (!on_device) CK(cudaMemcpyAsync(phi, dphi, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+pm_status pm_factor_stats(const pm_factor* F, pm_stats* out) {
+  if (!F || !out) { g_err = "pm_factor_stats: NULL argument"; return PM_ERR_INVALID_ARG; }
+  *out = F->stats;
+  return PM_OK;
+}
+
+pm_status pm_factor_skeleton(const pm_factor* F, int32_t level, int32_t box, int32_t* rows, int32_t* cols,
+                             int32_t cap, int32_t* k) {
+  if (!F || !k || level < 1 || level > F->L || box < 0 || box >= (int)F->lev[level].size()) {
+    g_err = "pm_factor_skeleton: bad argument";
+    return PM_ERR_INVALID_ARG;
+  }
+  const BoxF& b = F->lev[level][box];
+  *k = b.kb;
+  for (int i = 0; i < std::min(cap, b.kb); ++i) {
+    if (rows) rows[i] = b.srows[i];
+    if (cols) cols[i] = b.scols[i];
+  }
+  return PM_OK;
+}
+
+pm_status pm_matrix_entries(const pm_geometry* g, const int32_t* rows, int32_t M, const int32_t* cols, int32_t Nc,
+                            pm_c64* out) {
+  if (!g || !rows || !cols || !out || M < 1 || Nc < 1) { g_err = "pm_matrix_entries: bad argument"; return PM_ERR_INVALID_ARG; }
+  for (int i = 0; i < M; ++i) if (rows[i] < 0 || rows[i] >= g->N) { g_err = "pm_matrix_entries: row out of range"; return PM_ERR_INVALID_ARG; }
+  for (int j = 0; j < Nc; ++j) if (cols[j] < 0 || cols[j] >= g->N) { g_err = "pm_matrix_entries: column out of range"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_matrix_entries", [&] {
+    Arena ws;
+    cudaStream_t st = 0;
+    std::vector<int> t(M), s(Nc);
+    for (int i = 0; i < M; ++i) t[i] = g->code_of(rows[i]);
+    for (int j = 0; j < Nc; ++j) s[j] = g->code_of(cols[j]);
+    Cd* d = ws.get<Cd>((size_t)M * Nc);
+    GatherBatch gb;
+    gb.add(d, M, M, Nc, t, s, 0);
+    std::vector<int> dummy;
+    PointsDev P = make_points(g, {}, ws, st, dummy);
+    gb.run(ws, P, g->k0, st);
+    CK(cudaMemcpy(out, d, sizeof(Cd) * (size_t)M * Nc, cudaMemcpyDeviceToHost));
+    // same-inclusion pairs are not off-diagonal entries
+    for (int i = 0; i < M; ++i) {
+      int ji = int(std::upper_bound(g->row_off.begin(), g->row_off.end(), rows[i]) - g->row_off.begin()) - 1;
+      for (int j = 0; j < Nc; ++j) {
+        int jj = int(std::upper_bound(g->row_off.begin(), g->row_off.end(), cols[j]) - g->row_off.begin()) - 1;
+        if (ji == jj) out[i + (size_t)j * M] = pm_c64{0, 0};
+      }
+    }
+  });
+}
+
+pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out) {
+  if (!g || !out || j < 0 || j >= g->m) { g_err = "pm_self_block: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_self_block", [&] {
+    Arena ws;
+    cudaStream_t st = 0;
+    int n = g->inc[j].n_nodes;
+    Cd* d = ws.get<Cd>((size_t)4 * n * n);
+    assemble_self(g, {j}, {d}, {2 * n}, ws, st);
+    CK(cudaMemcpy(out, d, sizeof(Cd) * (size_t)4 * n * n, cudaMemcpyDeviceToHost));
+  });
+}
+
+void pm_factor_free(pm_factor* F) { delete F; }
+void pm_geometry_free(pm_geometry* g) { delete g; }
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+"""ctypes binding of libpmchwt.so: the same entry points as include/pmchwt.h.
+
+Argument marshalling only; every step of the solver runs in the CUDA
+library.  Loading fails loudly if the library has not been built (there is
+no CPU fallback).
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+from .build import LIB
+
+PM_OK = 0
+STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM_ERR_SINGULAR",
+          5: "PM_ERR_NOT_CONVERGED", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_GEOMETRY", 8: "PM_ERR_UNSUPPORTED"}
+PM_FP64 = 0
+
+
+class PmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pm_c64(ct.Structure):
+    _fields_ = [("re", ct.c_double), ("im", ct.c_double)]
+
+
+class pm_inclusion(ct.Structure):
+    _fields_ = [("shape", ct.c_int32), ("cx", ct.c_double), ("cy", ct.c_double), ("rot", ct.c_double),
+                ("prm", ct.c_double * 16), ("n_nodes", ct.c_int32), ("k_in", pm_c64)]
+
+
+class pm_problem(ct.Structure):
+    _fields_ = [("m", ct.c_int32), ("inc", ct.POINTER(pm_inclusion)), ("k_out", ct.c_double),
+                ("grid_nx", ct.c_int32), ("grid_ny", ct.c_int32), ("spacing", ct.c_double)]
+
+
+class pm_factor_opts(ct.Structure):
+    _fields_ = [("tol", ct.c_double), ("proxy_factor", ct.c_double), ("proxy_points", ct.c_int32),
+                ("precision", ct.c_int32), ("stream", ct.c_void_p), ("flags", ct.c_uint32)]
+
+
+class pm_stats(ct.Structure):
+    _fields_ = [("levels", ct.c_int32), ("N", ct.c_int32), ("K", ct.c_int32), ("skeleton", ct.c_int32 * 16),
+                ("ms_assemble", ct.c_double), ("ms_id", ct.c_double), ("ms_schur", ct.c_double),
+                ("ms_top", ct.c_double), ("ms_total", ct.c_double)]
+
+
+_lib = None
+
+EXPORTS = {
+    "pm_build_geometry": (ct.c_int, [ct.POINTER(pm_problem), ct.POINTER(ct.c_void_p)]),
+    "pm_geometry_size": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
+    "pm_geometry_nodes": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "pm_plane_wave_rhs": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
+    "pm_factorize": (ct.c_int, [ct.c_void_p, ct.POINTER(pm_factor_opts), ct.POINTER(ct.c_void_p)]),
+    "pm_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
+    "pm_factor_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(pm_stats)]),
+    "pm_factor_skeleton": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32,
+                                      ct.POINTER(ct.c_int32)]),
+    "pm_matrix_entries": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "pm_self_block": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "pm_factor_free": (None, [ct.c_void_p]),
+    "pm_geometry_free": (None, [ct.c_void_p]),
+    "pm_last_error": (ct.c_char_p, []),
+}
+
+
+def load(path=None):
+    """Load libpmchwt.so (built by __graft_entry__.build()); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} not built: run __graft_entry__.build() (no CPU fallback)")
+    lib = ct.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != PM_OK:
+        raise PmError(st, load().pm_last_error().decode())
+
+
+def make_problem(prob):
+    """pm_problem (and the inclusion array it points to) from a workload descriptor dict."""
+    m = len(prob["inclusions"])
+    arr = (pm_inclusion * m)()
+    for j, inc in enumerate(prob["inclusions"]):
+        a = arr[j]
+        a.shape = inc["shape"]; a.cx = inc["cx"]; a.cy = inc["cy"]; a.rot = inc["rot"]
+        for i, v in enumerate(inc["prm"]):
+            a.prm[i] = v
+        a.n_nodes = inc["n"]
+        a.k_in = pm_c64(complex(inc["k_in"]).real, complex(inc["k_in"]).imag)
+    p = pm_problem(m, arr, float(prob["k_out"]), int(prob.get("grid_nx", 0)), int(prob.get("grid_ny", 0)),
+                   float(prob["spacing"]))
+    return p, arr
+
+
+class Geometry:
+    def __init__(self, prob):
+        lib = load()
+        p, self._arr = make_problem(prob)
+        h = ct.c_void_p()
+        _check(lib.pm_build_geometry(ct.byref(p), ct.byref(h)))
+        self.h = h
+        N, T = ct.c_int32(), ct.c_int32()
+        _check(lib.pm_geometry_size(h, ct.byref(N), ct.byref(T)))
+        self.N, self.total_nodes = N.value, T.value
+
+    def nodes(self):
+        xy = np.zeros((self.total_nodes, 2)); nrm = np.zeros((self.total_nodes, 2)); w = np.zeros(self.total_nodes)
+        _check(load().pm_geometry_nodes(self.h, xy.ctypes.data, nrm.ctypes.data, w.ctypes.data))
+        return xy, nrm, w
+
+    def plane_wave(self, angles):
+        angles = np.ascontiguousarray(angles, dtype=np.float64)
+        out = np.zeros((len(angles), self.N), dtype=np.complex128)  # column-major N x nrhs
+        _check(load().pm_plane_wave_rhs(self.h, angles.ctypes.data, len(angles), out.ctypes.data, 0))
+        return out.T
+
+    def plane_wave_device(self, angles, out_ptr):
+        angles = np.ascontiguousarray(angles, dtype=np.float64)
+        _check(load().pm_plane_wave_rhs(self.h, angles.ctypes.data, len(angles), out_ptr, 1))
+
+    def matrix_entries(self, rows, cols):
+        rows = np.ascontiguousarray(rows, dtype=np.int32); cols = np.ascontiguousarray(cols, dtype=np.int32)
+        out = np.zeros((len(cols), len(rows)), dtype=np.complex128)
+        _check(load().pm_matrix_entries(self.h, rows.ctypes.data, len(rows), cols.ctypes.data, len(cols),
+                                        out.ctypes.data))
+        return out.T
+
+    def self_block(self, j, n):
+        out = np.zeros((2 * n, 2 * n), dtype=np.complex128)
+        _check(load().pm_self_block(self.h, j, out.ctypes.data))
+        return out.T  # column-major -> row-major view
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.pm_geometry_free(self.h)
+            self.h = None
+
+
+class Factor:
+    def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None):
+        lib = load()
+        self.geom = geom
+        o = pm_factor_opts(float(tol), float(proxy_factor), int(proxy_points), int(precision),
+                           ct.c_void_p(stream) if stream else None, 0)
+        h = ct.c_void_p()
+        _check(lib.pm_factorize(geom.h, ct.byref(o), ct.byref(h)))
+        self.h = h
+
+    def stats(self):
+        s = pm_stats()
+        _check(load().pm_factor_stats(self.h, ct.byref(s)))
+        return {"levels": s.levels, "N": s.N, "K": s.K, "skeleton": list(s.skeleton)[: s.levels + 1],
+                "ms_assemble": s.ms_assemble, "ms_id": s.ms_id, "ms_schur": s.ms_schur, "ms_top": s.ms_top,
+                "ms_total": s.ms_total}
+
+    def solve(self, rhs):
+        """Host solve: rhs (N,) or (N, nrhs) complex128 -> phi of the same shape."""
+        rhs = np.asarray(rhs, dtype=np.complex128)
+        vec = rhs.ndim == 1
+        R = rhs[:, None] if vec else rhs
+        nrhs = R.shape[1]
+        buf = np.ascontiguousarray(R.T)  # column-major N x nrhs
+        out = np.zeros_like(buf)
+        _check(load().pm_solve(self.h, buf.ctypes.data, nrhs, out.ctypes.data, 0))
+        phi = out.T
+        return phi[:, 0] if vec else phi
+
+    def solve_device(self, rhs_ptr, nrhs, phi_ptr):
+        _check(load().pm_solve(self.h, rhs_ptr, nrhs, phi_ptr, 1))
+
+    def skeleton(self, level, box, cap=100000):
+        rows = np.zeros(cap, dtype=np.int32); cols = np.zeros(cap, dtype=np.int32); k = ct.c_int32()
+        _check(load().pm_factor_skeleton(self.h, level, box, rows.ctypes.data, cols.ctypes.data, cap, ct.byref(k)))
+        return rows[: k.value].copy(), cols[: k.value].copy()
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.pm_factor_free(self.h)
+            self.h = None
