@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the PMCHWT (Omit) proxy fast direct solver on one GB300.
+
+A step is one pass of the whole hot path on the 16 x 16 star-grid workload
+(n = 128 nodes per star, N = 65,536 complex unknowns, tol 1e-10): geometry
+resident on the device, then factorization (self blocks, proxy IDs, Schur
+merges over 4 levels, top LU) and a solve of 8 plane-wave right-hand sides.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank factors its own replica of the workload
+(independent problems, no collective; weak scaling); the timed region is
+bracketed by barriers and the slowest rank's time is reported.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknowns factored/s and solve ms at rel err ≤1e-8 vs FP64 oracle; % roofline"
+UNIT = "unknowns/s"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (profiling recipe table)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        med = sorted(sm)[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+WORKLOADS = {"star16": 16, "star8": 8, "star4": 4}
+
+
+def workload(name="star16"):
+    """The 16x16 star grid (default); star8 / star4 are smaller blocks of the same
+    recipe, used only for profiler captures."""
+    from paper_2603_09381_gb300 import workloads as wl
+    nx = WORKLOADS[name]
+    prob, opts, angs = wl.config_star16(nx, nx)
+    return prob, opts, angs
+
+
+def cpu_oracle_sample(nx, reps=1):
+    """Time the CPU oracle (factor + 8-RHS solve) on an nx x nx block of the same star recipe."""
+    import numpy as np
+    from oracle import dense, proxy
+    from paper_2603_09381_gb300 import workloads as wl
+    prob = wl.star_grid(nx, nx, n=128, seed=1)
+    _, opts, angs = wl.config_star16()
+    N = wl.num_unknowns(prob)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fac = proxy.factor(prob, opts)
+        F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
+        proxy.solve(fac, F)
+        ts.append(time.perf_counter() - t0)
+    return N, ts
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    # each step: the oracle on a 4x4 block (about 10-20 s); 2x2 if the run would exceed ~4 min
+    nx = 4 if (args.steps + args.warmup) * 20 <= 240 else 2
+    N, _ = cpu_oracle_sample(nx, reps=max(args.warmup, 0)) if args.warmup else (None, None)
+    N, ts = cpu_oracle_sample(nx, reps=args.steps)
+    t = sum(ts) / len(ts)
+    val = N / t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"star grid {nx}x{nx} block of the 16x16 star recipe, n=128, tol 1e-10, 8 RHS",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"CPU oracle (NumPy/SciPy proxy solver), {nx}x{nx} stars, N={N}, "
+                                       f"factor + 8-RHS solve per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if its kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2603_09381_gb300", "csrc", ent["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_2603_09381_gb300 import pmchwt as pm
+    from paper_2603_09381_gb300 import workloads as wl
+
+    prob, opts, angs = workload(args.workload)
+    N = wl.num_unknowns(prob)
+    nrhs = len(angs)
+    stream = torch.cuda.current_stream()
+    g = pm.Geometry(prob)
+    F = torch.zeros((nrhs, N), dtype=torch.complex128, device="cuda")
+    X = torch.zeros_like(F)
+    g.plane_wave_device(angs, F.data_ptr())
+    torch.cuda.synchronize()
+
+    def step(profile=False):
+        f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"],
+                      stream=stream.cuda_stream, profile=profile)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.solve_device(F.data_ptr(), nrhs, X.data_ptr())
+        e1.record(stream)
+        return f, e0, e1
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = pm.launch_counter()
+    prof_tot = {}
+    solve_ms = []
+    fstats = []
+    with Clocks(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            f, e0, e1 = step(profile=True)
+            fstats.append(f.stats())
+            for k, v in f.profile().items():
+                a = prof_tot.setdefault(k, {"launches": 0, "ms": 0.0, "work": 0.0})
+                for kk in a:
+                    a[kk] += v[kk]
+            solve_ms.append((e0, e1))
+            del f
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = pm.launch_counter() - launches0
+    ms = t0.elapsed_time(t1) / args.steps
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(tt.item())
+    solve = sum(a.elapsed_time(b) for a, b in solve_ms) / len(solve_ms)
+    value = ws * N / (ms / 1e3)
+
+    # end to end through the public API with host buffers: descriptors and pinned
+    # right-hand sides in, solution out, every step
+    rhs_host = torch.from_numpy(g.plane_wave(angs).T.copy()).pin_memory()
+    out_host = torch.zeros_like(rhs_host).pin_memory()
+    h2d = nrhs * N * 16 + len(prob["inclusions"]) * 200
+    d2h = nrhs * N * 16
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        g2 = pm.Geometry(prob)
+        f2 = pm.Factor(g2, opts["tol"], opts["proxy_factor"], opts["proxy_points"], stream=stream.cuda_stream)
+        pm._check(pm.load().pm_solve(f2.h, rhs_host.data_ptr(), nrhs, out_host.data_ptr(), 0))
+        del f2, g2
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te) / args.steps
+    if ws > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    ok = np.allclose(out_host.numpy(), X.cpu().numpy(), rtol=0, atol=1e-10 * float(X.abs().max()))
+
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel
+    flop_kernels = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched",
+                    "interp_solve"}
+    dom = max(prof_tot.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    roof = {"kernel": name, "launches_per_step": d["launches"] / args.steps,
+            "kernel_ms_per_step": d["ms"] / args.steps}
+    if name in flop_kernels and d["ms"] > 0:
+        achieved = d["work"] / (d["ms"] / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 dense FP64 (recipe)",
+                     "traffic": _traffic_for(name)})
+    else:
+        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+    kernels = {k: {"launches": v["launches"] // args.steps, "ms": round(v["ms"] / args.steps, 3),
+                   "tflops": (round(v["work"] / (v["ms"] / 1e3) / 1e12, 4)
+                              if k in flop_kernels and v["ms"] > 0 else None)}
+               for k, v in sorted(prof_tot.items(), key=lambda kv: -kv[1]["ms"])}
+    st = fstats[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"{WORKLOADS[args.workload]}x{WORKLOADS[args.workload]} stars "
+                                   f"r=0.4(1+0.2cos5t), spacing 1, k0=2pi*20/16, k1=2k0, n=128, N={N}, "
+                                   f"tol 1e-10, {st['levels']} levels, 8 plane-wave RHS",
+                       "l2": "inputs larger than L2 (factor working set > 1 GB)", "parallelism": f"replicas{ws}"},
+            "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
+            "phase_ms": {k: st[k] for k in ("ms_assemble", "ms_id", "ms_schur", "ms_top")},
+            "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
+            "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "matches_device_result": bool(ok)},
+            "clocks": clk.summary()}
+    if ws == 1 and not args.no_cpu_baseline:
+        Nc, ts = cpu_oracle_sample(4, reps=1)
+        line["cpu_baseline"] = {"value": Nc / ts[0], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"CPU oracle (NumPy/SciPy proxy solver) on a 4x4 block of the same star "
+                                          f"recipe, N={Nc}, factor + 8-RHS solve, {ts[0]:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="star16", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

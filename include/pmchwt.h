@@ -156,6 +156,25 @@ pm_status pm_matrix_entries(const pm_geometry* g, const int32_t* rows, int32_t M
  * (paper Sec. 2.2: Kress log-split quadrature for S, D, D*; Maue's form of N). */
 pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out);
 
+/* Per-kernel timing of a factorization made with flags & PM_FLAG_PROFILE
+ * (no counterpart in the paper; measurement aid).  CUDA events bracket every
+ * launch on the factorization's stream.  `work` is the algorithmic work of
+ * all launches: real flops for cpqr_step, interp_solve, lu_*, getrs and
+ * gemm_batched; matrix entries for gather_entries; node pairs for
+ * self_pointwise.  Writes up to cap entries, *count = number available. */
+typedef struct {
+  char name[32];
+  int32_t launches;
+  double ms;
+  double work;
+} pm_kernel_stat;
+enum { PM_FLAG_PROFILE = 1 };
+pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
+
+/* Number of CUDA kernel launches this library has made in this process
+ * (no counterpart in the paper; measurement aid). */
+pm_status pm_launch_counter(uint64_t* out);
+
 void pm_factor_free(pm_factor* f);
 void pm_geometry_free(pm_geometry* g);
 const char* pm_last_error(void);

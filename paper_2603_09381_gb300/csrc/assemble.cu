@@ -7,6 +7,7 @@
 // (paper Sec. 2.1, eqs. slp, dlp, d_slp, d_dlp).  Bessel values for real
 // arguments come from CUDA's j0/j1/y0/y1 (FP64) or j0f/j1f/y0f/y1f (FP32).
 #include "assemble.cuh"
+#include "prof.cuh"
 
 namespace {
 
@@ -263,16 +264,19 @@ __global__ void __launch_bounds__(256) k_gather(const GatherProb<C>* __restrict_
 void geom_nodes(const InclDev* d_inc, NodesDev nodes, int total, const InclDev*, cudaStream_t st) {
   if (total <= 0) return;
   k_geom_nodes<<<(total + 127) / 128, 128, 0, st>>>(d_inc, nodes, total);
+  pm_launch_count_add(1);
 }
 
 void geom_points_from_nodes(NodesDev nodes, PointsDev pts, int total, cudaStream_t st) {
   if (total <= 0) return;
   k_points_from_nodes<<<(total + 255) / 256, 256, 0, st>>>(nodes, pts, total);
+  pm_launch_count_add(1);
 }
 
 void geom_proxy_points(const ProxyBoxDev* d_box, int nbox, PointsDev pts, int total, int off, cudaStream_t st) {
   if (total <= 0 || nbox <= 0) return;
   k_proxy_points<<<(total + 255) / 256, 256, 0, st>>>(d_box, nbox, pts, total, off);
+  pm_launch_count_add(1);
 }
 
 template <typename C>
@@ -281,6 +285,7 @@ void plane_wave_rhs(const InclDev* d_inc, NodesDev nodes, int total, double k0, 
   if (total <= 0 || nrhs <= 0) return;
   dim3 g((total + 255) / 256, nrhs);
   k_plane_wave<C><<<g, 256, 0, st>>>(d_inc, nodes, total, k0, d_ang, nrhs, F, ldf);
+  pm_launch_count_add(1);
 }
 
 template <typename C>
@@ -288,12 +293,16 @@ void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, doubl
                     const int* d_lda, C* const* d_Cm, cudaStream_t st) {
   if (m <= 0) return;
   dim3 g((maxn * maxn + 255) / 256, m);
+  KPROF_BEGIN(st);
   k_self_pointwise<C><<<g, 256, 0, st>>>(d_inc, nodes, k0, d_A, d_lda, d_Cm);
+  pm_launch_count_add(1);
+  KPROF_END(st, "self_pointwise", 0.0);
 }
 
 template <typename C>
 void diff_matrices(int n, C* Dt, cudaStream_t st) {
   k_diff_matrix<C><<<(n * n + 255) / 256, 256, 0, st>>>(n, Dt);
+  pm_launch_count_add(1);
 }
 
 template <typename C>
@@ -301,13 +310,17 @@ void scaled_diff(const InclDev* d_inc, int m, int maxn, NodesDev nodes, C* const
   if (m <= 0) return;
   dim3 g((maxn * maxn + 255) / 256, m);
   k_scaled_diff<C><<<g, 256, 0, st>>>(d_inc, nodes, d_DtS);
+  pm_launch_count_add(1);
 }
 
 template <typename C>
 void gather_assemble(const GatherProb<C>* d_prob, const int* d_tile_off, int nprob, int total_tiles,
                      PointsDev pts, double k0, cudaStream_t st) {
   if (nprob <= 0 || total_tiles <= 0) return;
+  KPROF_BEGIN(st);
   k_gather<C><<<total_tiles, 256, 0, st>>>(d_prob, d_tile_off, nprob, pts, k0);
+  pm_launch_count_add(1);
+  KPROF_END(st, "gather_entries", 0.0);
 }
 
 template void plane_wave_rhs<double2>(const InclDev*, NodesDev, int, double, const double*, int, double2*, int, cudaStream_t);

@@ -11,6 +11,7 @@
 // Work per entry and step: ~10 real FMAs on 48 bytes, so the FP64 pipe, not
 // HBM, bounds it on GB300.
 #include "cpqr.cuh"
+#include "prof.cuh"
 
 namespace {
 
@@ -197,33 +198,45 @@ void complete_perm(const PermFill* d_prob, int nprob, cudaStream_t st) {
     attr = true;
   }
   k_complete_perm<<<nprob, 256, 65536, st>>>(d_prob);
+  pm_launch_count_add(1);
 }
 
 template <typename C>
 void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, cudaStream_t st) {
-  if (nchunk > 0) k_init_norms<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk);
+  if (nchunk <= 0) return;
+  k_init_norms<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk);
+  pm_launch_count_add(1);
 }
 template <typename C>
 void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, cudaStream_t st) {
-  if (nchunk > 0) k_cpqr_step<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk, t);
+  if (nchunk <= 0) return;
+  KPROF_BEGIN(st);
+  k_cpqr_step<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk, t);
+  pm_launch_count_add(1);
+  KPROF_END(st, "cpqr_step", 0.0);   // flops are added per level from the steps performed
 }
 template <typename C>
 void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st) {
   if (nprob <= 0 || max_cols <= 0) return;
   dim3 g((max_cols + 63) / 64, nprob);
+  KPROF_BEGIN(st);
   k_interp<C><<<g, 64, 0, st>>>(d_prob);
+  pm_launch_count_add(1);
+  KPROF_END(st, "interp_solve", 0.0);
 }
 template <typename C>
 void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {
   if (nprob <= 0 || max_elems <= 0) return;
   dim3 g((max_elems + 255) / 256, nprob);
   k_scatter<C><<<g, 256, 0, st>>>(d_prob);
+  pm_launch_count_add(1);
 }
 template <typename C>
 void copy_batched(const CopyProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {
   if (nprob <= 0 || max_elems <= 0) return;
   dim3 g((max_elems + 255) / 256, nprob);
   k_copy<C><<<g, 256, 0, st>>>(d_prob);
+  pm_launch_count_add(1);
 }
 
 template void cpqr_init_norms<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, cudaStream_t);

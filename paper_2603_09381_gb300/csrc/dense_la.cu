@@ -5,6 +5,8 @@
 // the chip's FP64:HBM balance (~0.18).  The kernels therefore favour simple
 // shared-memory tiling with enough resident warps to keep the DFMA pipe busy.
 #include "dense_la.cuh"
+#include "prof.cuh"
+#include <algorithm>
 
 namespace {
 
@@ -249,55 +251,89 @@ template <typename C>
 void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob, int total_tiles,
                      cudaStream_t st) {
   if (nprob <= 0 || total_tiles <= 0) return;
+  KPROF_BEGIN(st);
   k_gemm_batched<C><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob);
+  pm_launch_count_add(1);
+  KPROF_END(st, "gemm_batched", 0.0);
 }
 
 constexpr int LU_NB = 16;
 constexpr int RS_NB = 32;
 
 template <typename C>
-void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, cudaStream_t st) {
+void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st) {
   if (nprob <= 0 || maxm <= 0) return;
   for (int p = 0; p < maxm; p += LU_NB) {
+    double fp = 0, fs = 0, fu = 0;
+    if (g_kprof) {
+      for (int i = 0; i < nprob; ++i) {
+        int m = h_m[i];
+        if (p >= m) continue;
+        double jb = std::min(LU_NB, m - p), rest = m - p - jb, h = m - p;
+        fp += 8.0 * (h * jb * jb / 2);          // panel: rank-1 updates inside the panel
+        fs += 8.0 * rest * jb * jb / 2;          // unit-lower solve of U12
+        fu += 8.0 * rest * rest * jb;            // trailing GEMM
+      }
+    }
+    KPROF_BEGIN(st);
     k_lu_panel<C><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
+    pm_launch_count_add(1);
+    KPROF_END(st, "lu_panel", fp);
     dim3 g1((maxm + 255) / 256, nprob);
+    KPROF_BEGIN(st);
     k_lu_swap_trsm<C><<<g1, 256, 0, st>>>(d_prob, p, LU_NB);
+    pm_launch_count_add(1);
+    KPROF_END(st, "lu_swap_trsm", fs);
     int mt = maxm - p - LU_NB;
     if (mt > 0) {
       int tiles = ((mt + TB - 1) / TB);
       dim3 g2(tiles * tiles, nprob);
+      KPROF_BEGIN(st);
       k_lu_update<C><<<g2, 256, 0, st>>>(d_prob, p, LU_NB);
+      pm_launch_count_add(1);
+      KPROF_END(st, "lu_update", fu);
     }
   }
 }
 
 template <typename C>
-void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, cudaStream_t st) {
+void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
+                      const int* h_rhs, cudaStream_t st) {
   if (nprob <= 0 || maxm <= 0 || maxrhs <= 0) return;
+  double fl = 0;
+  if (g_kprof)
+    for (int i = 0; i < nprob; ++i) fl += 8.0 * (double)h_m[i] * h_m[i] * h_rhs[i];
+  KPROF_BEGIN(st);
   dim3 gs((maxrhs + 127) / 128, nprob);
   k_getrs_swap<C><<<gs, 128, 0, st>>>(d_prob);
+  pm_launch_count_add(1);
   const int tiles_n = (maxrhs + TB - 1) / TB;
   for (int p = 0; p < maxm; p += RS_NB) {
     k_getrs_diag<C><<<gs, 128, 0, st>>>(d_prob, p, RS_NB, 1);
+    pm_launch_count_add(1);
     int mt = maxm - p - RS_NB;
     if (mt > 0) {
       dim3 g2(((mt + TB - 1) / TB) * tiles_n, nprob);
       k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 1);
+      pm_launch_count_add(1);
     }
   }
   int last = ((maxm - 1) / RS_NB) * RS_NB;
   for (int p = last; p >= 0; p -= RS_NB) {
     k_getrs_diag<C><<<gs, 128, 0, st>>>(d_prob, p, RS_NB, 0);
+    pm_launch_count_add(1);
     if (p > 0) {
       dim3 g2(((p + TB - 1) / TB) * tiles_n, nprob);
       k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 0);
+      pm_launch_count_add(1);
     }
   }
+  KPROF_END(st, "getrs", fl);
 }
 
 template void la_gemm_batched<double2>(const GemmDesc<double2>*, const int*, int, int, cudaStream_t);
 template void la_gemm_batched<float2>(const GemmDesc<float2>*, const int*, int, int, cudaStream_t);
-template void la_getrf_batched<double2>(const LuProb<double2>*, int, int, cudaStream_t);
-template void la_getrf_batched<float2>(const LuProb<float2>*, int, int, cudaStream_t);
-template void la_getrs_batched<double2>(const SolveProb<double2>*, int, int, int, cudaStream_t);
-template void la_getrs_batched<float2>(const SolveProb<float2>*, int, int, int, cudaStream_t);
+template void la_getrf_batched<double2>(const LuProb<double2>*, int, int, const int*, cudaStream_t);
+template void la_getrf_batched<float2>(const LuProb<float2>*, int, int, const int*, cudaStream_t);
+template void la_getrs_batched<double2>(const SolveProb<double2>*, int, int, int, const int*, const int*, cudaStream_t);
+template void la_getrs_batched<float2>(const SolveProb<float2>*, int, int, int, const int*, const int*, cudaStream_t);

@@ -33,10 +33,12 @@ struct SolveProb {     // B (m x nrhs) <- A^{-1} B using the LU of A
 template <typename C>
 void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob, int total_tiles,
                      cudaStream_t st);
+// h_m: host copy of the matrix sizes (flop accounting for the optional profiler)
 template <typename C>
-void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, cudaStream_t st);
+void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st);
 template <typename C>
-void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, cudaStream_t st);
+void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
+                      const int* h_rhs, cudaStream_t st);
 
 // tiles of a GEMM problem for the 32 x 32 output tiling
 inline int gemm_tiles(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }

@@ -3,6 +3,7 @@
 // Every numerical step runs in the CUDA kernels of assemble.cu, cpqr.cu and
 // dense_la.cu; this file only plans index lists and launches.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -14,8 +15,13 @@
 #include "assemble.cuh"
 #include "cpqr.cuh"
 #include "dense_la.cuh"
+#include "prof.cuh"
 
 typedef double2 Cd;
+
+thread_local KProf* g_kprof = nullptr;
+static std::atomic<unsigned long long> g_launches{0};
+void pm_launch_count_add(long n) { g_launches += (unsigned long long)n; }
 
 namespace {
 
@@ -152,6 +158,8 @@ struct pm_factor {
   Arena arena, scratch;
   pm_stats stats{};
   std::vector<std::vector<Box>> tree;  // the geometry's quadtree with this factorization's proxies
+  KProf prof;
+  bool profiling = false;
 };
 
 namespace {
@@ -285,6 +293,11 @@ void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std
   Cd** dC = upload(scr, Cm, st);
   Cd** dD = upload(scr, DtS, st);
   self_pointwise<Cd>(d_sub, m, maxn, g->nodes, g->k0, dA, dlda, dC, st);
+  if (g_kprof) {
+    double e = 0;
+    for (auto& c : sub) e += (double)c.n * c.n;
+    g_kprof->add_flops("self_pointwise", e);   // work unit: node pairs (two wavenumbers each)
+  }
   scaled_diff<Cd>(d_sub, m, maxn, g->nodes, dD, st);
   CK(cudaGetLastError());
   // Maue: N-block += diag(1/|x'|) Dt (S0+/e+ + S0-/e-) Dt
@@ -330,6 +343,11 @@ struct GatherBatch {
     auto* dp = upload(scr, probs, st);
     int* dt = upload(scr, tile_off, st);
     gather_assemble<Cd>(dp, dt, (int)probs.size(), tile_off.back(), pts, k0, st);
+    if (g_kprof) {
+      double e = 0;
+      for (auto& x : probs) e += (double)x.M * x.N;
+      g_kprof->add_flops("gather_entries", e);   // work unit: matrix entries
+    }
     CK(cudaGetLastError());
   }
 };
@@ -351,6 +369,11 @@ struct GemmBatch {
     auto* dd = upload(scr, d, st);
     int* dof = upload(scr, off, st);
     la_gemm_batched<Cd>(dd, dof, (int)d.size(), off.back(), st);
+    if (g_kprof) {
+      double f = 0;
+      for (auto& x : d) f += 8.0 * x.m * x.n * x.k;
+      g_kprof->add_flops("gemm_batched", f);
+    }
     CK(cudaGetLastError());
   }
 };
@@ -379,7 +402,9 @@ void lu_batch(std::vector<LuProb<Cd>>& probs, Arena& scr, cudaStream_t st, const
   int maxm = 0;
   for (int i = 0; i < n; ++i) { probs[i].info = info + i; maxm = std::max(maxm, probs[i].m); }
   auto* dp = upload(scr, probs, st);
-  la_getrf_batched<Cd>(dp, n, maxm, st);
+  std::vector<int> hm(n);
+  for (int i = 0; i < n; ++i) hm[i] = probs[i].m;
+  la_getrf_batched<Cd>(dp, n, maxm, hm.data(), st);
   CK(cudaGetLastError());
   std::vector<int> h(n);
   CK(cudaMemcpyAsync(h.data(), info, n * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -391,9 +416,13 @@ void lu_batch(std::vector<LuProb<Cd>>& probs, Arena& scr, cudaStream_t st, const
 void solve_batch(std::vector<SolveProb<Cd>>& probs, Arena& scr, cudaStream_t st) {
   if (probs.empty()) return;
   int maxm = 0, maxr = 0;
-  for (auto& p : probs) { maxm = std::max(maxm, p.m); maxr = std::max(maxr, p.nrhs); }
+  std::vector<int> hm, hr;
+  for (auto& p : probs) {
+    maxm = std::max(maxm, p.m); maxr = std::max(maxr, p.nrhs);
+    hm.push_back(p.m); hr.push_back(p.nrhs);
+  }
   auto* dp = upload(scr, probs, st);
-  la_getrs_batched<Cd>(dp, (int)probs.size(), maxm, maxr, st);
+  la_getrs_batched<Cd>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st);
   CK(cudaGetLastError());
 }
 
@@ -619,6 +648,16 @@ void process_level(pm_factor* F, int lev) {
     complete_perm(dpf, nid, st);
     CK(cudaGetLastError());
   }
+  if (g_kprof) {
+    double f = 0, fi = 0;
+    for (int i = 0; i < nid; ++i) {
+      int S = std::max(r[i], kk[i]);
+      for (int s2 = 0; s2 < S; ++s2) f += 20.0 * (double)(W[i] - s2 - 1) * (nn[i] - s2 - 1);
+      fi += 4.0 * (double)kk[i] * kk[i] * (nn[i] - kk[i]);
+    }
+    g_kprof->add_flops("cpqr_step", f);
+    g_kprof->add_flops("interp_solve", fi);
+  }
   std::vector<int> hperm(std::max(total_n, 1));
   CK(cudaMemcpyAsync(hperm.data(), perm, std::max(total_n, 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -699,7 +738,10 @@ void process_level(pm_factor* F, int lev) {
     Y[b] = scr.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
     ypiv[b] = scr.get<int>(std::max(bf.kb, 1));
     gy.add(bf.kb, bf.kb, bf.mb, bf.Rm, bf.kb, bf.X, bf.mb, Y[b], bf.kb, make_double2(1, 0), make_double2(0, 0), 1);
-    if (bf.kb > 0) k_identity<<<(bf.kb * bf.kb + 255) / 256, 256, 0, st>>>(bf.At, bf.kb, bf.kb);
+    if (bf.kb > 0) {
+      k_identity<<<(bf.kb * bf.kb + 255) / 256, 256, 0, st>>>(bf.At, bf.kb, bf.kb);
+      pm_launch_count_add(1);
+    }
   }
   gy.run(scr, st);
   std::vector<LuProb<Cd>> luy;
@@ -990,11 +1032,17 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
     F->stats.levels = F->L;
     F->stats.N = g->N;
     F->lev.assign(F->L + 1, {});
+    F->profiling = (opts->flags & 1u) != 0;
+    struct ProfScope {
+      explicit ProfScope(KProf* p) { g_kprof = p; }
+      ~ProfScope() { g_kprof = nullptr; }
+    } scope(F->profiling ? &F->prof : nullptr);
     Timer tt(F->st);
     for (int l = F->L; l >= 1; --l) process_level(F, l);
     factor_top(F);
-    F->scratch.release();
     F->stats.ms_total = tt.stop();
+    if (F->profiling) F->prof.collect();
+    F->scratch.release();
   });
   if (s != PM_OK) { delete F; return s; }
   *out = F;
@@ -1085,6 +1133,30 @@ pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out) {
     assemble_self(g, {j}, {d}, {2 * n}, ws, st);
     CK(cudaMemcpy(out, d, sizeof(Cd) * (size_t)4 * n * n, cudaMemcpyDeviceToHost));
   });
+}
+
+pm_status pm_factor_profile(const pm_factor* F, pm_kernel_stat* out, int32_t cap, int32_t* count) {
+  if (!F || !count) { g_err = "pm_factor_profile: NULL argument"; return PM_ERR_INVALID_ARG; }
+  int i = 0;
+  for (const auto& kv : F->prof.agg) {
+    if (out && i < cap) {
+      pm_kernel_stat& o = out[i];
+      std::memset(&o, 0, sizeof(o));
+      std::strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
+      o.launches = (int32_t)kv.second.launches;
+      o.ms = kv.second.ms;
+      o.work = kv.second.flops;
+    }
+    ++i;
+  }
+  *count = i;
+  return PM_OK;
+}
+
+pm_status pm_launch_counter(uint64_t* out) {
+  if (!out) { g_err = "pm_launch_counter: NULL argument"; return PM_ERR_INVALID_ARG; }
+  *out = g_launches.load();
+  return PM_OK;
 }
 
 void pm_factor_free(pm_factor* F) { delete F; }

@@ -48,6 +48,11 @@ class pm_stats(ct.Structure):
                 ("ms_top", ct.c_double), ("ms_total", ct.c_double)]
 
 
+class pm_kernel_stat(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int32), ("ms", ct.c_double), ("work", ct.c_double)]
+
+
+PM_FLAG_PROFILE = 1
 _lib = None
 
 EXPORTS = {
@@ -62,6 +67,8 @@ EXPORTS = {
                                       ct.POINTER(ct.c_int32)]),
     "pm_matrix_entries": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_self_block": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "pm_factor_profile": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "pm_launch_counter": (ct.c_int, [ct.POINTER(ct.c_uint64)]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
     "pm_last_error": (ct.c_char_p, []),
@@ -104,6 +111,12 @@ def make_problem(prob):
     p = pm_problem(m, arr, float(prob["k_out"]), int(prob.get("grid_nx", 0)), int(prob.get("grid_ny", 0)),
                    float(prob["spacing"]))
     return p, arr
+
+
+def launch_counter():
+    v = ct.c_uint64()
+    _check(load().pm_launch_counter(ct.byref(v)))
+    return v.value
 
 
 class Geometry:
@@ -151,11 +164,12 @@ class Geometry:
 
 
 class Factor:
-    def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None):
+    def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
+                 profile=False):
         lib = load()
         self.geom = geom
         o = pm_factor_opts(float(tol), float(proxy_factor), int(proxy_points), int(precision),
-                           ct.c_void_p(stream) if stream else None, 0)
+                           ct.c_void_p(stream) if stream else None, PM_FLAG_PROFILE if profile else 0)
         h = ct.c_void_p()
         _check(lib.pm_factorize(geom.h, ct.byref(o), ct.byref(h)))
         self.h = h
@@ -166,6 +180,13 @@ class Factor:
         return {"levels": s.levels, "N": s.N, "K": s.K, "skeleton": list(s.skeleton)[: s.levels + 1],
                 "ms_assemble": s.ms_assemble, "ms_id": s.ms_id, "ms_schur": s.ms_schur, "ms_top": s.ms_top,
                 "ms_total": s.ms_total}
+
+    def profile(self):
+        cnt = ct.c_int32()
+        _check(load().pm_factor_profile(self.h, None, 0, ct.byref(cnt)))
+        arr = (pm_kernel_stat * max(cnt.value, 1))()
+        _check(load().pm_factor_profile(self.h, arr, cnt.value, ct.byref(cnt)))
+        return {a.name.decode(): {"launches": a.launches, "ms": a.ms, "work": a.work} for a in arr[: cnt.value]}
 
     def solve(self, rhs):
         """Host solve: rhs (N,) or (N, nrhs) complex128 -> phi of the same shape."""
