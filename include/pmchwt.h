@@ -175,6 +175,22 @@ pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap
  * (no counterpart in the paper; measurement aid). */
 pm_status pm_launch_counter(uint64_t* out);
 
+/* The self block A_jj, like pm_self_block, without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library call cudaMalloc / cudaFree, because those calls may
+ * synchronise the device while the caller has work in flight, or because the
+ * caller runs under its own device-memory manager or a fixed budget.
+ *   out: caller-owned DEVICE buffer of (2 n_j)^2 pm_c64, column-major,
+ *        on the current device; fully overwritten.
+ * Scratch lives in a file-scope device array of 4 MiB + 64 KiB that every GPU
+ * loading the library holds until the process exits; it limits n_j to 256
+ * (larger n_j -> PM_ERR_INVALID_ARG, nothing written).  The first call on a
+ * device looks up that array's device address; make it before any stream
+ * capture.  Calls share the array and return only when their work on the
+ * default stream has finished, so calls overlapping on the GPU (e.g. from
+ * several host threads at once) race and must be serialised by the caller. */
+pm_status pm_self_block_noalloc(const pm_geometry* g, int32_t j, pm_c64* out);
+
 void pm_factor_free(pm_factor* f);
 void pm_geometry_free(pm_geometry* g);
 const char* pm_last_error(void);

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1163,3 +1164,90 @@ void pm_factor_free(pm_factor* F) { delete F; }
 void pm_geometry_free(pm_geometry* g) { delete g; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of pm_self_block.
+//
+// Some callers cannot let this library call cudaMalloc / cudaFree: those
+// calls may synchronise the whole device (stalling work the caller has in
+// flight on other streams), and a host application that runs under a fixed
+// device-memory budget or its own memory manager may forbid allocations by
+// libraries altogether.  pm_self_block_noalloc writes the self block into a
+// caller-provided device buffer and keeps all of its scratch (the Maue
+// factors and the launch descriptors) in the file-scope device array below.
+namespace {
+
+constexpr int NOALLOC_MAX_N = 256;                       // largest n_j accepted
+constexpr size_t NOALLOC_DESC_BYTES = 64 * 1024;         // launch descriptors
+constexpr size_t NOALLOC_MAT_BYTES = (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N * sizeof(Cd);
+constexpr size_t NOALLOC_BYTES = NOALLOC_DESC_BYTES + 4 * NOALLOC_MAT_BYTES;   // 4 MiB + 64 KiB
+
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device.  The host-side
+// symbol is only a stand-in, so the address is looked up once per device with
+// that device current (the first call on a device does this set-up).
+char* noalloc_scratch() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(PM_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (char*)p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" pm_status pm_self_block_noalloc(const pm_geometry* g, int32_t j, pm_c64* out) {
+  if (!g || !out || j < 0 || j >= g->m) { g_err = "pm_self_block_noalloc: bad argument"; return PM_ERR_INVALID_ARG; }
+  const int n = g->inc[j].n_nodes;
+  if (n > NOALLOC_MAX_N) {
+    g_err = "pm_self_block_noalloc: n_j = " + std::to_string(n) + " exceeds the scratch limit of " +
+            std::to_string(NOALLOC_MAX_N) + " nodes";
+    return PM_ERR_INVALID_ARG;
+  }
+  return run_guarded("pm_self_block_noalloc", [&] {
+    cudaStream_t st = 0;
+    char* base = noalloc_scratch();
+    Cd* A = (Cd*)out;
+    const int lda = 2 * n;
+    Cd* Cm = (Cd*)(base + NOALLOC_DESC_BYTES);
+    Cd* DtS = (Cd*)(base + NOALLOC_DESC_BYTES + NOALLOC_MAT_BYTES);
+    Cd* E = (Cd*)(base + NOALLOC_DESC_BYTES + 2 * NOALLOC_MAT_BYTES);
+    Cd* Dt = (Cd*)(base + NOALLOC_DESC_BYTES + 3 * NOALLOC_MAT_BYTES);
+    // descriptor area: fixed slots, every slot fully rewritten by each call
+    struct Desc {
+      GemmDesc<Cd> d1, d2;
+      int off1[2], off2[2];
+      Cd* Aptr[1];
+      int ldA[1];
+      Cd* Cptr[1];
+      Cd* Dptr[1];
+    } h;
+    static_assert(sizeof(Desc) <= NOALLOC_DESC_BYTES, "descriptor area too small");
+    h.d1 = GemmDesc<Cd>{n, n, n, Cm, n, Dt, n, E, n, make_double2(1, 0), make_double2(0, 0), 1};
+    h.d2 = GemmDesc<Cd>{n, n, n, DtS, n, E, n, A + n + (size_t)n * lda, lda, make_double2(1, 0),
+                        make_double2(1, 0), 0};
+    h.off1[0] = 0; h.off1[1] = gemm_tiles(n, n);
+    h.off2[0] = 0; h.off2[1] = gemm_tiles(n, n);
+    h.Aptr[0] = A; h.ldA[0] = lda; h.Cptr[0] = Cm; h.Dptr[0] = DtS;
+    Desc* d = (Desc*)base;
+    CK(cudaMemcpyAsync(d, &h, sizeof(Desc), cudaMemcpyHostToDevice, st));
+    const InclDev* dinc = g->d_inc + j;
+    diff_matrices<Cd>(n, Dt, st);
+    self_pointwise<Cd>(dinc, 1, n, g->nodes, g->k0, d->Aptr, d->ldA, d->Cptr, st);
+    scaled_diff<Cd>(dinc, 1, n, g->nodes, d->Dptr, st);
+    la_gemm_batched<Cd>(&d->d1, d->off1, 1, h.off1[1], st);
+    la_gemm_batched<Cd>(&d->d2, d->off2, 1, h.off2[1], st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}

@@ -69,6 +69,7 @@ EXPORTS = {
     "pm_self_block": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_factor_profile": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_launch_counter": (ct.c_int, [ct.POINTER(ct.c_uint64)]),
+    "pm_self_block_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
     "pm_last_error": (ct.c_char_p, []),
@@ -156,6 +157,10 @@ class Geometry:
         out = np.zeros((2 * n, 2 * n), dtype=np.complex128)
         _check(load().pm_self_block(self.h, j, out.ctypes.data))
         return out.T  # column-major -> row-major view
+
+    def self_block_noalloc(self, j, out_ptr):
+        """A_jj into a caller-owned device buffer, with no device allocation."""
+        _check(load().pm_self_block_noalloc(self.h, j, out_ptr))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
