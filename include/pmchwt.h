@@ -44,7 +44,7 @@ typedef enum {
 typedef struct { double re, im; } pm_c64;
 
 enum { PM_CIRCLE = 0, PM_ELLIPSE = 1, PM_STAR = 2, PM_FOURIER = 3 };
-enum { PM_FP64 = 0 };
+enum { PM_FP64 = 0, PM_MIXED = 1 };
 
 /* One inclusion (paper Sec. 2.1: Omega_j with smooth boundary Gamma_j).
  * Boundary x(t) = (cx, cy) + Rot(rot) rho(t), t in [0, 2 pi), counter-clockwise:
@@ -83,8 +83,18 @@ typedef struct pm_factor pm_factor;
  * proxy_factor: proxy circle radius / cell radius (> 1; default 1.5).
  * proxy_points: points on every proxy circle; 0 selects
  *      p = max(32, 8 ceil((2 k^+ R_p + ceil(ln(1/tol)/ln(proxy_factor)))/8)).
- * precision: PM_FP64.
- * stream: cudaStream_t to run on, or NULL for the default stream. */
+ * precision: PM_FP64 (everything complex128), or PM_MIXED: the levels are
+ *      factored in complex64 with ID threshold max(tol, low_tol) and serve as a
+ *      preconditioner; the top-level LU stays complex128 and pm_solve refines
+ *      the solution against the complex128 operator (no counterpart in the
+ *      paper).
+ * stream: cudaStream_t to run on, or NULL for the default stream.
+ * flags: PM_FLAG_PROFILE records per-kernel timings.
+ * refine_tol: PM_MIXED: stop refining once every column's relative residual
+ *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).
+ * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
+ *      refine_tol returns PM_ERR_NOT_CONVERGED.
+ * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 1e-5). */
 typedef struct {
   double tol;
   double proxy_factor;
@@ -92,7 +102,17 @@ typedef struct {
   int32_t precision;
   void* stream;
   uint32_t flags;
+  double refine_tol;
+  int32_t max_refine;
+  double low_tol;
 } pm_factor_opts;
+
+/* Outcome of a refined solve (PM_MIXED): steps taken and the final largest
+ * relative residual over the right-hand sides (-1 when not refined). */
+typedef struct {
+  int32_t iterations;
+  double residual;
+} pm_solve_info;
 
 /* Statistics of a factorization (filled by pm_factor_stats). */
 typedef struct {
@@ -136,6 +156,10 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
  * the recovery formula).  rhs and phi are N x nrhs column-major, device
  * pointers if on_device = 1, else host pointers; they may alias. */
 pm_status pm_solve(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device);
+
+/* pm_solve that also reports the refinement outcome (info may be NULL). */
+pm_status pm_solve_ex(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
+                      pm_solve_info* info);
 
 pm_status pm_factor_stats(const pm_factor* f, pm_stats* out);
 

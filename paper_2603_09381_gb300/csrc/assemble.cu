@@ -242,6 +242,37 @@ __device__ __forceinline__ C omit_entry(const PointsDev& P, int t, int s, double
   return mk((R)(-Him * f), (R)(Hre * f));
 }
 
+// Single-precision entry (the FP32 factorization of the mixed-precision mode).
+template <>
+__device__ __forceinline__ float2 omit_entry<float2>(const PointsDev& P, int t, int s, double k) {
+  const int pt = t >> 1, rg = t & 1, ps = s >> 1, cg = s & 1;
+  const float dx = (float)(P.x[pt] - P.x[ps]), dy = (float)(P.y[pt] - P.y[ps]);
+  const float r2 = dx * dx + dy * dy;
+  if (!(r2 > 0.f)) return make_float2(0.f, 0.f);
+  const float r = sqrtf(r2);
+  const float kf = (float)k;
+  const float z = kf * r;
+  const float w = (float)P.w[ps];
+  const float ntx = (float)P.nx[pt], nty = (float)P.ny[pt], nsx = (float)P.nx[ps], nsy = (float)P.ny[ps];
+  if (rg == 0 && cg == 0) return make_float2(0.25f * y0f(z) * w, -0.25f * j0f(z) * w);
+  const float J1 = j1f(z), Y1 = y1f(z);
+  if (rg == 0) {
+    float g = (nsx * dx + nsy * dy) / r * 0.25f * kf * w;
+    return make_float2(-Y1 * g, J1 * g);
+  }
+  if (cg == 0) {
+    float g = (ntx * dx + nty * dy) / r * 0.25f * kf * w;
+    return make_float2(-Y1 * g, J1 * g);
+  }
+  const float J0 = j0f(z), Y0 = y0f(z);
+  const float a = (ntx * dx + nty * dy) / r, b = (nsx * dx + nsy * dy) / r;
+  const float nn = ntx * nsx + nty * nsy;
+  const float c0 = kf * a * b, c1 = (nn - 2.f * a * b) / r;
+  const float Hre = c0 * J0 + c1 * J1, Him = c0 * Y0 + c1 * Y1;
+  const float f = 0.25f * kf * w;
+  return make_float2(-Him * f, Hre * f);
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_gather(const GatherProb<C>* __restrict__ prob, const int* __restrict__ tile_off,
                                                 int nprob, PointsDev P, double k) {
@@ -329,3 +360,9 @@ template void self_pointwise<double2>(const InclDev*, int, int, NodesDev, double
 template void diff_matrices<double2>(int, double2*, cudaStream_t);
 template void scaled_diff<double2>(const InclDev*, int, int, NodesDev, double2* const*, cudaStream_t);
 template void gather_assemble<double2>(const GatherProb<double2>*, const int*, int, int, PointsDev, double, cudaStream_t);
+
+template void self_pointwise<float2>(const InclDev*, int, int, NodesDev, double, float2* const*, const int*,
+                                     float2* const*, cudaStream_t);
+template void diff_matrices<float2>(int, float2*, cudaStream_t);
+template void scaled_diff<float2>(const InclDev*, int, int, NodesDev, float2* const*, cudaStream_t);
+template void gather_assemble<float2>(const GatherProb<float2>*, const int*, int, int, PointsDev, double, cudaStream_t);

@@ -12,6 +12,7 @@
 // HBM, bounds it on GB300.
 #include "cpqr.cuh"
 #include "prof.cuh"
+#include <algorithm>
 
 namespace {
 
@@ -32,14 +33,14 @@ __global__ void __launch_bounds__(256) k_init_norms(const CpqrProb<C>* __restric
   }
 }
 
+// One elimination step of the chunk's matrix on the chunk's columns (all 256
+// threads of the CTA take the same path through the barriers).
 template <typename C>
-__global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict__ P, const CpqrChunk* __restrict__ chunks, int t) {
+__device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t) {
   typedef typename real_of<C>::type R;
-  const CpqrChunk ch = chunks[blockIdx.x];
-  const CpqrProb<C> p = P[ch.id];
   const int s = p.base + t;
   if (s >= p.target) return;
-  if (p.mode == CPQR_FIND_RANK && *p.rank >= 0) return;
+  if (p.mode == CPQR_FIND_RANK && *(volatile int*)p.rank >= 0) return;
   const int n = p.n;
   const double* cur = p.norm2 + (s & 1) * n;
   double* nxt = p.norm2 + ((s + 1) & 1) * n;
@@ -130,6 +131,24 @@ __global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict
   }
 }
 
+// Persistent grid (a multiple of the SM count): CTAs take chunks from a
+// per-launch counter, largest matrices first, until none is left.
+template <typename C>
+__global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict__ P, const CpqrChunk* __restrict__ chunks,
+                                                   int nchunk, int t, int* __restrict__ counter) {
+  __shared__ int s_ci;
+  for (;;) {
+    if (threadIdx.x == 0) s_ci = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ci = s_ci;
+    if (ci >= nchunk) break;
+    const CpqrChunk ch = chunks[ci];
+    const CpqrProb<C> p = P[ch.id];
+    cpqr_chunk_step<C>(p, ch, t);
+    __syncthreads();
+  }
+}
+
 template <typename C>
 __global__ void k_interp(const InterpProb<C>* __restrict__ P) {
   const InterpProb<C> p = P[blockIdx.y];
@@ -164,13 +183,18 @@ __global__ void k_scatter(const ScatterProb<C>* __restrict__ P) {
   else p.out[(p.off + j) + (size_t)row * p.ld] = v;
 }
 
-template <typename C>
-__global__ void k_copy(const CopyProb<C>* __restrict__ P) {
-  const CopyProb<C> p = P[blockIdx.y];
+__device__ __forceinline__ double2 cvt(double2 a, double2*) { return a; }
+__device__ __forceinline__ float2 cvt(float2 a, float2*) { return a; }
+__device__ __forceinline__ double2 cvt(float2 a, double2*) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ float2 cvt(double2 a, float2*) { return make_float2((float)a.x, (float)a.y); }
+
+template <typename S, typename D>
+__global__ void k_copy(const CopyProb<S, D>* __restrict__ P) {
+  const CopyProb<S, D> p = P[blockIdx.y];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= p.m * p.n) return;
   const int i = e % p.m, j = e / p.m;
-  p.dst[i + (size_t)j * p.ldd] = p.src[i + (size_t)j * p.lds];
+  p.dst[i + (size_t)j * p.ldd] = cvt(p.src[i + (size_t)j * p.lds], (D*)nullptr);
 }
 
 // Completes a permutation: after `done` pivot steps, the remaining columns in
@@ -208,10 +232,19 @@ void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nc
   pm_launch_count_add(1);
 }
 template <typename C>
-void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, cudaStream_t st) {
+void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
+               cudaStream_t st) {
   if (nchunk <= 0) return;
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cpqr_step<C>, 256, 0);
+    grid = std::max(1, sms * std::max(per, 1));
+  }
   KPROF_BEGIN(st);
-  k_cpqr_step<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk, t);
+  k_cpqr_step<C><<<std::min(grid, nchunk), 256, 0, st>>>(d_prob, d_chunk, nchunk, t, d_counter);
   pm_launch_count_add(1);
   KPROF_END(st, "cpqr_step", 0.0);   // flops are added per level from the steps performed
 }
@@ -231,16 +264,23 @@ void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cuda
   k_scatter<C><<<g, 256, 0, st>>>(d_prob);
   pm_launch_count_add(1);
 }
-template <typename C>
-void copy_batched(const CopyProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {
+template <typename S, typename D>
+void copy_batched(const CopyProb<S, D>* d_prob, int nprob, int max_elems, cudaStream_t st) {
   if (nprob <= 0 || max_elems <= 0) return;
   dim3 g((max_elems + 255) / 256, nprob);
-  k_copy<C><<<g, 256, 0, st>>>(d_prob);
+  k_copy<S, D><<<g, 256, 0, st>>>(d_prob);
   pm_launch_count_add(1);
 }
 
 template void cpqr_init_norms<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, cudaStream_t);
-template void cpqr_step<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, int, cudaStream_t);
+template void cpqr_step<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, int, int*, cudaStream_t);
 template void interp_solve<double2>(const InterpProb<double2>*, int, int, cudaStream_t);
 template void scatter_interp<double2>(const ScatterProb<double2>*, int, int, cudaStream_t);
-template void copy_batched<double2>(const CopyProb<double2>*, int, int, cudaStream_t);
+template void copy_batched<double2, double2>(const CopyProb<double2, double2>*, int, int, cudaStream_t);
+template void copy_batched<float2, float2>(const CopyProb<float2, float2>*, int, int, cudaStream_t);
+template void copy_batched<float2, double2>(const CopyProb<float2, double2>*, int, int, cudaStream_t);
+template void copy_batched<double2, float2>(const CopyProb<double2, float2>*, int, int, cudaStream_t);
+template void cpqr_init_norms<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, cudaStream_t);
+template void cpqr_step<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, int, int*, cudaStream_t);
+template void interp_solve<float2>(const InterpProb<float2>*, int, int, cudaStream_t);
+template void scatter_interp<float2>(const ScatterProb<float2>*, int, int, cudaStream_t);

@@ -36,21 +36,24 @@ struct ScatterProb {             // dense L (rows = box positions) or R (columns
   const C* T; int ldt;
 };
 
-template <typename C>
-struct CopyProb { const C* src; int lds; C* dst; int ldd; int m; int n; };
+template <typename S, typename D = S>
+struct CopyProb { const S* src; int lds; D* dst; int ldd; int m; int n; };
 
 struct PermFill { int* perm; int n; int done; };   // perm[done..n) <- unchosen columns, ascending
 
 void complete_perm(const PermFill* d_prob, int nprob, cudaStream_t st);
 template <typename C>
 void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, cudaStream_t st);
+// One elimination step (launch index t) of every active matrix; d_counter:
+// a zeroed int, distinct for every launch (chunk dispenser).
 template <typename C>
-void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, cudaStream_t st);
+void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
+               cudaStream_t st);
 template <typename C>
 void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st);
 template <typename C>
 void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st);
-template <typename C>
-void copy_batched(const CopyProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st);
+template <typename S, typename D>
+void copy_batched(const CopyProb<S, D>* d_prob, int nprob, int max_elems, cudaStream_t st);
 
-constexpr int CPQR_CB = 32;      // columns per chunk
+constexpr int CPQR_CB = 16;      // columns per chunk

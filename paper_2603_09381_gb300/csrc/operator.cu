@@ -1,0 +1,192 @@
+// FP64 operator application for iterative refinement (mixed precision).
+//
+// Every target node accumulates the exterior-kernel contributions of every
+// source node on another inclusion, for all right-hand sides at once:
+//   y[u_t] += (-eps+ S w) x[q_s] + (D w) x[u_s]
+//   y[q_t] += (-D* w)     x[q_s] + (N/eps+ w) x[u_s]
+// (paper Sec. 2.2, off-diagonal blocks of eq. pmchwt_omit_bie).  Sources are
+// staged through shared memory in tiles of 64; the grid splits the sources
+// into segments whose partial sums meet in FP64 atomics.  One J0/Y0/J1/Y1
+// quadruple per node pair serves all four kernels and all right-hand sides,
+// so the kernel is bound by the FP64 pipe (Bessel evaluation + 32 complex
+// FMAs per pair at 8 right-hand sides).
+#include "operator.cuh"
+#include "prof.cuh"
+#include <algorithm>
+
+namespace {
+
+constexpr int OP_T = 128;   // targets per CTA
+constexpr int OP_S = 64;    // sources per shared-memory tile
+
+template <int NR>
+__global__ void __launch_bounds__(OP_T) k_apply_offdiag(OpNodes nd, int total, double k, const double2* __restrict__ X,
+                                                        int ldx, double2* __restrict__ Y, int ldy, int seg_len) {
+  __shared__ double sx[OP_S], sy[OP_S], snx[OP_S], sny[OP_S], sw[OP_S];
+  __shared__ int sinc[OP_S];
+  __shared__ double2 sxq[NR][OP_S], sxu[NR][OP_S];
+  const int t = blockIdx.x * OP_T + threadIdx.x;
+  const bool active = t < total;
+  double tx = 0, ty = 0, tnx = 0, tny = 0;
+  int tinc = -1;
+  if (active) { tx = nd.x[t]; ty = nd.y[t]; tnx = nd.nx[t]; tny = nd.ny[t]; tinc = nd.incl[t]; }
+  double2 au[NR], aq[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) { au[r] = make_double2(0, 0); aq[r] = make_double2(0, 0); }
+  const int s0 = blockIdx.y * seg_len;
+  const int s1 = min(total, s0 + seg_len);
+  for (int base = s0; base < s1; base += OP_S) {
+    __syncthreads();
+    const int ls = threadIdx.x;
+    if (ls < OP_S) {
+      const int s = base + ls;
+      if (s < s1) {
+        sx[ls] = nd.x[s]; sy[ls] = nd.y[s]; snx[ls] = nd.nx[s]; sny[ls] = nd.ny[s]; sw[ls] = nd.w[s];
+        sinc[ls] = nd.incl[s];
+        const int iq = nd.iu[s], iu = nd.iq[s];   // q density sits at the u-equation index, u density at the q index
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { sxq[r][ls] = X[iq + (size_t)r * ldx]; sxu[r][ls] = X[iu + (size_t)r * ldx]; }
+      } else {
+        sinc[ls] = -2;
+      }
+    }
+    __syncthreads();
+    if (!active) continue;
+    const int cnt = min(OP_S, s1 - base);
+    for (int j = 0; j < cnt; ++j) {
+      if (sinc[j] == tinc) continue;
+      const double dx = tx - sx[j], dy = ty - sy[j];
+      const double r = sqrt(dx * dx + dy * dy);
+      const double z = k * r;
+      const double J0 = j0(z), Y0 = y0(z), J1 = j1(z), Y1 = y1(z);
+      const double w = sw[j];
+      const double a = (tnx * dx + tny * dy) / r, b = (snx[j] * dx + sny[j] * dy) / r;
+      const double nn = tnx * snx[j] + tny * sny[j];
+      const double f = 0.25 * k * w;
+      const double2 S = make_double2(0.25 * Y0 * w, -0.25 * J0 * w);          // -eps+ S w
+      const double2 D = make_double2(-Y1 * b * f, J1 * b * f);                // D w
+      const double2 T = make_double2(-Y1 * a * f, J1 * a * f);                // -D* w
+      const double c0 = k * a * b, c1 = (nn - 2 * a * b) / r;
+      const double2 Nk = make_double2(-(c0 * Y0 + c1 * Y1) * f, (c0 * J0 + c1 * J1) * f);  // N/eps+ w
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const double2 xq = sxq[q][j], xu = sxu[q][j];
+        cfma(au[q], S, xq); cfma(au[q], D, xu);
+        cfma(aq[q], T, xq); cfma(aq[q], Nk, xu);
+      }
+    }
+  }
+  if (!active) return;
+  const int ru = nd.iu[t], rq = nd.iq[t];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    double2* yu = Y + ru + (size_t)q * ldy;
+    double2* yq = Y + rq + (size_t)q * ldy;
+    atomicAdd(&yu->x, au[q].x); atomicAdd(&yu->y, au[q].y);
+    atomicAdd(&yq->x, aq[q].x); atomicAdd(&yq->y, aq[q].y);
+  }
+}
+
+__global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,
+                           double* norms2) {
+  const int r = blockIdx.y;
+  double sr = 0, sb = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double2 b = B[i + (size_t)r * N], y = Y[i + (size_t)r * N];
+    const double2 v = make_double2(b.x - y.x, b.y - y.y);
+    R[i + (size_t)r * N] = v;
+    sr += v.x * v.x + v.y * v.y;
+    sb += b.x * b.x + b.y * b.y;
+  }
+  sr = warp_sum(sr); sb = warp_sum(sb);
+  if ((threadIdx.x & 31) == 0) { atomicAdd(&norms2[2 * r], sr); atomicAdd(&norms2[2 * r + 1], sb); }
+}
+
+__global__ void k_scale_to32(const double2* __restrict__ src, float2* __restrict__ dst, int N, const double* scale) {
+  const int r = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double s = scale[r];
+  const double2 v = src[i + (size_t)r * N];
+  dst[i + (size_t)r * N] = make_float2((float)(v.x * s), (float)(v.y * s));
+}
+
+__global__ void k_axpy_from32(double2* __restrict__ x, const float2* __restrict__ d, int N, const double* scale) {
+  const int r = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double s = scale[r];
+  const float2 v = d[i + (size_t)r * N];
+  double2& o = x[i + (size_t)r * N];
+  o.x += s * (double)v.x;
+  o.y += s * (double)v.y;
+}
+
+__global__ void k_axpy64(double2* __restrict__ X, const double2* __restrict__ D, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  X[i].x += D[i].x;
+  X[i].y += D[i].y;
+}
+
+template <int NR>
+void launch_apply(OpNodes nd, int total, double k0, const double2* X, int ldx, double2* Y, int ldy, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = (total + OP_T - 1) / OP_T;
+  // enough CTAs for several per SM: split the sources into segments
+  int segs = std::max(1, std::min(64, (sms * 8 + tiles - 1) / tiles));
+  int seg_len = (total + segs - 1) / segs;
+  seg_len = ((seg_len + OP_S - 1) / OP_S) * OP_S;
+  segs = (total + seg_len - 1) / seg_len;
+  dim3 g(tiles, segs);
+  k_apply_offdiag<NR><<<g, OP_T, 0, st>>>(nd, total, k0, X, ldx, Y, ldy, seg_len);
+  pm_launch_count_add(1);
+}
+
+}  // namespace
+
+void apply_offdiag64(OpNodes nd, int total, double k0, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                     cudaStream_t st) {
+  if (total <= 0 || nrhs <= 0) return;
+  KPROF_BEGIN(st);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    const double2* Xr = X + (size_t)r0 * ldx;
+    double2* Yr = Y + (size_t)r0 * ldy;
+    if (left >= 8) { launch_apply<8>(nd, total, k0, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_apply<4>(nd, total, k0, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_apply<2>(nd, total, k0, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_apply<1>(nd, total, k0, Xr, ldx, Yr, ldy, st); r0 += 1; }
+  }
+  KPROF_END(st, "apply_offdiag64", 0.0);
+}
+
+void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  dim3 g(std::min(1024, (N + 255) / 256), nrhs);
+  k_residual<<<g, 256, 0, st>>>(B, Y, R, N, norms2);
+  pm_launch_count_add(1);
+}
+
+void scale_to32(const double2* src, float2* dst, int N, int nrhs, const double* scale, cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  dim3 g((N + 255) / 256, nrhs);
+  k_scale_to32<<<g, 256, 0, st>>>(src, dst, N, scale);
+  pm_launch_count_add(1);
+}
+
+void axpy_from32(double2* x, const float2* d, int N, int nrhs, const double* scale, cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  dim3 g((N + 255) / 256, nrhs);
+  k_axpy_from32<<<g, 256, 0, st>>>(x, d, N, scale);
+  pm_launch_count_add(1);
+}
+
+void axpy64(double2* X, const double2* D, int N, int nrhs, cudaStream_t st) {
+  const size_t n = (size_t)N * nrhs;
+  if (n == 0) return;
+  k_axpy64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, D, n);
+  pm_launch_count_add(1);
+}

@@ -1,0 +1,26 @@
+// FP64 application of the PMCHWT (Omit) operator on the fly, used as the
+// residual of iterative refinement in the mixed-precision mode, and small
+// vector kernels for the refinement loop.
+#pragma once
+#include <cuda_runtime.h>
+#include "pm_common.cuh"
+
+struct OpNodes {
+  const double *x, *y, *nx, *ny, *w;
+  const int* incl;   // owning inclusion
+  const int* iu;     // row of the node's u-equation = column of its q density
+  const int* iq;     // row of the node's q-equation = column of its u density
+};
+
+// Y[:, 0:nrhs] += A_offdiag X[:, 0:nrhs]  (trapezoid-rule exterior kernels between
+// different inclusions; same-inclusion pairs are skipped).
+void apply_offdiag64(OpNodes nd, int total_nodes, double k0, const double2* X, int ldx, double2* Y, int ldy,
+                     int nrhs, cudaStream_t st);
+// R = B - Y, and norms2[2 r] += |R[:, r]|^2, norms2[2 r + 1] += |B[:, r]|^2 (norms2 zeroed by caller)
+void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st);
+// dst[:, r] = scale[r] * src[:, r] (FP64 -> FP32)
+void scale_to32(const double2* src, float2* dst, int N, int nrhs, const double* scale, cudaStream_t st);
+// X += D (FP64, N x nrhs, contiguous columns)
+void axpy64(double2* X, const double2* D, int N, int nrhs, cudaStream_t st);
+// x[:, r] += scale[r] * d[:, r] (FP32 -> FP64)
+void axpy_from32(double2* x, const float2* d, int N, int nrhs, const double* scale, cudaStream_t st);

@@ -9,6 +9,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,7 @@
 #include "assemble.cuh"
 #include "cpqr.cuh"
 #include "dense_la.cuh"
+#include "operator.cuh"
 #include "prof.cuh"
 
 typedef double2 Cd;
@@ -82,11 +84,12 @@ T* upload(Arena& a, const std::vector<T>& v, cudaStream_t st) {
   return d;
 }
 
-__global__ void k_identity(Cd* A, int m, int ld) {
+template <class C>
+__global__ void k_identity(C* A, int m, int ld) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * m) return;
   int i = e % m, j = e / m;
-  A[i + (size_t)j * ld] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  A[i + (size_t)j * ld] = mk((typename real_of<C>::type)(i == j ? 1 : 0), (typename real_of<C>::type)0);
 }
 
 uint64_t morton(uint32_t x, uint32_t y) {
@@ -137,15 +140,28 @@ struct pm_geometry {
 
 namespace {
 
+template <class C>
 struct BoxF {
   std::vector<int> rows, rgrp, cols, cgrp;
   int mb = 0, kb = 0, kg[2] = {0, 0};
-  Cd *D = nullptr, *X = nullptr, *Rm = nullptr, *At = nullptr;
+  C *D = nullptr, *X = nullptr, *Rm = nullptr, *At = nullptr;
   int* ipiv = nullptr;
   std::vector<int> srows, scols;
   std::vector<int> srgrp, scgrp;
   std::vector<int> child_off;  // offsets of the children's blocks in rows/cols
 };
+
+typedef float2 Cf;
+
+template <class C> inline C cone();
+template <> inline double2 cone<double2>() { return make_double2(1, 0); }
+template <> inline float2 cone<float2>() { return make_float2(1, 0); }
+template <class C> inline C cmone();
+template <> inline double2 cmone<double2>() { return make_double2(-1, 0); }
+template <> inline float2 cmone<float2>() { return make_float2(-1, 0); }
+template <class C> inline C czero_h();
+template <> inline double2 czero_h<double2>() { return make_double2(0, 0); }
+template <> inline float2 czero_h<float2>() { return make_float2(0, 0); }
 
 }  // namespace
 
@@ -154,14 +170,24 @@ struct pm_factor {
   pm_factor_opts opts{};
   cudaStream_t st = nullptr;
   int L = 0;
-  std::vector<std::vector<BoxF>> lev;
-  BoxF root;
+  int precision = PM_FP64;
+  std::vector<std::vector<BoxF<double2>>> lev64;   // FP64 mode
+  std::vector<std::vector<BoxF<float2>>> lev32;    // mixed mode (FP32 factorization)
+  BoxF<double2> root;                              // top-level system, always FP64
   Arena arena, scratch;
   pm_stats stats{};
   std::vector<std::vector<Box>> tree;  // the geometry's quadtree with this factorization's proxies
   KProf prof;
   bool profiling = false;
+  // mixed mode: FP64 self blocks (operator for the refinement residual)
+  std::vector<double2*> self64;
+  int* d_iu = nullptr;
+  int* d_iq = nullptr;
 };
+
+template <class C> std::vector<std::vector<BoxF<C>>>& levels_of(pm_factor* F);
+template <> std::vector<std::vector<BoxF<double2>>>& levels_of<double2>(pm_factor* F) { return F->lev64; }
+template <> std::vector<std::vector<BoxF<float2>>>& levels_of<float2>(pm_factor* F) { return F->lev32; }
 
 namespace {
 
@@ -267,70 +293,71 @@ void upload_inclusions(pm_geometry* g) {
 }
 
 // Self blocks A_jj of the listed inclusions into A[i] (leading dims lda[i]).
-void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std::vector<Cd*>& A,
+template <class C>
+void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std::vector<C*>& A,
                    const std::vector<int>& lda, Arena& scr, cudaStream_t st) {
   const int m = (int)incl.size();
   if (m == 0) return;
   std::vector<InclDev> sub(m);
   int maxn = 0;
-  std::map<int, Cd*> dts;
-  std::vector<Cd*> Cm(m), DtS(m), E(m);
+  std::map<int, C*> dts;
+  std::vector<C*> Cm(m), DtS(m), E(m);
   for (int i = 0; i < m; ++i) {
     sub[i] = g->hinc[incl[i]];
     int n = sub[i].n;
     maxn = std::max(maxn, n);
-    Cm[i] = scr.get<Cd>((size_t)n * n);
-    DtS[i] = scr.get<Cd>((size_t)n * n);
-    E[i] = scr.get<Cd>((size_t)n * n);
+    Cm[i] = scr.get<C>((size_t)n * n);
+    DtS[i] = scr.get<C>((size_t)n * n);
+    E[i] = scr.get<C>((size_t)n * n);
     if (!dts.count(n)) {
-      Cd* d = scr.get<Cd>((size_t)n * n);
-      diff_matrices<Cd>(n, d, st);
+      C* d = scr.get<C>((size_t)n * n);
+      diff_matrices<C>(n, d, st);
       dts[n] = d;
     }
   }
   InclDev* d_sub = upload(scr, sub, st);
-  Cd** dA = upload(scr, A, st);
+  C** dA = upload(scr, A, st);
   int* dlda = upload(scr, lda, st);
-  Cd** dC = upload(scr, Cm, st);
-  Cd** dD = upload(scr, DtS, st);
-  self_pointwise<Cd>(d_sub, m, maxn, g->nodes, g->k0, dA, dlda, dC, st);
+  C** dC = upload(scr, Cm, st);
+  C** dD = upload(scr, DtS, st);
+  self_pointwise<C>(d_sub, m, maxn, g->nodes, g->k0, dA, dlda, dC, st);
   if (g_kprof) {
     double e = 0;
     for (auto& c : sub) e += (double)c.n * c.n;
     g_kprof->add_flops("self_pointwise", e);   // work unit: node pairs (two wavenumbers each)
   }
-  scaled_diff<Cd>(d_sub, m, maxn, g->nodes, dD, st);
+  scaled_diff<C>(d_sub, m, maxn, g->nodes, dD, st);
   CK(cudaGetLastError());
   // Maue: N-block += diag(1/|x'|) Dt (S0+/e+ + S0-/e-) Dt
-  std::vector<GemmDesc<Cd>> d1(m), d2(m);
+  std::vector<GemmDesc<C>> d1(m), d2(m);
   std::vector<int> off1(m + 1, 0), off2(m + 1, 0);
   for (int i = 0; i < m; ++i) {
     int n = sub[i].n;
-    d1[i] = GemmDesc<Cd>{n, n, n, Cm[i], n, dts[n], n, E[i], n, make_double2(1, 0), make_double2(0, 0), 1};
-    d2[i] = GemmDesc<Cd>{n, n, n, DtS[i], n, E[i], n, A[i] + n + (size_t)n * lda[i], lda[i], make_double2(1, 0),
-                         make_double2(1, 0), 0};
+    d1[i] = GemmDesc<C>{n, n, n, Cm[i], n, dts[n], n, E[i], n, cone<C>(), czero_h<C>(), 1};
+    d2[i] = GemmDesc<C>{n, n, n, DtS[i], n, E[i], n, A[i] + n + (size_t)n * lda[i], lda[i], cone<C>(), cone<C>(), 0};
     off1[i + 1] = off1[i] + gemm_tiles(n, n);
     off2[i + 1] = off2[i] + gemm_tiles(n, n);
   }
   auto* dd1 = upload(scr, d1, st); auto* do1 = upload(scr, off1, st);
-  la_gemm_batched<Cd>(dd1, do1, m, off1[m], st);
+  la_gemm_batched<C>(dd1, do1, m, off1[m], st);
   auto* dd2 = upload(scr, d2, st); auto* do2 = upload(scr, off2, st);
-  la_gemm_batched<Cd>(dd2, do2, m, off2[m], st);
+  la_gemm_batched<C>(dd2, do2, m, off2[m], st);
   CK(cudaGetLastError());
 }
 
+template <class C>
 struct GatherBatch {
-  std::vector<GatherProb<Cd>> probs;
+  std::vector<GatherProb<C>> probs;
   std::vector<int> tile_off{0};
   std::vector<int> codes;                 // all target / source lists
   std::vector<std::pair<size_t, size_t>> lists;  // (tgt offset, src offset) per prob
-  void add(Cd* out, int ld, int M, int N, const std::vector<int>& tgt, const std::vector<int>& src, int trans) {
+  void add(C* out, int ld, int M, int N, const std::vector<int>& tgt, const std::vector<int>& src, int trans) {
     if (M <= 0 || N <= 0) return;
     size_t to = codes.size();
     codes.insert(codes.end(), tgt.begin(), tgt.end());
     size_t so = codes.size();
     codes.insert(codes.end(), src.begin(), src.end());
-    probs.push_back(GatherProb<Cd>{out, ld, M, N, nullptr, nullptr, trans});
+    probs.push_back(GatherProb<C>{out, ld, M, N, nullptr, nullptr, trans});
     lists.push_back({to, so});
     tile_off.push_back(tile_off.back() + gather_tiles(M, N));
   }
@@ -343,7 +370,7 @@ struct GatherBatch {
     }
     auto* dp = upload(scr, probs, st);
     int* dt = upload(scr, tile_off, st);
-    gather_assemble<Cd>(dp, dt, (int)probs.size(), tile_off.back(), pts, k0, st);
+    gather_assemble<C>(dp, dt, (int)probs.size(), tile_off.back(), pts, k0, st);
     if (g_kprof) {
       double e = 0;
       for (auto& x : probs) e += (double)x.M * x.N;
@@ -353,23 +380,24 @@ struct GatherBatch {
   }
 };
 
+template <class C>
 struct GemmBatch {
-  std::vector<GemmDesc<Cd>> d;
+  std::vector<GemmDesc<C>> d;
   std::vector<int> off{0};
-  void add(int m, int n, int k, const Cd* A, int lda, const Cd* B, int ldb, Cd* C, int ldc, Cd alpha, Cd beta,
+  void add(int m, int n, int k, const C* A, int lda, const C* B, int ldb, C* Cp, int ldc, C alpha, C beta,
            int beta_zero) {
     if (m <= 0 || n <= 0) return;
     if (k <= 0) {
       if (beta_zero) k = 0; else return;
     }
-    d.push_back(GemmDesc<Cd>{m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, beta_zero});
+    d.push_back(GemmDesc<C>{m, n, k, A, lda, B, ldb, Cp, ldc, alpha, beta, beta_zero});
     off.push_back(off.back() + gemm_tiles(m, n));
   }
   void run(Arena& scr, cudaStream_t st) {
     if (d.empty()) return;
     auto* dd = upload(scr, d, st);
     int* dof = upload(scr, off, st);
-    la_gemm_batched<Cd>(dd, dof, (int)d.size(), off.back(), st);
+    la_gemm_batched<C>(dd, dof, (int)d.size(), off.back(), st);
     if (g_kprof) {
       double f = 0;
       for (auto& x : d) f += 8.0 * x.m * x.n * x.k;
@@ -379,23 +407,25 @@ struct GemmBatch {
   }
 };
 
+template <class S, class D = S>
 struct CopyBatch {
-  std::vector<CopyProb<Cd>> p;
+  std::vector<CopyProb<S, D>> p;
   int maxe = 0;
-  void add(const Cd* src, int lds, Cd* dst, int ldd, int m, int n) {
+  void add(const S* src, int lds, D* dst, int ldd, int m, int n) {
     if (m <= 0 || n <= 0) return;
-    p.push_back(CopyProb<Cd>{src, lds, dst, ldd, m, n});
+    p.push_back(CopyProb<S, D>{src, lds, dst, ldd, m, n});
     maxe = std::max(maxe, m * n);
   }
   void run(Arena& scr, cudaStream_t st) {
     if (p.empty()) return;
     auto* dp = upload(scr, p, st);
-    copy_batched<Cd>(dp, (int)p.size(), maxe, st);
+    copy_batched<S, D>(dp, (int)p.size(), maxe, st);
     CK(cudaGetLastError());
   }
 };
 
-void lu_batch(std::vector<LuProb<Cd>>& probs, Arena& scr, cudaStream_t st, const char* what) {
+template <class C>
+void lu_batch(std::vector<LuProb<C>>& probs, Arena& scr, cudaStream_t st, const char* what) {
   if (probs.empty()) return;
   int n = (int)probs.size();
   int* info = scr.get<int>(n);
@@ -405,7 +435,7 @@ void lu_batch(std::vector<LuProb<Cd>>& probs, Arena& scr, cudaStream_t st, const
   auto* dp = upload(scr, probs, st);
   std::vector<int> hm(n);
   for (int i = 0; i < n; ++i) hm[i] = probs[i].m;
-  la_getrf_batched<Cd>(dp, n, maxm, hm.data(), st);
+  la_getrf_batched<C>(dp, n, maxm, hm.data(), st);
   CK(cudaGetLastError());
   std::vector<int> h(n);
   CK(cudaMemcpyAsync(h.data(), info, n * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -414,7 +444,8 @@ void lu_batch(std::vector<LuProb<Cd>>& probs, Arena& scr, cudaStream_t st, const
     if (h[i] != 0) fail(PM_ERR_SINGULAR, std::string(what) + ": exactly singular pivot in LU");
 }
 
-void solve_batch(std::vector<SolveProb<Cd>>& probs, Arena& scr, cudaStream_t st) {
+template <class C>
+void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st) {
   if (probs.empty()) return;
   int maxm = 0, maxr = 0;
   std::vector<int> hm, hr;
@@ -423,7 +454,7 @@ void solve_batch(std::vector<SolveProb<Cd>>& probs, Arena& scr, cudaStream_t st)
     hm.push_back(p.m); hr.push_back(p.nrhs);
   }
   auto* dp = upload(scr, probs, st);
-  la_getrs_batched<Cd>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st);
+  la_getrs_batched<C>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st);
   CK(cudaGetLastError());
 }
 
@@ -442,27 +473,29 @@ struct Timer {
 };
 
 // Active sets and D_b of a parent (or the root) from its children's compressed blocks.
-void merge_children(pm_factor* F, int lev, const Box& box, BoxF& bf, GatherBatch& gb, CopyBatch& cb) {
-  auto& kids = F->lev[lev + 1];
+// Cc: the children's arithmetic, Cp: the parent's.
+template <class Cc, class Cp>
+void merge_children(pm_factor* F, const std::vector<BoxF<Cc>>& kids, const Box& box, BoxF<Cp>& bf,
+                    GatherBatch<Cp>& gb, CopyBatch<Cc, Cp>& cb) {
   bf.rows.clear(); bf.rgrp.clear(); bf.cols.clear(); bf.cgrp.clear(); bf.child_off.clear();
   for (int c : box.children) {
     bf.child_off.push_back((int)bf.rows.size());
-    const BoxF& k = kids[c];
+    const BoxF<Cc>& k = kids[c];
     bf.rows.insert(bf.rows.end(), k.srows.begin(), k.srows.end());
     bf.rgrp.insert(bf.rgrp.end(), k.srgrp.begin(), k.srgrp.end());
     bf.cols.insert(bf.cols.end(), k.scols.begin(), k.scols.end());
     bf.cgrp.insert(bf.cgrp.end(), k.scgrp.begin(), k.scgrp.end());
   }
   bf.mb = (int)bf.rows.size();
-  bf.D = F->arena.get<Cd>((size_t)std::max(bf.mb, 1) * std::max(bf.mb, 1));
+  bf.D = F->arena.get<Cp>((size_t)std::max(bf.mb, 1) * std::max(bf.mb, 1));
   const pm_geometry* g = F->g;
   for (size_t a = 0; a < box.children.size(); ++a) {
-    const BoxF& ka = kids[box.children[a]];
+    const BoxF<Cc>& ka = kids[box.children[a]];
     std::vector<int> tcodes(ka.srows.size());
     for (size_t i = 0; i < ka.srows.size(); ++i) tcodes[i] = g->code_of(ka.srows[i]);
     for (size_t b = 0; b < box.children.size(); ++b) {
-      const BoxF& kb = kids[box.children[b]];
-      Cd* dst = bf.D + bf.child_off[a] + (size_t)bf.child_off[b] * bf.mb;
+      const BoxF<Cc>& kb = kids[box.children[b]];
+      Cp* dst = bf.D + bf.child_off[a] + (size_t)bf.child_off[b] * bf.mb;
       if (a == b) {
         cb.add(ka.At, ka.kb, dst, bf.mb, ka.kb, ka.kb);
       } else {
@@ -495,37 +528,39 @@ PointsDev make_points(const pm_geometry* g, const std::vector<Box>& boxes, Arena
   return P;
 }
 
-void process_level(pm_factor* F, int lev) {
+template <class C>
+void process_level(pm_factor* F, int lev, double tol) {
   const pm_geometry* g = F->g;
   cudaStream_t st = F->st;
   Arena& scr = F->scratch;
   scr.reset();
   const auto& boxes = F->tree[lev];
-  auto& BF = F->lev[lev];
+  auto& LV = levels_of<C>(F);
+  auto& BF = LV[lev];
   const int nb = (int)boxes.size();
-  BF.assign(nb, BoxF());
+  BF.assign(nb, BoxF<C>());
   Timer t_asm(st);
   // 1. active sets and diagonal blocks
   if (lev == F->L) {
     std::vector<int> incl(nb), lda(nb);
-    std::vector<Cd*> A(nb);
+    std::vector<C*> A(nb);
     for (int b = 0; b < nb; ++b) {
       int j = boxes[b].leaves[0];
       int n = g->inc[j].n_nodes;
-      BoxF& bf = BF[b];
+      BoxF<C>& bf = BF[b];
       bf.mb = 2 * n;
       for (int i = 0; i < 2 * n; ++i) {
         bf.rows.push_back(g->row_off[j] + i);
         bf.rgrp.push_back(i >= n);
       }
       bf.cols = bf.rows; bf.cgrp = bf.rgrp;
-      bf.D = F->arena.get<Cd>((size_t)bf.mb * bf.mb);
+      bf.D = F->arena.get<C>((size_t)bf.mb * bf.mb);
       incl[b] = j; A[b] = bf.D; lda[b] = bf.mb;
     }
-    assemble_self(g, incl, A, lda, scr, st);
+    assemble_self<C>(g, incl, A, lda, scr, st);
   } else {
-    GatherBatch gb; CopyBatch cb;
-    for (int b = 0; b < nb; ++b) merge_children(F, lev, boxes[b], BF[b], gb, cb);
+    GatherBatch<C> gb; CopyBatch<C, C> cb;
+    for (int b = 0; b < nb; ++b) merge_children<C, C>(F, LV[lev + 1], boxes[b], BF[b], gb, cb);
     std::vector<int> dummy;
     PointsDev P0 = make_points(g, {}, scr, st, dummy);
     gb.run(scr, P0, g->k0, st);
@@ -536,12 +571,12 @@ void process_level(pm_factor* F, int lev) {
   PointsDev P = make_points(g, boxes, scr, st, poff);
   const int nid = 4 * nb;
   std::vector<int> W(nid), nn(nid);
-  std::vector<Cd*> Z(nid);
+  std::vector<C*> Z(nid);
   std::vector<std::vector<int>> pos(nid);
-  GatherBatch gb;
+  GatherBatch<C> gb;
   for (int b = 0; b < nb; ++b) {
     const Box& box = boxes[b];
-    const BoxF& bf = BF[b];
+    const BoxF<C>& bf = BF[b];
     std::vector<int> ncols, nrows;
     for (int o : box.near) {
       for (int c : BF[o].cols) ncols.push_back(g->code_of(c));
@@ -559,7 +594,7 @@ void process_level(pm_factor* F, int lev) {
       std::vector<int> src = ncols;
       src.insert(src.end(), pcols.begin(), pcols.end());
       W[id] = (int)src.size(); nn[id] = (int)tgt.size();
-      Z[id] = scr.get<Cd>((size_t)W[id] * std::max(nn[id], 1));
+      Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
       gb.add(Z[id], W[id], W[id], nn[id], tgt, src, 1);
       // column ID of group grp: Z[w, c] = A(target w, column c), targets = near rows + proxy
       id = 4 * b + 2 + grp;
@@ -568,7 +603,7 @@ void process_level(pm_factor* F, int lev) {
       std::vector<int> tg = nrows;
       tg.insert(tg.end(), prows.begin(), prows.end());
       W[id] = (int)tg.size(); nn[id] = (int)srcc.size();
-      Z[id] = scr.get<Cd>((size_t)W[id] * std::max(nn[id], 1));
+      Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
       gb.add(Z[id], W[id], W[id], nn[id], tg, srcc, 0);
     }
   }
@@ -582,28 +617,32 @@ void process_level(pm_factor* F, int lev) {
   total_n = noff[nid];
   double* norm2 = scr.get<double>(2 * (size_t)std::max(total_n, 1));
   int* perm = scr.get<int>(std::max(total_n, 1));
-  Cd* rdiag = scr.get<Cd>(std::max(total_n, 1));
+  C* rdiag = scr.get<C>(std::max(total_n, 1));
   int* rank = scr.get<int>(nid);
   double* ref = scr.get<double>(nid);
   CK(cudaMemsetAsync(rank, 0xff, nid * sizeof(int), st));
   CK(cudaMemsetAsync(perm, 0, std::max(total_n, 1) * sizeof(int), st));
-  std::vector<CpqrProb<Cd>> cp(nid);
+  std::vector<CpqrProb<C>> cp(nid);
   std::vector<CpqrChunk> chunks;
   int maxT = 0;
   for (int i = 0; i < nid; ++i) {
     int tgt = std::min(W[i], nn[i]);
-    cp[i] = CpqrProb<Cd>{Z[i], W[i], W[i], nn[i], F->opts.tol, CPQR_FIND_RANK, 0, tgt,
-                         norm2 + 2 * (size_t)noff[i], perm + noff[i], rdiag + noff[i], rank + i, ref + i};
+    cp[i] = CpqrProb<C>{Z[i], W[i], W[i], nn[i], tol, CPQR_FIND_RANK, 0, tgt,
+                        norm2 + 2 * (size_t)noff[i], perm + noff[i], rdiag + noff[i], rank + i, ref + i};
     maxT = std::max(maxT, tgt);
     for (int c0 = 0; c0 < nn[i]; c0 += CPQR_CB) chunks.push_back(CpqrChunk{i, c0, std::min(c0 + CPQR_CB, nn[i]), c0 == 0});
   }
+  // tallest matrices first: their chunks carry the most work per step
+  std::stable_sort(chunks.begin(), chunks.end(), [&](const CpqrChunk& a, const CpqrChunk& b) { return W[a.id] > W[b.id]; });
+  int* ctr = scr.get<int>(2 * (size_t)maxT + 2);
+  CK(cudaMemsetAsync(ctr, 0, (2 * (size_t)maxT + 2) * sizeof(int), st));
   auto* dcp = upload(scr, cp, st);
   auto* dch = upload(scr, chunks, st);
   const int nch = (int)chunks.size();
-  cpqr_init_norms<Cd>(dcp, dch, nch, st);
+  cpqr_init_norms<C>(dcp, dch, nch, st);
   std::vector<int> hr(nid);
   for (int t = 0; t < maxT; ++t) {
-    cpqr_step<Cd>(dcp, dch, nch, t, st);
+    cpqr_step<C>(dcp, dch, nch, t, ctr + t, st);
     if ((t % 16 == 15) || t == maxT - 1) {
       CK(cudaMemcpyAsync(hr.data(), rank, nid * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -635,7 +674,7 @@ void process_level(pm_factor* F, int lev) {
   }
   if (maxExt > 0) {
     dcp = upload(scr, cp, st);
-    for (int t = 0; t < maxExt; ++t) cpqr_step<Cd>(dcp, dch, nch, t, st);
+    for (int t = 0; t < maxExt; ++t) cpqr_step<C>(dcp, dch, nch, t, ctr + maxT + t, st);
     CK(cudaGetLastError());
   }
   {
@@ -663,37 +702,37 @@ void process_level(pm_factor* F, int lev) {
   CK(cudaMemcpyAsync(hperm.data(), perm, std::max(total_n, 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   // 5. interpolation matrices T = R11^{-1} R12
-  std::vector<InterpProb<Cd>> ip;
-  std::vector<Cd*> T(nid, nullptr);
+  std::vector<InterpProb<C>> ip;
+  std::vector<C*> T(nid, nullptr);
   int maxcols = 0;
   for (int i = 0; i < nid; ++i) {
     int k = kk[i], n = nn[i];
     if (k <= 0 || n - k <= 0) continue;
-    T[i] = scr.get<Cd>((size_t)k * (n - k));
-    ip.push_back(InterpProb<Cd>{Z[i], W[i], n, k, perm + noff[i], rdiag + noff[i], T[i], k});
+    T[i] = scr.get<C>((size_t)k * (n - k));
+    ip.push_back(InterpProb<C>{Z[i], W[i], n, k, perm + noff[i], rdiag + noff[i], T[i], k});
     maxcols = std::max(maxcols, n - k);
   }
   if (!ip.empty()) {
     auto* dip = upload(scr, ip, st);
-    interp_solve<Cd>(dip, (int)ip.size(), maxcols, st);
+    interp_solve<C>(dip, (int)ip.size(), maxcols, st);
     CK(cudaGetLastError());
   }
   F->stats.ms_id += t_id.stop();
   Timer t_sc(st);
   // 6. skeleton lists, L (into X) and R
-  std::vector<ScatterProb<Cd>> sp;
+  std::vector<ScatterProb<C>> sp;
   std::vector<int> posall;
-  std::vector<std::pair<size_t, size_t>> posref;  // (offset into posall) per scatter
+  std::vector<size_t> posref;
   int maxe = 0;
   for (int b = 0; b < nb; ++b) {
-    BoxF& bf = BF[b];
+    BoxF<C>& bf = BF[b];
     bf.kb = bf.kg[0] + bf.kg[1];
-    bf.X = F->arena.get<Cd>((size_t)std::max(bf.mb, 1) * std::max(bf.kb, 1));
-    bf.Rm = F->arena.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.mb, 1));
-    bf.At = F->arena.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
+    bf.X = F->arena.get<C>((size_t)std::max(bf.mb, 1) * std::max(bf.kb, 1));
+    bf.Rm = F->arena.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.mb, 1));
+    bf.At = F->arena.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
     bf.ipiv = F->arena.get<int>(std::max(bf.mb, 1));
-    CK(cudaMemsetAsync(bf.X, 0, sizeof(Cd) * (size_t)bf.mb * bf.kb, st));
-    CK(cudaMemsetAsync(bf.Rm, 0, sizeof(Cd) * (size_t)bf.mb * bf.kb, st));
+    CK(cudaMemsetAsync(bf.X, 0, sizeof(C) * (size_t)bf.mb * bf.kb, st));
+    CK(cudaMemsetAsync(bf.Rm, 0, sizeof(C) * (size_t)bf.mb * bf.kb, st));
     int off = 0;
     for (int grp = 0; grp < 2; ++grp) {
       int k = bf.kg[grp];
@@ -708,10 +747,10 @@ void process_level(pm_factor* F, int lev) {
         int id = side == 0 ? ir : ic;
         size_t po = posall.size();
         posall.insert(posall.end(), pos[id].begin(), pos[id].end());
-        ScatterProb<Cd> s{side == 0 ? bf.X : bf.Rm, side == 0 ? bf.mb : bf.kb, off, side == 0,
+        ScatterProb<C> sc{side == 0 ? bf.X : bf.Rm, side == 0 ? bf.mb : bf.kb, off, side == 0,
                           nullptr, perm + noff[id], k, nn[id], T[id], k};
-        sp.push_back(s);
-        posref.push_back({po, 0});
+        sp.push_back(sc);
+        posref.push_back(po);
         maxe = std::max(maxe, k * nn[id]);
       }
       off += k;
@@ -719,174 +758,310 @@ void process_level(pm_factor* F, int lev) {
   }
   if (!sp.empty()) {
     int* dpos = upload(scr, posall, st);
-    for (size_t i = 0; i < sp.size(); ++i) sp[i].pos = dpos + posref[i].first;
+    for (size_t i = 0; i < sp.size(); ++i) sp[i].pos = dpos + posref[i];
     auto* dsp = upload(scr, sp, st);
-    scatter_interp<Cd>(dsp, (int)sp.size(), maxe, st);
+    scatter_interp<C>(dsp, (int)sp.size(), maxe, st);
     CK(cudaGetLastError());
   }
   // 7. LU of D_b, X = D_b^{-1} L_b, Y = R_b X, A~_b = Y^{-1}
-  std::vector<LuProb<Cd>> lu;
-  for (int b = 0; b < nb; ++b) lu.push_back(LuProb<Cd>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, nullptr});
-  lu_batch(lu, scr, st, "diagonal block");
-  std::vector<SolveProb<Cd>> sv;
-  for (int b = 0; b < nb; ++b) sv.push_back(SolveProb<Cd>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, BF[b].X, BF[b].mb, BF[b].kb});
-  solve_batch(sv, scr, st);
-  GemmBatch gy;
-  std::vector<Cd*> Y(nb);
+  std::vector<LuProb<C>> lu;
+  for (int b = 0; b < nb; ++b) lu.push_back(LuProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, nullptr});
+  lu_batch<C>(lu, scr, st, "diagonal block");
+  std::vector<SolveProb<C>> sv;
+  for (int b = 0; b < nb; ++b) sv.push_back(SolveProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, BF[b].X, BF[b].mb, BF[b].kb});
+  solve_batch<C>(sv, scr, st);
+  GemmBatch<C> gy;
+  std::vector<C*> Y(nb);
   std::vector<int*> ypiv(nb);
+  std::vector<CopyProb<C, C>> idp;
   for (int b = 0; b < nb; ++b) {
-    BoxF& bf = BF[b];
-    Y[b] = scr.get<Cd>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
+    BoxF<C>& bf = BF[b];
+    Y[b] = scr.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
     ypiv[b] = scr.get<int>(std::max(bf.kb, 1));
-    gy.add(bf.kb, bf.kb, bf.mb, bf.Rm, bf.kb, bf.X, bf.mb, Y[b], bf.kb, make_double2(1, 0), make_double2(0, 0), 1);
+    gy.add(bf.kb, bf.kb, bf.mb, bf.Rm, bf.kb, bf.X, bf.mb, Y[b], bf.kb, cone<C>(), czero_h<C>(), 1);
     if (bf.kb > 0) {
-      k_identity<<<(bf.kb * bf.kb + 255) / 256, 256, 0, st>>>(bf.At, bf.kb, bf.kb);
+      k_identity<C><<<(bf.kb * bf.kb + 255) / 256, 256, 0, st>>>(bf.At, bf.kb, bf.kb);
       pm_launch_count_add(1);
     }
   }
   gy.run(scr, st);
-  std::vector<LuProb<Cd>> luy;
-  std::vector<SolveProb<Cd>> svy;
+  std::vector<LuProb<C>> luy;
+  std::vector<SolveProb<C>> svy;
   for (int b = 0; b < nb; ++b) {
     if (BF[b].kb <= 0) continue;
-    luy.push_back(LuProb<Cd>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], nullptr});
-    svy.push_back(SolveProb<Cd>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], BF[b].At, BF[b].kb, BF[b].kb});
+    luy.push_back(LuProb<C>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], nullptr});
+    svy.push_back(SolveProb<C>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], BF[b].At, BF[b].kb, BF[b].kb});
   }
-  lu_batch(luy, scr, st, "R A^-1 L (compressed block)");
-  solve_batch(svy, scr, st);
+  lu_batch<C>(luy, scr, st, "R A^-1 L (compressed block)");
+  solve_batch<C>(svy, scr, st);
   F->stats.ms_schur += t_sc.stop();
   int sk = 0;
   for (auto& bf : BF) sk += bf.kb;
   if (lev < 16) F->stats.skeleton[lev] = sk;
 }
 
+// Top-level system in FP64 from the level-1 boxes (arithmetic Cc), or the
+// single inclusion's self block.
+template <class Cc>
 void factor_top(pm_factor* F) {
   const pm_geometry* g = F->g;
   cudaStream_t st = F->st;
   Arena& scr = F->scratch;
   scr.reset();
   Timer t(st);
-  BoxF& rt = F->root;
+  BoxF<double2>& rt = F->root;
   if (F->L == 0) {
     int j = F->tree[0][0].leaves[0];
     int n = g->inc[j].n_nodes;
     rt.mb = 2 * n;
     for (int i = 0; i < 2 * n; ++i) { rt.rows.push_back(g->row_off[j] + i); rt.rgrp.push_back(i >= n); }
     rt.cols = rt.rows; rt.cgrp = rt.rgrp;
-    rt.D = F->arena.get<Cd>((size_t)rt.mb * rt.mb);
-    assemble_self(g, {j}, {rt.D}, {rt.mb}, scr, st);
+    rt.D = F->arena.get<double2>((size_t)rt.mb * rt.mb);
+    assemble_self<double2>(g, {j}, {rt.D}, {rt.mb}, scr, st);
   } else {
-    GatherBatch gb; CopyBatch cb;
-    merge_children(F, 0, F->tree[0][0], rt, gb, cb);
+    GatherBatch<double2> gb; CopyBatch<Cc, double2> cb;
+    merge_children<Cc, double2>(F, levels_of<Cc>(F)[1], F->tree[0][0], rt, gb, cb);
     std::vector<int> dummy;
     PointsDev P0 = make_points(g, {}, scr, st, dummy);
     gb.run(scr, P0, g->k0, st);
     cb.run(scr, st);
   }
   rt.ipiv = F->arena.get<int>(std::max(rt.mb, 1));
-  std::vector<LuProb<Cd>> lu{LuProb<Cd>{rt.D, rt.mb, rt.mb, rt.ipiv, nullptr}};
-  lu_batch(lu, scr, st, "top-level system");
+  std::vector<LuProb<double2>> lu{LuProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, nullptr}};
+  lu_batch<double2>(lu, scr, st, "top-level system");
   F->stats.K = rt.mb;
   F->stats.ms_top += t.stop();
 }
 
-}  // namespace
-
 // ---------------------------------------------------------------------------------
 // Solve (paper Sec. 3): upward RHS compression, top solve, downward recovery.
-namespace {
+// C is the arithmetic of the compressed levels; the top system is FP64.
+template <class C>
+struct SolveWork {
+  std::vector<std::vector<C*>> fin, ft;   // per level and box: f_b (-> g_b -> x_b), f~_b
+  double2* froot = nullptr;
+};
 
-void solve_device(const pm_factor* Fc, const Cd* rhs, int nrhs, Cd* phi, Arena& ws, cudaStream_t st) {
-  pm_factor* F = const_cast<pm_factor*>(Fc);
+template <class C>
+void solve_up(pm_factor* F, const C* rhs, int nrhs, SolveWork<C>& w, Arena& ws, cudaStream_t st) {
   const pm_geometry* g = F->g;
   const int N = g->N;
   const int L = F->L;
-  if (L == 0) {
-    CopyBatch cb;
-    cb.add(rhs, N, phi, N, N, nrhs);
-    cb.run(ws, st);
-    std::vector<SolveProb<Cd>> sv{SolveProb<Cd>{F->root.D, F->root.mb, F->root.mb, F->root.ipiv, phi, N, nrhs}};
-    solve_batch(sv, ws, st);
-    return;
-  }
-  // per-level buffers: fin (m_b x nrhs, becomes g_b then x_b), ft (k_b x nrhs)
-  std::vector<std::vector<Cd*>> fin(L + 1), ft(L + 1);
+  auto& LV = levels_of<C>(F);
+  w.fin.assign(L + 1, {}); w.ft.assign(L + 1, {});
   for (int l = 1; l <= L; ++l) {
-    auto& BF = F->lev[l];
-    fin[l].resize(BF.size()); ft[l].resize(BF.size());
+    auto& BF = LV[l];
+    w.fin[l].resize(BF.size()); w.ft[l].resize(BF.size());
     for (size_t b = 0; b < BF.size(); ++b) {
-      fin[l][b] = ws.get<Cd>((size_t)std::max(BF[b].mb, 1) * nrhs);
-      ft[l][b] = ws.get<Cd>((size_t)std::max(BF[b].kb, 1) * nrhs);
+      w.fin[l][b] = ws.get<C>((size_t)std::max(BF[b].mb, 1) * nrhs);
+      w.ft[l][b] = ws.get<C>((size_t)std::max(BF[b].kb, 1) * nrhs);
     }
   }
-  BoxF& rt = F->root;
-  Cd* froot = ws.get<Cd>((size_t)std::max(rt.mb, 1) * nrhs);
-  const Cd one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
-  // leaves: gather the right-hand side (contiguous per inclusion)
+  BoxF<double2>& rt = F->root;
+  w.froot = ws.get<double2>((size_t)std::max(rt.mb, 1) * nrhs);
   {
-    CopyBatch cb;
-    auto& BF = F->lev[L];
-    for (size_t b = 0; b < BF.size(); ++b) cb.add(rhs + BF[b].rows[0], N, fin[L][b], BF[b].mb, BF[b].mb, nrhs);
+    CopyBatch<C, C> cb;
+    auto& BF = LV[L];
+    for (size_t b = 0; b < BF.size(); ++b) cb.add(rhs + BF[b].rows[0], N, w.fin[L][b], BF[b].mb, BF[b].mb, nrhs);
     cb.run(ws, st);
   }
   for (int l = L; l >= 1; --l) {
-    auto& BF = F->lev[l];
-    const auto& boxes = F->tree[l];
-    std::vector<SolveProb<Cd>> sv;
+    auto& BF = LV[l];
+    std::vector<SolveProb<C>> sv;
     for (size_t b = 0; b < BF.size(); ++b)
-      sv.push_back(SolveProb<Cd>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, fin[l][b], BF[b].mb, nrhs});
-    solve_batch(sv, ws, st);  // g_b = D_b^{-1} f_b
-    Cd* tmp = ws.get<Cd>(1);
-    (void)tmp;
-    std::vector<Cd*> t(BF.size());
-    GemmBatch g1, g2;
+      sv.push_back(SolveProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, w.fin[l][b], BF[b].mb, nrhs});
+    solve_batch<C>(sv, ws, st);  // g_b = D_b^{-1} f_b
+    std::vector<C*> t(BF.size());
+    GemmBatch<C> g1, g2;
     for (size_t b = 0; b < BF.size(); ++b) {
-      t[b] = ws.get<Cd>((size_t)std::max(BF[b].kb, 1) * nrhs);
-      g1.add(BF[b].kb, nrhs, BF[b].mb, BF[b].Rm, BF[b].kb, fin[l][b], BF[b].mb, t[b], BF[b].kb, one, zero, 1);
-      g2.add(BF[b].kb, nrhs, BF[b].kb, BF[b].At, BF[b].kb, t[b], BF[b].kb, ft[l][b], BF[b].kb, one, zero, 1);
+      t[b] = ws.get<C>((size_t)std::max(BF[b].kb, 1) * nrhs);
+      g1.add(BF[b].kb, nrhs, BF[b].mb, BF[b].Rm, BF[b].kb, w.fin[l][b], BF[b].mb, t[b], BF[b].kb, cone<C>(),
+             czero_h<C>(), 1);
+      g2.add(BF[b].kb, nrhs, BF[b].kb, BF[b].At, BF[b].kb, t[b], BF[b].kb, w.ft[l][b], BF[b].kb, cone<C>(),
+             czero_h<C>(), 1);
     }
     g1.run(ws, st);
     g2.run(ws, st);
     // f~ of every child into its parent's right-hand side
-    CopyBatch cb;
     const auto& parents = F->tree[l - 1];
-    for (size_t pidx = 0; pidx < parents.size(); ++pidx) {
-      const BoxF& pb = (l - 1 == 0) ? F->root : F->lev[l - 1][pidx];
-      Cd* pf = (l - 1 == 0) ? froot : fin[l - 1][pidx];
-      for (size_t a = 0; a < parents[pidx].children.size(); ++a) {
-        int c = parents[pidx].children[a];
-        cb.add(ft[l][c], BF[c].kb, pf + pb.child_off[a], pb.mb, BF[c].kb, nrhs);
+    if (l - 1 == 0) {
+      CopyBatch<C, double2> cb;
+      for (size_t a = 0; a < parents[0].children.size(); ++a) {
+        int c = parents[0].children[a];
+        cb.add(w.ft[l][c], BF[c].kb, w.froot + rt.child_off[a], rt.mb, BF[c].kb, nrhs);
       }
+      cb.run(ws, st);
+    } else {
+      CopyBatch<C, C> cb;
+      for (size_t pidx = 0; pidx < parents.size(); ++pidx) {
+        const BoxF<C>& pb = LV[l - 1][pidx];
+        for (size_t a = 0; a < parents[pidx].children.size(); ++a) {
+          int c = parents[pidx].children[a];
+          cb.add(w.ft[l][c], BF[c].kb, w.fin[l - 1][pidx] + pb.child_off[a], pb.mb, BF[c].kb, nrhs);
+        }
+      }
+      cb.run(ws, st);
     }
-    cb.run(ws, st);
-    (void)boxes;
   }
-  {
-    std::vector<SolveProb<Cd>> sv{SolveProb<Cd>{rt.D, rt.mb, rt.mb, rt.ipiv, froot, rt.mb, nrhs}};
-    solve_batch(sv, ws, st);
+}
+
+template <class C>
+void solve_down(pm_factor* F, int nrhs, SolveWork<C>& w, C* phi, Arena& ws, cudaStream_t st) {
+  const pm_geometry* g = F->g;
+  const int N = g->N;
+  const int L = F->L;
+  auto& LV = levels_of<C>(F);
+  BoxF<double2>& rt = F->root;
+  C* xroot = nullptr;
+  if (std::is_same<C, double2>::value) {
+    xroot = (C*)w.froot;
+  } else {
+    xroot = ws.get<C>((size_t)std::max(rt.mb, 1) * nrhs);
+    CopyBatch<double2, C> cb;
+    cb.add(w.froot, rt.mb, xroot, rt.mb, rt.mb, nrhs);
+    cb.run(ws, st);
   }
   for (int l = 1; l <= L; ++l) {
-    auto& BF = F->lev[l];
+    auto& BF = LV[l];
     const auto& parents = F->tree[l - 1];
-    GemmBatch g1, g2;
+    GemmBatch<C> g1, g2;
     for (size_t pidx = 0; pidx < parents.size(); ++pidx) {
-      const BoxF& pb = (l - 1 == 0) ? F->root : F->lev[l - 1][pidx];
-      const Cd* px = (l - 1 == 0) ? froot : fin[l - 1][pidx];
+      const int pmb = (l - 1 == 0) ? rt.mb : LV[l - 1][pidx].mb;
+      const std::vector<int>& coff = (l - 1 == 0) ? rt.child_off : LV[l - 1][pidx].child_off;
+      const C* px = (l - 1 == 0) ? xroot : w.fin[l - 1][pidx];
       for (size_t a = 0; a < parents[pidx].children.size(); ++a) {
         int c = parents[pidx].children[a];
-        const Cd* y = px + pb.child_off[a];
+        const C* y = px + coff[a];
         // f~ - A~ y, then x = g - X (f~ - A~ y)
-        g1.add(BF[c].kb, nrhs, BF[c].kb, BF[c].At, BF[c].kb, y, pb.mb, ft[l][c], BF[c].kb, mone, one, 0);
-        g2.add(BF[c].mb, nrhs, BF[c].kb, BF[c].X, BF[c].mb, ft[l][c], BF[c].kb, fin[l][c], BF[c].mb, mone, one, 0);
+        g1.add(BF[c].kb, nrhs, BF[c].kb, BF[c].At, BF[c].kb, y, pmb, w.ft[l][c], BF[c].kb, cmone<C>(), cone<C>(), 0);
+        g2.add(BF[c].mb, nrhs, BF[c].kb, BF[c].X, BF[c].mb, w.ft[l][c], BF[c].kb, w.fin[l][c], BF[c].mb, cmone<C>(),
+               cone<C>(), 0);
       }
     }
     g1.run(ws, st);
     g2.run(ws, st);
   }
-  CopyBatch cb;
-  auto& BF = F->lev[L];
-  for (size_t b = 0; b < BF.size(); ++b) cb.add(fin[L][b], BF[b].mb, phi + BF[b].cols[0], N, BF[b].mb, nrhs);
+  CopyBatch<C, C> cb;
+  auto& BF = LV[L];
+  for (size_t b = 0; b < BF.size(); ++b) cb.add(w.fin[L][b], BF[b].mb, phi + BF[b].cols[0], N, BF[b].mb, nrhs);
   cb.run(ws, st);
+}
+
+void root_solve(pm_factor* F, double2* x, int ldx, int nrhs, Arena& ws, cudaStream_t st) {
+  BoxF<double2>& rt = F->root;
+  std::vector<SolveProb<double2>> sv{SolveProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, x, ldx, nrhs}};
+  solve_batch<double2>(sv, ws, st);
+}
+
+// phi = M^{-1} rhs with the compressed factorization (FP64 levels).
+void apply_inverse64(pm_factor* F, const double2* rhs, int nrhs, double2* phi, Arena& ws, cudaStream_t st) {
+  const int N = F->g->N;
+  if (F->L == 0) {
+    CopyBatch<double2, double2> cb;
+    cb.add(rhs, N, phi, N, N, nrhs);
+    cb.run(ws, st);
+    root_solve(F, phi, N, nrhs, ws, st);
+    return;
+  }
+  SolveWork<double2> w;
+  solve_up<double2>(F, rhs, nrhs, w, ws, st);
+  root_solve(F, w.froot, F->root.mb, nrhs, ws, st);
+  solve_down<double2>(F, nrhs, w, phi, ws, st);
+}
+
+// phi = M^{-1} rhs with the mixed factorization (FP32 levels, FP64 top).
+// rhs is FP64; each column is scaled to unit norm for the FP32 part.
+void apply_inverse_mixed(pm_factor* F, const double2* rhs, int nrhs, double2* phi, const double* d_scale,
+                         const double* d_unscale, Arena& ws, cudaStream_t st) {
+  const int N = F->g->N;
+  CK(cudaMemsetAsync(phi, 0, sizeof(double2) * (size_t)N * nrhs, st));
+  if (F->L == 0) {
+    CopyBatch<double2, double2> cb;
+    cb.add(rhs, N, phi, N, N, nrhs);
+    cb.run(ws, st);
+    root_solve(F, phi, N, nrhs, ws, st);
+    return;
+  }
+  Cf* r32 = ws.get<Cf>((size_t)N * nrhs);
+  Cf* p32 = ws.get<Cf>((size_t)N * nrhs);
+  scale_to32(rhs, r32, N, nrhs, d_scale, st);
+  SolveWork<Cf> w;
+  solve_up<Cf>(F, r32, nrhs, w, ws, st);
+  root_solve(F, w.froot, F->root.mb, nrhs, ws, st);
+  solve_down<Cf>(F, nrhs, w, p32, ws, st);
+  axpy_from32(phi, p32, N, nrhs, d_unscale, st);
+  CK(cudaGetLastError());
+}
+
+// Y = A X with the FP64 operator (self blocks + on-the-fly off-diagonal kernels).
+void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Arena& ws, cudaStream_t st) {
+  const pm_geometry* g = F->g;
+  const int N = g->N;
+  GemmBatch<double2> gb;
+  for (int j = 0; j < g->m; ++j) {
+    const int r0 = g->row_off[j], m2 = 2 * g->inc[j].n_nodes;
+    gb.add(m2, nrhs, m2, F->self64[j], m2, X + r0, N, Y + r0, N, cone<double2>(), czero_h<double2>(), 1);
+  }
+  gb.run(ws, st);
+  OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
+  apply_offdiag64(nd, g->total_nodes, g->k0, X, N, Y, N, nrhs, st);
+  CK(cudaGetLastError());
+}
+
+// Iterative refinement (mixed mode): x <- x + M^{-1} (b - A x) until the
+// relative residual of every column is below refine_tol.
+void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& ws, cudaStream_t st,
+                   pm_solve_info* info) {
+  const int N = F->g->N;
+  double2* Y = ws.get<double2>((size_t)N * nrhs);
+  double2* R = ws.get<double2>((size_t)N * nrhs);
+  double2* dX = ws.get<double2>((size_t)N * nrhs);
+  double* norms = ws.get<double>(2 * (size_t)nrhs);
+  double* scal = ws.get<double>(2 * (size_t)nrhs);
+  std::vector<double> hn(2 * nrhs), hs(2 * nrhs);
+  auto residual = [&](const double2* x) {
+    apply_operator64(F, x, nrhs, Y, ws, st);
+    CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
+    residual64(B, Y, R, N, nrhs, norms, st);
+    CK(cudaMemcpyAsync(hn.data(), norms, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double worst = 0;
+    for (int r = 0; r < nrhs; ++r) worst = std::max(worst, std::sqrt(hn[2 * r]) / std::max(std::sqrt(hn[2 * r + 1]), 1e-300));
+    return worst;
+  };
+  auto precond = [&](const double2* rhs, double2* out, const std::vector<double>& colnorm) {
+    for (int r = 0; r < nrhs; ++r) {
+      double nr = colnorm[r] > 0 ? colnorm[r] : 1.0;
+      hs[r] = 1.0 / nr;
+      hs[nrhs + r] = nr;
+    }
+    CK(cudaMemcpyAsync(scal, hs.data(), 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    apply_inverse_mixed(F, rhs, nrhs, out, scal, scal + nrhs, ws, st);
+  };
+  // x0 = M^{-1} b (column norms of b from a zero residual pass)
+  CK(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)N * nrhs, st));
+  double res = residual(X);   // r = b
+  std::vector<double> cn(nrhs);
+  for (int r = 0; r < nrhs; ++r) cn[r] = std::sqrt(hn[2 * r]);
+  int it = 0;
+  const double tolr = F->opts.refine_tol > 0 ? F->opts.refine_tol : 1e-10;
+  const int maxit = F->opts.max_refine > 0 ? F->opts.max_refine : 10;
+  std::vector<double> hist;
+  while (it < maxit) {
+    precond(R, dX, cn);
+    // X += dX
+    axpy64(X, dX, N, nrhs, st);
+    ++it;
+    res = residual(X);
+    hist.push_back(res);
+    for (int r = 0; r < nrhs; ++r) cn[r] = std::sqrt(hn[2 * r]);
+    if (res <= tolr) break;
+  }
+  if (info) {
+    info->iterations = it;
+    info->residual = res;
+  }
+  if (res > tolr) fail(PM_ERR_NOT_CONVERGED, "iterative refinement stopped at relative residual " + std::to_string(res));
 }
 
 pm_status run_guarded(const char* where, const std::function<void()>& fn);
@@ -1020,7 +1195,11 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
   if (!(opts->tol > 0 && opts->tol < 1)) { g_err = "pm_factorize: tol must be in (0, 1)"; return PM_ERR_INVALID_ARG; }
   if (opts->proxy_factor != 0 && !(opts->proxy_factor > 1)) { g_err = "pm_factorize: proxy_factor must be > 1"; return PM_ERR_INVALID_ARG; }
   if (opts->proxy_points < 0 || opts->proxy_points > 100000) { g_err = "pm_factorize: bad proxy_points"; return PM_ERR_INVALID_ARG; }
-  if (opts->precision != PM_FP64) { g_err = "pm_factorize: unsupported precision"; return PM_ERR_UNSUPPORTED; }
+  if (opts->precision != PM_FP64 && opts->precision != PM_MIXED) { g_err = "pm_factorize: unsupported precision"; return PM_ERR_UNSUPPORTED; }
+  if (opts->precision == PM_MIXED && (opts->low_tol < 0 || opts->low_tol >= 1 || opts->refine_tol < 0 || opts->max_refine < 0)) {
+    g_err = "pm_factorize: bad refinement options";
+    return PM_ERR_INVALID_ARG;
+  }
   pm_factor* F = new pm_factor();
   pm_status s = run_guarded("pm_factorize", [&] {
     F->g = g;
@@ -1028,19 +1207,49 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
     if (F->opts.proxy_factor == 0) F->opts.proxy_factor = 1.5;
     F->st = (cudaStream_t)opts->stream;
     F->L = g->L;
+    F->precision = opts->precision;
     F->tree = g->levels;
-    plan_proxies(g, F->tree, &F->opts);
+    // the FP32 factorization of the mixed mode cannot resolve tolerances far below FP32 precision
+    const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 1e-5)
+                                                   : opts->tol;
+    pm_factor_opts popts = F->opts;
+    popts.tol = id_tol;
+    plan_proxies(g, F->tree, &popts);
     F->stats.levels = F->L;
     F->stats.N = g->N;
-    F->lev.assign(F->L + 1, {});
     F->profiling = (opts->flags & 1u) != 0;
     struct ProfScope {
       explicit ProfScope(KProf* p) { g_kprof = p; }
       ~ProfScope() { g_kprof = nullptr; }
     } scope(F->profiling ? &F->prof : nullptr);
     Timer tt(F->st);
-    for (int l = F->L; l >= 1; --l) process_level(F, l);
-    factor_top(F);
+    if (F->precision == PM_FP64) {
+      F->lev64.assign(F->L + 1, {});
+      for (int l = F->L; l >= 1; --l) process_level<double2>(F, l, id_tol);
+      factor_top<double2>(F);
+    } else {
+      F->lev32.assign(F->L + 1, {});
+      for (int l = F->L; l >= 1; --l) process_level<float2>(F, l, id_tol);
+      factor_top<float2>(F);
+      // FP64 self blocks and index maps for the refinement residual
+      F->scratch.reset();
+      std::vector<int> incl(g->m), lda(g->m);
+      F->self64.resize(g->m);
+      for (int j = 0; j < g->m; ++j) {
+        incl[j] = j;
+        lda[j] = 2 * g->inc[j].n_nodes;
+        F->self64[j] = F->arena.get<double2>((size_t)lda[j] * lda[j]);
+      }
+      assemble_self<double2>(g, incl, F->self64, lda, F->scratch, F->st);
+      std::vector<int> iu(g->total_nodes), iq(g->total_nodes);
+      for (int j = 0; j < g->m; ++j)
+        for (int l = 0; l < g->inc[j].n_nodes; ++l) {
+          iu[g->node_off[j] + l] = g->row_off[j] + l;
+          iq[g->node_off[j] + l] = g->row_off[j] + g->inc[j].n_nodes + l;
+        }
+      F->d_iu = upload(F->arena, iu, F->st);
+      F->d_iq = upload(F->arena, iq, F->st);
+    }
     F->stats.ms_total = tt.stop();
     if (F->profiling) F->prof.collect();
     F->scratch.release();
@@ -1050,8 +1259,11 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
   return PM_OK;
 }
 
-pm_status pm_solve(const pm_factor* F, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device) {
-  if (!F || !rhs || !phi || nrhs < 1) { g_err = "pm_solve: bad argument"; return PM_ERR_INVALID_ARG; }
+pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
+                      pm_solve_info* info) {
+  if (!Fc || !rhs || !phi || nrhs < 1) { g_err = "pm_solve: bad argument"; return PM_ERR_INVALID_ARG; }
+  if (info) { info->iterations = 0; info->residual = -1; }
+  pm_factor* F = const_cast<pm_factor*>(Fc);
   return run_guarded("pm_solve", [&] {
     Arena ws;
     cudaStream_t st = F->st;
@@ -1068,10 +1280,15 @@ pm_status pm_solve(const pm_factor* F, const pm_c64* rhs, int32_t nrhs, pm_c64* 
       CK(cudaMemcpyAsync(a, rhs, bytes, cudaMemcpyDeviceToDevice, st));
       drhs = a;
     }
-    solve_device(F, drhs, nrhs, dphi, ws, st);
+    if (F->precision == PM_FP64) apply_inverse64(F, drhs, nrhs, dphi, ws, st);
+    else solve_refined(F, drhs, nrhs, dphi, ws, st, info);
     if (!on_device) CK(cudaMemcpyAsync(phi, dphi, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   });
+}
+
+pm_status pm_solve(const pm_factor* F, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device) {
+  return pm_solve_ex(F, rhs, nrhs, phi, on_device, nullptr);
 }
 
 pm_status pm_factor_stats(const pm_factor* F, pm_stats* out) {
@@ -1082,15 +1299,23 @@ pm_status pm_factor_stats(const pm_factor* F, pm_stats* out) {
 
 pm_status pm_factor_skeleton(const pm_factor* F, int32_t level, int32_t box, int32_t* rows, int32_t* cols,
                              int32_t cap, int32_t* k) {
-  if (!F || !k || level < 1 || level > F->L || box < 0 || box >= (int)F->lev[level].size()) {
-    g_err = "pm_factor_skeleton: bad argument";
-    return PM_ERR_INVALID_ARG;
+  if (!F || !k || level < 1 || level > F->L) { g_err = "pm_factor_skeleton: bad argument"; return PM_ERR_INVALID_ARG; }
+  const std::vector<int>* sr = nullptr;
+  const std::vector<int>* sc = nullptr;
+  int kb = 0;
+  if (F->precision == PM_FP64) {
+    if (box < 0 || box >= (int)F->lev64[level].size()) { g_err = "pm_factor_skeleton: bad box"; return PM_ERR_INVALID_ARG; }
+    const auto& b = F->lev64[level][box];
+    sr = &b.srows; sc = &b.scols; kb = b.kb;
+  } else {
+    if (box < 0 || box >= (int)F->lev32[level].size()) { g_err = "pm_factor_skeleton: bad box"; return PM_ERR_INVALID_ARG; }
+    const auto& b = F->lev32[level][box];
+    sr = &b.srows; sc = &b.scols; kb = b.kb;
   }
-  const BoxF& b = F->lev[level][box];
-  *k = b.kb;
-  for (int i = 0; i < std::min(cap, b.kb); ++i) {
-    if (rows) rows[i] = b.srows[i];
-    if (cols) cols[i] = b.scols[i];
+  *k = kb;
+  for (int i = 0; i < std::min(cap, kb); ++i) {
+    if (rows) rows[i] = (*sr)[i];
+    if (cols) cols[i] = (*sc)[i];
   }
   return PM_OK;
 }
@@ -1107,7 +1332,7 @@ pm_status pm_matrix_entries(const pm_geometry* g, const int32_t* rows, int32_t M
     for (int i = 0; i < M; ++i) t[i] = g->code_of(rows[i]);
     for (int j = 0; j < Nc; ++j) s[j] = g->code_of(cols[j]);
     Cd* d = ws.get<Cd>((size_t)M * Nc);
-    GatherBatch gb;
+    GatherBatch<Cd> gb;
     gb.add(d, M, M, Nc, t, s, 0);
     std::vector<int> dummy;
     PointsDev P = make_points(g, {}, ws, st, dummy);
@@ -1131,7 +1356,7 @@ pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out) {
     cudaStream_t st = 0;
     int n = g->inc[j].n_nodes;
     Cd* d = ws.get<Cd>((size_t)4 * n * n);
-    assemble_self(g, {j}, {d}, {2 * n}, ws, st);
+    assemble_self<Cd>(g, {j}, {d}, {2 * n}, ws, st);
     CK(cudaMemcpy(out, d, sizeof(Cd) * (size_t)4 * n * n, cudaMemcpyDeviceToHost));
   });
 }

@@ -15,6 +15,7 @@ PM_OK = 0
 STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM_ERR_SINGULAR",
           5: "PM_ERR_NOT_CONVERGED", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_GEOMETRY", 8: "PM_ERR_UNSUPPORTED"}
 PM_FP64 = 0
+PM_MIXED = 1
 
 
 class PmError(RuntimeError):
@@ -39,7 +40,12 @@ class pm_problem(ct.Structure):
 
 class pm_factor_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("proxy_factor", ct.c_double), ("proxy_points", ct.c_int32),
-                ("precision", ct.c_int32), ("stream", ct.c_void_p), ("flags", ct.c_uint32)]
+                ("precision", ct.c_int32), ("stream", ct.c_void_p), ("flags", ct.c_uint32),
+                ("refine_tol", ct.c_double), ("max_refine", ct.c_int32), ("low_tol", ct.c_double)]
+
+
+class pm_solve_info(ct.Structure):
+    _fields_ = [("iterations", ct.c_int32), ("residual", ct.c_double)]
 
 
 class pm_stats(ct.Structure):
@@ -62,6 +68,8 @@ EXPORTS = {
     "pm_plane_wave_rhs": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
     "pm_factorize": (ct.c_int, [ct.c_void_p, ct.POINTER(pm_factor_opts), ct.POINTER(ct.c_void_p)]),
     "pm_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32]),
+    "pm_solve_ex": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32,
+                               ct.POINTER(pm_solve_info)]),
     "pm_factor_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(pm_stats)]),
     "pm_factor_skeleton": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32,
                                       ct.POINTER(ct.c_int32)]),
@@ -170,11 +178,13 @@ class Geometry:
 
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
-                 profile=False):
+                 profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0):
         lib = load()
         self.geom = geom
+        self.last_info = None
         o = pm_factor_opts(float(tol), float(proxy_factor), int(proxy_points), int(precision),
-                           ct.c_void_p(stream) if stream else None, PM_FLAG_PROFILE if profile else 0)
+                           ct.c_void_p(stream) if stream else None, PM_FLAG_PROFILE if profile else 0,
+                           float(refine_tol), int(max_refine), float(low_tol))
         h = ct.c_void_p()
         _check(lib.pm_factorize(geom.h, ct.byref(o), ct.byref(h)))
         self.h = h
@@ -201,12 +211,17 @@ class Factor:
         nrhs = R.shape[1]
         buf = np.ascontiguousarray(R.T)  # column-major N x nrhs
         out = np.zeros_like(buf)
-        _check(load().pm_solve(self.h, buf.ctypes.data, nrhs, out.ctypes.data, 0))
+        info = pm_solve_info()
+        _check(load().pm_solve_ex(self.h, buf.ctypes.data, nrhs, out.ctypes.data, 0, ct.byref(info)))
+        self.last_info = {"iterations": info.iterations, "residual": info.residual}
         phi = out.T
         return phi[:, 0] if vec else phi
 
     def solve_device(self, rhs_ptr, nrhs, phi_ptr):
-        _check(load().pm_solve(self.h, rhs_ptr, nrhs, phi_ptr, 1))
+        info = pm_solve_info()
+        _check(load().pm_solve_ex(self.h, rhs_ptr, nrhs, phi_ptr, 1, ct.byref(info)))
+        self.last_info = {"iterations": info.iterations, "residual": info.residual}
+        return self.last_info
 
     def skeleton(self, level, box, cap=100000):
         rows = np.zeros(cap, dtype=np.int32); cols = np.zeros(cap, dtype=np.int32); k = ct.c_int32()

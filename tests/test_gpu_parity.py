@@ -146,3 +146,41 @@ def test_ragged_grid_device_buffers(pm):
     f.solve_device(F.data_ptr(), len(angs), F.data_ptr())
     torch.cuda.synchronize()
     assert _rel(F.cpu().numpy().T, phi) < 1e-14
+
+
+# ---- mixed precision: FP32 factorization + FP64 refinement -------------------------
+
+def test_mixed_small_circles(pm):
+    prob, opts, angs = wl.config_fp64_small()
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=pm.PM_MIXED)
+    phi = f.solve(g.plane_wave(angs))
+    assert f.last_info["residual"] <= 1e-10
+    assert _rel(phi, dense.solve(prob, angs)) < 1e-8
+
+
+@pytest.mark.parametrize("nx,n", [(4, 64), (2, 128)])
+def test_mixed_star_grid_matches_dense(pm, nx, n):
+    prob = wl.star_grid(nx, nx, n=n, seed=1)
+    angs = [0.3, 1.9, 4.4]
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED)
+    F = g.plane_wave(angs)
+    phi = f.solve(F)
+    info = f.last_info
+    assert 1 <= info["iterations"] <= 6 and info["residual"] <= 1e-10
+    A = dense.assemble(prob)
+    ref = np.linalg.solve(A, F)
+    assert _rel(phi, ref) < 1e-8
+    # the refinement residual is the FP64 operator's: recompute it with the oracle's matrix
+    res = max(np.linalg.norm(F[:, r] - A @ phi[:, r]) / np.linalg.norm(F[:, r]) for r in range(len(angs)))
+    assert res <= 2e-10
+
+
+def test_mixed_refinement_reports_non_convergence(pm):
+    prob = wl.star_grid(2, 2, n=64, seed=1)
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, max_refine=1, refine_tol=1e-15)
+    with pytest.raises(pm.PmError) as e:
+        f.solve(g.plane_wave([0.5]))
+    assert e.value.status == 5
