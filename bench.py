@@ -5,6 +5,9 @@ A step is one pass of the whole hot path on the 16 x 16 star-grid workload
 (n = 128 nodes per star, N = 65,536 complex unknowns, tol 1e-10): geometry
 resident on the device, then factorization (self blocks, proxy IDs, Schur
 merges over 4 levels, top LU) and a solve of 8 plane-wave right-hand sides.
+The headline runs the mixed-precision mode (complex64 levels, complex128 top
+LU, refinement against the complex128 operator to a relative residual of
+1e-10); the plain complex128 solver is timed on the same inputs beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -161,6 +164,69 @@ def _traffic_for(kernel):
     return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
 
 
+FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",
+                "apply_offdiag64"}
+
+
+def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup):
+    """Warm-up, then `steps` timed factor + solve passes on the stream; returns per-step numbers."""
+    import torch
+    nrhs = len(angs)
+
+    def step(profile):
+        f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
+                      stream=stream.cuda_stream, profile=profile)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = f.solve_device(F.data_ptr(), nrhs, X.data_ptr())
+        e1.record(stream)
+        return f, e0, e1, info
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    launches0 = pm.launch_counter()
+    prof_tot, solve_ev, fstats, infos = {}, [], [], []
+    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        f, e0, e1, info = step(True)
+        fstats.append(f.stats())
+        infos.append(info)
+        for k, v in f.profile().items():
+            a = prof_tot.setdefault(k, {"launches": 0, "ms": 0.0, "work": 0.0})
+            for kk in a:
+                a[kk] += v[kk]
+        solve_ev.append((e0, e1))
+        del f
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    solve = sum(a.elapsed_time(b) for a, b in solve_ev) / len(solve_ev)
+    launches = pm.launch_counter() - launches0
+    return ms, solve, prof_tot, fstats[-1], infos[-1], launches
+
+
+def _kernel_table(prof_tot, steps):
+    return {k: {"launches": v["launches"] // steps, "ms": round(v["ms"] / steps, 3),
+                "tflops": (round(v["work"] / (v["ms"] / 1e3) / 1e12, 4)
+                           if k in FLOP_KERNELS and v["ms"] > 0 else None)}
+            for k, v in sorted(prof_tot.items(), key=lambda kv: -kv[1]["ms"])}
+
+
+def _roofline(prof_tot, steps):
+    name, d = max(prof_tot.items(), key=lambda kv: kv[1]["ms"])
+    roof = {"kernel": name, "launches_per_step": d["launches"] / steps, "kernel_ms_per_step": d["ms"] / steps}
+    if name in FLOP_KERNELS and d["ms"] > 0:
+        achieved = d["work"] / (d["ms"] / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 dense FP64 (recipe)",
+                     "traffic": _traffic_for(name)})
+    else:
+        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+    return roof
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -186,49 +252,19 @@ def run_ours(args):
     X = torch.zeros_like(F)
     g.plane_wave_device(angs, F.data_ptr())
     torch.cuda.synchronize()
-
-    def step(profile=False):
-        f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"],
-                      stream=stream.cuda_stream, profile=profile)
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        f.solve_device(F.data_ptr(), nrhs, X.data_ptr())
-        e1.record(stream)
-        return f, e0, e1
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    precision = pm.PM_MIXED if args.precision == "mixed" else pm.PM_FP64
     if ws > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    launches0 = pm.launch_counter()
-    prof_tot = {}
-    solve_ms = []
-    fstats = []
     with Clocks(local) as clk:
-        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(args.steps):
-            f, e0, e1 = step(profile=True)
-            fstats.append(f.stats())
-            for k, v in f.profile().items():
-                a = prof_tot.setdefault(k, {"launches": 0, "ms": 0.0, "work": 0.0})
-                for kk in a:
-                    a[kk] += v[kk]
-            solve_ms.append((e0, e1))
-            del f
-        t1.record(stream)
-        torch.cuda.synchronize()
-    launches = pm.launch_counter() - launches0
-    ms = t0.elapsed_time(t1) / args.steps
+        ms, solve, prof_tot, st, info, launches = _timed(pm, g, prob, opts, angs, F, X, stream, precision,
+                                                        args.steps, args.warmup)
     if ws > 1:
         tt = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
         ms = float(tt.item())
-    solve = sum(a.elapsed_time(b) for a, b in solve_ms) / len(solve_ms)
     value = ws * N / (ms / 1e3)
+    X_dev = X.cpu().numpy()
 
     # end to end through the public API with host buffers: descriptors and pinned
     # right-hand sides in, solution out, every step
@@ -240,8 +276,11 @@ def run_ours(args):
     te = time.perf_counter()
     for _ in range(args.steps):
         g2 = pm.Geometry(prob)
-        f2 = pm.Factor(g2, opts["tol"], opts["proxy_factor"], opts["proxy_points"], stream=stream.cuda_stream)
-        pm._check(pm.load().pm_solve(f2.h, rhs_host.data_ptr(), nrhs, out_host.data_ptr(), 0))
+        f2 = pm.Factor(g2, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
+                       stream=stream.cuda_stream)
+        inf2 = pm.pm_solve_info()
+        pm._check(pm.load().pm_solve_ex(f2.h, rhs_host.data_ptr(), nrhs, out_host.data_ptr(), 0,
+                                        pm.ct.byref(inf2)))
         del f2, g2
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / args.steps
@@ -249,42 +288,41 @@ def run_ours(args):
         tt = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    ok = np.allclose(out_host.numpy(), X.cpu().numpy(), rtol=0, atol=1e-10 * float(X.abs().max()))
+    scale = float(np.abs(X_dev).max())
+    e2e_match = bool(np.allclose(out_host.numpy(), X_dev, rtol=0, atol=1e-8 * scale))
+
+    # the plain FP64 GPU solver on the same inputs, for comparison
+    fp64 = None
+    if precision == pm.PM_MIXED and not args.no_fp64_compare:
+        X64 = torch.zeros_like(F)
+        ms64, solve64, prof64, st64, _, _ = _timed(pm, g, prob, opts, angs, F, X64, stream, pm.PM_FP64, 1, 1)
+        diff = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
+        fp64 = {"value": ws * N / (ms64 / 1e3), "ms_per_step": ms64, "solve_ms": solve64, "factor_ms": ms64 - solve64,
+                "K": st64["K"], "skeleton_per_level": st64["skeleton"], "roofline": _roofline(prof64, 1),
+                "kernels": _kernel_table(prof64, 1), "rel_diff_vs_mixed": diff,
+                "speedup_of_mixed": ms64 / ms}
 
     if rank != 0:
         return 0
-    # roofline of the dominant kernel
-    flop_kernels = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched",
-                    "interp_solve"}
-    dom = max(prof_tot.items(), key=lambda kv: kv[1]["ms"])
-    name, d = dom
-    roof = {"kernel": name, "launches_per_step": d["launches"] / args.steps,
-            "kernel_ms_per_step": d["ms"] / args.steps}
-    if name in flop_kernels and d["ms"] > 0:
-        achieved = d["work"] / (d["ms"] / 1e3) / 1e12
-        roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 dense FP64 (recipe)",
-                     "traffic": _traffic_for(name)})
-    else:
-        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
-    kernels = {k: {"launches": v["launches"] // args.steps, "ms": round(v["ms"] / args.steps, 3),
-                   "tflops": (round(v["work"] / (v["ms"] / 1e3) / 1e12, 4)
-                              if k in flop_kernels and v["ms"] > 0 else None)}
-               for k, v in sorted(prof_tot.items(), key=lambda kv: -kv[1]["ms"])}
-    st = fstats[-1]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "vs_baseline": None, "dtype": "c64+c128" if precision == pm.PM_MIXED else "c128",
+            "data": "synthetic",
             "config": {"workload": f"{WORKLOADS[args.workload]}x{WORKLOADS[args.workload]} stars "
                                    f"r=0.4(1+0.2cos5t), spacing 1, k0=2pi*20/16, k1=2k0, n=128, N={N}, "
                                    f"tol 1e-10, {st['levels']} levels, 8 plane-wave RHS",
+                       "precision": args.precision,
                        "l2": "inputs larger than L2 (factor working set > 1 GB)", "parallelism": f"replicas{ws}"},
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
+            "refinement": info,
             "phase_ms": {k: st[k] for k in ("ms_assemble", "ms_id", "ms_schur", "ms_top")},
-            "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
+            "roofline": _roofline(prof_tot, args.steps), "kernels": _kernel_table(prof_tot, args.steps),
+            "gpu_launches": int(launches),
             "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "matches_device_result": bool(ok)},
+                    "matches_device_result": e2e_match},
             "clocks": clk.summary()}
+    if fp64 is not None:
+        line["fp64_path"] = fp64
     if ws == 1 and not args.no_cpu_baseline:
         Nc, ts = cpu_oracle_sample(4, reps=1)
         line["cpu_baseline"] = {"value": Nc / ts[0], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -304,6 +342,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="star16", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -107,11 +107,13 @@ typedef struct {
   double low_tol;
 } pm_factor_opts;
 
-/* Outcome of a refined solve (PM_MIXED): steps taken and the final largest
- * relative residual over the right-hand sides (-1 when not refined). */
+/* Outcome of a refined solve (PM_MIXED): steps taken, the final largest
+ * relative residual over the right-hand sides (-1 when not refined) and the
+ * residual after each of the first 16 steps. */
 typedef struct {
   int32_t iterations;
   double residual;
+  double history[16];
 } pm_solve_info;
 
 /* Statistics of a factorization (filled by pm_factor_stats). */

@@ -4,9 +4,11 @@
 // Kernel normalisation G = (i/4) H0(k r); with d = x - y, r = |d|:
 //   S = (i/4) H0,  D = (ik/4) H1 (n_y.d)/r,  D* = -(ik/4) H1 (n_x.d)/r,
 //   N = (ik/4) [k H0 (n_x.d)(n_y.d)/r^2 + H1/r (n_x.n_y - 2 (n_x.d)(n_y.d)/r^2)]
-// (paper Sec. 2.1, eqs. slp, dlp, d_slp, d_dlp).  Bessel values for real
-// arguments come from CUDA's j0/j1/y0/y1 (FP64) or j0f/j1f/y0f/y1f (FP32).
+// (paper Sec. 2.1, eqs. slp, dlp, d_slp, d_dlp).  Off-diagonal FP64 entries
+// use hankel.cuh; the self blocks call CUDA's j0/j1/y0/y1, and the FP32
+// entries of the mixed mode j0f/j1f/y0f/y1f.
 #include "assemble.cuh"
+#include "hankel.cuh"
 #include "prof.cuh"
 
 namespace {
@@ -219,11 +221,10 @@ __device__ __forceinline__ C omit_entry(const PointsDev& P, int t, int s, double
   const double r = sqrt(r2);
   const double z = k * r;
   const double w = P.w[ps];
-  if (rg == 0 && cg == 0) {         // -eps+ S = -(i/4) H0 w
-    double J0 = j0(z), Y0 = y0(z);
+  double J0, Y0, J1, Y1;
+  hankel01(z, J0, Y0, J1, Y1);
+  if (rg == 0 && cg == 0)           // -eps+ S = -(i/4) H0 w
     return mk((R)(0.25 * Y0 * w), (R)(-0.25 * J0 * w));
-  }
-  const double J1 = j1(z), Y1 = y1(z);
   if (rg == 0) {                    // D = (ik/4) H1 (n_y.d)/r w
     double g = (P.nx[ps] * dx + P.ny[ps] * dy) / r * 0.25 * k * w;
     return mk((R)(-Y1 * g), (R)(J1 * g));
@@ -233,7 +234,6 @@ __device__ __forceinline__ C omit_entry(const PointsDev& P, int t, int s, double
     return mk((R)(-Y1 * g), (R)(J1 * g));
   }
   // N/eps+ = (ik/4) [k H0 a b + H1/r (nn - 2 a b)] w,  a = n_x.d/r, b = n_y.d/r
-  const double J0 = j0(z), Y0 = y0(z);
   const double a = (P.nx[pt] * dx + P.ny[pt] * dy) / r, b = (P.nx[ps] * dx + P.ny[ps] * dy) / r;
   const double nn = P.nx[pt] * P.nx[ps] + P.ny[pt] * P.ny[ps];
   const double c0 = k * a * b, c1 = (nn - 2 * a * b) / r;

@@ -40,15 +40,20 @@ __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t
   typedef typename real_of<C>::type R;
   const int s = p.base + t;
   if (s >= p.target) return;
-  if (p.mode == CPQR_FIND_RANK && *(volatile int*)p.rank >= 0) return;
-  const int n = p.n;
-  const double* cur = p.norm2 + (s & 1) * n;
-  double* nxt = p.norm2 + ((s + 1) & 1) * n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ double red[8];
   __shared__ int redi[8];
   __shared__ double s_mx;
   __shared__ int s_q;
+  __shared__ int s_done;
+  // Another CTA may set the rank during this launch: read it once so that the
+  // whole CTA takes the same path through the barriers below.
+  if (tid == 0) s_done = (p.mode == CPQR_FIND_RANK) && (*(volatile int*)p.rank >= 0);
+  __syncthreads();
+  if (s_done) return;
+  const int n = p.n;
+  const double* cur = p.norm2 + (s & 1) * n;
+  double* nxt = p.norm2 + ((s + 1) & 1) * n;
   // pass 1: largest squared norm among unpivoted columns
   double mx = -1.0;
   for (int c = tid; c < n; c += 256) mx = fmax(mx, cur[c]);

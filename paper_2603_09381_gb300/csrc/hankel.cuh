@@ -1,0 +1,110 @@
+// Bessel functions J0, J1, Y0, Y1 of a positive real argument in FP64, for the
+// Hankel functions H_nu = J_nu + i Y_nu of the Helmholtz kernels.
+//
+// z >= HK_ZA: Hankel's asymptotic expansion (DLMF 10.17.3-10.17.4;
+//   Abramowitz & Stegun 9.2.5-9.2.10)
+//     H_nu(z) = sqrt(2/(pi z)) e^{i w} (P_nu(z) + i Q_nu(z)),  w = z - nu pi/2 - pi/4,
+//     P = sum_k (-1)^k a_{2k}(nu) z^{-2k},  Q = sum_k (-1)^k a_{2k+1}(nu) z^{-2k-1},
+//     a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (k! 8^k).
+//   For real z the remainder is bounded by the first omitted term (DLMF
+//   10.17(iii)); with 27 terms it is below 1e-18 for z >= 20.  One sincos(z)
+//   serves both orders: w_1 = w_0 - pi/2.
+// z < HK_ZA: Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from
+//   an even start M > z + 25 + 3 sqrt(z), normalised by 1 = J0 + 2 sum J_2k
+//   (A&S 9.1.27, 9.1.46), and Neumann's series (A&S 9.1.88)
+//     (pi/2) Y0 = (ln(z/2) + gamma) J0 - 2 sum_{k>=1} (-1)^k J_2k / k,
+//   with its derivative for Y1 = -Y0':
+//     (pi/2) Y1 = -J0/z + (ln(z/2) + gamma) J1 + sum_{k>=1} (-1)^k (J_{2k-1} - J_{2k+1})/k.
+#pragma once
+#include <cuda_runtime.h>
+
+constexpr double HK_ZA = 20.0;
+constexpr int HK_TERMS = 27;   // a_0 .. a_26
+
+// a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (8 j), with the (-1)^floor(k/2)
+// sign of the series folded in (evaluated at compile time).
+constexpr double hk_coef(int nu, int k) {
+  double a = 1.0;
+  for (int j = 1; j <= k; ++j) a *= (4.0 * nu * nu - (2.0 * j - 1) * (2.0 * j - 1)) / (8.0 * j);
+  return ((k / 2) & 1) ? -a : a;
+}
+#define HK_ROW(nu) \
+  {hk_coef(nu, 0), hk_coef(nu, 1), hk_coef(nu, 2), hk_coef(nu, 3), hk_coef(nu, 4), hk_coef(nu, 5), hk_coef(nu, 6), \
+   hk_coef(nu, 7), hk_coef(nu, 8), hk_coef(nu, 9), hk_coef(nu, 10), hk_coef(nu, 11), hk_coef(nu, 12),             \
+   hk_coef(nu, 13), hk_coef(nu, 14), hk_coef(nu, 15), hk_coef(nu, 16), hk_coef(nu, 17), hk_coef(nu, 18),          \
+   hk_coef(nu, 19), hk_coef(nu, 20), hk_coef(nu, 21), hk_coef(nu, 22), hk_coef(nu, 23), hk_coef(nu, 24),          \
+   hk_coef(nu, 25), hk_coef(nu, 26)}
+static __constant__ double c_hk_a0[HK_TERMS] = HK_ROW(0);
+static __constant__ double c_hk_a1[HK_TERMS] = HK_ROW(1);
+#undef HK_ROW
+
+__device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
+  const double u = iz * iz;
+  double P0 = c_hk_a0[HK_TERMS - 1 - ((HK_TERMS - 1) & 1)], P1 = c_hk_a1[HK_TERMS - 1 - ((HK_TERMS - 1) & 1)];
+  double Q0 = c_hk_a0[HK_TERMS - 1 - ((HK_TERMS) & 1)], Q1 = c_hk_a1[HK_TERMS - 1 - ((HK_TERMS) & 1)];
+#pragma unroll
+  for (int k = HK_TERMS - 3 - ((HK_TERMS - 1) & 1); k >= 0; k -= 2) {
+    P0 = fma(P0, u, c_hk_a0[k]);
+    P1 = fma(P1, u, c_hk_a1[k]);
+  }
+#pragma unroll
+  for (int k = HK_TERMS - 3 - (HK_TERMS & 1); k >= 1; k -= 2) {
+    Q0 = fma(Q0, u, c_hk_a0[k]);
+    Q1 = fma(Q1, u, c_hk_a1[k]);
+  }
+  Q0 *= iz;
+  Q1 *= iz;
+  double sn, cs;
+  sincos(z, &sn, &cs);
+  const double s = sqrt(0.63661977236758134308 * iz);          // sqrt(2/(pi z))
+  const double c = (cs + sn) * 0.70710678118654752440;         // cos(z - pi/4)
+  const double d = (sn - cs) * 0.70710678118654752440;         // sin(z - pi/4)
+  J0 = s * (P0 * c - Q0 * d);
+  Y0 = s * (P0 * d + Q0 * c);
+  J1 = s * (P1 * d + Q1 * c);
+  Y1 = s * (Q1 * d - P1 * c);
+}
+
+__device__ __forceinline__ void hankel_miller(double z, double& J0, double& Y0, double& J1, double& Y1) {
+  int M = (int)(z + 25.0 + 3.0 * sqrt(z));
+  M += (M & 1);
+  const double t2z = 2.0 / z;
+  double jp1 = 0.0, jn = 1e-30;      // J_{M+1}, J_M (unnormalised)
+  double norm = 0.0, s0 = 0.0, s1 = 0.0;
+  // index n holds jn; M is even
+  for (int n = M; n >= 1; --n) {
+    if ((n & 1) == 0) {              // even n = 2k >= 2
+      const int k = n >> 1;
+      norm += 2.0 * jn;
+      s0 += ((k & 1) ? -jn : jn) / k;
+    } else {                          // odd n = 2m - 1
+      const int m = (n + 1) >> 1;
+      if (m == 1) s1 -= jn;
+      else s1 += ((m & 1) ? -jn : jn) * (1.0 / m + 1.0 / (m - 1));
+    }
+    const double jm1 = n * t2z * jn - jp1;
+    jp1 = jn;
+    jn = jm1;
+  }
+  // jn = J0, jp1 = J1 (unnormalised)
+  norm += jn;
+  const double inv = 1.0 / norm;
+  J0 = jn * inv;
+  J1 = jp1 * inv;
+  s0 *= inv;
+  s1 *= inv;
+  const double lg = log(0.5 * z) + 0.57721566490153286061;
+  Y0 = 0.63661977236758134308 * (lg * J0 - 2.0 * s0);
+  Y1 = 0.63661977236758134308 * (-J0 / z + lg * J1 + s1);
+}
+
+__device__ __forceinline__ void hankel01(double z, double& J0, double& Y0, double& J1, double& Y1) {
+  if (z >= HK_ZA) hankel_asym(z, 1.0 / z, J0, Y0, J1, Y1);
+  else hankel_miller(z, J0, Y0, J1, Y1);
+}
+
+// Same, with 1/z supplied by the caller.
+__device__ __forceinline__ void hankel01_inv(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
+  if (z >= HK_ZA) hankel_asym(z, iz, J0, Y0, J1, Y1);
+  else hankel_miller(z, J0, Y0, J1, Y1);
+}

@@ -7,10 +7,11 @@
 // (paper Sec. 2.2, off-diagonal blocks of eq. pmchwt_omit_bie).  Sources are
 // staged through shared memory in tiles of 64; the grid splits the sources
 // into segments whose partial sums meet in FP64 atomics.  One J0/Y0/J1/Y1
-// quadruple per node pair serves all four kernels and all right-hand sides,
+// quadruple per node pair (hankel.cuh) serves all four kernels and all right-hand sides,
 // so the kernel is bound by the FP64 pipe (Bessel evaluation + 32 complex
 // FMAs per pair at 8 right-hand sides).
 #include "operator.cuh"
+#include "hankel.cuh"
 #include "prof.cuh"
 #include <algorithm>
 
@@ -27,6 +28,7 @@ __global__ void __launch_bounds__(OP_T) k_apply_offdiag(OpNodes nd, int total, d
   __shared__ double2 sxq[NR][OP_S], sxu[NR][OP_S];
   const int t = blockIdx.x * OP_T + threadIdx.x;
   const bool active = t < total;
+  const double ik = 1.0 / k;
   double tx = 0, ty = 0, tnx = 0, tny = 0;
   int tinc = -1;
   if (active) { tx = nd.x[t]; ty = nd.y[t]; tnx = nd.nx[t]; tny = nd.ny[t]; tinc = nd.incl[t]; }
@@ -56,17 +58,19 @@ __global__ void __launch_bounds__(OP_T) k_apply_offdiag(OpNodes nd, int total, d
     for (int j = 0; j < cnt; ++j) {
       if (sinc[j] == tinc) continue;
       const double dx = tx - sx[j], dy = ty - sy[j];
-      const double r = sqrt(dx * dx + dy * dy);
+      const double ir = rsqrt(dx * dx + dy * dy);       // one reciprocal square root per pair
+      const double r = (dx * dx + dy * dy) * ir;
       const double z = k * r;
-      const double J0 = j0(z), Y0 = y0(z), J1 = j1(z), Y1 = y1(z);
+      double J0, Y0, J1, Y1;
+      hankel01_inv(z, ir * ik, J0, Y0, J1, Y1);
       const double w = sw[j];
-      const double a = (tnx * dx + tny * dy) / r, b = (snx[j] * dx + sny[j] * dy) / r;
+      const double a = (tnx * dx + tny * dy) * ir, b = (snx[j] * dx + sny[j] * dy) * ir;
       const double nn = tnx * snx[j] + tny * sny[j];
       const double f = 0.25 * k * w;
       const double2 S = make_double2(0.25 * Y0 * w, -0.25 * J0 * w);          // -eps+ S w
       const double2 D = make_double2(-Y1 * b * f, J1 * b * f);                // D w
       const double2 T = make_double2(-Y1 * a * f, J1 * a * f);                // -D* w
-      const double c0 = k * a * b, c1 = (nn - 2 * a * b) / r;
+      const double c0 = k * a * b, c1 = (nn - 2 * a * b) * ir;
       const double2 Nk = make_double2(-(c0 * Y0 + c1 * Y1) * f, (c0 * J0 + c1 * J1) * f);  // N/eps+ w
 #pragma unroll
       for (int q = 0; q < NR; ++q) {

@@ -1005,6 +1005,14 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
   gb.run(ws, st);
   OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
   apply_offdiag64(nd, g->total_nodes, g->k0, X, N, Y, N, nrhs, st);
+  if (g_kprof) {
+    // algorithmic FP64 flops per node pair: 164 for geometry, Hankel expansion and
+    // kernels + 32 per right-hand side (4 complex multiply-adds); special
+    // functions (rsqrt, sincos, sqrt) not counted
+    double pairs = (double)g->total_nodes * g->total_nodes;
+    for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
+    g_kprof->add_flops("apply_offdiag64", pairs * (164.0 + 32.0 * nrhs));
+  }
   CK(cudaGetLastError());
 }
 
@@ -1038,9 +1046,14 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     CK(cudaMemcpyAsync(scal, hs.data(), 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
     apply_inverse_mixed(F, rhs, nrhs, out, scal, scal + nrhs, ws, st);
   };
-  // x0 = M^{-1} b (column norms of b from a zero residual pass)
+  // x0 = 0, r0 = b (no operator application needed)
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)N * nrhs, st));
-  double res = residual(X);   // r = b
+  CK(cudaMemsetAsync(Y, 0, sizeof(double2) * (size_t)N * nrhs, st));
+  CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
+  residual64(B, Y, R, N, nrhs, norms, st);
+  CK(cudaMemcpyAsync(hn.data(), norms, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double res = 1.0;
   std::vector<double> cn(nrhs);
   for (int r = 0; r < nrhs; ++r) cn[r] = std::sqrt(hn[2 * r]);
   int it = 0;
@@ -1060,6 +1073,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   if (info) {
     info->iterations = it;
     info->residual = res;
+    for (size_t i = 0; i < hist.size() && i < 16; ++i) info->history[i] = hist[i];
   }
   if (res > tolr) fail(PM_ERR_NOT_CONVERGED, "iterative refinement stopped at relative residual " + std::to_string(res));
 }
@@ -1262,7 +1276,10 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
 pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
                       pm_solve_info* info) {
   if (!Fc || !rhs || !phi || nrhs < 1) { g_err = "pm_solve: bad argument"; return PM_ERR_INVALID_ARG; }
-  if (info) { info->iterations = 0; info->residual = -1; }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->residual = -1;
+  }
   pm_factor* F = const_cast<pm_factor*>(Fc);
   return run_guarded("pm_solve", [&] {
     Arena ws;
@@ -1280,10 +1297,15 @@ pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c
       CK(cudaMemcpyAsync(a, rhs, bytes, cudaMemcpyDeviceToDevice, st));
       drhs = a;
     }
+    struct ProfScope {
+      explicit ProfScope(KProf* p) { g_kprof = p; }
+      ~ProfScope() { g_kprof = nullptr; }
+    } scope(F->profiling ? &F->prof : nullptr);
     if (F->precision == PM_FP64) apply_inverse64(F, drhs, nrhs, dphi, ws, st);
     else solve_refined(F, drhs, nrhs, dphi, ws, st, info);
     if (!on_device) CK(cudaMemcpyAsync(phi, dphi, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (F->profiling) F->prof.collect();
   });
 }
 

@@ -45,7 +45,7 @@ class pm_factor_opts(ct.Structure):
 
 
 class pm_solve_info(ct.Structure):
-    _fields_ = [("iterations", ct.c_int32), ("residual", ct.c_double)]
+    _fields_ = [("iterations", ct.c_int32), ("residual", ct.c_double), ("history", ct.c_double * 16)]
 
 
 class pm_stats(ct.Structure):
@@ -213,14 +213,16 @@ class Factor:
         out = np.zeros_like(buf)
         info = pm_solve_info()
         _check(load().pm_solve_ex(self.h, buf.ctypes.data, nrhs, out.ctypes.data, 0, ct.byref(info)))
-        self.last_info = {"iterations": info.iterations, "residual": info.residual}
+        self.last_info = {"iterations": info.iterations, "residual": info.residual,
+                          "history": list(info.history)[: info.iterations]}
         phi = out.T
         return phi[:, 0] if vec else phi
 
     def solve_device(self, rhs_ptr, nrhs, phi_ptr):
         info = pm_solve_info()
         _check(load().pm_solve_ex(self.h, rhs_ptr, nrhs, phi_ptr, 1, ct.byref(info)))
-        self.last_info = {"iterations": info.iterations, "residual": info.residual}
+        self.last_info = {"iterations": info.iterations, "residual": info.residual,
+                          "history": list(info.history)[: info.iterations]}
         return self.last_info
 
     def skeleton(self, level, box, cap=100000):

@@ -64,7 +64,7 @@ def test_offdiagonal_entries_match_oracle(pm):
     ref = proxy.entries(ix, prob["k_out"], rows, cols)
     same = (rows[:, None] // 128) == (cols[None, :] // 128)
     ref[same] = 0
-    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
 def test_plane_wave_rhs(pm):
@@ -184,3 +184,22 @@ def test_mixed_refinement_reports_non_convergence(pm):
     with pytest.raises(pm.PmError) as e:
         f.solve(g.plane_wave([0.5]))
     assert e.value.status == 5
+
+
+def test_offdiagonal_entries_large_arguments(pm):
+    # 16 x 16 stars, k0 = 7.85: k r spans ~0.3 .. 170 (both Hankel branches)
+    prob, _, _ = wl.config_star16()
+    g = pm.Geometry(prob)
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, g.N, 200)
+    cols = rng.integers(0, g.N, 300)
+    got = g.matrix_entries(rows, cols)
+    nds = geometry.all_nodes(prob)
+    ix = proxy._Index(prob, nds)
+    ref = proxy.entries(ix, prob["k_out"], rows, cols)
+    same = (rows[:, None] // 256) == (cols[None, :] // 256)
+    ref[same] = 0
+    got[same] = 0
+    err = np.abs(got - ref)
+    assert np.max(err) < 1e-13 * np.max(np.abs(ref))
+    assert np.max(err / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))) < 1e-11
