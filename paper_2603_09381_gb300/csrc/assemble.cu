@@ -112,6 +112,56 @@ __device__ __forceinline__ void bessel4(double z, double& j0v, double& y0v, doub
   j0v = j0(z); y0v = y0(z); j1v = j1(z); y1v = y1(z);
 }
 
+// Kress-split S, D, D* of one wavenumber at node pair (i, l) of one curve
+// (complex wavenumber allowed); outputs the quadrature-weighted entries.
+struct SelfGeo {
+  int i, l, n;
+  double h, Rw, spi, spl, curv, ndy, ndx, r, logsin;
+};
+
+__device__ __forceinline__ void kress_entries(const SelfGeo& q, double2 k, double2& S, double2& D, double2& T) {
+  const double PI4 = 4 * PI;
+  if (q.i == q.l) {
+    // M1 = -|x'|/(4 pi); M2 = [i/4 - C/(2 pi) - ln(k |x'|/2)/(2 pi)] |x'|;  L2 = L2* = (n.x'')/(4 pi |x'|)
+    const double M1 = -q.spi / PI4;
+    const double2 lg = zlog(make_double2(0.5 * k.x * q.spi, 0.5 * k.y * q.spi));
+    const double2 M2 = make_double2((-EULER_C / (2 * PI) - lg.x / (2 * PI)) * q.spi, (0.25 - lg.y / (2 * PI)) * q.spi);
+    S = make_double2(q.Rw * M1 + q.h * M2.x, q.h * M2.y);
+    const double L2 = q.curv / PI4;
+    D = make_double2(q.h * L2, 0);
+    T = D;
+    return;
+  }
+  double2 J0, Y0, J1, Y1;
+  const double2 z = make_double2(k.x * q.r, k.y * q.r);
+  if (k.y == 0) {
+    double j0r, y0r, j1r, y1r;
+    bessel4(z.x, j0r, y0r, j1r, y1r);
+    J0 = make_double2(j0r, 0); Y0 = make_double2(y0r, 0); J1 = make_double2(j1r, 0); Y1 = make_double2(y1r, 0);
+  } else {
+    bessel_complex(z, J0, Y0, J1, Y1);
+  }
+  // single layer: M = (i/4) H0 |x'| = (i J0 - Y0)/4 |x'|,  M1 = -(1/4pi) J0 |x'|
+  const double2 M = make_double2(-0.25 * Y0.x * q.spl - 0.25 * J0.y * q.spl, 0.25 * J0.x * q.spl - 0.25 * Y0.y * q.spl);
+  const double2 M1 = make_double2(-J0.x * q.spl / PI4, -J0.y * q.spl / PI4);
+  S = make_double2(q.Rw * M1.x + q.h * (M.x - M1.x * q.logsin), q.Rw * M1.y + q.h * (M.y - M1.y * q.logsin));
+  // H1 = J1 + i Y1;  (i k/4) H1 g  and  -(k/4pi) J1 g
+  const double2 H1 = make_double2(J1.x - Y1.y, J1.y + Y1.x);
+  const double2 ik4 = make_double2(-0.25 * k.y, 0.25 * k.x);
+  const double2 kH = zmul(ik4, H1);
+  const double2 kJ = zmul(make_double2(k.x / PI4, k.y / PI4), J1);
+  {
+    const double g = q.ndy * q.spl;          // double layer
+    const double2 L = make_double2(kH.x * g, kH.y * g), L1 = make_double2(-kJ.x * g, -kJ.y * g);
+    D = make_double2(q.Rw * L1.x + q.h * (L.x - L1.x * q.logsin), q.Rw * L1.y + q.h * (L.y - L1.y * q.logsin));
+  }
+  {
+    const double g = q.ndx * q.spl;          // adjoint: the same with -g
+    const double2 L = make_double2(-kH.x * g, -kH.y * g), L1 = make_double2(kJ.x * g, kJ.y * g);
+    T = make_double2(q.Rw * L1.x + q.h * (L.x - L1.x * q.logsin), q.Rw * L1.y + q.h * (L.y - L1.y * q.logsin));
+  }
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_self_pointwise(const InclDev* __restrict__ inc, NodesDev nd, double k0,
                                                         C* const* __restrict__ Aptr, const int* __restrict__ ldA,
@@ -122,61 +172,45 @@ __global__ void __launch_bounds__(256) k_self_pointwise(const InclDev* __restric
   const int n = c.n;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
-  const int i = e % n, l = e / n;   // target node i, source node l
-  const int gi = c.node_off + i, gl = c.node_off + l;
-  const double h = 2 * PI / n;
-  const double spl = nd.speed[gl], spi = nd.speed[gi];
+  SelfGeo q;
+  q.i = e % n; q.l = e / n; q.n = n;
+  const int gi = c.node_off + q.i, gl = c.node_off + q.l;
+  q.h = 2 * PI / n;
+  q.spl = nd.speed[gl]; q.spi = nd.speed[gi];
+  q.curv = nd.curv[gi];
   const double nxi = nd.nx[gi], nyi = nd.ny[gi], nxl = nd.nx[gl], nyl = nd.ny[gl];
   const double nn = nxi * nxl + nyi * nyl;
-  const double ks[2] = {k0, c.k_in_re};
-  const double eps_in = c.eps_in_re;
-  double Sre[2], Sim[2], Dre[2], Dim[2], Tre[2], Tim[2];
-  const int d = (i - l + n) % n;
-  const double Rw = nd.kress[c.node_off + d];
-  if (i == l) {
-    for (int q = 0; q < 2; ++q) {
-      double k = ks[q];
-      double M1 = -spi / (4 * PI);
-      double M2re = (-EULER_C / (2 * PI) - log(k * spi / 2) / (2 * PI)) * spi, M2im = 0.25 * spi;
-      Sre[q] = Rw * M1 + h * M2re; Sim[q] = h * M2im;
-      double L2 = nd.curv[gi] / (4 * PI);
-      Dre[q] = h * L2; Dim[q] = 0; Tre[q] = h * L2; Tim[q] = 0;
-    }
-  } else {
+  q.Rw = nd.kress[c.node_off + (q.i - q.l + n) % n];
+  q.r = 0; q.ndy = 0; q.ndx = 0; q.logsin = 0;
+  if (q.i != q.l) {
     const double dx = nd.x[gi] - nd.x[gl], dy = nd.y[gi] - nd.y[gl];
-    const double r = sqrt(dx * dx + dy * dy);
-    const double ndy = (nxl * dx + nyl * dy) / r, ndx = (nxi * dx + nyi * dy) / r;
-    double sn = sin(PI * (double)(i - l) / n);
-    const double logsin = log(4 * sn * sn);
-    for (int q = 0; q < 2; ++q) {
-      double k = ks[q];
-      double J0, Y0, J1, Y1;
-      bessel4(k * r, J0, Y0, J1, Y1);
-      // single layer: M = (i/4) H0 |x'|, M1 = -(1/4pi) J0 |x'|
-      double Mre = -0.25 * Y0 * spl, Mim = 0.25 * J0 * spl;
-      double M1 = -J0 * spl / (4 * PI);
-      Sre[q] = Rw * M1 + h * (Mre - M1 * logsin); Sim[q] = h * Mim;
-      // double layer: L = (ik/4) H1 (n_y.d)/r |x'|, L1 = -(k/4pi) J1 (n_y.d)/r |x'|
-      double Lre = -0.25 * k * Y1 * ndy * spl, Lim = 0.25 * k * J1 * ndy * spl;
-      double L1 = -k * J1 * ndy * spl / (4 * PI);
-      Dre[q] = Rw * L1 + h * (Lre - L1 * logsin); Dim[q] = h * Lim;
-      // adjoint: L* = -(ik/4) H1 (n_x.d)/r |x'|, L1* = (k/4pi) J1 (n_x.d)/r |x'|
-      double Tre_ = 0.25 * k * Y1 * ndx * spl, Tim_ = -0.25 * k * J1 * ndx * spl;
-      double T1 = k * J1 * ndx * spl / (4 * PI);
-      Tre[q] = Rw * T1 + h * (Tre_ - T1 * logsin); Tim[q] = h * Tim_;
-    }
+    q.r = sqrt(dx * dx + dy * dy);
+    q.ndy = (nxl * dx + nyl * dy) / q.r;
+    q.ndx = (nxi * dx + nyi * dy) / q.r;
+    const double sn = sin(PI * (double)(q.i - q.l) / n);
+    q.logsin = log(4 * sn * sn);
   }
+  double2 Sp, Dp, Tp, Sm, Dm, Tm;
+  kress_entries(q, make_double2(k0, 0), Sp, Dp, Tp);
+  const double2 km = make_double2(c.k_in_re, c.k_in_im);
+  kress_entries(q, km, Sm, Dm, Tm);
+  const double2 em = make_double2(c.eps_in_re, c.eps_in_im);
   C* A = Aptr[j];
   const size_t lda = ldA[j];
+  const int i = q.i, l = q.l;
   // [[-(e+ S+ + e- S-), D+ + D-], [-(D*+ + D*-), k+^2/e+ S+ o nn + k-^2/e- S- o nn (+ Maue part)]]
-  A[i + (size_t)l * lda] = mk((R)(-(Sre[0] + eps_in * Sre[1])), (R)(-(Sim[0] + eps_in * Sim[1])));
-  A[i + (size_t)(n + l) * lda] = mk((R)(Dre[0] + Dre[1]), (R)(Dim[0] + Dim[1]));
-  A[n + i + (size_t)l * lda] = mk((R)(-(Tre[0] + Tre[1])), (R)(-(Tim[0] + Tim[1])));
-  const double a0 = k0 * k0 * nn, a1 = ks[1] * ks[1] / eps_in * nn;
-  A[n + i + (size_t)(n + l) * lda] = mk((R)(a0 * Sre[0] + a1 * Sre[1]), (R)(a0 * Sim[0] + a1 * Sim[1]));
+  const double2 eS = zmul(em, Sm);
+  A[i + (size_t)l * lda] = mk((R)(-(Sp.x + eS.x)), (R)(-(Sp.y + eS.y)));
+  A[i + (size_t)(n + l) * lda] = mk((R)(Dp.x + Dm.x), (R)(Dp.y + Dm.y));
+  A[n + i + (size_t)l * lda] = mk((R)(-(Tp.x + Tm.x)), (R)(-(Tp.y + Tm.y)));
+  const double2 k2e = zdiv(zmul(km, km), em);
+  const double a0 = k0 * k0 * nn;
+  const double2 nS = zmul(make_double2(k2e.x * nn, k2e.y * nn), Sm);
+  A[n + i + (size_t)(n + l) * lda] = mk((R)(a0 * Sp.x + nS.x), (R)(a0 * Sp.y + nS.y));
   // Maue middle factor: S0+/e+ + S0-/e-, S0 = S / |x'(tau)|
+  const double2 Se = zdiv(Sm, em);
   C* Cm = Cptr[j];
-  Cm[i + (size_t)l * n] = mk((R)((Sre[0] + Sre[1] / eps_in) / spl), (R)((Sim[0] + Sim[1] / eps_in) / spl));
+  Cm[i + (size_t)l * n] = mk((R)((Sp.x + Se.x) / q.spl), (R)((Sp.y + Se.y) / q.spl));
 }
 
 template <typename C>

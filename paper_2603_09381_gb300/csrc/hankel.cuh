@@ -108,3 +108,52 @@ __device__ __forceinline__ void hankel01_inv(double z, double iz, double& J0, do
   if (z >= HK_ZA) hankel_asym(z, iz, J0, Y0, J1, Y1);
   else hankel_miller(z, J0, Y0, J1, Y1);
 }
+
+// ---- complex argument (lossy interior wavenumbers, self blocks only) ---------------
+// Same Miller / Neumann construction in complex arithmetic (principal branch
+// of the logarithm); valid for moderate |z| and Im z >= 0 (the self blocks
+// need |z| <= k- diam(Gamma)).
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 zlog(double2 a) { return make_double2(log(hypot(a.x, a.y)), atan2(a.y, a.x)); }
+
+__device__ __forceinline__ void bessel_complex(double2 z, double2& J0, double2& Y0, double2& J1, double2& Y1) {
+  const double az = hypot(z.x, z.y);
+  int M = (int)(az + 25.0 + 3.0 * sqrt(az));
+  M += (M & 1);
+  const double2 t2z = zdiv(make_double2(2.0, 0.0), z);
+  double2 jp1 = make_double2(0, 0), jn = make_double2(1e-30, 0);
+  double2 norm = make_double2(0, 0), s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+  for (int n = M; n >= 1; --n) {
+    if ((n & 1) == 0) {
+      const int k = n >> 1;
+      norm.x += 2.0 * jn.x; norm.y += 2.0 * jn.y;
+      const double c = ((k & 1) ? -1.0 : 1.0) / k;
+      s0.x += c * jn.x; s0.y += c * jn.y;
+    } else {
+      const int m = (n + 1) >> 1;
+      const double c = (m == 1) ? -1.0 : ((m & 1) ? -1.0 : 1.0) * (1.0 / m + 1.0 / (m - 1));
+      s1.x += c * jn.x; s1.y += c * jn.y;
+    }
+    const double2 a = zmul(make_double2(n * t2z.x, n * t2z.y), jn);
+    const double2 jm1 = make_double2(a.x - jp1.x, a.y - jp1.y);
+    jp1 = jn;
+    jn = jm1;
+  }
+  norm.x += jn.x; norm.y += jn.y;
+  const double2 inv = zdiv(make_double2(1, 0), norm);
+  J0 = zmul(jn, inv);
+  J1 = zmul(jp1, inv);
+  s0 = zmul(s0, inv);
+  s1 = zmul(s1, inv);
+  double2 lg = zlog(make_double2(0.5 * z.x, 0.5 * z.y));
+  lg.x += 0.57721566490153286061;
+  const double tp = 0.63661977236758134308;
+  const double2 a0 = zmul(lg, J0);
+  Y0 = make_double2(tp * (a0.x - 2.0 * s0.x), tp * (a0.y - 2.0 * s0.y));
+  const double2 q = zdiv(J0, z), a1 = zmul(lg, J1);
+  Y1 = make_double2(tp * (-q.x + a1.x + s1.x), tp * (-q.y + a1.y + s1.y));
+}

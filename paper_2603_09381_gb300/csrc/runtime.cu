@@ -286,8 +286,9 @@ void upload_inclusions(pm_geometry* g) {
     d.cx = c.cx; d.cy = c.cy; d.rot = c.rot;
     for (int i = 0; i < 16; ++i) d.prm[i] = c.prm[i];
     d.k_in_re = c.k_in.re; d.k_in_im = c.k_in.im;
-    double r = c.k_in.re / g->k0;
-    d.eps_in_re = r * r; d.eps_in_im = 0;
+    // eps- = (k- / k+)^2 (eps+ = 1), complex for a lossy interior
+    const double a = c.k_in.re / g->k0, b = c.k_in.im / g->k0;
+    d.eps_in_re = a * a - b * b; d.eps_in_im = 2 * a * b;
     g->hinc[j] = d;
   }
 }
@@ -1129,7 +1130,7 @@ pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out) {
       for (int i = 0; i < 16; ++i) if (!std::isfinite(c.prm[i])) fail(PM_ERR_INVALID_ARG, "non-finite shape parameter");
       if (!(c.prm[0] > 0)) fail(PM_ERR_INVALID_ARG, "shape size must be positive");
       if (!(c.k_in.re > 0)) fail(PM_ERR_INVALID_ARG, "k_in must have positive real part");
-      if (c.k_in.im != 0) fail(PM_ERR_UNSUPPORTED, "complex interior wavenumber not supported by this build");
+      if (!(c.k_in.im >= 0) || !std::isfinite(c.k_in.im)) fail(PM_ERR_INVALID_ARG, "k_in must have Im >= 0");
     }
     check_device();
     g = new pm_geometry();

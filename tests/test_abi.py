@@ -46,7 +46,7 @@ def test_invalid_arguments_rejected_before_device_use():
     with pytest.raises(pm.PmError) as e:
         pm.Geometry(prob)
     assert e.value.status == 1
-    prob = wl.circle_grid(1, 1, k_in=3 + 0.1j)
+    prob = wl.circle_grid(1, 1, k_in=3 - 0.1j)   # gain medium: Im k- < 0 is rejected
     with pytest.raises(pm.PmError) as e:
         pm.Geometry(prob)
-    assert e.value.status == 8
+    assert e.value.status == 1

@@ -28,6 +28,7 @@ def _mixed_problem():
     prob["inclusions"][2] = wl._inclusion(wl.SHAPE_FOURIER, 0.0, 1.0, 0.0,
                                           [0.4, .04, .01, .03, .02, .04, 1, 2, 3, 4, 5], 80, 20.0)
     prob["inclusions"][3] = wl._inclusion(wl.SHAPE_CIRCLE, 1.0, 1.0, 0.3, [0.35], 32, 9.0)
+    prob["inclusions"][0]["k_in"] = 15.7 * (1 + 0.05j)   # a lossy interior
     return prob
 
 
@@ -203,3 +204,24 @@ def test_offdiagonal_entries_large_arguments(pm):
     err = np.abs(got - ref)
     assert np.max(err) < 1e-13 * np.max(np.abs(ref))
     assert np.max(err / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))) < 1e-11
+
+
+# ---- lossy interiors (complex k-), FP64 and mixed ---------------------------------
+
+def test_lossy_small_circles_fp64_and_mixed(pm):
+    prob, opts, angs = wl.config_lossy_small()
+    g = pm.Geometry(prob)
+    ref = dense.solve(prob, angs)
+    f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"])
+    assert _rel(f.solve(g.plane_wave(angs)), ref) < 1e-10
+    fm = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=pm.PM_MIXED)
+    phi = fm.solve(g.plane_wave(angs))
+    assert fm.last_info["residual"] <= 1e-10
+    assert _rel(phi, ref) < 1e-8
+    # the lossy Mie / multipole solution as an independent check
+    k1 = prob["inclusions"][0]["k_in"]
+    U, Q, M = mie.disks_solution([(i["cx"], i["cy"]) for i in prob["inclusions"]], 0.4, prob["k_out"], k1,
+                                 (k1 / prob["k_out"]) ** 2, angs[0])
+    th = geometry.nodes(prob["inclusions"][0])["t"]
+    exact = np.concatenate([np.concatenate(mie.boundary_values(U[j], Q[j], th, M)[::-1]) for j in range(4)])
+    assert _rel(phi[:, 0], exact) < 1e-9
