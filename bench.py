@@ -168,14 +168,14 @@ FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "
                 "apply_offdiag64"}
 
 
-def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup):
+def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None):
     """Warm-up, then `steps` timed factor + solve passes on the stream; returns per-step numbers."""
     import torch
     nrhs = len(angs)
 
     def step(profile):
         f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
-                      stream=stream.cuda_stream, profile=profile)
+                      stream=stream.cuda_stream, profile=profile, rank_model=model_ptr)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         info = f.solve_device(F.data_ptr(), nrhs, X.data_ptr())
@@ -253,11 +253,19 @@ def run_ours(args):
     g.plane_wave_device(angs, F.data_ptr())
     torch.cuda.synchronize()
     precision = pm.PM_MIXED if args.precision == "mixed" else pm.PM_FP64
+    # the learned rank predictor (trained by the library's own kernels) presizes the CPQR rank search
+    model_dev, model_ptr = None, None
+    if not args.no_rank_model:
+        from paper_2603_09381_gb300 import rank_predictor as rp
+        mdl = rp.load_model()
+        if mdl is not None:
+            model_dev = rp.to_device(mdl)
+            model_ptr = model_dev.data_ptr()
     if ws > 1:
         torch.distributed.barrier()
     with Clocks(local) as clk:
         ms, solve, prof_tot, st, info, launches = _timed(pm, g, prob, opts, angs, F, X, stream, precision,
-                                                        args.steps, args.warmup)
+                                                        args.steps, args.warmup, model_ptr)
     if ws > 1:
         tt = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -277,7 +285,7 @@ def run_ours(args):
     for _ in range(args.steps):
         g2 = pm.Geometry(prob)
         f2 = pm.Factor(g2, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
-                       stream=stream.cuda_stream)
+                       stream=stream.cuda_stream, rank_model=model_ptr)
         inf2 = pm.pm_solve_info()
         pm._check(pm.load().pm_solve_ex(f2.h, rhs_host.data_ptr(), nrhs, out_host.data_ptr(), 0,
                                         pm.ct.byref(inf2)))
@@ -315,6 +323,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (factor working set > 1 GB)", "parallelism": f"replicas{ws}"},
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
             "refinement": info,
+            "rank_predictor": {"used": model_ptr is not None, "cpqr_launches": st["cpqr_launches"],
+                               "rank_checks": st["rank_checks"], "fallbacks": st["predictor_fallbacks"]},
             "phase_ms": {k: st[k] for k in ("ms_assemble", "ms_id", "ms_schur", "ms_top")},
             "roofline": _roofline(prof_tot, args.steps), "kernels": _kernel_table(prof_tot, args.steps),
             "gpu_launches": int(launches),
@@ -334,6 +344,39 @@ def run_ours(args):
     return 0
 
 
+def run_batch_workload(args):
+    """64 independent ellipse problems (uneven m and n) factored and solved concurrently."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_09381_gb300 import pmchwt as pm
+    from paper_2603_09381_gb300 import workloads as wl
+    probs = wl.ellipse_batch(count=args.batch_count, seed=3, m_hi=args.batch_m_hi)
+    geoms = [pm.Geometry(p) for p in probs]
+    N = sum(g.N for g in geoms)
+    angs = wl.plane_wave_angles(8)
+    rhs = [g.plane_wave(angs) for g in geoms]
+    prec = pm.PM_MIXED if args.precision == "mixed" else pm.PM_FP64
+    for _ in range(args.warmup):
+        pm.solve_batch(pm.factor_batch(geoms, 1e-10, precision=prec, workers=args.workers), rhs, workers=args.workers)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        facs = pm.factor_batch(geoms, 1e-10, precision=prec, workers=args.workers)
+        pm.solve_batch(facs, rhs, workers=args.workers)
+        del facs
+    torch.cuda.synchronize()
+    s = (time.perf_counter() - t) / args.steps
+    print(json.dumps({"metric": METRIC, "value": N / s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * s, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "c64+c128" if prec == pm.PM_MIXED else "c128",
+                      "data": "synthetic",
+                      "config": {"workload": f"{len(probs)} ellipse problems, m~U{{4..{args.batch_m_hi}}}, "
+                                             f"n in 64..256, N total {N}, tol 1e-10, 8 RHS each",
+                                 "workers": args.workers, "precision": args.precision}}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,12 +384,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="star16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="star16", choices=sorted(WORKLOADS) + ["ellipse_batch"])
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-m-hi", type=int, default=400)
+    ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-rank-model", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ellipse_batch":
+        return run_batch_workload(args)
     return run_ours(args)
 
 

@@ -94,7 +94,13 @@ typedef struct pm_factor pm_factor;
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
  *      refine_tol returns PM_ERR_NOT_CONVERGED.
- * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 1e-5). */
+ * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 1e-5).
+ * rank_model: NULL, or a trained rank predictor on the device (float32:
+ *      PM_MLP_NPARAM weights, then 8 feature means and 8 feature scales); the
+ *      CPQR of every level then runs up to the median predicted rank before its
+ *      first rank check (host synchronisation) instead of checking every 16
+ *      steps; IDs whose rank exceeds the prediction continue under the regular
+ *      checks, so the factorization is the same with or without it. */
 typedef struct {
   double tol;
   double proxy_factor;
@@ -105,6 +111,7 @@ typedef struct {
   double refine_tol;
   int32_t max_refine;
   double low_tol;
+  const float* rank_model;
 } pm_factor_opts;
 
 /* Outcome of a refined solve (PM_MIXED): steps taken, the final largest
@@ -123,6 +130,9 @@ typedef struct {
   int32_t K;                /* size of the top-level dense system */
   int32_t skeleton[16];     /* sum of box ranks per level, index = level (1..L) */
   double ms_assemble, ms_id, ms_schur, ms_top, ms_total;   /* factor phase times */
+  int32_t cpqr_launches;    /* CPQR elimination-step launches */
+  int32_t rank_checks;      /* device-to-host rank checks (host synchronisations) */
+  int32_t predictor_fallbacks;  /* IDs whose rank exceeded the predicted bound */
 } pm_stats;
 
 /* Build node geometry on the device (paper Sec. 2.2) and the quadtree
@@ -163,6 +173,19 @@ pm_status pm_solve(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* 
 pm_status pm_solve_ex(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
                       pm_solve_info* info);
 
+/* Many independent problems (no counterpart in the paper; the paper factors
+ * one system at a time).  pm_factor_batch factors g[0..count) with `workers`
+ * host threads (0 -> 8), each driving its own CUDA stream, so the problems'
+ * kernels overlap on the GPU; out[i] receives each handle (all NULL on
+ * error, which names the failing problem).  opts->stream is ignored; the
+ * returned handles run later pm_solve calls on the default stream.
+ * pm_solve_batch solves each factor for its own right-hand sides rhs[i] ->
+ * phi[i] (N_i x nrhs each), concurrently in the same way. */
+pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_factor_opts* opts, pm_factor** out,
+                          int32_t workers);
+pm_status pm_solve_batch(const pm_factor* const* f, int32_t count, const pm_c64* const* rhs, int32_t nrhs,
+                         pm_c64* const* phi, int32_t on_device, int32_t workers);
+
 pm_status pm_factor_stats(const pm_factor* f, pm_stats* out);
 
 /* Skeleton (selected) global row / column indices of one box, for inspection.
@@ -196,6 +219,31 @@ typedef struct {
 } pm_kernel_stat;
 enum { PM_FLAG_PROFILE = 1 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
+
+/* ---- learned ID-rank predictor (no counterpart in the paper) ----------------
+ * An MLP 8 -> 64 -> 64 -> 2 (tanh) maps features of a box and index group
+ * (log n_g, log W of the row and column ID inputs, k+ r_cell, log10 tol,
+ * log2 of the box's inclusions, the group, mean k-/k+) to the adaptive ranks
+ * of its row and column IDs divided by n_g.  Parameters: one flat array of
+ * PM_MLP_NPARAM numbers (row-major W1 64x8, b1, W2 64x64, b2, W3 2x64, b3).
+ * Loss (1/B) sum (1 + lam [y < t]) (y - t)^2; Adam.  All pointers except
+ * the host arrays of pm_factor_rank_data / pm_mlp_train's X, T and
+ * loss_history are device pointers; dtype 0 = float32, 1 = float64. */
+enum { PM_MLP_NPARAM = 4866 };
+/* Training samples recorded by a factorization: X (count x 8), T (count x 2), host. */
+pm_status pm_factor_rank_data(const pm_factor* f, float* X, float* T, int32_t cap, int32_t* count);
+pm_status pm_mlp_forward(int32_t dtype, const void* theta, int32_t B, const void* X, void* Y, void* stream);
+/* loss (1 value) and gradient (PM_MLP_NPARAM) of a batch, overwritten. */
+pm_status pm_mlp_loss_grad(int32_t dtype, const void* theta, int32_t B, const void* X, const void* T, double lam,
+                           void* grad, void* loss, void* stream);
+pm_status pm_mlp_adam_step(int32_t dtype, void* theta, const void* grad, void* m, void* v, int32_t t, double lr,
+                           double b1, double b2, double eps, void* stream);
+/* Train float32 parameters in place: epochs of shuffled minibatches (splitmix64
+ * with `seed`), Adam (b1 0.9, b2 0.999, eps 1e-8).  X, T: device, row-major
+ * nsamples x 8 / x 2 (features already standardised); loss_history: host,
+ * one mean loss per epoch, or NULL. */
+pm_status pm_mlp_train(void* theta, int32_t nsamples, const float* X, const float* T, int32_t epochs, int32_t batch,
+                       double lr, double lam, uint64_t seed, double* loss_history, void* stream);
 
 /* Number of CUDA kernel launches this library has made in this process
  * (no counterpart in the paper; measurement aid). */

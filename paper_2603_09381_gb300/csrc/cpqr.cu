@@ -13,6 +13,8 @@
 #include "cpqr.cuh"
 #include "prof.cuh"
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 namespace {
 
@@ -221,11 +223,8 @@ __global__ void k_complete_perm(const PermFill* __restrict__ P) {
 
 void complete_perm(const PermFill* d_prob, int nprob, cudaStream_t st) {
   if (nprob <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_complete_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-    attr = true;
-  }
+  static std::once_flag attr;
+  std::call_once(attr, [] { cudaFuncSetAttribute(k_complete_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536); });
   k_complete_perm<<<nprob, 256, 65536, st>>>(d_prob);
   pm_launch_count_add(1);
 }
@@ -240,13 +239,15 @@ template <typename C>
 void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
                cudaStream_t st) {
   if (nchunk <= 0) return;
-  static int grid = 0;
+  static std::atomic<int> grid_cache{0};
+  int grid = grid_cache.load();
   if (grid == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cpqr_step<C>, 256, 0);
     grid = std::max(1, sms * std::max(per, 1));
+    grid_cache.store(grid);
   }
   KPROF_BEGIN(st);
   k_cpqr_step<C><<<std::min(grid, nchunk), 256, 0, st>>>(d_prob, d_chunk, nchunk, t, d_counter);

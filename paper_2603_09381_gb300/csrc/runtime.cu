@@ -9,6 +9,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -17,6 +18,7 @@
 #include "assemble.cuh"
 #include "cpqr.cuh"
 #include "dense_la.cuh"
+#include "mlp.cuh"
 #include "operator.cuh"
 #include "prof.cuh"
 
@@ -179,6 +181,8 @@ struct pm_factor {
   std::vector<std::vector<Box>> tree;  // the geometry's quadtree with this factorization's proxies
   KProf prof;
   bool profiling = false;
+  // learned rank predictor: features and adaptive ranks of every (box, group)
+  std::vector<float> rank_X, rank_T;
   // mixed mode: FP64 self blocks (operator for the refinement residual)
   std::vector<double2*> self64;
   int* d_iu = nullptr;
@@ -611,6 +615,51 @@ void process_level(pm_factor* F, int lev, double tol) {
   gb.run(scr, P, g->k0, st);
   F->stats.ms_assemble += t_asm.stop();
   Timer t_id(st);
+  // features of every (box, group) for the learned rank predictor
+  std::vector<float> feat(2 * (size_t)nb * MLP_IN);
+  for (int b = 0; b < nb; ++b) {
+    double kin = 0;
+    for (int j : boxes[b].leaves) kin += g->inc[j].k_in.re;
+    kin /= std::max<size_t>(boxes[b].leaves.size(), 1);
+    for (int grp = 0; grp < 2; ++grp) {
+      float* f = &feat[(2 * (size_t)b + grp) * MLP_IN];
+      f[0] = (float)std::log((double)std::max(nn[4 * b + grp], 1));
+      f[1] = (float)std::log((double)std::max(W[4 * b + grp], 1));
+      f[2] = (float)std::log((double)std::max(W[4 * b + 2 + grp], 1));
+      f[3] = (float)(g->k0 * boxes[b].r_cell);
+      f[4] = (float)std::log10(tol);
+      f[5] = (float)std::log2((double)boxes[b].leaves.size());
+      f[6] = (float)grp;
+      f[7] = (float)(kin / g->k0);
+    }
+  }
+  std::vector<int> khat;   // predicted rank bound per ID (empty: no predictor)
+  if (F->opts.rank_model) {
+    const float* mdl = F->opts.rank_model;   // theta | mean (8) | std (8), device
+    std::vector<float> musd(2 * MLP_IN);
+    CK(cudaMemcpyAsync(musd.data(), mdl + MLP_NPARAM, sizeof(float) * 2 * MLP_IN, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<float> xn(feat.size());
+    for (size_t i = 0; i < feat.size(); ++i) {
+      const int c = (int)(i % MLP_IN);
+      xn[i] = (feat[i] - musd[c]) / (musd[MLP_IN + c] > 0 ? musd[MLP_IN + c] : 1.f);
+    }
+    float* dx = upload(scr, xn, st);
+    float* dy = scr.get<float>(2 * (size_t)nb * MLP_OUT);
+    mlp_forward<float>(mdl, 2 * nb, dx, dy, st);
+    std::vector<float> yp(2 * (size_t)nb * MLP_OUT);
+    CK(cudaMemcpyAsync(yp.data(), dy, sizeof(float) * yp.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    khat.assign(nid, 0);
+    for (int b = 0; b < nb; ++b)
+      for (int grp = 0; grp < 2; ++grp) {
+        const float* y = &yp[(2 * (size_t)b + grp) * MLP_OUT];
+        const int n = nn[4 * b + grp];
+        const double frac = std::min(1.0, std::max(0.0, (double)std::max(y[0], y[1])));
+        const int k = std::min(n, (int)std::ceil(frac * n + 2 + 0.02 * n));
+        khat[4 * b + grp] = khat[4 * b + 2 + grp] = k;
+      }
+  }
   // 3. CPQR with rank detection
   int total_n = 0;
   std::vector<int> noff(nid + 1, 0);
@@ -642,14 +691,35 @@ void process_level(pm_factor* F, int lev, double tol) {
   const int nch = (int)chunks.size();
   cpqr_init_norms<C>(dcp, dch, nch, st);
   std::vector<int> hr(nid);
+  // With predicted ranks, run the predicted number of steps (+1, where the stop
+  // test of the last rank happens) before the first check; otherwise check
+  // every 16 steps.  Launches and results are the same either way.
+  int first_check = 15;
+  if (!khat.empty()) {
+    // first check once half of the IDs should have found their rank; the rest
+    // (over- or under-predicted bounds) finish under the regular 16-step checks
+    std::vector<int> due;
+    for (int i = 0; i < nid; ++i)
+      if (cp[i].target > 0) due.push_back(std::min(cp[i].target, khat[i] + 1) - 1);
+    if (!due.empty()) {
+      std::sort(due.begin(), due.end());
+      first_check = std::max(0, due[(due.size() - 1) / 2]);
+    }
+  }
   for (int t = 0; t < maxT; ++t) {
     cpqr_step<C>(dcp, dch, nch, t, ctr + t, st);
-    if ((t % 16 == 15) || t == maxT - 1) {
+    F->stats.cpqr_launches++;
+    const bool check = khat.empty() ? ((t % 16 == 15) || t == maxT - 1)
+                                    : (t == first_check || (t > first_check && ((t - first_check) % 16 == 0)) ||
+                                       t == maxT - 1);
+    if (check) {
       CK(cudaMemcpyAsync(hr.data(), rank, nid * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      bool all = true;
-      for (int i = 0; i < nid; ++i) if (hr[i] < 0 && t + 1 < cp[i].target) { all = false; break; }
-      if (all) break;
+      F->stats.rank_checks++;
+      int pending = 0;
+      for (int i = 0; i < nid; ++i) if (hr[i] < 0 && t + 1 < cp[i].target) ++pending;
+      if (!khat.empty() && t == first_check) F->stats.predictor_fallbacks += pending;
+      if (pending == 0) break;
     }
   }
   CK(cudaGetLastError());
@@ -676,8 +746,18 @@ void process_level(pm_factor* F, int lev, double tol) {
   if (maxExt > 0) {
     dcp = upload(scr, cp, st);
     for (int t = 0; t < maxExt; ++t) cpqr_step<C>(dcp, dch, nch, t, ctr + maxT + t, st);
+    F->stats.cpqr_launches += maxExt;
     CK(cudaGetLastError());
   }
+  // training data for the rank predictor: features -> (row rank, column rank) / n
+  for (int b = 0; b < nb; ++b)
+    for (int grp = 0; grp < 2; ++grp) {
+      const float* f = &feat[(2 * (size_t)b + grp) * MLP_IN];
+      F->rank_X.insert(F->rank_X.end(), f, f + MLP_IN);
+      const double n = std::max(nn[4 * b + grp], 1);
+      F->rank_T.push_back((float)(r[4 * b + grp] / n));
+      F->rank_T.push_back((float)(r[4 * b + 2 + grp] / n));
+    }
   {
     // the unchosen columns follow the pivots, ascending (defines the column order of T)
     std::vector<PermFill> pf;
@@ -1274,8 +1354,9 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
   return PM_OK;
 }
 
-pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
-                      pm_solve_info* info) {
+namespace {
+pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
+                     pm_solve_info* info, cudaStream_t st) {
   if (!Fc || !rhs || !phi || nrhs < 1) { g_err = "pm_solve: bad argument"; return PM_ERR_INVALID_ARG; }
   if (info) {
     std::memset(info, 0, sizeof(*info));
@@ -1284,7 +1365,6 @@ pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c
   pm_factor* F = const_cast<pm_factor*>(Fc);
   return run_guarded("pm_solve", [&] {
     Arena ws;
-    cudaStream_t st = F->st;
     const size_t bytes = sizeof(Cd) * (size_t)F->g->N * nrhs;
     const Cd* drhs = (const Cd*)rhs;
     Cd* dphi = (Cd*)phi;
@@ -1309,9 +1389,72 @@ pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c
     if (F->profiling) F->prof.collect();
   });
 }
+}  // namespace
+
+pm_status pm_solve_ex(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device,
+                      pm_solve_info* info) {
+  return solve_impl(Fc, rhs, nrhs, phi, on_device, info, Fc ? Fc->st : nullptr);
+}
 
 pm_status pm_solve(const pm_factor* F, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device) {
   return pm_solve_ex(F, rhs, nrhs, phi, on_device, nullptr);
+}
+
+// Independent problems factored concurrently: `workers` host threads, each
+// with its own CUDA stream, take problems from a shared counter.
+namespace {
+pm_status run_batch(int count, int workers, const std::function<pm_status(int, cudaStream_t)>& one) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { g_err = "batch: no CUDA device"; return PM_ERR_CUDA; }
+  workers = std::max(1, std::min(workers, count));
+  std::atomic<int> next{0};
+  std::vector<pm_status> st(count, PM_OK);
+  std::vector<std::string> msg(count);
+  auto body = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      st[i] = one(i, s);
+      if (st[i] != PM_OK) msg[i] = g_err;
+    }
+    if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < workers; ++w) th.emplace_back(body);
+  body();
+  for (auto& t : th) t.join();
+  for (int i = 0; i < count; ++i)
+    if (st[i] != PM_OK) { g_err = "problem " + std::to_string(i) + ": " + msg[i]; return st[i]; }
+  return PM_OK;
+}
+}  // namespace
+
+pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_factor_opts* opts, pm_factor** out,
+                          int32_t workers) {
+  if (!g || !opts || !out || count < 1) { g_err = "pm_factor_batch: bad argument"; return PM_ERR_INVALID_ARG; }
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  pm_status s = run_batch(count, workers > 0 ? workers : 8, [&](int i, cudaStream_t st) {
+    pm_factor_opts o = *opts;
+    o.stream = st;
+    pm_status r = pm_factorize(g[i], &o, &out[i]);
+    if (out[i]) out[i]->st = nullptr;   // the worker streams end with the batch
+    return r;
+  });
+  if (s != PM_OK) {
+    for (int i = 0; i < count; ++i) { delete out[i]; out[i] = nullptr; }
+  }
+  return s;
+}
+
+pm_status pm_solve_batch(const pm_factor* const* f, int32_t count, const pm_c64* const* rhs, int32_t nrhs,
+                         pm_c64* const* phi, int32_t on_device, int32_t workers) {
+  if (!f || !rhs || !phi || count < 1 || nrhs < 1) { g_err = "pm_solve_batch: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_batch(count, workers > 0 ? workers : 8, [&](int i, cudaStream_t st) {
+    return solve_impl(f[i], rhs[i], nrhs, phi[i], on_device, nullptr, st);
+  });
 }
 
 pm_status pm_factor_stats(const pm_factor* F, pm_stats* out) {
@@ -1400,6 +1543,118 @@ pm_status pm_factor_profile(const pm_factor* F, pm_kernel_stat* out, int32_t cap
   }
   *count = i;
   return PM_OK;
+}
+
+pm_status pm_factor_rank_data(const pm_factor* F, float* X, float* T, int32_t cap, int32_t* count) {
+  if (!F || !count) { g_err = "pm_factor_rank_data: NULL argument"; return PM_ERR_INVALID_ARG; }
+  const int n = (int)(F->rank_X.size() / MLP_IN);
+  *count = n;
+  for (int i = 0; i < std::min(cap, n); ++i) {
+    if (X) std::memcpy(X + (size_t)i * MLP_IN, &F->rank_X[(size_t)i * MLP_IN], sizeof(float) * MLP_IN);
+    if (T) std::memcpy(T + (size_t)i * MLP_OUT, &F->rank_T[(size_t)i * MLP_OUT], sizeof(float) * MLP_OUT);
+  }
+  return PM_OK;
+}
+
+pm_status pm_mlp_forward(int32_t dtype, const void* theta, int32_t B, const void* X, void* Y, void* stream) {
+  if (!theta || !X || !Y || B < 0 || (dtype != 0 && dtype != 1)) { g_err = "pm_mlp_forward: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_mlp_forward", [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == 0) mlp_forward<float>((const float*)theta, B, (const float*)X, (float*)Y, st);
+    else mlp_forward<double>((const double*)theta, B, (const double*)X, (double*)Y, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+pm_status pm_mlp_loss_grad(int32_t dtype, const void* theta, int32_t B, const void* X, const void* T, double lam,
+                           void* grad, void* loss, void* stream) {
+  if (!theta || !X || !T || !grad || !loss || B < 1 || (dtype != 0 && dtype != 1)) {
+    g_err = "pm_mlp_loss_grad: bad argument";
+    return PM_ERR_INVALID_ARG;
+  }
+  return run_guarded("pm_mlp_loss_grad", [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == 0) {
+      CK(cudaMemsetAsync(grad, 0, sizeof(float) * MLP_NPARAM, st));
+      CK(cudaMemsetAsync(loss, 0, sizeof(float), st));
+      mlp_loss_grad<float>((const float*)theta, B, (const float*)X, (const float*)T, lam, (float*)grad, (float*)loss, st);
+    } else {
+      CK(cudaMemsetAsync(grad, 0, sizeof(double) * MLP_NPARAM, st));
+      CK(cudaMemsetAsync(loss, 0, sizeof(double), st));
+      mlp_loss_grad<double>((const double*)theta, B, (const double*)X, (const double*)T, lam, (double*)grad,
+                            (double*)loss, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+pm_status pm_mlp_adam_step(int32_t dtype, void* theta, const void* grad, void* m, void* v, int32_t t, double lr,
+                           double b1, double b2, double eps, void* stream) {
+  if (!theta || !grad || !m || !v || t < 1 || (dtype != 0 && dtype != 1)) { g_err = "pm_mlp_adam_step: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_mlp_adam_step", [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == 0) mlp_adam<float>((float*)theta, (const float*)grad, (float*)m, (float*)v, t, lr, b1, b2, eps, st);
+    else mlp_adam<double>((double*)theta, (const double*)grad, (double*)m, (double*)v, t, lr, b1, b2, eps, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+pm_status pm_mlp_train(void* theta, int32_t nsamples, const float* X, const float* T, int32_t epochs, int32_t batch,
+                       double lr, double lam, uint64_t seed, double* loss_history, void* stream) {
+  if (!theta || !X || !T || nsamples < 1 || epochs < 1 || batch < 1) { g_err = "pm_mlp_train: bad argument"; return PM_ERR_INVALID_ARG; }
+  return run_guarded("pm_mlp_train", [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena ws;
+    ws.min_block = 1 << 20;
+    float* th = (float*)theta;
+    float* g = ws.get<float>(MLP_NPARAM);
+    float* mm = ws.get<float>(MLP_NPARAM);
+    float* vv = ws.get<float>(MLP_NPARAM);
+    float* loss = ws.get<float>(1);
+    float* xb = ws.get<float>((size_t)batch * MLP_IN);
+    float* tb = ws.get<float>((size_t)batch * MLP_OUT);
+    int* idx = ws.get<int>(nsamples);
+    CK(cudaMemsetAsync(mm, 0, sizeof(float) * MLP_NPARAM, st));
+    CK(cudaMemsetAsync(vv, 0, sizeof(float) * MLP_NPARAM, st));
+    std::vector<int> perm(nsamples);
+    uint64_t state = seed;
+    auto next = [&]() {  // splitmix64
+      uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    int step = 0;
+    for (int e = 0; e < epochs; ++e) {
+      for (int i = 0; i < nsamples; ++i) perm[i] = i;
+      for (int i = nsamples - 1; i > 0; --i) std::swap(perm[i], perm[(int)(next() % (uint64_t)(i + 1))]);
+      CK(cudaMemcpyAsync(idx, perm.data(), sizeof(int) * nsamples, cudaMemcpyHostToDevice, st));
+      double esum = 0;
+      int nb = 0;
+      for (int b0 = 0; b0 < nsamples; b0 += batch) {
+        const int B = std::min(batch, nsamples - b0);
+        mlp_gather_rows<float>(X, idx + b0, B, MLP_IN, xb, st);
+        mlp_gather_rows<float>(T, idx + b0, B, MLP_OUT, tb, st);
+        CK(cudaMemsetAsync(g, 0, sizeof(float) * MLP_NPARAM, st));
+        CK(cudaMemsetAsync(loss, 0, sizeof(float), st));
+        mlp_loss_grad<float>(th, B, xb, tb, lam, g, loss, st);
+        mlp_adam<float>(th, g, mm, vv, ++step, lr, 0.9, 0.999, 1e-8, st);
+        if (loss_history) {
+          float hl = 0;
+          CK(cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          esum += hl;
+          ++nb;
+        }
+      }
+      if (loss_history) loss_history[e] = nb ? esum / nb : 0;
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
 }
 
 pm_status pm_launch_counter(uint64_t* out) {

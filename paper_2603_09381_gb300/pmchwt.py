@@ -41,7 +41,8 @@ class pm_problem(ct.Structure):
 class pm_factor_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("proxy_factor", ct.c_double), ("proxy_points", ct.c_int32),
                 ("precision", ct.c_int32), ("stream", ct.c_void_p), ("flags", ct.c_uint32),
-                ("refine_tol", ct.c_double), ("max_refine", ct.c_int32), ("low_tol", ct.c_double)]
+                ("refine_tol", ct.c_double), ("max_refine", ct.c_int32), ("low_tol", ct.c_double),
+                ("rank_model", ct.c_void_p)]
 
 
 class pm_solve_info(ct.Structure):
@@ -51,7 +52,8 @@ class pm_solve_info(ct.Structure):
 class pm_stats(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("N", ct.c_int32), ("K", ct.c_int32), ("skeleton", ct.c_int32 * 16),
                 ("ms_assemble", ct.c_double), ("ms_id", ct.c_double), ("ms_schur", ct.c_double),
-                ("ms_top", ct.c_double), ("ms_total", ct.c_double)]
+                ("ms_top", ct.c_double), ("ms_total", ct.c_double), ("cpqr_launches", ct.c_int32),
+                ("rank_checks", ct.c_int32), ("predictor_fallbacks", ct.c_int32)]
 
 
 class pm_kernel_stat(ct.Structure):
@@ -71,12 +73,23 @@ EXPORTS = {
     "pm_solve_ex": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32,
                                ct.POINTER(pm_solve_info)]),
     "pm_factor_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(pm_stats)]),
+    "pm_factor_batch": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.POINTER(pm_factor_opts), ct.c_void_p, ct.c_int32]),
+    "pm_solve_batch": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32,
+                                  ct.c_int32]),
     "pm_factor_skeleton": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32,
                                       ct.POINTER(ct.c_int32)]),
     "pm_matrix_entries": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_self_block": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_factor_profile": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_launch_counter": (ct.c_int, [ct.POINTER(ct.c_uint64)]),
+    "pm_factor_rank_data": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "pm_mlp_forward": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "pm_mlp_loss_grad": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_double,
+                                    ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "pm_mlp_adam_step": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32,
+                                    ct.c_double, ct.c_double, ct.c_double, ct.c_double, ct.c_void_p]),
+    "pm_mlp_train": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32,
+                                ct.c_double, ct.c_double, ct.c_uint64, ct.c_void_p, ct.c_void_p]),
     "pm_self_block_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
@@ -178,13 +191,15 @@ class Geometry:
 
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
-                 profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0):
+                 profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None):
+        """rank_model: device pointer (int) of a trained predictor, or None."""
         lib = load()
         self.geom = geom
         self.last_info = None
         o = pm_factor_opts(float(tol), float(proxy_factor), int(proxy_points), int(precision),
                            ct.c_void_p(stream) if stream else None, PM_FLAG_PROFILE if profile else 0,
-                           float(refine_tol), int(max_refine), float(low_tol))
+                           float(refine_tol), int(max_refine), float(low_tol),
+                           ct.c_void_p(rank_model) if rank_model else None)
         h = ct.c_void_p()
         _check(lib.pm_factorize(geom.h, ct.byref(o), ct.byref(h)))
         self.h = h
@@ -194,7 +209,17 @@ class Factor:
         _check(load().pm_factor_stats(self.h, ct.byref(s)))
         return {"levels": s.levels, "N": s.N, "K": s.K, "skeleton": list(s.skeleton)[: s.levels + 1],
                 "ms_assemble": s.ms_assemble, "ms_id": s.ms_id, "ms_schur": s.ms_schur, "ms_top": s.ms_top,
-                "ms_total": s.ms_total}
+                "ms_total": s.ms_total, "cpqr_launches": s.cpqr_launches, "rank_checks": s.rank_checks,
+                "predictor_fallbacks": s.predictor_fallbacks}
+
+    def rank_data(self):
+        """(X, T): features (n x 8) and adaptive ranks / n_g (n x 2) of every box and group."""
+        cnt = ct.c_int32()
+        _check(load().pm_factor_rank_data(self.h, None, None, 0, ct.byref(cnt)))
+        X = np.zeros((cnt.value, 8), dtype=np.float32)
+        T = np.zeros((cnt.value, 2), dtype=np.float32)
+        _check(load().pm_factor_rank_data(self.h, X.ctypes.data, T.ctypes.data, cnt.value, ct.byref(cnt)))
+        return X, T
 
     def profile(self):
         cnt = ct.c_int32()
@@ -234,3 +259,61 @@ class Factor:
         if getattr(self, "h", None) and _lib is not None:
             _lib.pm_factor_free(self.h)
             self.h = None
+
+
+def mlp_forward(dtype, theta_ptr, B, x_ptr, y_ptr, stream=None):
+    _check(load().pm_mlp_forward(dtype, theta_ptr, B, x_ptr, y_ptr, stream))
+
+
+def mlp_loss_grad(dtype, theta_ptr, B, x_ptr, t_ptr, lam, grad_ptr, loss_ptr, stream=None):
+    _check(load().pm_mlp_loss_grad(dtype, theta_ptr, B, x_ptr, t_ptr, lam, grad_ptr, loss_ptr, stream))
+
+
+def mlp_adam_step(dtype, theta_ptr, grad_ptr, m_ptr, v_ptr, t, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _check(load().pm_mlp_adam_step(dtype, theta_ptr, grad_ptr, m_ptr, v_ptr, t, lr, b1, b2, eps, stream))
+
+
+def mlp_train(theta_ptr, nsamples, x_ptr, t_ptr, epochs, batch, lr, lam, seed, stream=None):
+    hist = np.zeros(epochs)
+    _check(load().pm_mlp_train(theta_ptr, nsamples, x_ptr, t_ptr, epochs, batch, lr, lam, seed,
+                               hist.ctypes.data, stream))
+    return hist
+
+
+class _Handle:
+    """A factor handle produced by factor_batch (same interface as Factor)."""
+
+    def __init__(self, geom, h):
+        self.geom, self.h, self.last_info = geom, h, None
+
+    stats = Factor.stats
+    solve = Factor.solve
+    solve_device = Factor.solve_device
+    skeleton = Factor.skeleton
+    profile = Factor.profile
+    __del__ = Factor.__del__
+
+
+def factor_batch(geoms, tol, precision=PM_FP64, workers=8, rank_model=None, **kw):
+    """Factor independent problems concurrently (one stream per worker thread)."""
+    n = len(geoms)
+    o = pm_factor_opts(float(tol), float(kw.get("proxy_factor", 1.5)), int(kw.get("proxy_points", 0)),
+                       int(precision), None, 0, float(kw.get("refine_tol", 0.0)), int(kw.get("max_refine", 0)),
+                       float(kw.get("low_tol", 0.0)), ct.c_void_p(rank_model) if rank_model else None)
+    gh = (ct.c_void_p * n)(*[g.h.value for g in geoms])
+    out = (ct.c_void_p * n)()
+    _check(load().pm_factor_batch(gh, n, ct.byref(o), out, workers))
+    return [_Handle(g, ct.c_void_p(out[i])) for i, g in enumerate(geoms)]
+
+
+def solve_batch(factors, rhs_list, workers=8):
+    """Host right-hand sides (N_i x nrhs complex128 each) -> solutions, solved concurrently."""
+    n = len(factors)
+    nrhs = rhs_list[0].shape[1]
+    bufs = [np.ascontiguousarray(r.T) for r in rhs_list]
+    outs = [np.zeros_like(b) for b in bufs]
+    fh = (ct.c_void_p * n)(*[f.h.value for f in factors])
+    rp = (ct.c_void_p * n)(*[b.ctypes.data for b in bufs])
+    op = (ct.c_void_p * n)(*[o.ctypes.data for o in outs])
+    _check(load().pm_solve_batch(fh, n, rp, nrhs, op, 0, workers))
+    return [o.T for o in outs]

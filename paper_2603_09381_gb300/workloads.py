@@ -86,15 +86,17 @@ def fourier_grid(nx, ny, n=128, seed=4, k_out=5.0, spacing=1.0, r0=0.4, amax=0.0
             "spacing": float(spacing)}
 
 
-def ellipse_batch(count=64, seed=3, m_lo=4, m_hi=400, spacing=1.0):
-    """Independent problems with uneven sizes: ellipses on square-ish grids."""
+def ellipse_batch(count=64, seed=3, m_lo=4, m_hi=400, spacing=1.0, n_lo=64, n_hi=256):
+    """Independent problems with uneven sizes: ellipses on square-ish grids,
+    m ~ U{m_lo..m_hi}, n ~ U{n_lo, n_lo+32, .., n_hi}, k0 = 2 pi L / (cols spacing)
+    with L ~ U(2, 25) wavelengths per grid side, k1/k0 ~ U(1.5, 3)."""
     rng = np.random.default_rng(seed)
     probs = []
     for _ in range(count):
         m = int(rng.integers(m_lo, m_hi + 1))
         cols = int(math.ceil(math.sqrt(m)))
         rows = int(math.ceil(m / cols))
-        n = int(rng.choice(np.arange(64, 257, 32)))
+        n = int(rng.choice(np.arange(n_lo, n_hi + 1, 32)))
         lam = rng.uniform(2.0, 25.0)
         k_out = 2 * math.pi * lam / (spacing * cols)
         inc = []
