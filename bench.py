@@ -165,7 +165,7 @@ def _traffic_for(kernel):
 
 
 FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",
-                "apply_offdiag64"}
+                "apply_offdiag64", "dense_matvec64", "dense_offdiag64"}
 
 
 def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None):

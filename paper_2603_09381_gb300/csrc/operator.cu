@@ -91,6 +91,73 @@ __global__ void __launch_bounds__(OP_T) k_apply_offdiag(OpNodes nd, int total, d
   }
 }
 
+// Dense off-diagonal operator: thread = (target node t, source node s), targets
+// fastest so that the writes along a column are coalesced.
+__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double2* __restrict__ A,
+                                                       size_t lda) {
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  const int s = blockIdx.y;
+  if (t >= total) return;
+  const int ti = nd.incl[t], si = nd.incl[s];
+  if (ti == si) return;
+  const double dx = nd.x[t] - nd.x[s], dy = nd.y[t] - nd.y[s];
+  const double ir = rsqrt(dx * dx + dy * dy);
+  const double r = (dx * dx + dy * dy) * ir;
+  const double z = k * r;
+  double J0, Y0, J1, Y1;
+  hankel01_inv(z, ir / k, J0, Y0, J1, Y1);
+  const double w = nd.w[s];
+  const double tnx = nd.nx[t], tny = nd.ny[t], snx = nd.nx[s], sny = nd.ny[s];
+  const double a = (tnx * dx + tny * dy) * ir, b = (snx * dx + sny * dy) * ir;
+  const double nn = tnx * snx + tny * sny;
+  const double f = 0.25 * k * w;
+  const double c0 = k * a * b, c1 = (nn - 2 * a * b) * ir;
+  const size_t ru = nd.iu[t], rq = nd.iq[t], cq = nd.iu[s], cu = nd.iq[s];
+  A[ru + cq * lda] = make_double2(0.25 * Y0 * w, -0.25 * J0 * w);                       // -eps+ S w
+  A[ru + cu * lda] = make_double2(-Y1 * b * f, J1 * b * f);                             // D w
+  A[rq + cq * lda] = make_double2(-Y1 * a * f, J1 * a * f);                             // -D* w
+  A[rq + cu * lda] = make_double2(-(c0 * Y0 + c1 * Y1) * f, (c0 * J0 + c1 * J1) * f);   // N/eps+ w
+}
+
+// Skinny product Y = A X: a CTA owns 128 rows and one segment of the columns of
+// A; the segment's rows of X are staged in shared memory; partial sums meet in
+// FP64 atomics.  Every A entry is read once and feeds NR complex FMAs.
+constexpr int MV_ROWS = 128, MV_KT = 64;
+template <int NR>
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const double2* __restrict__ A, size_t lda, int N,
+                                                          const double2* __restrict__ X, int ldx, double2* __restrict__ Y,
+                                                          int ldy, int seg) {
+  __shared__ double2 xs[NR][MV_KT];
+  const int row = blockIdx.x * MV_ROWS + threadIdx.x;
+  const int k0 = blockIdx.y * seg, k1 = min(N, k0 + seg);
+  double2 acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = make_double2(0, 0);
+  for (int kb = k0; kb < k1; kb += MV_KT) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NR * MV_KT; e += MV_ROWS) {
+      const int q = e / MV_KT, kk = e % MV_KT;
+      xs[q][kk] = (kb + kk < k1) ? X[kb + kk + (size_t)q * ldx] : make_double2(0, 0);
+    }
+    __syncthreads();
+    if (row < N) {
+      const int cnt = min(MV_KT, k1 - kb);
+      const double2* col = A + row + (size_t)kb * lda;
+      for (int kk = 0; kk < cnt; ++kk) {
+        const double2 a = __ldg(col + (size_t)kk * lda);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
+      }
+    }
+  }
+  if (row >= N) return;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    atomicAdd(&Y[row + (size_t)q * ldy].x, acc[q].x);
+    atomicAdd(&Y[row + (size_t)q * ldy].y, acc[q].y);
+  }
+}
+
 __global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,
                            double* norms2) {
   const int r = blockIdx.y;
@@ -165,6 +232,47 @@ void apply_offdiag64(OpNodes nd, int total, double k0, const double2* X, int ldx
     else { launch_apply<1>(nd, total, k0, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "apply_offdiag64", 0.0);
+}
+
+void assemble_dense_offdiag64(OpNodes nd, int total, double k0, double2* A, size_t lda, cudaStream_t st) {
+  if (total <= 0) return;
+  dim3 g((total + 255) / 256, total);
+  KPROF_BEGIN(st);
+  k_dense_offdiag<<<g, 256, 0, st>>>(nd, total, k0, A, lda);
+  pm_launch_count_add(1);
+  KPROF_END(st, "dense_offdiag64", 0.0);
+}
+
+template <int NR>
+void launch_matvec(const double2* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int rb = (N + MV_ROWS - 1) / MV_ROWS;
+  int segs = std::max(1, (sms * 12 + rb - 1) / rb);
+  int seg = (N + segs - 1) / segs;
+  seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
+  segs = (N + seg - 1) / seg;
+  dim3 g(rb, segs);
+  k_dense_matvec<NR><<<g, MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  pm_launch_count_add(1);
+}
+
+void dense_matvec64(const double2* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                    cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
+  KPROF_BEGIN(st);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    const double2* Xr = X + (size_t)r0 * ldx;
+    double2* Yr = Y + (size_t)r0 * ldy;
+    if (left >= 8) { launch_matvec<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+  }
+  KPROF_END(st, "dense_matvec64", 0.0);
 }
 
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st) {

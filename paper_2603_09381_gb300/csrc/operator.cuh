@@ -16,6 +16,14 @@ struct OpNodes {
 // different inclusions; same-inclusion pairs are skipped).
 void apply_offdiag64(OpNodes nd, int total_nodes, double k0, const double2* X, int ldx, double2* Y, int ldy,
                      int nrhs, cudaStream_t st);
+// The off-diagonal part of the operator written out densely (FP64, column-major,
+// leading dimension lda); same-inclusion pairs are left untouched (the caller
+// copies the self blocks in).  One Hankel evaluation per node pair fills the
+// pair's 2 x 2 entries.
+void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, double2* A, size_t lda, cudaStream_t st);
+// Y (N x nrhs) = A (N x N) X (N x nrhs), nrhs <= 8 per pass; Y overwritten.
+void dense_matvec64(const double2* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                    cudaStream_t st);
 // R = B - Y, and norms2[2 r] += |R[:, r]|^2, norms2[2 r + 1] += |B[:, r]|^2 (norms2 zeroed by caller)
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st);
 // dst[:, r] = scale[r] * src[:, r] (FP64 -> FP32)

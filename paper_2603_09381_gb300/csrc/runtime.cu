@@ -187,6 +187,8 @@ struct pm_factor {
   std::vector<double2*> self64;
   int* d_iu = nullptr;
   int* d_iq = nullptr;
+  double2* dense64 = nullptr;   // the whole FP64 operator, N x N, when it fits the memory budget
+  ~pm_factor() { if (dense64) cudaFree(dense64); }
 };
 
 template <class C> std::vector<std::vector<BoxF<C>>>& levels_of(pm_factor* F);
@@ -718,7 +720,6 @@ void process_level(pm_factor* F, int lev, double tol) {
       F->stats.rank_checks++;
       int pending = 0;
       for (int i = 0; i < nid; ++i) if (hr[i] < 0 && t + 1 < cp[i].target) ++pending;
-      if (!khat.empty() && t == first_check) F->stats.predictor_fallbacks += pending;
       if (pending == 0) break;
     }
   }
@@ -727,6 +728,8 @@ void process_level(pm_factor* F, int lev, double tol) {
   CK(cudaStreamSynchronize(st));
   std::vector<int> r(nid);
   for (int i = 0; i < nid; ++i) r[i] = hr[i] >= 0 ? hr[i] : cp[i].target;
+  if (!khat.empty())
+    for (int i = 0; i < nid; ++i) F->stats.predictor_fallbacks += r[i] > khat[i];   // rank above the predicted bound
   // 4. pair ranks k_g = max(row rank, column rank); extend the shorter factorization
   std::vector<int> kk(nid);
   int maxExt = 0;
@@ -1078,6 +1081,12 @@ void apply_inverse_mixed(pm_factor* F, const double2* rhs, int nrhs, double2* ph
 void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Arena& ws, cudaStream_t st) {
   const pm_geometry* g = F->g;
   const int N = g->N;
+  if (F->dense64) {
+    dense_matvec64(F->dense64, (size_t)N, N, X, N, Y, N, nrhs, st);
+    if (g_kprof) g_kprof->add_flops("dense_matvec64", 8.0 * (double)N * N * nrhs);
+    CK(cudaGetLastError());
+    return;
+  }
   GemmBatch<double2> gb;
   for (int j = 0; j < g->m; ++j) {
     const int r0 = g->row_off[j], m2 = 2 * g->inc[j].n_nodes;
@@ -1344,6 +1353,28 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
         }
       F->d_iu = upload(F->arena, iu, F->st);
       F->d_iq = upload(F->arena, iq, F->st);
+      // With room in HBM, write the FP64 operator out once: each refinement step
+      // is then a skinny FP64 GEMM instead of a Hankel evaluation per node pair.
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      const size_t need = sizeof(double2) * (size_t)g->N * g->N;
+      if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535 && need <= fr / 10 * 6) {
+        CK(cudaMalloc(&F->dense64, need));
+        OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
+        assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense64, (size_t)g->N, F->st);
+        if (g_kprof) {
+          double pairs = (double)g->total_nodes * g->total_nodes;
+          for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
+          g_kprof->add_flops("dense_offdiag64", pairs * 164.0);
+        }
+        CopyBatch<double2, double2> cb;
+        for (int j = 0; j < g->m; ++j) {
+          const int m2 = 2 * g->inc[j].n_nodes;
+          cb.add(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, g->N, m2, m2);
+        }
+        cb.run(F->scratch, F->st);
+        CK(cudaGetLastError());
+      }
     }
     F->stats.ms_total = tt.stop();
     if (F->profiling) F->prof.collect();

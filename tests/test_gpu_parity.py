@@ -225,3 +225,19 @@ def test_lossy_small_circles_fp64_and_mixed(pm):
     th = geometry.nodes(prob["inclusions"][0])["t"]
     exact = np.concatenate([np.concatenate(mie.boundary_values(U[j], Q[j], th, M)[::-1]) for j in range(4)])
     assert _rel(phi[:, 0], exact) < 1e-9
+
+
+def test_mixed_dense_and_on_the_fly_operators_agree(pm):
+    prob = wl.star_grid(4, 4, n=64, seed=2)
+    g = pm.Geometry(prob)
+    F = g.plane_wave([0.9, 3.1])
+    a = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, dense_operator=True)
+    b = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, dense_operator=False)
+    xa, xb = a.solve(F), b.solve(F)
+    assert a.last_info["iterations"] == b.last_info["iterations"]
+    ha, hb = np.array(a.last_info["history"]), np.array(b.last_info["history"])
+    big = ha > 1e-12          # below that the residuals are FP64 rounding noise
+    assert np.allclose(ha[big], hb[big], rtol=1e-2, atol=0)
+    assert _rel(xa, xb) < 1e-12
+    ref = dense.solve(prob, [0.9, 3.1])
+    assert _rel(xa, ref) < 1e-8
