@@ -165,7 +165,18 @@ def _traffic_for(kernel):
 
 
 FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",
-                "apply_offdiag64", "dense_matvec64", "dense_offdiag64"}
+                "apply_offdiag64", "dense_matvec64", "dense_offdiag64"}        # FP64 flops
+FP32_FLOP_KERNELS = {"lu_update32", "lu_panel32", "lu_swap_trsm32", "getrs32", "gemm_batched32", "interp_solve32"}
+BYTE_KERNELS = {"cpqr_step32"}     # memory-bound FP32 CPQR: algorithmic bytes
+
+
+def _peaks():
+    """Measured pool peaks (generated file) or the recipe's fallback."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback (recipe)"
 
 
 def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None):
@@ -208,10 +219,15 @@ def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, mode
 
 
 def _kernel_table(prof_tot, steps):
-    return {k: {"launches": v["launches"] // steps, "ms": round(v["ms"] / steps, 3),
-                "tflops": (round(v["work"] / (v["ms"] / 1e3) / 1e12, 4)
-                           if k in FLOP_KERNELS and v["ms"] > 0 else None)}
-            for k, v in sorted(prof_tot.items(), key=lambda kv: -kv[1]["ms"])}
+    out = {}
+    for k, v in sorted(prof_tot.items(), key=lambda kv: -kv[1]["ms"]):
+        e = {"launches": v["launches"] // steps, "ms": round(v["ms"] / steps, 3)}
+        if v["ms"] > 0 and (k in FLOP_KERNELS or k in FP32_FLOP_KERNELS):
+            e["tflops"] = round(v["work"] / (v["ms"] / 1e3) / 1e12, 4)
+        if v["ms"] > 0 and k in BYTE_KERNELS:
+            e["gbs"] = round(v["work"] / (v["ms"] / 1e3) / 1e9, 1)
+        out[k] = e
+    return out
 
 
 def _roofline(prof_tot, steps):
@@ -222,6 +238,11 @@ def _roofline(prof_tot, steps):
         roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 dense FP64 (recipe)",
                      "traffic": _traffic_for(name)})
+    elif name in BYTE_KERNELS and d["ms"] > 0:
+        peak, src = _peaks()
+        achieved = d["work"] / (d["ms"] / 1e3) / 1e9
+        roof.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": src, "traffic": _traffic_for(name)})
     else:
         roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
     return roof

@@ -137,6 +137,7 @@ typedef struct {
   int32_t cpqr_launches;    /* CPQR elimination-step launches */
   int32_t rank_checks;      /* device-to-host rank checks (host synchronisations) */
   int32_t predictor_fallbacks;  /* IDs whose rank exceeded the predicted bound */
+  double ms_level[16];      /* wall time of each compressed level (index = level) */
 } pm_stats;
 
 /* Build node geometry on the device (paper Sec. 2.2) and the quadtree

@@ -256,7 +256,13 @@ __device__ __forceinline__ C omit_entry(const PointsDev& P, int t, int s, double
   const double z = k * r;
   const double w = P.w[ps];
   double J0, Y0, J1, Y1;
-  hankel01(z, J0, Y0, J1, Y1);
+  if (z < HK_ZA) {                  // near entries: only the Bessel pair the entry needs
+    if (rg == 0 && cg == 0) return mk((R)(0.25 * y0(z) * w), (R)(-0.25 * j0(z) * w));
+    J1 = j1(z); Y1 = y1(z);
+    if (rg == 1 && cg == 1) { J0 = j0(z); Y0 = y0(z); } else { J0 = 0; Y0 = 0; }
+  } else {
+    hankel01(z, J0, Y0, J1, Y1);
+  }
   if (rg == 0 && cg == 0)           // -eps+ S = -(i/4) H0 w
     return mk((R)(0.25 * Y0 * w), (R)(-0.25 * J0 * w));
   if (rg == 0) {                    // D = (ik/4) H1 (n_y.d)/r w
@@ -361,7 +367,7 @@ void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, doubl
   KPROF_BEGIN(st);
   k_self_pointwise<C><<<g, 256, 0, st>>>(d_inc, nodes, k0, d_A, d_lda, d_Cm);
   pm_launch_count_add(1);
-  KPROF_END(st, "self_pointwise", 0.0);
+  KPROF_END(st, kname<C>("self_pointwise", "self_pointwise32"), 0.0);
 }
 
 template <typename C>
@@ -385,7 +391,7 @@ void gather_assemble(const GatherProb<C>* d_prob, const int* d_tile_off, int npr
   KPROF_BEGIN(st);
   k_gather<C><<<total_tiles, 256, 0, st>>>(d_prob, d_tile_off, nprob, pts, k0);
   pm_launch_count_add(1);
-  KPROF_END(st, "gather_entries", 0.0);
+  KPROF_END(st, kname<C>("gather_entries", "gather_entries32"), 0.0);
 }
 
 template void plane_wave_rhs<double2>(const InclDev*, NodesDev, int, double, const double*, int, double2*, int, cudaStream_t);

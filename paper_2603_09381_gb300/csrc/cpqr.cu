@@ -35,6 +35,68 @@ __global__ void __launch_bounds__(256) k_init_norms(const CpqrProb<C>* __restric
   }
 }
 
+// Sum of one value over the 256 threads of the CTA (every thread gets it).
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R* sh) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R t = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += sh[w];
+  return t;
+}
+
+// The chunk's columns one at a time, each held by the whole CTA in registers
+// (RPT rows per thread): one read and one write of every trailing entry, with
+// all of a thread's loads in flight together.  Requires W - s - 1 <= 256 RPT.
+template <typename C, int RPT>
+__device__ void cta_columns(const CpqrProb<C>& p, const CpqrChunk& ch, int s, int q, const C* xq, C ctau, C csc,
+                            C sc, const double* cur, double* nxt) {
+  typedef typename real_of<C>::type R;
+  __shared__ R shx[8], shy[8], shn[8];
+  const int tid = threadIdx.x;
+  for (int c = ch.c0; c < ch.c1; ++c) {
+    if (cur[c] < 0 || c == q) { if (tid == 0) nxt[c] = -1.0; continue; }
+    C* col = p.Z + (size_t)c * p.ld;
+    C v[RPT];
+    C dot = czero<C>();
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = s + 1 + tid + 256 * i;
+      v[i] = (r < p.W) ? col[r] : czero<C>();
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = s + 1 + tid + 256 * i;
+      if (r < p.W) cfma_conj(dot, __ldg(&xq[r]), v[i]);
+    }
+    dot.x = block_sum(dot.x, shx);
+    dot.y = block_sum(dot.y, shy);
+    const C a_s = col[s];
+    const C d = a_s + csc * dot;     // v^H a with v = [1; x/(alpha - beta)]
+    const C f = ctau * d;            // H^H a = a - conj(tau) v (v^H a)
+    const C fs = f * sc;
+    R e = 0;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = s + 1 + tid + 256 * i;
+      if (r < p.W) {
+        cfms(v[i], fs, __ldg(&xq[r]));
+        col[r] = v[i];
+        e += abs2(v[i]);
+      }
+    }
+    e = block_sum(e, shn);
+    if (tid == 0) {
+      col[s] = a_s - f;
+      nxt[c] = (double)e;
+    }
+    __syncthreads();
+  }
+}
+
 // One elimination step of the chunk's matrix on the chunk's columns (all 256
 // threads of the CTA take the same path through the barriers).
 template <typename C>
@@ -104,6 +166,15 @@ __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t
     sc = cdiv(mk((R)1, (R)0), alpha - bm);
   }
   const C ctau = conj(tau), csc = conj(sc);
+  // complex64 tall enough to fill the CTA (short columns are barrier-bound) and fitting in registers
+  if (sizeof(C) == 8 && reflect && p.W >= 2048 && p.W <= 256 * 32) {
+    cta_columns<C, 32>(p, ch, s, q, xq, ctau, csc, sc, cur, nxt);
+    if (tid == 0 && q >= ch.c0 && q < ch.c1) {
+      p.rdiag[s] = mk(beta, (R)0);
+      p.perm[s] = q;
+    }
+    return;
+  }
   for (int c = ch.c0 + warp; c < ch.c1; c += 8) {
     if (cur[c] < 0 || c == q) { if (lane == 0) nxt[c] = -1.0; continue; }
     C* col = p.Z + (size_t)c * p.ld;
@@ -114,21 +185,38 @@ __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t
       if (lane == 0) nxt[c] = (double)acc;
       continue;
     }
-    C dot = czero<C>();
-    for (int r = s + 1 + lane; r < p.W; r += 32) cfma_conj(dot, __ldg(&xq[r]), col[r]);
+    // four independent partial sums keep several loads in flight per lane
+    C d0 = czero<C>(), d1 = czero<C>(), d2 = czero<C>(), d3 = czero<C>();
+    int r = s + 1 + lane;
+    for (; r + 96 < p.W; r += 128) {
+      const C x0 = __ldg(&xq[r]), x1 = __ldg(&xq[r + 32]), x2 = __ldg(&xq[r + 64]), x3 = __ldg(&xq[r + 96]);
+      const C a0 = col[r], a1 = col[r + 32], a2 = col[r + 64], a3 = col[r + 96];
+      cfma_conj(d0, x0, a0); cfma_conj(d1, x1, a1); cfma_conj(d2, x2, a2); cfma_conj(d3, x3, a3);
+    }
+    for (; r < p.W; r += 32) cfma_conj(d0, __ldg(&xq[r]), col[r]);
+    C dot = (d0 + d1) + (d2 + d3);
     dot.x = warp_sum(dot.x); dot.y = warp_sum(dot.y);
     const C a_s = col[s];
     dot = a_s + csc * dot;          // v^H a with v = [1; x/(alpha - beta)]
     const C f = ctau * dot;         // H^H a = a - conj(tau) v (v^H a)
     const C fs = f * sc;
     if (lane == 0) col[s] = a_s - f;
-    R acc = 0;
-    for (int r = s + 1 + lane; r < p.W; r += 32) {
+    R e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    r = s + 1 + lane;
+    for (; r + 96 < p.W; r += 128) {
+      C v0 = col[r], v1 = col[r + 32], v2 = col[r + 64], v3 = col[r + 96];
+      cfms(v0, fs, __ldg(&xq[r])); cfms(v1, fs, __ldg(&xq[r + 32]));
+      cfms(v2, fs, __ldg(&xq[r + 64])); cfms(v3, fs, __ldg(&xq[r + 96]));
+      col[r] = v0; col[r + 32] = v1; col[r + 64] = v2; col[r + 96] = v3;
+      e0 += abs2(v0); e1 += abs2(v1); e2 += abs2(v2); e3 += abs2(v3);
+    }
+    for (; r < p.W; r += 32) {
       C v = col[r];
       cfms(v, fs, __ldg(&xq[r]));
       col[r] = v;
-      acc += abs2(v);
+      e0 += abs2(v);
     }
+    R acc = (e0 + e1) + (e2 + e3);
     acc = warp_sum(acc);
     if (lane == 0) nxt[c] = (double)acc;
   }
@@ -252,7 +340,7 @@ void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, 
   KPROF_BEGIN(st);
   k_cpqr_step<C><<<std::min(grid, nchunk), 256, 0, st>>>(d_prob, d_chunk, nchunk, t, d_counter);
   pm_launch_count_add(1);
-  KPROF_END(st, "cpqr_step", 0.0);   // flops are added per level from the steps performed
+  KPROF_END(st, kname<C>("cpqr_step", "cpqr_step32"), 0.0);   // work is added per level from the steps performed
 }
 template <typename C>
 void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st) {
@@ -261,7 +349,7 @@ void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStre
   KPROF_BEGIN(st);
   k_interp<C><<<g, 64, 0, st>>>(d_prob);
   pm_launch_count_add(1);
-  KPROF_END(st, "interp_solve", 0.0);
+  KPROF_END(st, kname<C>("interp_solve", "interp_solve32"), 0.0);
 }
 template <typename C>
 void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {

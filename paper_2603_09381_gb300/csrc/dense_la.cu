@@ -254,7 +254,7 @@ void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob
   KPROF_BEGIN(st);
   k_gemm_batched<C><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob);
   pm_launch_count_add(1);
-  KPROF_END(st, "gemm_batched", 0.0);
+  KPROF_END(st, kname<C>("gemm_batched", "gemm_batched32"), 0.0);
 }
 
 constexpr int LU_NB = 16;
@@ -278,12 +278,12 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
     KPROF_BEGIN(st);
     k_lu_panel<C><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
-    KPROF_END(st, "lu_panel", fp);
+    KPROF_END(st, kname<C>("lu_panel", "lu_panel32"), fp);
     dim3 g1((maxm + 255) / 256, nprob);
     KPROF_BEGIN(st);
     k_lu_swap_trsm<C><<<g1, 256, 0, st>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
-    KPROF_END(st, "lu_swap_trsm", fs);
+    KPROF_END(st, kname<C>("lu_swap_trsm", "lu_swap_trsm32"), fs);
     int mt = maxm - p - LU_NB;
     if (mt > 0) {
       int tiles = ((mt + TB - 1) / TB);
@@ -291,7 +291,7 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
       KPROF_BEGIN(st);
       k_lu_update<C><<<g2, 256, 0, st>>>(d_prob, p, LU_NB);
       pm_launch_count_add(1);
-      KPROF_END(st, "lu_update", fu);
+      KPROF_END(st, kname<C>("lu_update", "lu_update32"), fu);
     }
   }
 }
@@ -328,7 +328,7 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
       pm_launch_count_add(1);
     }
   }
-  KPROF_END(st, "getrs", fl);
+  KPROF_END(st, kname<C>("getrs", "getrs32"), fl);
 }
 
 template void la_gemm_batched<double2>(const GemmDesc<double2>*, const int*, int, int, cudaStream_t);

@@ -7,11 +7,14 @@
 //     P = sum_k (-1)^k a_{2k}(nu) z^{-2k},  Q = sum_k (-1)^k a_{2k+1}(nu) z^{-2k-1},
 //     a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (k! 8^k).
 //   For real z the remainder is bounded by the first omitted term (DLMF
-//   10.17(iii)); with 27 terms it is below 1e-18 for z >= 20.  One sincos(z)
-//   serves both orders: w_1 = w_0 - pi/2.
-// z < HK_ZA: Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from
-//   an even start M > z + 25 + 3 sqrt(z), normalised by 1 = J0 + 2 sum J_2k
-//   (A&S 9.1.27, 9.1.46), and Neumann's series (A&S 9.1.88)
+//   10.17(iii)): below 1e-17 with 27 terms for z >= 20, 17 terms for z >= 30
+//   and 12 terms for z >= 60.  One sincos(z) serves both orders:
+//   w_1 = w_0 - pi/2.
+// z < HK_ZA: CUDA's j0 / y0 / j1 / y1.
+// Complex z (lossy interiors, self blocks): Miller's backward recurrence
+//   J_{n-1} = (2n/z) J_n - J_{n+1} from an even start M > |z| + 25 + 3 sqrt|z|,
+//   normalised by 1 = J0 + 2 sum J_2k (A&S 9.1.27, 9.1.46), and Neumann's
+//   series (A&S 9.1.88)
 //     (pi/2) Y0 = (ln(z/2) + gamma) J0 - 2 sum_{k>=1} (-1)^k J_2k / k,
 //   with its derivative for Y1 = -Y0':
 //     (pi/2) Y1 = -J0/z + (ln(z/2) + gamma) J1 + sum_{k>=1} (-1)^k (J_{2k-1} - J_{2k+1})/k.
@@ -38,17 +41,23 @@ static __constant__ double c_hk_a0[HK_TERMS] = HK_ROW(0);
 static __constant__ double c_hk_a1[HK_TERMS] = HK_ROW(1);
 #undef HK_ROW
 
-__device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
+// Expansion with the first T terms a_0 .. a_{T-1}: P from the even, Q from
+// the odd indices.  Terms needed for a remainder below 1e-17: 27 at z >= 20,
+// 17 at z >= 30, 12 at z >= 60.
+template <int T>
+__device__ __forceinline__ void hankel_asym_t(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
+  constexpr int PE = (T - 1) - ((T - 1) & 1);   // highest even index < T
+  constexpr int QO = (T - 1) - (T & 1);         // highest odd index < T
   const double u = iz * iz;
-  double P0 = c_hk_a0[HK_TERMS - 1 - ((HK_TERMS - 1) & 1)], P1 = c_hk_a1[HK_TERMS - 1 - ((HK_TERMS - 1) & 1)];
-  double Q0 = c_hk_a0[HK_TERMS - 1 - ((HK_TERMS) & 1)], Q1 = c_hk_a1[HK_TERMS - 1 - ((HK_TERMS) & 1)];
+  double P0 = c_hk_a0[PE], P1 = c_hk_a1[PE];
+  double Q0 = c_hk_a0[QO], Q1 = c_hk_a1[QO];
 #pragma unroll
-  for (int k = HK_TERMS - 3 - ((HK_TERMS - 1) & 1); k >= 0; k -= 2) {
+  for (int k = PE - 2; k >= 0; k -= 2) {
     P0 = fma(P0, u, c_hk_a0[k]);
     P1 = fma(P1, u, c_hk_a1[k]);
   }
 #pragma unroll
-  for (int k = HK_TERMS - 3 - (HK_TERMS & 1); k >= 1; k -= 2) {
+  for (int k = QO - 2; k >= 1; k -= 2) {
     Q0 = fma(Q0, u, c_hk_a0[k]);
     Q1 = fma(Q1, u, c_hk_a1[k]);
   }
@@ -65,54 +74,28 @@ __device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, dou
   Y1 = s * (Q1 * d - P1 * c);
 }
 
-__device__ __forceinline__ void hankel_miller(double z, double& J0, double& Y0, double& J1, double& Y1) {
-  int M = (int)(z + 25.0 + 3.0 * sqrt(z));
-  M += (M & 1);
-  const double t2z = 2.0 / z;
-  double jp1 = 0.0, jn = 1e-30;      // J_{M+1}, J_M (unnormalised)
-  double norm = 0.0, s0 = 0.0, s1 = 0.0;
-  // index n holds jn; M is even
-  for (int n = M; n >= 1; --n) {
-    if ((n & 1) == 0) {              // even n = 2k >= 2
-      const int k = n >> 1;
-      norm += 2.0 * jn;
-      s0 += ((k & 1) ? -jn : jn) / k;
-    } else {                          // odd n = 2m - 1
-      const int m = (n + 1) >> 1;
-      if (m == 1) s1 -= jn;
-      else s1 += ((m & 1) ? -jn : jn) * (1.0 / m + 1.0 / (m - 1));
-    }
-    const double jm1 = n * t2z * jn - jp1;
-    jp1 = jn;
-    jn = jm1;
-  }
-  // jn = J0, jp1 = J1 (unnormalised)
-  norm += jn;
-  const double inv = 1.0 / norm;
-  J0 = jn * inv;
-  J1 = jp1 * inv;
-  s0 *= inv;
-  s1 *= inv;
-  const double lg = log(0.5 * z) + 0.57721566490153286061;
-  Y0 = 0.63661977236758134308 * (lg * J0 - 2.0 * s0);
-  Y1 = 0.63661977236758134308 * (-J0 / z + lg * J1 + s1);
+__device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
+  if (z >= 60.0) hankel_asym_t<12>(z, iz, J0, Y0, J1, Y1);
+  else if (z >= 30.0) hankel_asym_t<17>(z, iz, J0, Y0, J1, Y1);
+  else hankel_asym_t<HK_TERMS>(z, iz, J0, Y0, J1, Y1);
 }
 
+// Below z = 20 CUDA's j0/y0/j1/y1 (~1e-15 absolute below 8, ~2e-13 up to
+// 30, measured against scipy on GB300) are much cheaper than a recurrence.
 __device__ __forceinline__ void hankel01(double z, double& J0, double& Y0, double& J1, double& Y1) {
   if (z >= HK_ZA) hankel_asym(z, 1.0 / z, J0, Y0, J1, Y1);
-  else hankel_miller(z, J0, Y0, J1, Y1);
+  else { J0 = j0(z); Y0 = y0(z); J1 = j1(z); Y1 = y1(z); }
 }
 
 // Same, with 1/z supplied by the caller.
 __device__ __forceinline__ void hankel01_inv(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
   if (z >= HK_ZA) hankel_asym(z, iz, J0, Y0, J1, Y1);
-  else hankel_miller(z, J0, Y0, J1, Y1);
+  else { J0 = j0(z); Y0 = y0(z); J1 = j1(z); Y1 = y1(z); }
 }
 
 // ---- complex argument (lossy interior wavenumbers, self blocks only) ---------------
-// Same Miller / Neumann construction in complex arithmetic (principal branch
-// of the logarithm); valid for moderate |z| and Im z >= 0 (the self blocks
-// need |z| <= k- diam(Gamma)).
+// Miller / Neumann in complex arithmetic (principal branch of the logarithm);
+// valid for moderate |z| and Im z >= 0 (the self blocks need |z| <= k- diam(Gamma)).
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
   const double d = b.x * b.x + b.y * b.y;

@@ -91,13 +91,23 @@ __global__ void __launch_bounds__(OP_T) k_apply_offdiag(OpNodes nd, int total, d
   }
 }
 
-// Dense off-diagonal operator: thread = (target node t, source node s), targets
-// fastest so that the writes along a column are coalesced.
-__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double2* __restrict__ A,
-                                                       size_t lda) {
-  const int t = blockIdx.x * 256 + threadIdx.x;
+__device__ __forceinline__ float4 split4(double re, double im) {
+  const float hr = (float)re, hi = (float)im;
+  return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+}
+
+// Dense off-diagonal operator: thread = (node t, node s) with t < s, nodes t
+// fastest.  One Hankel evaluation fills both 2 x 2 blocks of the pair:
+// with d = x_t - x_s, a = n_t.d/r, b = n_s.d/r and c = (ik/4) H1,
+//   (t <- s): -eps+S w_s,  D = c b w_s,  -D* = c a w_s,  N = (ik/4)[..] w_s
+//   (s <- t): -eps+S w_t,  D = -c a w_t, -D* = -c b w_t, N = (ik/4)[..] w_t
+// (the bracket of N is symmetric in the pair).
+__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double ik,
+                                                       float4* __restrict__ A, size_t lda) {
   const int s = blockIdx.y;
-  if (t >= total) return;
+  if (blockIdx.x * 256 >= s) return;          // whole block on or below the diagonal
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  if (t >= s) return;
   const int ti = nd.incl[t], si = nd.incl[s];
   if (ti == si) return;
   const double dx = nd.x[t] - nd.x[s], dy = nd.y[t] - nd.y[s];
@@ -105,18 +115,25 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
   const double r = (dx * dx + dy * dy) * ir;
   const double z = k * r;
   double J0, Y0, J1, Y1;
-  hankel01_inv(z, ir / k, J0, Y0, J1, Y1);
-  const double w = nd.w[s];
+  hankel01_inv(z, ir * ik, J0, Y0, J1, Y1);
+  const double ws = nd.w[s], wt = nd.w[t];
   const double tnx = nd.nx[t], tny = nd.ny[t], snx = nd.nx[s], sny = nd.ny[s];
   const double a = (tnx * dx + tny * dy) * ir, b = (snx * dx + sny * dy) * ir;
   const double nn = tnx * snx + tny * sny;
-  const double f = 0.25 * k * w;
+  const double q = 0.25 * k;
   const double c0 = k * a * b, c1 = (nn - 2 * a * b) * ir;
-  const size_t ru = nd.iu[t], rq = nd.iq[t], cq = nd.iu[s], cu = nd.iq[s];
-  A[ru + cq * lda] = make_double2(0.25 * Y0 * w, -0.25 * J0 * w);                       // -eps+ S w
-  A[ru + cu * lda] = make_double2(-Y1 * b * f, J1 * b * f);                             // D w
-  A[rq + cq * lda] = make_double2(-Y1 * a * f, J1 * a * f);                             // -D* w
-  A[rq + cu * lda] = make_double2(-(c0 * Y0 + c1 * Y1) * f, (c0 * J0 + c1 * J1) * f);   // N/eps+ w
+  const double Nre = -(c0 * Y0 + c1 * Y1) * q, Nim = (c0 * J0 + c1 * J1) * q;   // (ik/4)[..]
+  const size_t ut = nd.iu[t], qt = nd.iq[t], us = nd.iu[s], qs = nd.iq[s];
+  // rows of t, columns of s (column index: q density at the u-equation index, u density at the q index)
+  A[ut + us * lda] = split4(0.25 * Y0 * ws, -0.25 * J0 * ws);
+  A[ut + qs * lda] = split4(-Y1 * q * b * ws, J1 * q * b * ws);
+  A[qt + us * lda] = split4(-Y1 * q * a * ws, J1 * q * a * ws);
+  A[qt + qs * lda] = split4(Nre * ws, Nim * ws);
+  // rows of s, columns of t
+  A[us + ut * lda] = split4(0.25 * Y0 * wt, -0.25 * J0 * wt);
+  A[us + qt * lda] = split4(Y1 * q * a * wt, -J1 * q * a * wt);
+  A[qs + ut * lda] = split4(Y1 * q * b * wt, -J1 * q * b * wt);
+  A[qs + qt * lda] = split4(Nre * wt, Nim * wt);
 }
 
 // Skinny product Y = A X: a CTA owns 128 rows and one segment of the columns of
@@ -124,7 +141,7 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
 // FP64 atomics.  Every A entry is read once and feeds NR complex FMAs.
 constexpr int MV_ROWS = 128, MV_KT = 64;
 template <int NR>
-__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const double2* __restrict__ A, size_t lda, int N,
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restrict__ A, size_t lda, int N,
                                                           const double2* __restrict__ X, int ldx, double2* __restrict__ Y,
                                                           int ldy, int seg) {
   __shared__ double2 xs[NR][MV_KT];
@@ -142,9 +159,10 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const double2* __restr
     __syncthreads();
     if (row < N) {
       const int cnt = min(MV_KT, k1 - kb);
-      const double2* col = A + row + (size_t)kb * lda;
+      const float4* col = A + row + (size_t)kb * lda;
       for (int kk = 0; kk < cnt; ++kk) {
-        const double2 a = __ldg(col + (size_t)kk * lda);
+        const float4 s4 = __ldg(col + (size_t)kk * lda);
+        const double2 a = make_double2((double)s4.x + (double)s4.z, (double)s4.y + (double)s4.w);
 #pragma unroll
         for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
       }
@@ -156,6 +174,78 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const double2* __restr
     atomicAdd(&Y[row + (size_t)q * ldy].x, acc[q].x);
     atomicAdd(&Y[row + (size_t)q * ldy].y, acc[q].y);
   }
+}
+
+// Float-float building blocks (Dekker / Knuth): exact FP32 product error via
+// FMA, exact sum error via TwoSum.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// acc (hi, lo) += a * x for split a = (ah, al), x = (xh, xl): the hi products
+// are split exactly (fmaf), the cross terms and all errors go to lo.
+__device__ __forceinline__ void ff_mac(float& hi, float& lo, float ah, float al, float xh, float xl, float sgn) {
+  const float p = ah * xh;
+  const float pe = fmaf(ah, xh, -p);
+  const float cross = fmaf(ah, xl, al * xh);
+  float s, e;
+  two_sum(hi, sgn * p, s, e);
+  hi = s;
+  lo += e + sgn * (pe + cross);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float4* __restrict__ A, size_t lda, int N,
+                                                             const double2* __restrict__ X, int ldx,
+                                                             double2* __restrict__ Y, int ldy, int seg) {
+  __shared__ float4 xs[NR][MV_KT];   // {hi(re), hi(im), lo(re), lo(im)} of x
+  const int row = blockIdx.x * MV_ROWS + threadIdx.x;
+  const int k0 = blockIdx.y * seg, k1 = min(N, k0 + seg);
+  float rh[NR], rl[NR], ih[NR], il[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) { rh[q] = rl[q] = ih[q] = il[q] = 0.f; }
+  for (int kb = k0; kb < k1; kb += MV_KT) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NR * MV_KT; e += MV_ROWS) {
+      const int q = e / MV_KT, kk = e % MV_KT;
+      const double2 v = (kb + kk < k1) ? X[kb + kk + (size_t)q * ldx] : make_double2(0, 0);
+      xs[q][kk] = split4(v.x, v.y);
+    }
+    __syncthreads();
+    if (row < N) {
+      const int cnt = min(MV_KT, k1 - kb);
+      const float4* col = A + row + (size_t)kb * lda;
+      for (int kk = 0; kk < cnt; ++kk) {
+        const float4 a = __ldg(col + (size_t)kk * lda);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const float4 x = xs[q][kk];
+          // re += a.re x.re - a.im x.im ;  im += a.re x.im + a.im x.re
+          ff_mac(rh[q], rl[q], a.x, a.z, x.x, x.z, 1.f);
+          ff_mac(rh[q], rl[q], a.y, a.w, x.y, x.w, -1.f);
+          ff_mac(ih[q], il[q], a.x, a.z, x.y, x.w, 1.f);
+          ff_mac(ih[q], il[q], a.y, a.w, x.x, x.z, 1.f);
+        }
+      }
+    }
+  }
+  if (row >= N) return;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    atomicAdd(&Y[row + (size_t)q * ldy].x, (double)rh[q] + (double)rl[q]);
+    atomicAdd(&Y[row + (size_t)q * ldy].y, (double)ih[q] + (double)il[q]);
+  }
+}
+
+__global__ void k_split_copy(const double2* __restrict__ src, int lds, float4* __restrict__ dst, size_t ldd, int m,
+                             int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  const int i = e % m, j = e / m;
+  const double2 v = src[i + (size_t)j * lds];
+  dst[i + (size_t)j * ldd] = split4(v.x, v.y);
 }
 
 __global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,
@@ -234,17 +324,23 @@ void apply_offdiag64(OpNodes nd, int total, double k0, const double2* X, int ldx
   KPROF_END(st, "apply_offdiag64", 0.0);
 }
 
-void assemble_dense_offdiag64(OpNodes nd, int total, double k0, double2* A, size_t lda, cudaStream_t st) {
+void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return;
+  k_split_copy<<<(m * n + 255) / 256, 256, 0, st>>>(src, lds, dst, ldd, m, n);
+  pm_launch_count_add(1);
+}
+
+void assemble_dense_offdiag64(OpNodes nd, int total, double k0, float4* A, size_t lda, cudaStream_t st) {
   if (total <= 0) return;
   dim3 g((total + 255) / 256, total);
   KPROF_BEGIN(st);
-  k_dense_offdiag<<<g, 256, 0, st>>>(nd, total, k0, A, lda);
+  k_dense_offdiag<<<g, 256, 0, st>>>(nd, total, k0, 1.0 / k0, A, lda);
   pm_launch_count_add(1);
   KPROF_END(st, "dense_offdiag64", 0.0);
 }
 
 template <int NR>
-void launch_matvec(const double2* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, cudaStream_t st) {
+void launch_matvec(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -258,7 +354,7 @@ void launch_matvec(const double2* A, size_t lda, int N, const double2* X, int ld
   pm_launch_count_add(1);
 }
 
-void dense_matvec64(const double2* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st) {
   if (N <= 0 || nrhs <= 0) return;
   for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
@@ -273,6 +369,39 @@ void dense_matvec64(const double2* A, size_t lda, int N, const double2* X, int l
     else { launch_matvec<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "dense_matvec64", 0.0);
+}
+
+template <int NR>
+void launch_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy,
+                      cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int rb = (N + MV_ROWS - 1) / MV_ROWS;
+  int segs = std::max(1, (sms * 12 + rb - 1) / rb);
+  int seg = (N + segs - 1) / segs;
+  seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
+  segs = (N + seg - 1) / seg;
+  dim3 g(rb, segs);
+  k_dense_matvec_ff<NR><<<g, MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  pm_launch_count_add(1);
+}
+
+void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                     cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
+  KPROF_BEGIN(st);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    const double2* Xr = X + (size_t)r0 * ldx;
+    double2* Yr = Y + (size_t)r0 * ldy;
+    if (left >= 8) { launch_matvec_ff<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec_ff<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec_ff<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec_ff<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+  }
+  KPROF_END(st, "dense_matvec_ff", 0.0);
 }
 
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st) {

@@ -16,14 +16,23 @@ struct OpNodes {
 // different inclusions; same-inclusion pairs are skipped).
 void apply_offdiag64(OpNodes nd, int total_nodes, double k0, const double2* X, int ldx, double2* Y, int ldy,
                      int nrhs, cudaStream_t st);
-// The off-diagonal part of the operator written out densely (FP64, column-major,
-// leading dimension lda); same-inclusion pairs are left untouched (the caller
-// copies the self blocks in).  One Hankel evaluation per node pair fills the
-// pair's 2 x 2 entries.
-void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, double2* A, size_t lda, cudaStream_t st);
-// Y (N x nrhs) = A (N x N) X (N x nrhs), nrhs <= 8 per pass; Y overwritten.
-void dense_matvec64(const double2* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+// The dense operator is stored split: each complex entry a as float4
+// {hi(re), hi(im), lo(re), lo(im)} with hi = fl32(a), lo = fl32(a - hi), so
+// hi + lo represents the FP64 entry to ~4e-15 relative in 16 bytes.
+// Off-diagonal part written out densely (column-major, leading dimension lda);
+// same-inclusion pairs untouched (the caller copies the self blocks in).  One
+// Hankel evaluation per node pair fills the pair's 2 x 2 entries.
+void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, float4* A, size_t lda, cudaStream_t st);
+// dst (split) <- src (FP64) for an m x n block.
+void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, cudaStream_t st);
+// Y (N x nrhs) = A X in FP64 arithmetic (entries hi + lo); Y overwritten.
+void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st);
+// The same product in float-float arithmetic on the FP32 pipes: error-free
+// FP32 products of the hi parts (FMA), first-order cross terms, compensated
+// sums; ~1e-13 relative, for refinement residuals.
+void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                     cudaStream_t st);
 // R = B - Y, and norms2[2 r] += |R[:, r]|^2, norms2[2 r + 1] += |B[:, r]|^2 (norms2 zeroed by caller)
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st);
 // dst[:, r] = scale[r] * src[:, r] (FP64 -> FP32)

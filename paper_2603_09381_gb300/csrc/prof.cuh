@@ -44,6 +44,11 @@ struct KProf {
   }
 };
 
+// Profiler name of a kernel by arithmetic: FP32 variants carry a "32" suffix.
+template <typename C> inline const char* kname(const char* base64, const char* base32);
+template <> inline const char* kname<double2>(const char* b64, const char*) { return b64; }
+template <> inline const char* kname<float2>(const char*, const char* b32) { return b32; }
+
 // Process-wide count of kernel launches made by this library.
 void pm_launch_count_add(long n);
 

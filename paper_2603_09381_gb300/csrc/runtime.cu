@@ -187,7 +187,7 @@ struct pm_factor {
   std::vector<double2*> self64;
   int* d_iu = nullptr;
   int* d_iq = nullptr;
-  double2* dense64 = nullptr;   // the whole FP64 operator, N x N, when it fits the memory budget
+  float4* dense64 = nullptr;    // the whole FP64 operator, N x N, split hi/lo, when it fits the memory budget
   ~pm_factor() { if (dense64) cudaFree(dense64); }
 };
 
@@ -381,7 +381,7 @@ struct GatherBatch {
     if (g_kprof) {
       double e = 0;
       for (auto& x : probs) e += (double)x.M * x.N;
-      g_kprof->add_flops("gather_entries", e);   // work unit: matrix entries
+      g_kprof->add_flops(kname<C>("gather_entries", "gather_entries32"), e);   // work unit: matrix entries
     }
     CK(cudaGetLastError());
   }
@@ -408,7 +408,7 @@ struct GemmBatch {
     if (g_kprof) {
       double f = 0;
       for (auto& x : d) f += 8.0 * x.m * x.n * x.k;
-      g_kprof->add_flops("gemm_batched", f);
+      g_kprof->add_flops(kname<C>("gemm_batched", "gemm_batched32"), f);
     }
     CK(cudaGetLastError());
   }
@@ -779,8 +779,11 @@ void process_level(pm_factor* F, int lev, double tol) {
       for (int s2 = 0; s2 < S; ++s2) f += 20.0 * (double)(W[i] - s2 - 1) * (nn[i] - s2 - 1);
       fi += 4.0 * (double)kk[i] * kk[i] * (nn[i] - kk[i]);
     }
-    g_kprof->add_flops("cpqr_step", f);
-    g_kprof->add_flops("interp_solve", fi);
+    // FP64: 20 flops per trailing entry and step; FP32 (memory-bound): the
+    // algorithmic bytes, one read and one write of every trailing entry
+    if (std::is_same<C, double2>::value) g_kprof->add_flops("cpqr_step", f);
+    else g_kprof->add_flops("cpqr_step32", f / 20.0 * 2.0 * sizeof(C));
+    g_kprof->add_flops(kname<C>("interp_solve", "interp_solve32"), fi);
   }
   std::vector<int> hperm(std::max(total_n, 1));
   CK(cudaMemcpyAsync(hperm.data(), perm, std::max(total_n, 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1107,18 +1110,21 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
 }
 
 // Iterative refinement (mixed mode): x <- x + M^{-1} (b - A x) until the
-// relative residual of every column is below refine_tol.
+// relative residual of every column is below refine_tol.  With the dense
+// operator the residuals are formed in float-float arithmetic on the FP32
+// pipes (~1e-13 relative); once that residual meets the tolerance an FP64
+// product confirms it, and only FP64 residuals decide convergence.
 void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& ws, cudaStream_t st,
                    pm_solve_info* info) {
-  const int N = F->g->N;
+  const pm_geometry* g = F->g;
+  const int N = g->N;
   double2* Y = ws.get<double2>((size_t)N * nrhs);
   double2* R = ws.get<double2>((size_t)N * nrhs);
   double2* dX = ws.get<double2>((size_t)N * nrhs);
   double* norms = ws.get<double>(2 * (size_t)nrhs);
   double* scal = ws.get<double>(2 * (size_t)nrhs);
   std::vector<double> hn(2 * nrhs), hs(2 * nrhs);
-  auto residual = [&](const double2* x) {
-    apply_operator64(F, x, nrhs, Y, ws, st);
+  auto finish = [&]() {   // R = B - Y, column norms -> worst relative residual
     CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
     residual64(B, Y, R, N, nrhs, norms, st);
     CK(cudaMemcpyAsync(hn.data(), norms, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1126,6 +1132,15 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     double worst = 0;
     for (int r = 0; r < nrhs; ++r) worst = std::max(worst, std::sqrt(hn[2 * r]) / std::max(std::sqrt(hn[2 * r + 1]), 1e-300));
     return worst;
+  };
+  auto residual = [&](const double2* x) {
+    apply_operator64(F, x, nrhs, Y, ws, st);
+    return finish();
+  };
+  auto residual_low = [&](const double2* x) {
+    dense_matvec_ff(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
+    CK(cudaGetLastError());
+    return finish();
   };
   auto precond = [&](const double2* rhs, double2* out, const std::vector<double>& colnorm) {
     for (int r = 0; r < nrhs; ++r) {
@@ -1139,11 +1154,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   // x0 = 0, r0 = b (no operator application needed)
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)N * nrhs, st));
   CK(cudaMemsetAsync(Y, 0, sizeof(double2) * (size_t)N * nrhs, st));
-  CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
-  residual64(B, Y, R, N, nrhs, norms, st);
-  CK(cudaMemcpyAsync(hn.data(), norms, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  double res = 1.0;
+  double res = finish();
   std::vector<double> cn(nrhs);
   for (int r = 0; r < nrhs; ++r) cn[r] = std::sqrt(hn[2 * r]);
   int it = 0;
@@ -1152,13 +1163,18 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   std::vector<double> hist;
   while (it < maxit) {
     precond(R, dX, cn);
-    // X += dX
     axpy64(X, dX, N, nrhs, st);
     ++it;
-    res = residual(X);
+    res = -1;
+    if (F->dense64) {
+      const double low = residual_low(X);
+      if (low > tolr) res = low;   // not converged yet: the float-float residual drives the next step
+    }
+    const bool exact = res < 0;
+    if (exact) res = residual(X);
     hist.push_back(res);
     for (int r = 0; r < nrhs; ++r) cn[r] = std::sqrt(hn[2 * r]);
-    if (res <= tolr) break;
+    if (exact && res <= tolr) break;
   }
   if (info) {
     info->iterations = it;
@@ -1329,11 +1345,19 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
     Timer tt(F->st);
     if (F->precision == PM_FP64) {
       F->lev64.assign(F->L + 1, {});
-      for (int l = F->L; l >= 1; --l) process_level<double2>(F, l, id_tol);
+      for (int l = F->L; l >= 1; --l) {
+        Timer tl(F->st);
+        process_level<double2>(F, l, id_tol);
+        if (l < 16) F->stats.ms_level[l] = tl.stop(); else tl.stop();
+      }
       factor_top<double2>(F);
     } else {
       F->lev32.assign(F->L + 1, {});
-      for (int l = F->L; l >= 1; --l) process_level<float2>(F, l, id_tol);
+      for (int l = F->L; l >= 1; --l) {
+        Timer tl(F->st);
+        process_level<float2>(F, l, id_tol);
+        if (l < 16) F->stats.ms_level[l] = tl.stop(); else tl.stop();
+      }
       factor_top<float2>(F);
       // FP64 self blocks and index maps for the refinement residual
       F->scratch.reset();
@@ -1357,7 +1381,7 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
       // is then a skinny FP64 GEMM instead of a Hankel evaluation per node pair.
       size_t fr = 0, tot = 0;
       CK(cudaMemGetInfo(&fr, &tot));
-      const size_t need = sizeof(double2) * (size_t)g->N * g->N;
+      const size_t need = sizeof(float4) * (size_t)g->N * g->N;
       if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535 && need <= fr / 10 * 6) {
         CK(cudaMalloc(&F->dense64, need));
         OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
@@ -1367,12 +1391,11 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
           for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
           g_kprof->add_flops("dense_offdiag64", pairs * 164.0);
         }
-        CopyBatch<double2, double2> cb;
         for (int j = 0; j < g->m; ++j) {
           const int m2 = 2 * g->inc[j].n_nodes;
-          cb.add(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, g->N, m2, m2);
+          split_copy(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, (size_t)g->N, m2,
+                     m2, F->st);
         }
-        cb.run(F->scratch, F->st);
         CK(cudaGetLastError());
       }
     }

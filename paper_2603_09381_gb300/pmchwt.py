@@ -53,7 +53,7 @@ class pm_stats(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("N", ct.c_int32), ("K", ct.c_int32), ("skeleton", ct.c_int32 * 16),
                 ("ms_assemble", ct.c_double), ("ms_id", ct.c_double), ("ms_schur", ct.c_double),
                 ("ms_top", ct.c_double), ("ms_total", ct.c_double), ("cpqr_launches", ct.c_int32),
-                ("rank_checks", ct.c_int32), ("predictor_fallbacks", ct.c_int32)]
+                ("rank_checks", ct.c_int32), ("predictor_fallbacks", ct.c_int32), ("ms_level", ct.c_double * 16)]
 
 
 class pm_kernel_stat(ct.Structure):
@@ -212,7 +212,7 @@ class Factor:
         return {"levels": s.levels, "N": s.N, "K": s.K, "skeleton": list(s.skeleton)[: s.levels + 1],
                 "ms_assemble": s.ms_assemble, "ms_id": s.ms_id, "ms_schur": s.ms_schur, "ms_top": s.ms_top,
                 "ms_total": s.ms_total, "cpqr_launches": s.cpqr_launches, "rank_checks": s.rank_checks,
-                "predictor_fallbacks": s.predictor_fallbacks}
+                "predictor_fallbacks": s.predictor_fallbacks, "ms_level": list(s.ms_level)[: s.levels + 1]}
 
     def rank_data(self):
         """(X, T): features (n x 8) and adaptive ranks / n_g (n x 2) of every box and group."""

