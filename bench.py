@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "unknowns factored/s and solve ms at rel err ≤1e-8 vs FP64 oracle; % roofline"
 UNIT = "unknowns/s"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (profiling recipe table)
+FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock (recipe SM count and clock)
 
 
 def _dist():
@@ -166,7 +167,8 @@ def _traffic_for(kernel):
 
 FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",
                 "apply_offdiag64", "dense_matvec64", "dense_offdiag64"}        # FP64 flops
-FP32_FLOP_KERNELS = {"lu_update32", "lu_panel32", "lu_swap_trsm32", "getrs32", "gemm_batched32", "interp_solve32"}
+FP32_FLOP_KERNELS = {"lu_update32", "lu_panel32", "lu_swap_trsm32", "getrs32", "gemm_batched32", "interp_solve32",
+                     "qr_update32", "tc_gemm32"}
 BYTE_KERNELS = {"cpqr_step32"}     # memory-bound FP32 CPQR: algorithmic bytes
 
 
@@ -238,6 +240,11 @@ def _roofline(prof_tot, steps):
         roof.update({"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 dense FP64 (recipe)",
                      "traffic": _traffic_for(name)})
+    elif name in FP32_FLOP_KERNELS and d["ms"] > 0:
+        achieved = d["work"] / (d["ms"] / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": achieved, "peak": FP32_DERIVED_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_DERIVED_TFLOPS,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz", "traffic": _traffic_for(name)})
     elif name in BYTE_KERNELS and d["ms"] > 0:
         peak, src = _peaks()
         achieved = d["work"] / (d["ms"] / 1e3) / 1e9

@@ -93,7 +93,10 @@ typedef struct pm_factor pm_factor;
  *      complex128 operator out densely (N^2 x 16 bytes) when it fits in 60% of
  *      the free device memory and sum n_j <= 65535, so that each refinement
  *      step is one matrix product; PM_FLAG_NO_DENSE_OPERATOR keeps the
- *      on-the-fly operator instead.
+ *      on-the-fly operator instead.  PM_MIXED reduces every complex64 ID
+ *      input with at least twice as many rows as candidate columns to its
+ *      triangular factor (unpivoted Householder QR) before the pivoted QR;
+ *      PM_FLAG_NO_QR_FIRST pivots on the full input instead.
  * refine_tol: PM_MIXED: stop refining once every column's relative residual
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
@@ -222,7 +225,7 @@ typedef struct {
   double ms;
   double work;
 } pm_kernel_stat;
-enum { PM_FLAG_PROFILE = 1, PM_FLAG_NO_DENSE_OPERATOR = 2 };
+enum { PM_FLAG_PROFILE = 1, PM_FLAG_NO_DENSE_OPERATOR = 2, PM_FLAG_NO_QR_FIRST = 4 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 
 /* ---- learned ID-rank predictor (no counterpart in the paper) ----------------

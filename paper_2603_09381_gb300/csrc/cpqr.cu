@@ -197,6 +197,7 @@ __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t
     C dot = (d0 + d1) + (d2 + d3);
     dot.x = warp_sum(dot.x); dot.y = warp_sum(dot.y);
     const C a_s = col[s];
+    __syncwarp();                   // every lane has read col[s] before lane 0 rewrites it
     dot = a_s + csc * dot;          // v^H a with v = [1; x/(alpha - beta)]
     const C f = ctau * dot;         // H^H a = a - conj(tau) v (v^H a)
     const C fs = f * sc;

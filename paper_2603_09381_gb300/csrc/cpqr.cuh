@@ -41,6 +41,27 @@ struct CopyProb { const S* src; int lds; D* dst; int ldd; int m; int n; };
 
 struct PermFill { int* perm; int n; int done; };   // perm[done..n) <- unchosen columns, ascending
 
+// Unpivoted blocked Householder QR of a tall Z (W x n, W > n) in place: the
+// n x n triangle R ends in the top rows with zeros below its diagonal.  Column
+// norms of every trailing block are those of Z, so the column-pivoted QR of R
+// picks the pivots and R factor of Z's (exact arithmetic).
+constexpr int QR_NB = 32;        // panel width
+template <typename C>
+struct QrProb {
+  C* Z; int ld; int W; int n;
+  C* T;                          // QR_NB x QR_NB: compact-WY factor of the current panel
+  C* V;                          // W x QR_NB (leading dimension W), or NULL: the panel's V
+                                 // (rows j0.. at rows 0..) written out with its unit diagonal
+};
+// Panels [j0, j0 + QR_NB) of every matrix with j0 < n; max_tiles = the most
+// 32-column tiles right of a panel in any matrix.
+template <typename C>
+void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st);
+template <typename C>
+void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, cudaStream_t st);
+template <typename C>
+void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t st);
+
 void complete_perm(const PermFill* d_prob, int nprob, cudaStream_t st);
 template <typename C>
 void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, cudaStream_t st);

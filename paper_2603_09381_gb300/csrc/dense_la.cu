@@ -12,6 +12,7 @@ namespace {
 
 constexpr int TB = 32;   // output tile
 constexpr int TK = 16;   // k step
+constexpr int MAXNB = 16;   // panel width bound of the LU kernels
 
 // One 32 x 32 output tile of  Cm = alpha * A * B + beta * Cm  (256 threads).
 template <typename C>
@@ -79,10 +80,21 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const GemmDesc<C>* __restr
 
 // ---- LU with partial pivoting (blocked, right-looking) ---------------------------------
 
-// Panel: columns [p, p+jb) of rows [p, m), one CTA per matrix.  Pivot = the
-// largest |a|^2 in the column, lowest row index on ties.
-template <typename C>
-__global__ void __launch_bounds__(256) k_lu_panel(const LuProb<C>* __restrict__ P, int p, int nb) {
+__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float2 shfl_c(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Panel: columns [p, p+jb) of rows [p, m), one CTA per matrix, left-looking
+// (Crout): column c is brought up to date only when it is reached, from the
+// final L entries of the panel's earlier columns, so every entry is stored
+// once per column step and the update is fused with the pivot search.
+// Pivot = the largest |a|^2 in the column, lowest row index on ties (the
+// same choice as the right-looking order, up to rounding).
+template <typename C, int NT>
+__global__ void __launch_bounds__(NT) k_lu_panel(const LuProb<C>* __restrict__ P, int p, int nb) {
   typedef typename real_of<C>::type R;
   const LuProb<C> pr = P[blockIdx.x];
   const int m = pr.m;
@@ -90,30 +102,66 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuProb<C>* __restrict__ 
   const int jb = min(nb, m - p);
   C* A = pr.A;
   const size_t ld = pr.ld;
-  __shared__ R sval[256];
-  __shared__ int sidx[256];
-  __shared__ C rowc[64];
+  __shared__ R sval[NT / 32];
+  __shared__ int sidx[NT / 32];
+  __shared__ C s_l[MAXNB][MAXNB + 1];
+  __shared__ C s_u[MAXNB];
   __shared__ int s_piv;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int jj = 0; jj < jb; ++jj) {
     const int c = p + jj;
-    R best = -1; int bi = m;
-    for (int r = c + tid; r < m; r += 256) {
-      R v = abs2(A[r + c * ld]);
-      if (v > best) { best = v; bi = r; }
-    }
-    sval[tid] = best; sidx[tid] = bi;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) {
-        R v2 = sval[tid + s]; int i2 = sidx[tid + s];
-        if (v2 > sval[tid] || (v2 == sval[tid] && i2 < sidx[tid])) { sval[tid] = v2; sidx[tid] = i2; }
+    C* colc = A + (size_t)c * ld;
+    if (jj > 0) {
+      // U[0:jj, jj] = L11^{-1} A[p:c, c] (unit lower L11 of the current rows)
+      for (int e = tid; e < jj * jj; e += NT) s_l[e % jj][e / jj] = A[p + e % jj + (size_t)(p + e / jj) * ld];
+      __syncthreads();
+      if (warp == 0) {
+        C x = lane < jj ? colc[p + lane] : czero<C>();
+        for (int l = 0; l < jj - 1; ++l) {
+          const C xl = shfl_c(x, l);
+          if (lane > l && lane < jj) cfms(x, s_l[lane][l], xl);
+        }
+        if (lane < jj) {
+          s_u[lane] = x;
+          colc[p + lane] = x;
+        }
       }
       __syncthreads();
     }
+    // rows c..m-1: a -= L[r, p:c] u, then the pivot search on the result
+    R best = -1;
+    int bi = m;
+    for (int r = c + tid; r < m; r += NT) {
+      C lr[MAXNB];   // the row's L entries, loaded together
+#pragma unroll
+      for (int l = 0; l < MAXNB; ++l) if (l < jj) lr[l] = A[r + (size_t)(p + l) * ld];
+      // four partial sums: short dependent chains (FP64 latency)
+      C a0 = colc[r], a1 = czero<C>(), a2 = czero<C>(), a3 = czero<C>();
+#pragma unroll
+      for (int l = 0; l < MAXNB; l += 4) {
+        if (l < jj) cfms(a0, lr[l], s_u[l]);
+        if (l + 1 < jj) cfms(a1, lr[l + 1], s_u[l + 1]);
+        if (l + 2 < jj) cfms(a2, lr[l + 2], s_u[l + 2]);
+        if (l + 3 < jj) cfms(a3, lr[l + 3], s_u[l + 3]);
+      }
+      const C a = (a0 + a1) + (a2 + a3);
+      if (jj > 0) colc[r] = a;
+      const R v = abs2(a);
+      if (v > best) { best = v; bi = r; }   // rows ascend: the first of equal values stays
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+    }
+    if (lane == 0) { sval[warp] = best; sidx[warp] = bi; }
+    __syncthreads();
     if (tid == 0) {
+      R bv = sval[0];
       int piv = sidx[0];
-      if (!(sval[0] > 0)) { piv = c; if (*pr.info == 0) *pr.info = c + 1; }
+      for (int w = 1; w < NT / 32; ++w)
+        if (sval[w] > bv || (sval[w] == bv && sidx[w] < piv)) { bv = sval[w]; piv = sidx[w]; }
+      if (!(bv > 0)) { piv = c; if (*pr.info == 0) *pr.info = c + 1; }
       s_piv = piv;
       pr.ipiv[c] = piv;
     }
@@ -122,19 +170,19 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuProb<C>* __restrict__ 
     if (piv != c && tid < jb) {
       C* a = A + c + (size_t)(p + tid) * ld;
       C* b = A + piv + (size_t)(p + tid) * ld;
-      C t = *a; *a = *b; *b = t;
+      const C t = *a; *a = *b; *b = t;
     }
     __syncthreads();
-    if (tid < jb) rowc[tid] = A[c + (size_t)(p + tid) * ld];
-    __syncthreads();
-    const C d = rowc[jj];
+    const C d = colc[c];
     if (abs2(d) > 0) {
       const C inv = cdiv(mk((R)1, (R)0), d);
-      for (int r = c + 1 + tid; r < m; r += 256) {
-        C l = A[r + c * ld] * inv;
-        A[r + c * ld] = l;
-        for (int j = jj + 1; j < jb; ++j) cfms(A[r + (size_t)(p + j) * ld], l, rowc[j]);
+      int r = c + 1 + tid;
+      for (; r + NT < m; r += 2 * NT) {   // two rows per pass: both loads in flight
+        const C a0 = colc[r], a1 = colc[r + NT];
+        colc[r] = a0 * inv;
+        colc[r + NT] = a1 * inv;
       }
+      if (r < m) colc[r] = colc[r] * inv;
     }
     __syncthreads();
   }
@@ -142,28 +190,56 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuProb<C>* __restrict__ 
 
 // Row interchanges of the panel applied to every other column, then the unit
 // lower triangular solve U12 = L11^{-1} A12 on the columns right of the panel.
+// Thread 0 composes the panel's jb interchanges into one map over the rows
+// they touch (the jb panel rows first, then at most jb rows below), so each
+// column does independent gathers instead of a chain of dependent swaps.
 template <typename C>
 __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuProb<C>* __restrict__ P, int p, int nb) {
+  constexpr int MB = MAXNB;
   const LuProb<C> pr = P[blockIdx.y];
   const int m = pr.m;
   if (p >= m) return;
   const int jb = min(nb, m - p);
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m || (j >= p && j < p + jb)) return;
+  __shared__ int s_row[2 * MB], s_org[2 * MB];
+  __shared__ int s_cnt;
+  __shared__ C s_l[MB][MB + 1];
   C* A = pr.A;
   const size_t ld = pr.ld;
-  C* col = A + (size_t)j * ld;
-  for (int c = p; c < p + jb; ++c) {
-    int r = pr.ipiv[c];
-    if (r != c) { C t = col[c]; col[c] = col[r]; col[r] = t; }
-  }
-  if (j >= p + jb) {
-    for (int r = 1; r < jb; ++r) {
-      C acc = col[p + r];
-      for (int s = 0; s < r; ++s) cfms(acc, A[p + r + (size_t)(p + s) * ld], col[p + s]);
-      col[p + r] = acc;
+  if (threadIdx.x == 0) {
+    int cnt = jb;
+    for (int i = 0; i < jb; ++i) { s_row[i] = p + i; s_org[i] = p + i; }
+    for (int c = 0; c < jb; ++c) {
+      const int r = pr.ipiv[p + c];
+      int ir = r - p;
+      if (ir >= jb) {
+        ir = -1;
+        for (int i = jb; i < cnt; ++i) if (s_row[i] == r) ir = i;
+        if (ir < 0) { ir = cnt++; s_row[ir] = r; s_org[ir] = r; }
+      }
+      const int t = s_org[c]; s_org[c] = s_org[ir]; s_org[ir] = t;
     }
+    s_cnt = cnt;
   }
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) s_l[e % jb][e / jb] = A[p + e % jb + (size_t)(p + e / jb) * ld];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m || (j >= p && j < p + jb)) return;
+  C* col = A + (size_t)j * ld;
+  const int cnt = s_cnt;
+  C v[2 * MB];
+#pragma unroll
+  for (int i = 0; i < 2 * MB; ++i) v[i] = i < cnt ? col[s_org[i]] : czero<C>();
+#pragma unroll
+  for (int i = 0; i < 2 * MB; ++i) if (i >= jb && i < cnt) col[s_row[i]] = v[i];   // rows below the panel
+  if (j >= p + jb) {
+#pragma unroll
+    for (int r = 1; r < MB; ++r)
+#pragma unroll
+      for (int q = 0; q < r; ++q)
+        if (r < jb) cfms(v[r], s_l[r][q], v[q]);
+  }
+#pragma unroll
+  for (int i = 0; i < MB; ++i) if (i < jb) col[p + i] = v[i];
 }
 
 // Trailing update A22 -= L21 * U12.
@@ -200,29 +276,73 @@ __global__ void k_getrs_swap(const SolveProb<C>* __restrict__ P) {
   }
 }
 
-// Diagonal block solve on rows [p, p+jb): unit lower (lower=1) or upper.
+// Row interchanges: thread 0 composes the m interchanges into one map in
+// shared memory (position i receives original row src[i]); the CTA then
+// gathers each of its right-hand sides through a shared-memory stage.
+constexpr int SW_RHS = 32;   // right-hand sides per CTA
 template <typename C>
-__global__ void k_getrs_diag(const SolveProb<C>* __restrict__ P, int p, int nb, int lower) {
+__global__ void __launch_bounds__(256) k_getrs_swap_smem(const SolveProb<C>* __restrict__ P) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const SolveProb<C> pr = P[blockIdx.y];
+  const int j0 = blockIdx.x * SW_RHS;
+  if (j0 >= pr.nrhs) return;
+  C* stage = reinterpret_cast<C*>(sm_raw);
+  int* src = reinterpret_cast<int*>(stage + pr.m);
+  for (int i = threadIdx.x; i < pr.m; i += blockDim.x) src[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int c = 0; c < pr.m; ++c) {
+      const int r = pr.ipiv[c];
+      if (r != c) { const int t = src[c]; src[c] = src[r]; src[r] = t; }
+    }
+  __syncthreads();
+  const int j1 = min(pr.nrhs, j0 + SW_RHS);
+  for (int j = j0; j < j1; ++j) {
+    C* col = pr.B + (size_t)j * pr.ldb;
+    for (int i = threadIdx.x; i < pr.m; i += blockDim.x) stage[i] = col[src[i]];
+    __syncthreads();
+    for (int i = threadIdx.x; i < pr.m; i += blockDim.x) col[i] = stage[i];
+    __syncthreads();
+  }
+}
+
+// Diagonal block solve on rows [p, p+jb), jb <= 32: unit lower (lower=1) or
+// upper.  The block is staged in shared memory; one warp per right-hand side,
+// lane r holding row p+r, each solved entry broadcast by a shuffle.
+constexpr int DG_RHS = 32;   // right-hand sides per CTA (8 warps)
+template <typename C>
+__global__ void __launch_bounds__(256) k_getrs_diag(const SolveProb<C>* __restrict__ P, int p, int nb, int lower) {
+  typedef typename real_of<C>::type R;
+  __shared__ C sa[32][33];
   const SolveProb<C> pr = P[blockIdx.y];
   if (p >= pr.m) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= pr.nrhs) return;
   const int jb = min(nb, pr.m - p);
-  const C* A = pr.A;
-  const size_t ld = pr.ld;
-  C* col = pr.B + (size_t)j * pr.ldb;
-  if (lower) {
-    for (int r = 1; r < jb; ++r) {
-      C acc = col[p + r];
-      for (int s = 0; s < r; ++s) cfms(acc, A[p + r + (size_t)(p + s) * ld], col[p + s]);
-      col[p + r] = acc;
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    const int r = e % jb, c = e / jb;
+    sa[r][c] = pr.A[p + r + (size_t)(p + c) * pr.ld];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  // reciprocals of the diagonal, all lanes at once (the solve chain below
+  // then multiplies instead of dividing: FP64 division is a long sequence)
+  const C dinv = (!lower && lane < jb) ? cdiv(mk((R)1, (R)0), sa[lane][lane]) : czero<C>();
+  const int j1 = min(pr.nrhs, (int)(blockIdx.x + 1) * DG_RHS);
+  for (int j = blockIdx.x * DG_RHS + (threadIdx.x >> 5); j < j1; j += blockDim.x >> 5) {
+    C* col = pr.B + (size_t)j * pr.ldb + p;
+    C x = lane < jb ? col[lane] : czero<C>();
+    if (lower) {
+      for (int c = 0; c < jb - 1; ++c) {
+        const C xc = shfl_c(x, c);
+        if (lane > c && lane < jb) cfms(x, sa[lane][c], xc);
+      }
+    } else {
+      for (int c = jb - 1; c >= 0; --c) {
+        if (lane == c) x = x * dinv;
+        const C xc = shfl_c(x, c);
+        if (lane < c) cfms(x, sa[lane][c], xc);
+      }
     }
-  } else {
-    for (int r = jb - 1; r >= 0; --r) {
-      C acc = col[p + r];
-      for (int s = r + 1; s < jb; ++s) cfms(acc, A[p + r + (size_t)(p + s) * ld], col[p + s]);
-      col[p + r] = cdiv(acc, A[p + r + (size_t)(p + r) * ld]);
-    }
+    if (lane < jb) col[lane] = x;
   }
 }
 
@@ -258,6 +378,7 @@ void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob
 }
 
 constexpr int LU_NB = 16;
+static_assert(LU_NB <= MAXNB, "LU panel wider than the kernels' shared tiles");
 constexpr int RS_NB = 32;
 
 template <typename C>
@@ -276,7 +397,9 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
       }
     }
     KPROF_BEGIN(st);
-    k_lu_panel<C><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
+    // a few large matrices (the top-level LU): more threads per column
+    if (nprob <= 8 && maxm >= 2048) k_lu_panel<C, 512><<<nprob, 512, 0, st>>>(d_prob, p, LU_NB);
+    else k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
     KPROF_END(st, kname<C>("lu_panel", "lu_panel32"), fp);
     dim3 g1((maxm + 255) / 256, nprob);
@@ -304,12 +427,21 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
   if (g_kprof)
     for (int i = 0; i < nprob; ++i) fl += 8.0 * (double)h_m[i] * h_m[i] * h_rhs[i];
   KPROF_BEGIN(st);
-  dim3 gs((maxrhs + 127) / 128, nprob);
-  k_getrs_swap<C><<<gs, 128, 0, st>>>(d_prob);
+  const size_t swap_smem = (size_t)maxm * (sizeof(C) + sizeof(int));
+  if (swap_smem <= 200 * 1024) {
+    // the same value every time: idempotent across threads and devices
+    if (swap_smem > 48 * 1024)
+      cudaFuncSetAttribute(k_getrs_swap_smem<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    k_getrs_swap_smem<C><<<dim3((maxrhs + SW_RHS - 1) / SW_RHS, nprob), 256, swap_smem, st>>>(d_prob);
+  } else {
+    dim3 gsw((maxrhs + 127) / 128, nprob);
+    k_getrs_swap<C><<<gsw, 128, 0, st>>>(d_prob);
+  }
   pm_launch_count_add(1);
+  dim3 gs((maxrhs + DG_RHS - 1) / DG_RHS, nprob);
   const int tiles_n = (maxrhs + TB - 1) / TB;
   for (int p = 0; p < maxm; p += RS_NB) {
-    k_getrs_diag<C><<<gs, 128, 0, st>>>(d_prob, p, RS_NB, 1);
+    k_getrs_diag<C><<<gs, 256, 0, st>>>(d_prob, p, RS_NB, 1);
     pm_launch_count_add(1);
     int mt = maxm - p - RS_NB;
     if (mt > 0) {
@@ -320,7 +452,7 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
   }
   int last = ((maxm - 1) / RS_NB) * RS_NB;
   for (int p = last; p >= 0; p -= RS_NB) {
-    k_getrs_diag<C><<<gs, 128, 0, st>>>(d_prob, p, RS_NB, 0);
+    k_getrs_diag<C><<<gs, 256, 0, st>>>(d_prob, p, RS_NB, 0);
     pm_launch_count_add(1);
     if (p > 0) {
       dim3 g2(((p + TB - 1) / TB) * tiles_n, nprob);

@@ -1,0 +1,324 @@
+// Blocked, unpivoted Householder QR of the tall ID inputs (W x n, W > n),
+// ahead of their column-pivoted QR (paper Sec. 3 computes the ID by CPQR).
+// Q^H preserves the norm of every trailing column block, so the pivoted
+// factorization of the n x n triangle R picks the pivots of Z and returns its
+// R (exact arithmetic); the pivoted steps then stream n instead of W rows.
+//
+// Per panel of QR_NB columns: one CTA per matrix factors the panel (LAPACK
+// zlarfg phase convention, H = I - tau v v^H, Q^H applied) with one pass over
+// the panel per reflector (the pass that applies reflector j also sums the
+// norm and the dot products that define reflector j+1), and forms the
+// compact-WY factor T (Q = I - V T V^H); then one CTA per (matrix, 32-column
+// tile) applies Q^H = I - V T^H V^H to the tile in two passes over its rows
+// (Y = V^H C, then C -= V (T^H Y)).
+#include "cpqr.cuh"
+#include "prof.cuh"
+
+namespace {
+
+constexpr int PT = 512;      // panel CTA: two threads per row, 16 panel columns each
+constexpr int PR = PT / 2;   // rows per sweep of the panel CTA
+constexpr int UT = 256;      // update CTA
+constexpr int RC = 32;       // rows per staged chunk
+constexpr int HB = QR_NB / 2;
+
+// V entry (row r, panel column j) of a panel starting at j0: unit diagonal,
+// zero above, the stored reflector below.
+template <typename C>
+__device__ __forceinline__ C v_entry(const QrProb<C>& p, int j0, int jb, int r, int j) {
+  typedef typename real_of<C>::type R;
+  if (j >= jb || r >= p.W) return czero<C>();
+  const int d = j0 + j;
+  if (r < d) return czero<C>();
+  if (r == d) return mk((R)1, (R)0);
+  return p.Z[r + (size_t)d * p.ld];
+}
+
+// One pass over the panel rows: applies reflector `ja` (if ja >= 0; its
+// factors f_k in s_f, its column scaled by sc into v) and accumulates the
+// inputs of step jn = ja + 1: N = sum_{r >= c'} |a_jn[r]|^2 and
+// S_k = sum_{r > c'} conj(a_jn[r]) a_k[r] for k > jn (c' = j0 + jn), with row
+// c' itself stored to s_row.  Lanes 0-15 of a warp hold panel columns 0-15 of
+// 16 rows, lanes 16-31 columns 16-31 of the same rows; every entry a thread
+// needs is loaded before the pair stores anything.
+template <typename C>
+__device__ __forceinline__ void panel_pass(const QrProb<C>& p, int j0, int jb, int ja, const C* s_f, C sc,
+                                           C* s_row, typename real_of<C>::type& N, C* S) {
+  typedef typename real_of<C>::type R;
+  const int jn = ja + 1;
+  const int ca = j0 + ja, cn = j0 + jn;
+  C* Zp = p.Z + (size_t)j0 * p.ld;
+  const size_t ld = p.ld;
+  const int lane = threadIdx.x & 31, half = lane >> 4;
+  const int kb = half * HB;
+  const int kmin = ja >= 0 ? ja : jn;
+  const C fjn = (ja >= 0 && jn < jb) ? s_f[jn] : czero<C>();
+  // warp-uniform sweep (the __syncwarp below needs every lane), rows guarded
+  for (int r0 = (ja >= 0 ? ca : cn) + (threadIdx.x >> 5) * 16; r0 < p.W; r0 += PR) {
+    const int r = r0 + (lane & 15);
+    const bool act = r < p.W;
+    C v[HB];
+#pragma unroll
+    for (int k = 0; k < HB; ++k)
+      if (act && kb + k >= kmin && kb + k < jb) v[k] = Zp[r + (size_t)(kb + k) * ld];
+    const C x = (act && ja >= 0) ? Zp[r + (size_t)ja * ld] : czero<C>();
+    const C yold = (act && jn < jb) ? Zp[r + (size_t)jn * ld] : czero<C>();
+    __syncwarp();   // both threads of the pair have read the row before either writes it
+    if (!act) continue;
+    C vr = czero<C>();
+    if (ja >= 0) {
+      vr = (r == ca) ? mk((R)1, (R)0) : x * sc;
+      if (r > ca && half == (ja >= HB)) Zp[r + (size_t)ja * ld] = vr;
+#pragma unroll
+      for (int k = 0; k < HB; ++k)
+        if (kb + k > ja && kb + k < jb) {
+          cfms(v[k], s_f[kb + k], vr);
+          Zp[r + (size_t)(kb + k) * ld] = v[k];
+        }
+    }
+    if (jn < jb && r >= cn) {
+      C y = yold;
+      if (ja >= 0) cfms(y, fjn, vr);
+      if (half == 0) N += abs2(y);
+      if (r == cn) {
+#pragma unroll
+        for (int k = 0; k < HB; ++k) if (kb + k >= jn && kb + k < jb) s_row[kb + k] = v[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < HB; ++k) if (kb + k > jn && kb + k < jb) cfma_conj(S[k], y, v[k]);
+      }
+    }
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P, int j0) {
+  typedef typename real_of<C>::type R;
+  const QrProb<C> p = P[blockIdx.x];
+  if (j0 >= p.n) return;
+  const int jb = min(QR_NB, p.n - j0);
+  const int W = p.W;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4;
+  __shared__ R s_red[PT / 32][2 * QR_NB + 1];
+  __shared__ R s_tot[2 * QR_NB + 1];
+  __shared__ C s_f[QR_NB];
+  __shared__ C s_row[QR_NB];
+  __shared__ C s_tau[QR_NB];
+  __shared__ C s_sc;
+  __shared__ C s_v[RC][QR_NB + 1];
+  __shared__ C s_g[QR_NB][QR_NB + 1];
+  __shared__ C s_t[QR_NB][QR_NB + 1];
+  C sc = czero<C>();
+  for (int ja = -1; ja < jb; ++ja) {
+    R N = 0;
+    C S[HB];
+#pragma unroll
+    for (int k = 0; k < HB; ++k) S[k] = czero<C>();
+    panel_pass(p, j0, jb, ja, s_f, sc, s_row, N, S);
+    const int jn = ja + 1;
+    if (jn >= jb) break;
+    // block sums: N over all lanes, S_k over the 16 lanes of each half
+    N = warp_sum(N);
+#pragma unroll
+    for (int k = 0; k < HB; ++k)
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        S[k].x += __shfl_xor_sync(0xffffffffu, S[k].x, o);
+        S[k].y += __shfl_xor_sync(0xffffffffu, S[k].y, o);
+      }
+    if ((lane & 15) == 0) {
+#pragma unroll
+      for (int k = 0; k < HB; ++k) {
+        s_red[warp][2 * (half * HB + k)] = S[k].x;
+        s_red[warp][2 * (half * HB + k) + 1] = S[k].y;
+      }
+      if (half == 0) s_red[warp][2 * QR_NB] = N;
+    }
+    __syncthreads();
+    if (tid < 2 * QR_NB + 1) {
+      R t = 0;
+#pragma unroll
+      for (int w = 0; w < PT / 32; ++w) t += s_red[w][tid];
+      s_tot[tid] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // reflector of column jn (LAPACK zlarfg phase), factors of the next pass
+      const int c = j0 + jn;
+      const C alpha = s_row[jn];
+      const R xnorm = sqrt(s_tot[2 * QR_NB]);
+      C tau = czero<C>(), scn = czero<C>();
+      R beta = 0;
+      if (xnorm > 0) {
+        beta = -copysign(xnorm, alpha.x);
+        const C bm = mk(beta, (R)0);
+        tau = cdiv(bm - alpha, bm);
+        scn = cdiv(mk((R)1, (R)0), alpha - bm);
+      }
+      p.Z[c + (size_t)c * p.ld] = mk(beta, (R)0);
+      s_tau[jn] = tau;
+      s_sc = scn;
+      const C ctau = conj(tau), cscn = conj(scn);
+      for (int k = jn + 1; k < jb; ++k) s_f[k] = ctau * (s_row[k] + cscn * mk(s_tot[2 * k], s_tot[2 * k + 1]));
+    }
+    __syncthreads();
+    sc = s_sc;
+  }
+  __syncthreads();
+  // G = V^H V over chunks of rows staged in shared memory (V also written out)
+  {
+    const int gi = tid & 31, gj = tid >> 5;   // G[gi][gj] and G[gi][gj + 16]
+    C g0 = czero<C>(), g1 = czero<C>();
+    for (int r0 = j0; r0 < W; r0 += RC) {
+      for (int e = tid; e < RC * QR_NB; e += PT) {
+        const int i = e % RC, j = e / RC;
+        const C v = v_entry(p, j0, jb, r0 + i, j);
+        s_v[i][j] = v;
+        if (p.V && r0 + i < W) p.V[(r0 + i - j0) + (size_t)j * p.W] = v;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int i = 0; i < RC; ++i) {
+        const C a = s_v[i][gi];
+        cfma_conj(g0, a, s_v[i][gj]);
+        cfma_conj(g1, a, s_v[i][gj + 16]);
+      }
+      __syncthreads();
+    }
+    s_g[gi][gj] = g0;
+    s_g[gi][gj + 16] = g1;
+  }
+  // T: T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
+  for (int e = tid; e < QR_NB * QR_NB; e += PT) {
+    const int i = e % QR_NB, j = e / QR_NB;
+    s_t[i][j] = (i == j && i < jb) ? s_tau[i] : czero<C>();
+  }
+  __syncthreads();
+  for (int j = 1; j < jb; ++j) {
+    if (tid < j) {
+      C acc = czero<C>();
+      for (int l = tid; l < j; ++l) cfma(acc, s_t[tid][l], s_g[l][j]);
+      s_t[tid][j] = -(s_tau[j] * acc);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < QR_NB * QR_NB; e += PT) p.T[e] = s_t[e % QR_NB][e / QR_NB];
+}
+
+template <typename C>
+__global__ void __launch_bounds__(UT) k_qr_update(const QrProb<C>* __restrict__ P, int j0) {
+  const QrProb<C> p = P[blockIdx.y];
+  if (j0 >= p.n) return;
+  const int jb = min(QR_NB, p.n - j0);
+  const int c0 = j0 + jb + blockIdx.x * 32;
+  if (c0 >= p.n) return;
+  const int nc = min(32, p.n - c0);
+  const int W = p.W, tid = threadIdx.x;
+  __shared__ C s_v[RC][QR_NB + 1];
+  __shared__ C s_c[RC][33];
+  __shared__ C s_y[QR_NB][33];
+  __shared__ C s_t[QR_NB][QR_NB + 1];
+  const int tx = tid & 15, ty = tid >> 4;
+  // pass 1: Y = V^H C
+  C y00 = czero<C>(), y01 = czero<C>(), y10 = czero<C>(), y11 = czero<C>();
+  for (int r0 = j0; r0 < W; r0 += RC) {
+    for (int e = tid; e < RC * 32; e += UT) {
+      const int i = e % RC, j = e / RC, r = r0 + i;
+      s_v[i][j] = v_entry(p, j0, jb, r, j);
+      s_c[i][j] = (j < nc && r < W) ? p.Z[r + (size_t)(c0 + j) * p.ld] : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int i = 0; i < RC; ++i) {
+      const C a0 = s_v[i][tx], a1 = s_v[i][tx + 16], b0 = s_c[i][ty], b1 = s_c[i][ty + 16];
+      cfma_conj(y00, a0, b0); cfma_conj(y01, a0, b1);
+      cfma_conj(y10, a1, b0); cfma_conj(y11, a1, b1);
+    }
+    __syncthreads();
+  }
+  s_y[tx][ty] = y00; s_y[tx][ty + 16] = y01;
+  s_y[tx + 16][ty] = y10; s_y[tx + 16][ty + 16] = y11;
+  for (int e = tid; e < QR_NB * QR_NB; e += UT) s_t[e % QR_NB][e / QR_NB] = p.T[e];
+  __syncthreads();
+  // Y <- T^H Y (T upper triangular)
+  C z[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = tx + 16 * a, cc = ty + 16 * b;
+      C acc = czero<C>();
+      for (int l = 0; l <= i; ++l) cfma_conj(acc, s_t[l][i], s_y[l][cc]);
+      z[a][b] = acc;
+    }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) s_y[tx + 16 * a][ty + 16 * b] = z[a][b];
+  __syncthreads();
+  // pass 2: C -= V Y; thread: one row of the chunk, 4 columns
+  const int ri = tid & 31, g = tid >> 5;
+  for (int r0 = j0; r0 < W; r0 += RC) {
+    for (int e = tid; e < RC * QR_NB; e += UT) {
+      const int i = e % RC, j = e / RC;
+      s_v[i][j] = v_entry(p, j0, jb, r0 + i, j);
+    }
+    __syncthreads();
+    C acc[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
+    for (int j = 0; j < jb; ++j) {
+      const C v = s_v[ri][j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cfma(acc[q], v, s_y[j][4 * g + q]);
+    }
+    const int r = r0 + ri;
+    if (r < W) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * g + q < nc) {
+          C* pz = p.Z + r + (size_t)(c0 + 4 * g + q) * p.ld;
+          *pz = *pz - acc[q];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// Zeros below the diagonal of the top n x n block (the reflectors' storage).
+template <typename C>
+__global__ void k_qr_zero_lower(const QrProb<C>* __restrict__ P) {
+  const QrProb<C> p = P[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= p.n) return;
+  C* col = p.Z + (size_t)j * p.ld;
+  for (int r = j + 1 + threadIdx.x; r < p.n; r += blockDim.x) col[r] = czero<C>();
+}
+
+}  // namespace
+
+template <typename C>
+void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st) {
+  if (nprob <= 0) return;
+  KPROF_BEGIN(st);
+  k_qr_panel<C><<<nprob, PT, 0, st>>>(d_prob, j0);
+  pm_launch_count_add(1);
+  KPROF_END(st, kname<C>("qr_panel", "qr_panel32"), 0.0);
+}
+template <typename C>
+void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, cudaStream_t st) {
+  if (nprob <= 0 || max_tiles <= 0) return;
+  KPROF_BEGIN(st);
+  k_qr_update<C><<<dim3(max_tiles, nprob), UT, 0, st>>>(d_prob, j0);
+  pm_launch_count_add(1);
+  KPROF_END(st, kname<C>("qr_update", "qr_update32"), 0.0);
+}
+template <typename C>
+void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t st) {
+  if (nprob <= 0 || max_n <= 0) return;
+  k_qr_zero_lower<C><<<dim3(max_n, nprob), 256, 0, st>>>(d_prob);
+  pm_launch_count_add(1);
+}
+
+template void qr_panel<float2>(const QrProb<float2>*, int, int, cudaStream_t);
+template void qr_update<float2>(const QrProb<float2>*, int, int, int, cudaStream_t);
+template void qr_zero_lower<float2>(const QrProb<float2>*, int, int, cudaStream_t);
