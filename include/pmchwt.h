@@ -36,7 +36,7 @@ typedef enum {
   PM_ERR_CUDA = 3,          /* CUDA runtime error (message names the call) */
   PM_ERR_SINGULAR = 4,      /* exactly singular pivot in an LU, or R A^{-1} L singular */
   PM_ERR_NOT_CONVERGED = 5, /* reserved for iterative refinement */
-  PM_ERR_TIMEOUT = 6,       /* reserved for bounded device waits */
+  PM_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (tensor-core completion) */
   PM_ERR_GEOMETRY = 7,      /* inclusions not on a grid, two in one cell, ... */
   PM_ERR_UNSUPPORTED = 8    /* valid input the library does not handle yet */
 } pm_status;
@@ -96,7 +96,11 @@ typedef struct pm_factor pm_factor;
  *      on-the-fly operator instead.  PM_MIXED reduces every complex64 ID
  *      input with at least twice as many rows as candidate columns to its
  *      triangular factor (unpivoted Householder QR) before the pivoted QR;
- *      PM_FLAG_NO_QR_FIRST pivots on the full input instead.
+ *      PM_FLAG_NO_QR_FIRST pivots on the full input instead.  The trailing
+ *      updates of that QR run on the FP32 CUDA cores; PM_FLAG_TENSOR_CORES
+ *      moves them to the tensor cores (pm_gemm_c32's kernel), which is
+ *      slower today and, over the long row reductions, adds enough rounding
+ *      error to raise the ranks at the complex64 threshold.
  * refine_tol: PM_MIXED: stop refining once every column's relative residual
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
@@ -225,7 +229,7 @@ typedef struct {
   double ms;
   double work;
 } pm_kernel_stat;
-enum { PM_FLAG_PROFILE = 1, PM_FLAG_NO_DENSE_OPERATOR = 2, PM_FLAG_NO_QR_FIRST = 4 };
+enum { PM_FLAG_PROFILE = 1, PM_FLAG_NO_DENSE_OPERATOR = 2, PM_FLAG_NO_QR_FIRST = 4, PM_FLAG_TENSOR_CORES = 8 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 
 /* ---- learned ID-rank predictor (no counterpart in the paper) ----------------
@@ -256,6 +260,22 @@ pm_status pm_mlp_train(void* theta, int32_t nsamples, const float* X, const floa
 /* Number of CUDA kernel launches this library has made in this process
  * (no counterpart in the paper; measurement aid). */
 pm_status pm_launch_counter(uint64_t* out);
+
+/* Complex64 product on the tensor cores: the tcgen05 kernel (kind::tf32
+ * with each FP32 operand split into two tf32 parts, three products, FP32
+ * accumulation in tensor memory) that the complex64 QR updates can use,
+ * exported so that its numerics can be checked on their own.  No counterpart
+ * in the paper.  C = alpha op(A) op(B) + beta C with column-major DEVICE
+ * buffers of interleaved (re, im) floats: op(A) is m x k, A itself (lda >= m)
+ * or with conj_a != 0 the conjugate transpose of a stored k x m matrix
+ * (lda >= k); op(B) is k x n, B (ldb >= k) or with conj_b the conjugate
+ * transpose of a stored n x k matrix (ldb >= n); C is m x n (ldc >= m).
+ * alpha, beta: host pointers to (re, im).  Runs on `stream` (NULL: default
+ * stream) and returns once it has finished.  PM_ERR_TIMEOUT: a wait on the
+ * tensor cores ran out (about a second); C is then undefined. */
+pm_status pm_gemm_c32(int32_t m, int32_t n, int32_t k, const void* A, int32_t lda, int32_t conj_a, const void* B,
+                      int32_t ldb, int32_t conj_b, void* C, int32_t ldc, const float* alpha, const float* beta,
+                      void* stream);
 
 /* The self block A_jj, like pm_self_block, without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that

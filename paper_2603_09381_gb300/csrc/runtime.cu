@@ -17,6 +17,7 @@
 #include "../../include/pmchwt.h"
 #include "assemble.cuh"
 #include "cpqr.cuh"
+#include "tc_gemm.cuh"
 #include "dense_la.cuh"
 #include "mlp.cuh"
 #include "operator.cuh"
@@ -684,15 +685,77 @@ void process_level(pm_factor* F, int lev, double tol) {
         const int nq = (int)qp.size();
         C* tws = scr.get<C>((size_t)nq * QR_NB * QR_NB);
         for (int q = 0; q < nq; ++q) qp[q].T = tws + (size_t)q * QR_NB * QR_NB;
-        auto* dqp = upload(scr, qp, st);
-        for (int j0 = 0; j0 < maxn; j0 += QR_NB) {
-          qr_panel<C>(dqp, nq, j0, st);
-          const int tiles = (maxn - j0 - QR_NB + 31) / 32;
-          if (tiles > 0) qr_update<C>(dqp, nq, j0, tiles, st);
+        if (!(F->opts.flags & PM_FLAG_TENSOR_CORES)) {
+          auto* dqp = upload(scr, qp, st);
+          for (int j0 = 0; j0 < maxn; j0 += QR_NB) {
+            qr_panel<C>(dqp, nq, j0, st);
+            const int tiles = (maxn - j0 - QR_NB + 31) / 32;
+            if (tiles > 0) qr_update<C>(dqp, nq, j0, tiles, st);
+          }
+          qr_zero_lower<C>(dqp, nq, maxn, st);
+          if (g_kprof) g_kprof->add_flops("qr_update32", fl);
+        } else {
+          // Trailing update of every panel on the tensor cores: with V the
+          // panel's reflectors (unit diagonal) and C its trailing block,
+          // Y^H = C^H V, Y^H <- Y^H T, C -= V Y.  All panels' problem lists
+          // are built and uploaded at once.
+          std::vector<C*> yh(nq), y2h(nq);
+          for (int q = 0; q < nq; ++q) {
+            qp[q].V = scr.get<C>((size_t)qp[q].W * QR_NB);
+            yh[q] = scr.get<C>((size_t)qp[q].n * QR_NB);
+            y2h[q] = scr.get<C>((size_t)qp[q].n * QR_NB);
+          }
+          std::vector<TcGemmProb> gl[3];
+          std::vector<int> toff[3];
+          std::vector<int> pstart, pcount;   // per panel: first problem and problem count of each list
+          const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f), mone = make_float2(-1.f, 0.f);
+          for (int j0 = 0; j0 < maxn; j0 += QR_NB) {
+            pstart.push_back((int)gl[0].size());
+            int cnt = 0;
+            for (int q = 0; q < nq; ++q) {
+              const int n = qp[q].n, Wq = qp[q].W, ld = qp[q].ld;
+              if (j0 >= n) continue;
+              const int jb = std::min(QR_NB, n - j0), nt = n - j0 - jb;
+              if (nt <= 0) continue;
+              float2* Cb = (float2*)(qp[q].Z + j0 + (size_t)(j0 + jb) * ld);
+              float2* V = (float2*)qp[q].V;
+              gl[0].push_back(TcGemmProb{Cb, ld, 1, V, Wq, 0, (float2*)yh[q], n, nt, jb, Wq - j0, one, zero});
+              gl[1].push_back(TcGemmProb{(float2*)yh[q], n, 0, (float2*)qp[q].T, QR_NB, 0, (float2*)y2h[q], n, nt, jb,
+                                         jb, one, zero});
+              gl[2].push_back(TcGemmProb{V, Wq, 0, (float2*)y2h[q], n, 1, Cb, ld, Wq - j0, nt, jb, mone, one});
+              ++cnt;
+            }
+            pcount.push_back(cnt);
+          }
+          for (int l = 0; l < 3; ++l) {
+            toff[l].assign(gl[l].size() + 1, 0);
+            for (size_t i = 0; i < gl[l].size(); ++i) toff[l][i + 1] = toff[l][i] + tc_tiles(gl[l][i].m, gl[l][i].n);
+          }
+          TcGemmProb* dg[3];
+          int* dt[3];
+          for (int l = 0; l < 3; ++l) { dg[l] = upload(scr, gl[l], st); dt[l] = upload(scr, toff[l], st); }
+          int* terr = scr.get<int>(1);
+          CK(cudaMemsetAsync(terr, 0, sizeof(int), st));
+          auto* dqp = upload(scr, qp, st);
+          int pi = 0;
+          for (int j0 = 0; j0 < maxn; j0 += QR_NB, ++pi) {
+            qr_panel<C>(dqp, nq, j0, st);
+            const int s0 = pstart[pi], c = pcount[pi];
+            if (c == 0) continue;
+            for (int l = 0; l < 3; ++l) {
+              const int t0 = toff[l][s0], t1 = toff[l][s0 + c];
+              tc_gemm_batched(dg[l] + s0, dt[l] + s0, c, t1 - t0, terr, st, t0);
+            }
+          }
+          qr_zero_lower<C>(dqp, nq, maxn, st);
+          CK(cudaGetLastError());
+          int herr = 0;
+          CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if (herr) fail(PM_ERR_TIMEOUT, "a wait on the tensor cores ran out (QR update)");
+          if (g_kprof) g_kprof->add_flops("tc_gemm32", fl);
         }
-        qr_zero_lower<C>(dqp, nq, maxn, st);
         CK(cudaGetLastError());
-        if (g_kprof) g_kprof->add_flops("qr_update32", fl);
       }
     }
   }
@@ -1749,6 +1812,36 @@ pm_status pm_mlp_train(void* theta, int32_t nsamples, const float* X, const floa
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
+  });
+}
+
+pm_status pm_gemm_c32(int32_t m, int32_t n, int32_t k, const void* A, int32_t lda, int32_t conj_a, const void* B,
+                      int32_t ldb, int32_t conj_b, void* C, int32_t ldc, const float* alpha, const float* beta,
+                      void* stream) {
+  if (m < 0 || n < 0 || k < 0 || !alpha || !beta || ((size_t)m * n > 0 && !C) ||
+      ((size_t)m * n * k > 0 && (!A || !B)) || ldc < std::max(m, 1) || lda < std::max(conj_a ? k : m, 1) ||
+      ldb < std::max(conj_b ? n : k, 1)) {
+    g_err = "pm_gemm_c32: bad argument";
+    return PM_ERR_INVALID_ARG;
+  }
+  if (m == 0 || n == 0) return PM_OK;
+  return run_guarded("pm_gemm_c32", [&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena ws;
+    TcGemmProb pr{(const float2*)A, lda, conj_a != 0, (const float2*)B, ldb, conj_b != 0, (float2*)C, ldc, m, n, k,
+                  make_float2(alpha[0], alpha[1]), make_float2(beta[0], beta[1])};
+    std::vector<TcGemmProb> v{pr};
+    std::vector<int> off{0, tc_tiles(m, n)};
+    auto* dp = upload(ws, v, st);
+    int* doff = upload(ws, off, st);
+    int* derr = ws.get<int>(1);
+    CK(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    tc_gemm_batched(dp, doff, 1, off[1], derr, st);
+    CK(cudaGetLastError());
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) fail(PM_ERR_TIMEOUT, "a wait on the tensor cores ran out");
   });
 }
 

@@ -63,6 +63,7 @@ class pm_kernel_stat(ct.Structure):
 PM_FLAG_PROFILE = 1
 PM_FLAG_NO_DENSE_OPERATOR = 2
 PM_FLAG_NO_QR_FIRST = 4
+PM_FLAG_TENSOR_CORES = 8
 _lib = None
 
 EXPORTS = {
@@ -93,6 +94,9 @@ EXPORTS = {
     "pm_mlp_train": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32,
                                 ct.c_double, ct.c_double, ct.c_uint64, ct.c_void_p, ct.c_void_p]),
     "pm_self_block_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "pm_gemm_c32": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p,
+                               ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_float),
+                               ct.POINTER(ct.c_float), ct.c_void_p]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
     "pm_last_error": (ct.c_char_p, []),
@@ -135,6 +139,14 @@ def make_problem(prob):
     p = pm_problem(m, arr, float(prob["k_out"]), int(prob.get("grid_nx", 0)), int(prob.get("grid_ny", 0)),
                    float(prob["spacing"]))
     return p, arr
+
+
+def gemm_c32(m, n, k, A_ptr, lda, conj_a, B_ptr, ldb, conj_b, C_ptr, ldc, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha op(A) op(B) + beta C on the tensor cores (device pointers, complex64, column-major)."""
+    al = (ct.c_float * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ct.c_float * 2)(complex(beta).real, complex(beta).imag)
+    _check(load().pm_gemm_c32(m, n, k, A_ptr, lda, int(conj_a), B_ptr, ldb, int(conj_b), C_ptr, ldc, al, be,
+                              ct.c_void_p(stream) if stream else None))
 
 
 def launch_counter():
@@ -194,7 +206,7 @@ class Geometry:
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
-                 qr_first=True):
+                 qr_first=True, tensor_cores=False):
         """rank_model: device pointer (int) of a trained predictor, or None."""
         lib = load()
         self.geom = geom
@@ -202,7 +214,7 @@ class Factor:
         o = pm_factor_opts(float(tol), float(proxy_factor), int(proxy_points), int(precision),
                            ct.c_void_p(stream) if stream else None,
                            (PM_FLAG_PROFILE if profile else 0) | (0 if dense_operator else PM_FLAG_NO_DENSE_OPERATOR)
-                           | (0 if qr_first else PM_FLAG_NO_QR_FIRST),
+                           | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0),
                            float(refine_tol), int(max_refine), float(low_tol),
                            ct.c_void_p(rank_model) if rank_model else None)
         h = ct.c_void_p()

@@ -160,14 +160,16 @@ def test_mixed_small_circles(pm):
     assert _rel(phi, dense.solve(prob, angs)) < 1e-8
 
 
-@pytest.mark.parametrize("nx,n,qr_first", [(4, 64, True), (2, 128, True), (4, 64, False)])
-def test_mixed_star_grid_matches_dense(pm, nx, n, qr_first):
-    """Both complex64 ID variants: pivoting on the full input, or on its
-    triangle after an unpivoted blocked QR."""
+@pytest.mark.parametrize("nx,n,qr_first,tensor_cores", [(4, 64, True, False), (2, 128, True, False),
+                                                        (4, 64, False, False), (4, 64, True, True)])
+def test_mixed_star_grid_matches_dense(pm, nx, n, qr_first, tensor_cores):
+    """Every complex64 ID variant: pivoting on the full input, on its
+    triangle after an unpivoted blocked QR, that QR's updates on the tensor
+    cores."""
     prob = wl.star_grid(nx, nx, n=n, seed=1)
     angs = [0.3, 1.9, 4.4]
     g = pm.Geometry(prob)
-    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, qr_first=qr_first)
+    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, qr_first=qr_first, tensor_cores=tensor_cores)
     F = g.plane_wave(angs)
     phi = f.solve(F)
     info = f.last_info
