@@ -4,15 +4,20 @@
 // factorization of the n x n triangle R picks the pivots of Z and returns its
 // R (exact arithmetic); the pivoted steps then stream n instead of W rows.
 //
-// Per panel of QR_NB columns: one CTA per matrix factors the panel (LAPACK
-// zlarfg phase convention, H = I - tau v v^H, Q^H applied) with one pass over
-// the panel per reflector (the pass that applies reflector j also sums the
-// norm and the dot products that define reflector j+1), and forms the
-// compact-WY factor T (Q = I - V T V^H); then one CTA per (matrix, 32-column
-// tile) applies Q^H = I - V T^H V^H to the tile in two passes over its rows
-// (Y = V^H C, then C -= V (T^H Y)).
+// Per panel of QR_NB columns: a cluster of 1-8 CTAs per matrix factors the
+// panel (LAPACK zlarfg phase convention, H = I - tau v v^H, Q^H applied) with
+// one pass over the panel per reflector (the pass that applies reflector j
+// also sums the norm and the dot products that define reflector j+1); the
+// cluster's CTAs split the rows and add their partial sums through
+// distributed shared memory, every CTA forming the same reflector from the
+// same sums.  It then forms the compact-WY factor T (Q = I - V T V^H); one
+// CTA per (matrix, 32-column tile) applies Q^H = I - V T^H V^H to the tile in
+// two passes over its rows (Y = V^H C, then C -= V (T^H Y)).
 #include "cpqr.cuh"
 #include "prof.cuh"
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -43,7 +48,7 @@ __device__ __forceinline__ C v_entry(const QrProb<C>& p, int j0, int jb, int r, 
 // needs is loaded before the pair stores anything.
 template <typename C>
 __device__ __forceinline__ void panel_pass(const QrProb<C>& p, int j0, int jb, int ja, const C* s_f, C sc,
-                                           C* s_row, typename real_of<C>::type& N, C* S) {
+                                           C* s_row, typename real_of<C>::type& N, C* S, int rank, int csize) {
   typedef typename real_of<C>::type R;
   const int jn = ja + 1;
   const int ca = j0 + ja, cn = j0 + jn;
@@ -54,7 +59,7 @@ __device__ __forceinline__ void panel_pass(const QrProb<C>& p, int j0, int jb, i
   const int kmin = ja >= 0 ? ja : jn;
   const C fjn = (ja >= 0 && jn < jb) ? s_f[jn] : czero<C>();
   // warp-uniform sweep (the __syncwarp below needs every lane), rows guarded
-  for (int r0 = (ja >= 0 ? ca : cn) + (threadIdx.x >> 5) * 16; r0 < p.W; r0 += PR) {
+  for (int r0 = (ja >= 0 ? ca : cn) + (threadIdx.x >> 5) * 16 + rank * PR; r0 < p.W; r0 += PR * csize) {
     const int r = r0 + (lane & 15);
     const bool act = r < p.W;
     C v[HB];
@@ -94,30 +99,37 @@ __device__ __forceinline__ void panel_pass(const QrProb<C>& p, int j0, int jb, i
 template <typename C>
 __global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P, int j0) {
   typedef typename real_of<C>::type R;
-  const QrProb<C> p = P[blockIdx.x];
-  if (j0 >= p.n) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int csize = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const QrProb<C> p = P[blockIdx.x / csize];
+  if (j0 >= p.n) return;   // the whole cluster (same matrix) leaves
   const int jb = min(QR_NB, p.n - j0);
   const int W = p.W;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4;
+  constexpr int NV = 4 * QR_NB + 1;   // S (re, im), N, row c' (re, im)
   __shared__ R s_red[PT / 32][2 * QR_NB + 1];
-  __shared__ R s_tot[2 * QR_NB + 1];
+  __shared__ R s_part[2][NV];         // this CTA's partial sums, by pass parity
+  __shared__ R s_tot[NV];
   __shared__ C s_f[QR_NB];
-  __shared__ C s_row[QR_NB];
+  __shared__ C s_row[QR_NB];          // row c' entries held by this CTA (zero elsewhere)
   __shared__ C s_tau[QR_NB];
   __shared__ C s_sc;
   __shared__ C s_v[RC][QR_NB + 1];
   __shared__ C s_g[QR_NB][QR_NB + 1];
   __shared__ C s_t[QR_NB][QR_NB + 1];
+  if (tid < QR_NB) s_row[tid] = czero<C>();
+  __syncthreads();
   C sc = czero<C>();
-  for (int ja = -1; ja < jb; ++ja) {
+  int par = 0;
+  for (int ja = -1; ja < jb; ++ja, par ^= 1) {
     R N = 0;
     C S[HB];
 #pragma unroll
     for (int k = 0; k < HB; ++k) S[k] = czero<C>();
-    panel_pass(p, j0, jb, ja, s_f, sc, s_row, N, S);
+    panel_pass(p, j0, jb, ja, s_f, sc, s_row, N, S, rank, csize);
     const int jn = ja + 1;
     if (jn >= jb) break;
-    // block sums: N over all lanes, S_k over the 16 lanes of each half
+    // CTA sums: N over all lanes, S_k over the 16 lanes of each half
     N = warp_sum(N);
 #pragma unroll
     for (int k = 0; k < HB; ++k)
@@ -139,13 +151,23 @@ __global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P
       R t = 0;
 #pragma unroll
       for (int w = 0; w < PT / 32; ++w) t += s_red[w][tid];
+      s_part[par][tid] = t;
+    } else if (tid < NV) {
+      const int k = (tid - 2 * QR_NB - 1) >> 1;
+      s_part[par][tid] = ((tid - 2 * QR_NB - 1) & 1) ? s_row[k].y : s_row[k].x;
+    }
+    cluster.sync();   // every CTA's partials of this pass are written
+    if (tid < NV) {
+      R t = 0;
+      for (int q = 0; q < csize; ++q) t += cluster.map_shared_rank(&s_part[par][0], q)[tid];   // rank order
       s_tot[tid] = t;
     }
+    if (tid < QR_NB) s_row[tid] = czero<C>();
     __syncthreads();
     if (tid == 0) {
       // reflector of column jn (LAPACK zlarfg phase), factors of the next pass
       const int c = j0 + jn;
-      const C alpha = s_row[jn];
+      const C alpha = mk(s_tot[2 * QR_NB + 1 + 2 * jn], s_tot[2 * QR_NB + 2 + 2 * jn]);
       const R xnorm = sqrt(s_tot[2 * QR_NB]);
       C tau = czero<C>(), scn = czero<C>();
       R beta = 0;
@@ -155,21 +177,27 @@ __global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P
         tau = cdiv(bm - alpha, bm);
         scn = cdiv(mk((R)1, (R)0), alpha - bm);
       }
-      p.Z[c + (size_t)c * p.ld] = mk(beta, (R)0);
+      if (rank == 0) p.Z[c + (size_t)c * p.ld] = mk(beta, (R)0);
       s_tau[jn] = tau;
       s_sc = scn;
       const C ctau = conj(tau), cscn = conj(scn);
-      for (int k = jn + 1; k < jb; ++k) s_f[k] = ctau * (s_row[k] + cscn * mk(s_tot[2 * k], s_tot[2 * k + 1]));
+      for (int k = jn + 1; k < jb; ++k) {
+        const C rowk = mk(s_tot[2 * QR_NB + 1 + 2 * k], s_tot[2 * QR_NB + 2 + 2 * k]);
+        s_f[k] = ctau * (rowk + cscn * mk(s_tot[2 * k], s_tot[2 * k + 1]));
+      }
     }
     __syncthreads();
     sc = s_sc;
   }
-  __syncthreads();
-  // G = V^H V over chunks of rows staged in shared memory (V also written out)
+  // the last pass stored its reflector in rows that other CTAs of the
+  // cluster read below (rows are dealt out differently there)
+  cluster.sync();
+  // G = V^H V over chunks of this CTA's rows staged in shared memory (V also
+  // written out), then summed over the cluster
   {
     const int gi = tid & 31, gj = tid >> 5;   // G[gi][gj] and G[gi][gj + 16]
     C g0 = czero<C>(), g1 = czero<C>();
-    for (int r0 = j0; r0 < W; r0 += RC) {
+    for (int r0 = j0 + rank * RC; r0 < W; r0 += RC * csize) {
       for (int e = tid; e < RC * QR_NB; e += PT) {
         const int i = e % RC, j = e / RC;
         const C v = v_entry(p, j0, jb, r0 + i, j);
@@ -185,8 +213,18 @@ __global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P
       }
       __syncthreads();
     }
-    s_g[gi][gj] = g0;
-    s_g[gi][gj + 16] = g1;
+    s_t[gi][gj] = g0;   // s_t holds this CTA's partial G until T is built
+    s_t[gi][gj + 16] = g1;
+    cluster.sync();
+    C a0 = czero<C>(), a1 = czero<C>();
+    for (int q = 0; q < csize; ++q) {
+      const C* rt = &cluster.map_shared_rank(&s_t[0][0], q)[0];
+      a0 = a0 + rt[gi * (QR_NB + 1) + gj];
+      a1 = a1 + rt[gi * (QR_NB + 1) + gj + 16];
+    }
+    s_g[gi][gj] = a0;
+    s_g[gi][gj + 16] = a1;
+    cluster.sync();   // no CTA reuses s_t (or leaves) while another still reads it
   }
   // T: T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
   for (int e = tid; e < QR_NB * QR_NB; e += PT) {
@@ -202,7 +240,8 @@ __global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P
     }
     __syncthreads();
   }
-  for (int e = tid; e < QR_NB * QR_NB; e += PT) p.T[e] = s_t[e % QR_NB][e / QR_NB];
+  if (rank == 0)
+    for (int e = tid; e < QR_NB * QR_NB; e += PT) p.T[e] = s_t[e % QR_NB][e / QR_NB];
 }
 
 template <typename C>
@@ -299,8 +338,26 @@ __global__ void k_qr_zero_lower(const QrProb<C>* __restrict__ P) {
 template <typename C>
 void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st) {
   if (nprob <= 0) return;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // cluster of up to 8 CTAs per matrix, enough to fill the SMs (one CTA per SM)
+  int cs = 1;
+  while (cs < 8 && (long)nprob * cs * 2 <= sms) cs *= 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nprob * cs);
+  cfg.blockDim = dim3(PT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   KPROF_BEGIN(st);
-  k_qr_panel<C><<<nprob, PT, 0, st>>>(d_prob, j0);
+  cudaLaunchKernelEx(&cfg, k_qr_panel<C>, d_prob, j0);
   pm_launch_count_add(1);
   KPROF_END(st, kname<C>("qr_panel", "qr_panel32"), 0.0);
 }

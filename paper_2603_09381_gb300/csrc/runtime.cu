@@ -1434,7 +1434,7 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
     F->precision = opts->precision;
     F->tree = g->levels;
     // the FP32 factorization of the mixed mode cannot resolve tolerances far below FP32 precision
-    const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 1e-5)
+    const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 7e-6)
                                                    : opts->tol;
     pm_factor_opts popts = F->opts;
     popts.tol = id_tol;
