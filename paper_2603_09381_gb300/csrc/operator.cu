@@ -91,6 +91,58 @@ __global__ void __launch_bounds__(OP_T) k_apply_offdiag(OpNodes nd, int total, d
   }
 }
 
+// The dense operator's entries are stored as float pairs d = hi + lo (48
+// significant bits).  The kernels that write and read them are bound by the
+// FP64 pipe, so the split and the join work on the bit patterns with integer
+// instructions: hi = d truncated to 24 significant bits, lo = the next 24 bits
+// of the remainder (so lo has hi's sign and |lo| < ulp(hi)); joining adds the
+// aligned mantissas exactly.  Values outside the normal float range, and pairs
+// not of that form, take the FP64 conversions instead.
+__device__ __forceinline__ void split_trunc(double d, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0 || ef >= 255) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+    return;
+  }
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29));
+  const unsigned int r = (unsigned int)(m & 0x1FFFFFFFu);   // remainder: 29 bits below hi
+  if (r == 0) { lo = __uint_as_float(sign); return; }
+  const int lz = __clz((int)r);                               // >= 3
+  const int el = ef - 52 + (31 - lz);                         // biased float exponent of lo
+  if (el <= 0) { lo = __uint_as_float(sign); return; }        // |lo| below 2^-126: dropped
+  lo = __uint_as_float(sign | ((unsigned int)el << 23) | (((r << lz) >> 8) & 0x7FFFFFu));
+}
+
+__device__ __forceinline__ double join_trunc(float hi, float lo) {
+  const unsigned int H = __float_as_uint(hi), L = __float_as_uint(lo);
+  const int eh = (int)((H >> 23) & 0xFF), el = (int)((L >> 23) & 0xFF);
+  const bool lzero = (L & 0x7FFFFFFFu) == 0;
+  if (eh == 0 || eh == 255 || (!lzero && (el == 0 || ((H ^ L) & 0x80000000u)))) return (double)hi + (double)lo;
+  unsigned long long M = (unsigned long long)((H & 0x7FFFFFu) | 0x800000u) << 29;   // 53-bit significand of hi
+  if (!lzero) {
+    const int sh = el - eh + 29;   // lo's significand position in units of the double's last place
+    const unsigned long long ml = (L & 0x7FFFFFu) | 0x800000u;
+    if (sh >= 0 && sh <= 5) M += ml << sh;
+    else if (sh < 0 && sh > -24 && (ml & ((1ull << -sh) - 1)) == 0) M += ml >> -sh;
+    else return (double)hi + (double)lo;
+    if (M >> 53) return (double)hi + (double)lo;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(H & 0x80000000u) << 32) |
+                                          ((unsigned long long)(eh - 127 + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ float4 split4t(double re, double im) {
+  float4 v;
+  split_trunc(re, v.x, v.z);
+  split_trunc(im, v.y, v.w);
+  return v;
+}
+
 __device__ __forceinline__ float4 split4(double re, double im) {
   const float hr = (float)re, hi = (float)im;
   return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
@@ -125,15 +177,15 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
   const double Nre = -(c0 * Y0 + c1 * Y1) * q, Nim = (c0 * J0 + c1 * J1) * q;   // (ik/4)[..]
   const size_t ut = nd.iu[t], qt = nd.iq[t], us = nd.iu[s], qs = nd.iq[s];
   // rows of t, columns of s (column index: q density at the u-equation index, u density at the q index)
-  A[ut + us * lda] = split4(0.25 * Y0 * ws, -0.25 * J0 * ws);
-  A[ut + qs * lda] = split4(-Y1 * q * b * ws, J1 * q * b * ws);
-  A[qt + us * lda] = split4(-Y1 * q * a * ws, J1 * q * a * ws);
-  A[qt + qs * lda] = split4(Nre * ws, Nim * ws);
+  A[ut + us * lda] = split4t(0.25 * Y0 * ws, -0.25 * J0 * ws);
+  A[ut + qs * lda] = split4t(-Y1 * q * b * ws, J1 * q * b * ws);
+  A[qt + us * lda] = split4t(-Y1 * q * a * ws, J1 * q * a * ws);
+  A[qt + qs * lda] = split4t(Nre * ws, Nim * ws);
   // rows of s, columns of t
-  A[us + ut * lda] = split4(0.25 * Y0 * wt, -0.25 * J0 * wt);
-  A[us + qt * lda] = split4(Y1 * q * a * wt, -J1 * q * a * wt);
-  A[qs + ut * lda] = split4(Y1 * q * b * wt, -J1 * q * b * wt);
-  A[qs + qt * lda] = split4(Nre * wt, Nim * wt);
+  A[us + ut * lda] = split4t(0.25 * Y0 * wt, -0.25 * J0 * wt);
+  A[us + qt * lda] = split4t(Y1 * q * a * wt, -J1 * q * a * wt);
+  A[qs + ut * lda] = split4t(Y1 * q * b * wt, -J1 * q * b * wt);
+  A[qs + qt * lda] = split4t(Nre * wt, Nim * wt);
 }
 
 // Skinny product Y = A X: a CTA owns 128 rows and one segment of the columns of
@@ -162,7 +214,7 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restri
       const float4* col = A + row + (size_t)kb * lda;
       for (int kk = 0; kk < cnt; ++kk) {
         const float4 s4 = __ldg(col + (size_t)kk * lda);
-        const double2 a = make_double2((double)s4.x + (double)s4.z, (double)s4.y + (double)s4.w);
+        const double2 a = make_double2(join_trunc(s4.x, s4.z), join_trunc(s4.y, s4.w));
 #pragma unroll
         for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
       }
@@ -245,7 +297,7 @@ __global__ void k_split_copy(const double2* __restrict__ src, int lds, float4* _
   if (e >= m * n) return;
   const int i = e % m, j = e / m;
   const double2 v = src[i + (size_t)j * lds];
-  dst[i + (size_t)j * ldd] = split4(v.x, v.y);
+  dst[i + (size_t)j * ldd] = split4t(v.x, v.y);
 }
 
 __global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,
