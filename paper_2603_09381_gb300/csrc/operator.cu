@@ -228,6 +228,46 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restri
   }
 }
 
+// The same product with the hi parts only, in FP32 arithmetic (~1e-7
+// relative to |A| |X|): for the first refinement residual, which is ~1e-3 of
+// the right-hand side.  Bound by the one read of A.
+template <int NR>
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec32(const float4* __restrict__ A, size_t lda, int N,
+                                                            const double2* __restrict__ X, int ldx,
+                                                            double2* __restrict__ Y, int ldy, int seg) {
+  __shared__ float2 xs[NR][MV_KT];
+  const int row = blockIdx.x * MV_ROWS + threadIdx.x;
+  const int k0 = blockIdx.y * seg, k1 = min(N, k0 + seg);
+  float2 acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int kb = k0; kb < k1; kb += MV_KT) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NR * MV_KT; e += MV_ROWS) {
+      const int q = e / MV_KT, kk = e % MV_KT;
+      const double2 v = (kb + kk < k1) ? X[kb + kk + (size_t)q * ldx] : make_double2(0, 0);
+      xs[q][kk] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+    if (row < N) {
+      const int cnt = min(MV_KT, k1 - kb);
+      const float4* col = A + row + (size_t)kb * lda;
+      for (int kk = 0; kk < cnt; ++kk) {
+        const float4 s4 = __ldg(col + (size_t)kk * lda);
+        const float2 a = make_float2(s4.x, s4.y);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
+      }
+    }
+  }
+  if (row >= N) return;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    atomicAdd(&Y[row + (size_t)q * ldy].x, (double)acc[q].x);
+    atomicAdd(&Y[row + (size_t)q * ldy].y, (double)acc[q].y);
+  }
+}
+
 // Float-float building blocks (Dekker / Knuth): exact FP32 product error via
 // FMA, exact sum error via TwoSum.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -437,6 +477,38 @@ void launch_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int 
   dim3 g(rb, segs);
   k_dense_matvec_ff<NR><<<g, MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
   pm_launch_count_add(1);
+}
+
+template <int NR>
+void launch_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy,
+                     cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int rb = (N + MV_ROWS - 1) / MV_ROWS;
+  int segs = std::max(1, (sms * 12 + rb - 1) / rb);
+  int seg = (N + segs - 1) / segs;
+  seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
+  segs = (N + seg - 1) / seg;
+  k_dense_matvec32<NR><<<dim3(rb, segs), MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  pm_launch_count_add(1);
+}
+
+void dense_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                    cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
+  KPROF_BEGIN(st);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    const double2* Xr = X + (size_t)r0 * ldx;
+    double2* Yr = Y + (size_t)r0 * ldy;
+    if (left >= 8) { launch_matvec32<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec32<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec32<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec32<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+  }
+  KPROF_END(st, "dense_matvec32", 0.0);
 }
 
 void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,

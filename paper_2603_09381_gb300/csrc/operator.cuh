@@ -33,6 +33,10 @@ void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ld
 // sums; ~1e-13 relative, for refinement residuals.
 void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                      cudaStream_t st);
+// The same product with the hi parts in FP32 arithmetic (~1e-7 relative to
+// |A| |X|): the first refinement residual only.
+void dense_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                    cudaStream_t st);
 // R = B - Y, and norms2[2 r] += |R[:, r]|^2, norms2[2 r + 1] += |B[:, r]|^2 (norms2 zeroed by caller)
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st);
 // dst[:, r] = scale[r] * src[:, r] (FP64 -> FP32)

@@ -1208,8 +1208,9 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
 
 // Iterative refinement (mixed mode): x <- x + M^{-1} (b - A x) until the
 // relative residual of every column is below refine_tol.  With the dense
-// operator the intermediate residuals are formed in float-float arithmetic on
-// the FP32 pipes (~1e-13 relative); only FP64 residuals decide convergence.
+// operator the first residual is an FP32 product, the later intermediate ones
+// float-float (~1e-13 relative) on the FP32 pipes; only FP64 residuals decide
+// convergence.
 void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& ws, cudaStream_t st,
                    pm_solve_info* info) {
   const pm_geometry* g = F->g;
@@ -1235,6 +1236,11 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   };
   auto residual_low = [&](const double2* x) {
     dense_matvec_ff(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
+    CK(cudaGetLastError());
+    return finish();
+  };
+  auto residual_f32 = [&](const double2* x) {
+    dense_matvec32(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     return finish();
   };
@@ -1272,7 +1278,14 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
       const double rate = prev > 0 ? res / prev : 1.0;
       exact = res * rate <= tolr;
     }
-    double r_new = exact ? residual(X) : residual_low(X);
+    double r_new;
+    if (exact) r_new = residual(X);
+    else if (prev < 0) {
+      // first step (x0 = 0): its residual is ~1e-3 of b, far above the ~1e-6
+      // error of an FP32 product; a smaller one is formed again in float-float
+      r_new = residual_f32(X);
+      if (r_new < 1e-4) r_new = residual_low(X);
+    } else r_new = residual_low(X);
     if (!exact && r_new <= tolr) { r_new = residual(X); exact = true; }
     prev = res;
     res = r_new;
