@@ -365,6 +365,38 @@ __global__ void __launch_bounds__(256) k_getrs_update(const SolveProb<C>* __rest
                mk((R)-1, (R)0), mk((R)1, (R)0), 0, t % tiles_m, t / tiles_m);
 }
 
+// The same update for at most 8 right-hand sides: one thread per (row,
+// right-hand side), the block's B rows staged in shared memory (the 32 x 32
+// tile of the general kernel would spend 3/4 of its FP64 work on padding).
+constexpr int TH_ROWS = 16;
+template <typename C>
+__global__ void __launch_bounds__(128) k_getrs_update_thin(const SolveProb<C>* __restrict__ P, int p, int nb, int lower) {
+  __shared__ C sb[32][8];
+  const SolveProb<C> pr = P[blockIdx.y];
+  if (p >= pr.m) return;
+  const int jb = min(nb, pr.m - p);
+  const int r0 = lower ? p + jb : 0;
+  const int mt = lower ? pr.m - p - jb : p;
+  if (mt <= 0 || blockIdx.x * TH_ROWS >= mt) return;
+  for (int e = threadIdx.x; e < jb * pr.nrhs; e += blockDim.x) {
+    const int l = e % jb, q = e / jb;
+    sb[l][q] = pr.B[p + l + (size_t)q * pr.ldb];
+  }
+  __syncthreads();
+  const int i = blockIdx.x * TH_ROWS + (threadIdx.x & (TH_ROWS - 1)), q = threadIdx.x / TH_ROWS;
+  if (i >= mt || q >= pr.nrhs) return;
+  const C* a = pr.A + r0 + i + (size_t)p * pr.ld;
+  C acc0 = czero<C>(), acc1 = czero<C>();   // two chains (FP64 latency)
+  int l = 0;
+  for (; l + 1 < jb; l += 2) {
+    cfma(acc0, a[(size_t)l * pr.ld], sb[l][q]);
+    cfma(acc1, a[(size_t)(l + 1) * pr.ld], sb[l + 1][q]);
+  }
+  if (l < jb) cfma(acc0, a[(size_t)l * pr.ld], sb[l][q]);
+  C* out = pr.B + r0 + i + (size_t)q * pr.ldb;
+  *out = *out - (acc0 + acc1);
+}
+
 }  // namespace
 
 template <typename C>
@@ -445,8 +477,12 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
     pm_launch_count_add(1);
     int mt = maxm - p - RS_NB;
     if (mt > 0) {
-      dim3 g2(((mt + TB - 1) / TB) * tiles_n, nprob);
-      k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 1);
+      if (maxrhs <= 8 && sizeof(C) == sizeof(double2)) {   // FP64: padding costs the bounding pipe
+        k_getrs_update_thin<C><<<dim3((mt + TH_ROWS - 1) / TH_ROWS, nprob), 128, 0, st>>>(d_prob, p, RS_NB, 1);
+      } else {
+        dim3 g2(((mt + TB - 1) / TB) * tiles_n, nprob);
+        k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 1);
+      }
       pm_launch_count_add(1);
     }
   }
@@ -455,8 +491,12 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
     k_getrs_diag<C><<<gs, 256, 0, st>>>(d_prob, p, RS_NB, 0);
     pm_launch_count_add(1);
     if (p > 0) {
-      dim3 g2(((p + TB - 1) / TB) * tiles_n, nprob);
-      k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 0);
+      if (maxrhs <= 8 && sizeof(C) == sizeof(double2)) {   // FP64: padding costs the bounding pipe
+        k_getrs_update_thin<C><<<dim3((p + TH_ROWS - 1) / TH_ROWS, nprob), 128, 0, st>>>(d_prob, p, RS_NB, 0);
+      } else {
+        dim3 g2(((p + TB - 1) / TB) * tiles_n, nprob);
+        k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 0);
+      }
       pm_launch_count_add(1);
     }
   }
