@@ -7,6 +7,7 @@
 #include "dense_la.cuh"
 #include "prof.cuh"
 #include <algorithm>
+#include <cooperative_groups.h>
 
 namespace {
 
@@ -185,6 +186,118 @@ __global__ void __launch_bounds__(NT) k_lu_panel(const LuProb<C>* __restrict__ P
       if (r < m) colc[r] = colc[r] * inv;
     }
     __syncthreads();
+  }
+}
+
+// The same left-looking panel for one large matrix on a cluster of CTAs
+// (the top-level LU): the CTAs split the rows, so the lazy column updates
+// (FP64-bound on one SM) spread over the cluster's SMs.  Per column: every
+// CTA solves the small triangular system for U[0:jj] itself, updates its
+// rows and proposes a pivot; the proposals meet through distributed shared
+// memory (largest |a|^2, lowest row on ties, as in k_lu_panel); rank 0 swaps
+// the two rows; every CTA scales its rows.  Three cluster barriers per column
+// order these steps.
+template <typename C, int NT>
+__global__ void __launch_bounds__(NT) k_lu_panel_cluster(const LuProb<C>* __restrict__ P, int p, int nb) {
+  typedef typename real_of<C>::type R;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int csize = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const LuProb<C> pr = P[blockIdx.x / csize];
+  const int m = pr.m;
+  if (p >= m) return;   // the whole cluster leaves
+  const int jb = min(nb, m - p);
+  C* A = pr.A;
+  const size_t ld = pr.ld;
+  __shared__ R sval[NT / 32];
+  __shared__ int sidx[NT / 32];
+  __shared__ R c_val;   // this CTA's proposal, read by the cluster
+  __shared__ int c_idx;
+  __shared__ C s_l[MAXNB][MAXNB + 1];
+  __shared__ C s_u[MAXNB];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int stride = NT * csize;
+  for (int jj = 0; jj < jb; ++jj) {
+    const int c = p + jj;
+    C* colc = A + (size_t)c * ld;
+    if (jj > 0) {
+      for (int e = tid; e < jj * jj; e += NT) s_l[e % jj][e / jj] = A[p + e % jj + (size_t)(p + e / jj) * ld];
+      __syncthreads();
+      if (warp == 0) {
+        C x = lane < jj ? colc[p + lane] : czero<C>();
+        for (int l = 0; l < jj - 1; ++l) {
+          const C xl = shfl_c(x, l);
+          if (lane > l && lane < jj) cfms(x, s_l[lane][l], xl);
+        }
+        if (lane < jj) s_u[lane] = x;
+      }
+      __syncthreads();
+    }
+    R best = -1;
+    int bi = m;
+    for (int r = c + rank * NT + tid; r < m; r += stride) {
+      C lr[MAXNB];
+#pragma unroll
+      for (int l = 0; l < MAXNB; ++l) if (l < jj) lr[l] = A[r + (size_t)(p + l) * ld];
+      C a0 = colc[r], a1 = czero<C>(), a2 = czero<C>(), a3 = czero<C>();
+#pragma unroll
+      for (int l = 0; l < MAXNB; l += 4) {
+        if (l < jj) cfms(a0, lr[l], s_u[l]);
+        if (l + 1 < jj) cfms(a1, lr[l + 1], s_u[l + 1]);
+        if (l + 2 < jj) cfms(a2, lr[l + 2], s_u[l + 2]);
+        if (l + 3 < jj) cfms(a3, lr[l + 3], s_u[l + 3]);
+      }
+      const C a = (a0 + a1) + (a2 + a3);
+      if (jj > 0) colc[r] = a;
+      const R v = abs2(a);
+      if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+    }
+    if (lane == 0) { sval[warp] = best; sidx[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      R bv = sval[0];
+      int bix = sidx[0];
+      for (int w = 1; w < NT / 32; ++w)
+        if (sval[w] > bv || (sval[w] == bv && sidx[w] < bix)) { bv = sval[w]; bix = sidx[w]; }
+      c_val = bv;
+      c_idx = bix;
+    }
+    cluster.sync();   // proposals and updated column entries are visible
+    if (tid == 0) {
+      R bv = -1;
+      int piv = m;
+      for (int q = 0; q < csize; ++q) {
+        const R v = *cluster.map_shared_rank(&c_val, q);
+        const int i = *cluster.map_shared_rank(&c_idx, q);
+        if (v > bv || (v == bv && i < piv)) { bv = v; piv = i; }
+      }
+      if (!(bv > 0)) { piv = c; if (rank == 0 && *pr.info == 0) *pr.info = c + 1; }
+      s_piv = piv;
+      if (rank == 0) pr.ipiv[c] = piv;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (rank == 0) {
+      if (jj > 0 && tid < jj) colc[p + tid] = s_u[tid];   // U entries of this column
+      if (piv != c && tid < jb) {
+        C* a = A + c + (size_t)(p + tid) * ld;
+        C* b = A + piv + (size_t)(p + tid) * ld;
+        const C t = *a; *a = *b; *b = t;
+      }
+    }
+    cluster.sync();   // the swap is visible; every CTA has read its proposal slots
+    const C d = colc[c];
+    if (abs2(d) > 0) {
+      const C inv = cdiv(mk((R)1, (R)0), d);
+      for (int r = c + 1 + rank * NT + tid; r < m; r += stride) colc[r] = colc[r] * inv;
+    }
+    cluster.sync();   // scaled column visible before the next column reads it
   }
 }
 
@@ -429,9 +542,24 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
       }
     }
     KPROF_BEGIN(st);
-    // a few large matrices (the top-level LU): more threads per column
-    if (nprob <= 8 && maxm >= 2048) k_lu_panel<C, 512><<<nprob, 512, 0, st>>>(d_prob, p, LU_NB);
-    else k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
+    if (nprob <= 8 && maxm >= 2048) {
+      // a few large matrices (the top-level LU): a cluster of 8 CTAs each
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nprob * 8);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 8;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_lu_panel_cluster<C, 256>, d_prob, p, LU_NB);
+    } else {
+      k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
+    }
     pm_launch_count_add(1);
     KPROF_END(st, kname<C>("lu_panel", "lu_panel32"), fp);
     dim3 g1((maxm + 255) / 256, nprob);
