@@ -105,7 +105,7 @@ typedef struct pm_factor pm_factor;
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
  *      refine_tol returns PM_ERR_NOT_CONVERGED.
- * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 7e-6).
+ * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 5e-6).
  * rank_model: NULL, or a trained rank predictor on the device (float32:
  *      PM_MLP_NPARAM weights, then 8 feature means and 8 feature scales); the
  *      CPQR of every level then runs up to the median predicted rank before its

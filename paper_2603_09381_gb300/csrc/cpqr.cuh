@@ -46,19 +46,23 @@ struct PermFill { int* perm; int n; int done; };   // perm[done..n) <- unchosen 
 // norms of every trailing block are those of Z, so the column-pivoted QR of R
 // picks the pivots and R factor of Z's (exact arithmetic).
 constexpr int QR_NB = 32;        // panel width
+constexpr int QR_RB = 256;       // rows per block of the trailing update
 template <typename C>
 struct QrProb {
   C* Z; int ld; int W; int n;
   C* T;                          // QR_NB x QR_NB: compact-WY factor of the current panel
   C* V;                          // W x QR_NB (leading dimension W), or NULL: the panel's V
                                  // (rows j0.. at rows 0..) written out with its unit diagonal
+  C* Yp;                         // update workspace: ceil(n/32) x mrb blocks of 32 x 32
+  int mrb;                       // row blocks of QR_RB rows covering W
 };
 // Panels [j0, j0 + QR_NB) of every matrix with j0 < n; max_tiles = the most
 // 32-column tiles right of a panel in any matrix.
 template <typename C>
 void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st);
+// max_rb: the most QR_RB-row blocks of rows j0..W-1 in any matrix.
 template <typename C>
-void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, cudaStream_t st);
+void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, int max_rb, cudaStream_t st);
 template <typename C>
 void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t st);
 

@@ -228,9 +228,10 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restri
   }
 }
 
-// The same product with the hi parts only, in FP32 arithmetic (~1e-7
-// relative to |A| |X|): for the first refinement residual, which is ~1e-3 of
-// the right-hand side.  Bound by the one read of A.
+// The same product with the hi parts only, in FP32 arithmetic over runs of
+// MV_KT columns whose sums are folded into FP64 accumulators (~1e-7 relative
+// to |A| |X|, not growing with N): for the first refinement residual, which
+// is ~1e-3 of the right-hand side.  Bound by the one read of A.
 template <int NR>
 __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec32(const float4* __restrict__ A, size_t lda, int N,
                                                             const double2* __restrict__ X, int ldx,
@@ -238,10 +239,13 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec32(const float4* __rest
   __shared__ float2 xs[NR][MV_KT];
   const int row = blockIdx.x * MV_ROWS + threadIdx.x;
   const int k0 = blockIdx.y * seg, k1 = min(N, k0 + seg);
-  float2 acc[NR];
+  double2 accd[NR];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < NR; ++q) accd[q] = make_double2(0.0, 0.0);
   for (int kb = k0; kb < k1; kb += MV_KT) {
+    float2 acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int e = threadIdx.x; e < NR * MV_KT; e += MV_ROWS) {
       const int q = e / MV_KT, kk = e % MV_KT;
@@ -259,12 +263,14 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec32(const float4* __rest
         for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
       }
     }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) { accd[q].x += (double)acc[q].x; accd[q].y += (double)acc[q].y; }
   }
   if (row >= N) return;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
-    atomicAdd(&Y[row + (size_t)q * ldy].x, (double)acc[q].x);
-    atomicAdd(&Y[row + (size_t)q * ldy].y, (double)acc[q].y);
+    atomicAdd(&Y[row + (size_t)q * ldy].x, accd[q].x);
+    atomicAdd(&Y[row + (size_t)q * ldy].y, accd[q].y);
   }
 }
 

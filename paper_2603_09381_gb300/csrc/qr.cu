@@ -244,27 +244,30 @@ __global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P
     for (int e = tid; e < QR_NB * QR_NB; e += PT) p.T[e] = s_t[e % QR_NB][e / QR_NB];
 }
 
+// Trailing update Q^H C = C - V (T^H (V^H C)) for every 32-column tile of
+// the trailing block, in three launches so that the rows of a tall matrix
+// spread over many CTAs: partial products Y_b = V_b^H C_b of each block of
+// QR_RB rows; their sum (fixed order) times T^H; C_b -= V_b Y.
 template <typename C>
-__global__ void __launch_bounds__(UT) k_qr_update(const QrProb<C>* __restrict__ P, int j0) {
-  const QrProb<C> p = P[blockIdx.y];
+__global__ void __launch_bounds__(UT) k_qr_ypart(const QrProb<C>* __restrict__ P, int j0) {
+  const QrProb<C> p = P[blockIdx.z];
   if (j0 >= p.n) return;
   const int jb = min(QR_NB, p.n - j0);
-  const int c0 = j0 + jb + blockIdx.x * 32;
-  if (c0 >= p.n) return;
-  const int nc = min(32, p.n - c0);
-  const int W = p.W, tid = threadIdx.x;
+  const int tile = blockIdx.x, rb = blockIdx.y;
+  const int c0 = j0 + jb + tile * 32;
+  const int rbeg = j0 + rb * QR_RB;
+  if (c0 >= p.n || rbeg >= p.W) return;
+  const int nc = min(32, p.n - c0), rend = min(p.W, rbeg + QR_RB);
+  const int tid = threadIdx.x;
   __shared__ C s_v[RC][QR_NB + 1];
   __shared__ C s_c[RC][33];
-  __shared__ C s_y[QR_NB][33];
-  __shared__ C s_t[QR_NB][QR_NB + 1];
   const int tx = tid & 15, ty = tid >> 4;
-  // pass 1: Y = V^H C
   C y00 = czero<C>(), y01 = czero<C>(), y10 = czero<C>(), y11 = czero<C>();
-  for (int r0 = j0; r0 < W; r0 += RC) {
+  for (int r0 = rbeg; r0 < rend; r0 += RC) {
     for (int e = tid; e < RC * 32; e += UT) {
       const int i = e % RC, j = e / RC, r = r0 + i;
-      s_v[i][j] = v_entry(p, j0, jb, r, j);
-      s_c[i][j] = (j < nc && r < W) ? p.Z[r + (size_t)(c0 + j) * p.ld] : czero<C>();
+      s_v[i][j] = r < rend ? v_entry(p, j0, jb, r, j) : czero<C>();
+      s_c[i][j] = (j < nc && r < rend) ? p.Z[r + (size_t)(c0 + j) * p.ld] : czero<C>();
     }
     __syncthreads();
 #pragma unroll 8
@@ -275,30 +278,60 @@ __global__ void __launch_bounds__(UT) k_qr_update(const QrProb<C>* __restrict__ 
     }
     __syncthreads();
   }
-  s_y[tx][ty] = y00; s_y[tx][ty + 16] = y01;
-  s_y[tx + 16][ty] = y10; s_y[tx + 16][ty + 16] = y11;
+  C* yp = p.Yp + ((size_t)tile * p.mrb + rb) * (QR_NB * 32);
+  yp[tx + QR_NB * ty] = y00;
+  yp[tx + QR_NB * (ty + 16)] = y01;
+  yp[tx + 16 + QR_NB * ty] = y10;
+  yp[tx + 16 + QR_NB * (ty + 16)] = y11;
+}
+
+// Y = sum of the row blocks' partials (in block order), then T^H Y into the
+// tile's first partial slot.
+template <typename C>
+__global__ void __launch_bounds__(UT) k_qr_yreduce(const QrProb<C>* __restrict__ P, int j0) {
+  const QrProb<C> p = P[blockIdx.y];
+  if (j0 >= p.n) return;
+  const int jb = min(QR_NB, p.n - j0);
+  const int tile = blockIdx.x;
+  if (j0 + jb + tile * 32 >= p.n) return;
+  const int nrb = (p.W - j0 + QR_RB - 1) / QR_RB;
+  const int tid = threadIdx.x;
+  __shared__ C s_y[QR_NB][33];
+  __shared__ C s_t[QR_NB][QR_NB + 1];
+  C* yp = p.Yp + (size_t)tile * p.mrb * (QR_NB * 32);
+  for (int e = tid; e < QR_NB * 32; e += UT) {
+    C acc = czero<C>();
+    for (int b = 0; b < nrb; ++b) acc = acc + yp[(size_t)b * (QR_NB * 32) + e];
+    s_y[e % QR_NB][e / QR_NB] = acc;
+  }
   for (int e = tid; e < QR_NB * QR_NB; e += UT) s_t[e % QR_NB][e / QR_NB] = p.T[e];
   __syncthreads();
-  // Y <- T^H Y (T upper triangular)
-  C z[2][2];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int i = tx + 16 * a, cc = ty + 16 * b;
-      C acc = czero<C>();
-      for (int l = 0; l <= i; ++l) cfma_conj(acc, s_t[l][i], s_y[l][cc]);
-      z[a][b] = acc;
-    }
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) s_y[tx + 16 * a][ty + 16 * b] = z[a][b];
-  __syncthreads();
-  // pass 2: C -= V Y; thread: one row of the chunk, 4 columns
+  for (int e = tid; e < QR_NB * 32; e += UT) {
+    const int i = e % QR_NB, cc = e / QR_NB;
+    C acc = czero<C>();
+    for (int l = 0; l <= i; ++l) cfma_conj(acc, s_t[l][i], s_y[l][cc]);
+    yp[e] = acc;
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(UT) k_qr_apply(const QrProb<C>* __restrict__ P, int j0) {
+  const QrProb<C> p = P[blockIdx.z];
+  if (j0 >= p.n) return;
+  const int jb = min(QR_NB, p.n - j0);
+  const int tile = blockIdx.x, rb = blockIdx.y;
+  const int c0 = j0 + jb + tile * 32;
+  const int rbeg = j0 + rb * QR_RB;
+  if (c0 >= p.n || rbeg >= p.W) return;
+  const int nc = min(32, p.n - c0), rend = min(p.W, rbeg + QR_RB);
+  const int tid = threadIdx.x;
+  __shared__ C s_v[RC][QR_NB + 1];
+  __shared__ C s_y[QR_NB][33];
+  const C* yp = p.Yp + (size_t)tile * p.mrb * (QR_NB * 32);
+  for (int e = tid; e < QR_NB * 32; e += UT) s_y[e % QR_NB][e / QR_NB] = yp[e];
   const int ri = tid & 31, g = tid >> 5;
-  for (int r0 = j0; r0 < W; r0 += RC) {
+  for (int r0 = rbeg; r0 < rend; r0 += RC) {
+    __syncthreads();
     for (int e = tid; e < RC * QR_NB; e += UT) {
       const int i = e % RC, j = e / RC;
       s_v[i][j] = v_entry(p, j0, jb, r0 + i, j);
@@ -311,7 +344,7 @@ __global__ void __launch_bounds__(UT) k_qr_update(const QrProb<C>* __restrict__ 
       for (int q = 0; q < 4; ++q) cfma(acc[q], v, s_y[j][4 * g + q]);
     }
     const int r = r0 + ri;
-    if (r < W) {
+    if (r < rend) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (4 * g + q < nc) {
@@ -319,7 +352,6 @@ __global__ void __launch_bounds__(UT) k_qr_update(const QrProb<C>* __restrict__ 
           *pz = *pz - acc[q];
         }
     }
-    __syncthreads();
   }
 }
 
@@ -362,11 +394,13 @@ void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st) {
   KPROF_END(st, kname<C>("qr_panel", "qr_panel32"), 0.0);
 }
 template <typename C>
-void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, cudaStream_t st) {
-  if (nprob <= 0 || max_tiles <= 0) return;
+void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, int max_rb, cudaStream_t st) {
+  if (nprob <= 0 || max_tiles <= 0 || max_rb <= 0) return;
   KPROF_BEGIN(st);
-  k_qr_update<C><<<dim3(max_tiles, nprob), UT, 0, st>>>(d_prob, j0);
-  pm_launch_count_add(1);
+  k_qr_ypart<C><<<dim3(max_tiles, max_rb, nprob), UT, 0, st>>>(d_prob, j0);
+  k_qr_yreduce<C><<<dim3(max_tiles, nprob), UT, 0, st>>>(d_prob, j0);
+  k_qr_apply<C><<<dim3(max_tiles, max_rb, nprob), UT, 0, st>>>(d_prob, j0);
+  pm_launch_count_add(3);
   KPROF_END(st, kname<C>("qr_update", "qr_update32"), 0.0);
 }
 template <typename C>
@@ -377,5 +411,5 @@ void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t s
 }
 
 template void qr_panel<float2>(const QrProb<float2>*, int, int, cudaStream_t);
-template void qr_update<float2>(const QrProb<float2>*, int, int, int, cudaStream_t);
+template void qr_update<float2>(const QrProb<float2>*, int, int, int, int, cudaStream_t);
 template void qr_zero_lower<float2>(const QrProb<float2>*, int, int, cudaStream_t);

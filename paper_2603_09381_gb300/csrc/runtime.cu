@@ -673,7 +673,7 @@ void process_level(pm_factor* F, int lev, double tol) {
       double fl = 0;
       for (int i = 0; i < nid; ++i)
         if (nn[i] > 0 && W[i] >= 2 * nn[i]) {
-          qp.push_back(QrProb<C>{Z[i], W[i], W[i], nn[i], nullptr, nullptr});
+          qp.push_back(QrProb<C>{Z[i], W[i], W[i], nn[i], nullptr, nullptr, nullptr, 0});
           We[i] = nn[i];
           maxn = std::max(maxn, nn[i]);
           for (int j0 = 0; j0 < nn[i]; j0 += QR_NB) {
@@ -686,11 +686,18 @@ void process_level(pm_factor* F, int lev, double tol) {
         C* tws = scr.get<C>((size_t)nq * QR_NB * QR_NB);
         for (int q = 0; q < nq; ++q) qp[q].T = tws + (size_t)q * QR_NB * QR_NB;
         if (!(F->opts.flags & PM_FLAG_TENSOR_CORES)) {
+          int maxW = 0;
+          for (int q = 0; q < nq; ++q) {
+            qp[q].mrb = (qp[q].W + QR_RB - 1) / QR_RB;
+            qp[q].Yp = scr.get<C>((size_t)((qp[q].n + 31) / 32) * qp[q].mrb * QR_NB * 32);
+            maxW = std::max(maxW, qp[q].W);
+          }
           auto* dqp = upload(scr, qp, st);
           for (int j0 = 0; j0 < maxn; j0 += QR_NB) {
             qr_panel<C>(dqp, nq, j0, st);
             const int tiles = (maxn - j0 - QR_NB + 31) / 32;
-            if (tiles > 0) qr_update<C>(dqp, nq, j0, tiles, st);
+            const int rbs = (maxW - j0 + QR_RB - 1) / QR_RB;
+            if (tiles > 0) qr_update<C>(dqp, nq, j0, tiles, rbs, st);
           }
           qr_zero_lower<C>(dqp, nq, maxn, st);
           if (g_kprof) g_kprof->add_flops("qr_update32", fl);
@@ -1275,8 +1282,9 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
       // in FP64 straight away (a wrong guess costs nothing: that residual
       // drives the next step).  Otherwise float-float, confirmed in FP64 once
       // it meets the tolerance.
+      // (factor 2 of margin: a wrong guess costs a second FP64 product)
       const double rate = prev > 0 ? res / prev : 1.0;
-      exact = res * rate <= tolr;
+      exact = res * rate <= 0.5 * tolr;
     }
     double r_new;
     if (exact) r_new = residual(X);
@@ -1447,7 +1455,7 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
     F->precision = opts->precision;
     F->tree = g->levels;
     // the FP32 factorization of the mixed mode cannot resolve tolerances far below FP32 precision
-    const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 7e-6)
+    const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 5e-6)
                                                    : opts->tol;
     pm_factor_opts popts = F->opts;
     popts.tol = id_tol;
