@@ -99,7 +99,7 @@ __device__ void cta_columns(const CpqrProb<C>& p, const CpqrChunk& ch, int s, in
 
 // One elimination step of the chunk's matrix on the chunk's columns (all 256
 // threads of the CTA take the same path through the barriers).
-template <typename C>
+template <typename C, bool TALL>
 __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t) {
   typedef typename real_of<C>::type R;
   const int s = p.base + t;
@@ -167,7 +167,7 @@ __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t
   }
   const C ctau = conj(tau), csc = conj(sc);
   // complex64 tall enough to fill the CTA (short columns are barrier-bound) and fitting in registers
-  if (sizeof(C) == 8 && reflect && p.W >= 2048 && p.W <= 256 * 32) {
+  if (TALL && sizeof(C) == 8 && reflect && p.W >= 2048 && p.W <= 256 * 32) {
     cta_columns<C, 32>(p, ch, s, q, xq, ctau, csc, sc, cur, nxt);
     if (tid == 0 && q >= ch.c0 && q < ch.c1) {
       p.rdiag[s] = mk(beta, (R)0);
@@ -228,8 +228,11 @@ __device__ void cpqr_chunk_step(const CpqrProb<C>& p, const CpqrChunk& ch, int t
 }
 
 // Persistent grid (a multiple of the SM count): CTAs take chunks from a
-// per-launch counter, largest matrices first, until none is left.
-template <typename C>
+// per-launch counter, largest matrices first, until none is left.  TALL
+// compiles in the register-resident path for tall complex64 columns; without
+// it the kernel needs far fewer registers (more resident CTAs), which is what
+// the n x n triangles of the QR-first path want.
+template <typename C, bool TALL>
 __global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict__ P, const CpqrChunk* __restrict__ chunks,
                                                    int nchunk, int t, int* __restrict__ counter) {
   __shared__ int s_ci;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict
     if (ci >= nchunk) break;
     const CpqrChunk ch = chunks[ci];
     const CpqrProb<C> p = P[ch.id];
-    cpqr_chunk_step<C>(p, ch, t);
+    cpqr_chunk_step<C, TALL>(p, ch, t);
     __syncthreads();
   }
 }
@@ -324,22 +327,28 @@ void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nc
   k_init_norms<C><<<nchunk, 256, 0, st>>>(d_prob, d_chunk);
   pm_launch_count_add(1);
 }
-template <typename C>
-void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
-               cudaStream_t st) {
-  if (nchunk <= 0) return;
+template <typename C, bool TALL>
+int cpqr_grid() {   // SMs x resident CTAs, once per instance
   static std::atomic<int> grid_cache{0};
   int grid = grid_cache.load();
   if (grid == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cpqr_step<C>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cpqr_step<C, TALL>, 256, 0);
     grid = std::max(1, sms * std::max(per, 1));
     grid_cache.store(grid);
   }
+  return grid;
+}
+
+template <typename C>
+void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
+               cudaStream_t st, bool tall) {
+  if (nchunk <= 0) return;
   KPROF_BEGIN(st);
-  k_cpqr_step<C><<<std::min(grid, nchunk), 256, 0, st>>>(d_prob, d_chunk, nchunk, t, d_counter);
+  if (tall) k_cpqr_step<C, true><<<std::min(cpqr_grid<C, true>(), nchunk), 256, 0, st>>>(d_prob, d_chunk, nchunk, t, d_counter);
+  else k_cpqr_step<C, false><<<std::min(cpqr_grid<C, false>(), nchunk), 256, 0, st>>>(d_prob, d_chunk, nchunk, t, d_counter);
   pm_launch_count_add(1);
   KPROF_END(st, kname<C>("cpqr_step", "cpqr_step32"), 0.0);   // work is added per level from the steps performed
 }
@@ -368,7 +377,7 @@ void copy_batched(const CopyProb<S, D>* d_prob, int nprob, int max_elems, cudaSt
 }
 
 template void cpqr_init_norms<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, cudaStream_t);
-template void cpqr_step<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, int, int*, cudaStream_t);
+template void cpqr_step<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, int, int*, cudaStream_t, bool);
 template void interp_solve<double2>(const InterpProb<double2>*, int, int, cudaStream_t);
 template void scatter_interp<double2>(const ScatterProb<double2>*, int, int, cudaStream_t);
 template void copy_batched<double2, double2>(const CopyProb<double2, double2>*, int, int, cudaStream_t);
@@ -376,6 +385,6 @@ template void copy_batched<float2, float2>(const CopyProb<float2, float2>*, int,
 template void copy_batched<float2, double2>(const CopyProb<float2, double2>*, int, int, cudaStream_t);
 template void copy_batched<double2, float2>(const CopyProb<double2, float2>*, int, int, cudaStream_t);
 template void cpqr_init_norms<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, cudaStream_t);
-template void cpqr_step<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, int, int*, cudaStream_t);
+template void cpqr_step<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, int, int*, cudaStream_t, bool);
 template void interp_solve<float2>(const InterpProb<float2>*, int, int, cudaStream_t);
 template void scatter_interp<float2>(const ScatterProb<float2>*, int, int, cudaStream_t);

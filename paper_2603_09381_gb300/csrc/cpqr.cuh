@@ -70,10 +70,12 @@ void complete_perm(const PermFill* d_prob, int nprob, cudaStream_t st);
 template <typename C>
 void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, cudaStream_t st);
 // One elimination step (launch index t) of every active matrix; d_counter:
-// a zeroed int, distinct for every launch (chunk dispenser).
+// a zeroed int, distinct for every launch (chunk dispenser).  tall: some
+// complex64 matrix has W >= 2048 rows (selects the kernel instance with the
+// register-resident column path).
 template <typename C>
 void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
-               cudaStream_t st);
+               cudaStream_t st, bool tall);
 template <typename C>
 void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st);
 template <typename C>

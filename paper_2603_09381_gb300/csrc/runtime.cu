@@ -790,6 +790,8 @@ void process_level(pm_factor* F, int lev, double tol) {
   }
   // tallest matrices first: their chunks carry the most work per step
   std::stable_sort(chunks.begin(), chunks.end(), [&](const CpqrChunk& a, const CpqrChunk& b) { return We[a.id] > We[b.id]; });
+  bool tall = false;   // any complex64 input pivoted on >= 2048 rows
+  for (int i = 0; i < nid; ++i) tall = tall || We[i] >= 2048;
   int* ctr = scr.get<int>(2 * (size_t)maxT + 2);
   CK(cudaMemsetAsync(ctr, 0, (2 * (size_t)maxT + 2) * sizeof(int), st));
   auto* dcp = upload(scr, cp, st);
@@ -813,7 +815,7 @@ void process_level(pm_factor* F, int lev, double tol) {
     }
   }
   for (int t = 0; t < maxT; ++t) {
-    cpqr_step<C>(dcp, dch, nch, t, ctr + t, st);
+    cpqr_step<C>(dcp, dch, nch, t, ctr + t, st, tall);
     F->stats.cpqr_launches++;
     const bool check = khat.empty() ? ((t % 16 == 15) || t == maxT - 1)
                                     : (t == first_check || (t > first_check && ((t - first_check) % 16 == 0)) ||
@@ -852,7 +854,7 @@ void process_level(pm_factor* F, int lev, double tol) {
   }
   if (maxExt > 0) {
     dcp = upload(scr, cp, st);
-    for (int t = 0; t < maxExt; ++t) cpqr_step<C>(dcp, dch, nch, t, ctr + maxT + t, st);
+    for (int t = 0; t < maxExt; ++t) cpqr_step<C>(dcp, dch, nch, t, ctr + maxT + t, st, tall);
     F->stats.cpqr_launches += maxExt;
     CK(cudaGetLastError());
   }
