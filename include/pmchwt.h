@@ -91,8 +91,9 @@ typedef struct pm_factor pm_factor;
  * stream: cudaStream_t to run on, or NULL for the default stream.
  * flags: PM_FLAG_PROFILE records per-kernel timings.  PM_MIXED writes the
  *      complex128 operator out densely (N^2 x 16 bytes) when it fits in 60% of
- *      the free device memory and sum n_j <= 65535, so that each refinement
- *      step is one matrix product; PM_FLAG_NO_DENSE_OPERATOR keeps the
+ *      the free device memory, the dense operators of all live factorizations
+ *      of the process stay within 40% of the device, and sum n_j <= 65535, so
+ *      that each refinement step is one matrix product; PM_FLAG_NO_DENSE_OPERATOR keeps the
  *      on-the-fly operator instead.  PM_MIXED reduces every complex64 ID
  *      input with at least twice as many rows as candidate columns to its
  *      triangular factor (unpivoted Householder QR) before the pivoted QR;

@@ -189,8 +189,24 @@ struct pm_factor {
   int* d_iu = nullptr;
   int* d_iq = nullptr;
   float4* dense64 = nullptr;    // the whole FP64 operator, N x N, split hi/lo, when it fits the memory budget
-  ~pm_factor() { if (dense64) cudaFree(dense64); }
+  size_t dense_bytes = 0;
+  ~pm_factor();
 };
+
+namespace {
+// Dense operators held by live factorizations, process-wide: concurrent
+// factorizations (batches) must not each take a share of the same free memory.
+std::mutex g_dense_mu;
+size_t g_dense_held = 0;
+}  // namespace
+
+pm_factor::~pm_factor() {
+  if (dense64) {
+    cudaFree(dense64);
+    std::lock_guard<std::mutex> lk(g_dense_mu);
+    g_dense_held -= dense_bytes;
+  }
+}
 
 template <class C> std::vector<std::vector<BoxF<C>>>& levels_of(pm_factor* F);
 template <> std::vector<std::vector<BoxF<double2>>>& levels_of<double2>(pm_factor* F) { return F->lev64; }
@@ -1506,11 +1522,25 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
       F->d_iq = upload(F->arena, iq, F->st);
       // With room in HBM, write the FP64 operator out once: each refinement step
       // is then a skinny FP64 GEMM instead of a Hankel evaluation per node pair.
-      size_t fr = 0, tot = 0;
-      CK(cudaMemGetInfo(&fr, &tot));
+      // Budget: 60% of the free memory, and all dense operators held in the
+      // process at most 40% of the device; otherwise (or if the allocation
+      // fails) the refinement applies the operator on the fly.
       const size_t need = sizeof(float4) * (size_t)g->N * g->N;
-      if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535 && need <= fr / 10 * 6) {
-        CK(cudaMalloc(&F->dense64, need));
+      if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535) {
+        std::lock_guard<std::mutex> lk(g_dense_mu);
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        if (need <= fr / 10 * 6 && g_dense_held + need <= tot / 10 * 4) {
+          if (cudaMalloc(&F->dense64, need) == cudaSuccess) {
+            F->dense_bytes = need;
+            g_dense_held += need;
+          } else {
+            F->dense64 = nullptr;
+            cudaGetLastError();   // clear the failed allocation's error
+          }
+        }
+      }
+      if (F->dense64) {
         OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
         assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense64, (size_t)g->N, F->st);
         if (g_kprof) {
