@@ -195,8 +195,10 @@ __global__ void __launch_bounds__(NT) k_lu_panel(const LuProb<C>* __restrict__ P
 // CTA solves the small triangular system for U[0:jj] itself, updates its
 // rows and proposes a pivot; the proposals meet through distributed shared
 // memory (largest |a|^2, lowest row on ties, as in k_lu_panel); rank 0 swaps
-// the two rows; every CTA scales its rows.  Three cluster barriers per column
-// order these steps.
+// the two rows; every CTA scales its rows.  Two cluster barriers per column
+// order these steps: a row's scaled L entry is next read by the thread that
+// wrote it (rows keep their thread from column to column), and the next
+// column's triangular solve reads only rows at or above the diagonal.
 template <typename C, int NT>
 __global__ void __launch_bounds__(NT) k_lu_panel_cluster(const LuProb<C>* __restrict__ P, int p, int nb) {
   typedef typename real_of<C>::type R;
@@ -297,8 +299,9 @@ __global__ void __launch_bounds__(NT) k_lu_panel_cluster(const LuProb<C>* __rest
       const C inv = cdiv(mk((R)1, (R)0), d);
       for (int r = c + 1 + rank * NT + tid; r < m; r += stride) colc[r] = colc[r] * inv;
     }
-    cluster.sync();   // scaled column visible before the next column reads it
+    __syncthreads();
   }
+  cluster.sync();   // no CTA leaves while another may still read its proposal slots
 }
 
 // Row interchanges of the panel applied to every other column, then the unit

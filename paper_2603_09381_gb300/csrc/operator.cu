@@ -175,16 +175,20 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
   const double q = 0.25 * k;
   const double c0 = k * a * b, c1 = (nn - 2 * a * b) * ir;
   const double Nre = -(c0 * Y0 + c1 * Y1) * q, Nim = (c0 * J0 + c1 * J1) * q;   // (ik/4)[..]
+  // common factors, formed once (the FP64 pipe bounds this kernel)
+  const double s0r = 0.25 * Y0, s0i = -0.25 * J0;          // -eps+ S / w
+  const double y1q = Y1 * q, j1q = J1 * q;
+  const double ya = y1q * a, ja = j1q * a, yb = y1q * b, jb = j1q * b;
   const size_t ut = nd.iu[t], qt = nd.iq[t], us = nd.iu[s], qs = nd.iq[s];
   // rows of t, columns of s (column index: q density at the u-equation index, u density at the q index)
-  A[ut + us * lda] = split4t(0.25 * Y0 * ws, -0.25 * J0 * ws);
-  A[ut + qs * lda] = split4t(-Y1 * q * b * ws, J1 * q * b * ws);
-  A[qt + us * lda] = split4t(-Y1 * q * a * ws, J1 * q * a * ws);
+  A[ut + us * lda] = split4t(s0r * ws, s0i * ws);
+  A[ut + qs * lda] = split4t(-yb * ws, jb * ws);
+  A[qt + us * lda] = split4t(-ya * ws, ja * ws);
   A[qt + qs * lda] = split4t(Nre * ws, Nim * ws);
   // rows of s, columns of t
-  A[us + ut * lda] = split4t(0.25 * Y0 * wt, -0.25 * J0 * wt);
-  A[us + qt * lda] = split4t(Y1 * q * a * wt, -J1 * q * a * wt);
-  A[qs + ut * lda] = split4t(Y1 * q * b * wt, -J1 * q * b * wt);
+  A[us + ut * lda] = split4t(s0r * wt, s0i * wt);
+  A[us + qt * lda] = split4t(ya * wt, -ja * wt);
+  A[qs + ut * lda] = split4t(yb * wt, -jb * wt);
   A[qs + qt * lda] = split4t(Nre * wt, Nim * wt);
 }
 
