@@ -10,9 +10,11 @@
 // also sums the norm and the dot products that define reflector j+1); the
 // cluster's CTAs split the rows and add their partial sums through
 // distributed shared memory, every CTA forming the same reflector from the
-// same sums.  It then forms the compact-WY factor T (Q = I - V T V^H); one
-// CTA per (matrix, 32-column tile) applies Q^H = I - V T^H V^H to the tile in
-// two passes over its rows (Y = V^H C, then C -= V (T^H Y)).
+// same sums.  It then forms the compact-WY factor T (Q = I - V T V^H).
+// Q^H = I - V T^H V^H is applied to every 32-column tile of the trailing
+// block in three launches: partial products Y_b = V_b^H C_b per (tile,
+// QR_RB-row block), their sum in block order times T^H, and C_b -= V_b Y per
+// (tile, block), so that the rows of a tall matrix spread over many CTAs.
 #include "cpqr.cuh"
 #include "prof.cuh"
 #include <cooperative_groups.h>
