@@ -41,6 +41,20 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x, device):
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, ws, ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's ms."""
+    return ws * units_per_rank / (ms / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling (200 ms) while the timed region runs."""
 
@@ -295,11 +309,9 @@ def run_ours(args):
         ms, solve, prof_tot, st, info, launches = _timed(pm, g, prob, opts, angs, F, X, stream, precision,
                                                         args.steps, args.warmup, model_ptr)
     if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = _max_over_ranks(ms, "cuda")
         torch.distributed.barrier()
-        ms = float(tt.item())
-    value = ws * N / (ms / 1e3)
+    value = _job_rate(N, ws, ms)
     X_dev = X.cpu().numpy()
 
     # end to end through the public API with host buffers: descriptors and pinned
@@ -321,9 +333,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / args.steps
     if ws > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+        e2e_s = _max_over_ranks(e2e_s, "cuda")
     scale = float(np.abs(X_dev).max())
     e2e_match = bool(np.allclose(out_host.numpy(), X_dev, rtol=0, atol=1e-8 * scale))
 
@@ -332,8 +342,10 @@ def run_ours(args):
     if precision == pm.PM_MIXED and not args.no_fp64_compare:
         X64 = torch.zeros_like(F)
         ms64, solve64, prof64, st64, _, _ = _timed(pm, g, prob, opts, angs, F, X64, stream, pm.PM_FP64, 1, 1)
+        if ws > 1:
+            ms64 = _max_over_ranks(ms64, "cuda")
         diff = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
-        fp64 = {"value": ws * N / (ms64 / 1e3), "ms_per_step": ms64, "solve_ms": solve64, "factor_ms": ms64 - solve64,
+        fp64 = {"value": _job_rate(N, ws, ms64), "ms_per_step": ms64, "solve_ms": solve64, "factor_ms": ms64 - solve64,
                 "K": st64["K"], "skeleton_per_level": st64["skeleton"], "roofline": _roofline(prof64, 1),
                 "kernels": _kernel_table(prof64, 1), "rel_diff_vs_mixed": diff,
                 "speedup_of_mixed": ms64 / ms}
@@ -356,7 +368,7 @@ def run_ours(args):
             "phase_ms": {k: st[k] for k in ("ms_assemble", "ms_id", "ms_schur", "ms_top")},
             "roofline": _roofline(prof_tot, args.steps), "kernels": _kernel_table(prof_tot, args.steps),
             "gpu_launches": int(launches),
-            "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "e2e": {"value": _job_rate(N, ws, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "matches_device_result": e2e_match},
             "clocks": clk.summary()}
     if fp64 is not None:

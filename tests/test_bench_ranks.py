@@ -1,0 +1,80 @@
+"""Multi-rank host logic of bench.py on the CPU (gloo, world size 2).
+
+Each GPU of a multi-GPU run factors its own replica (no collective on the
+data path); the bench reports the slowest rank's time and counts the units
+of every rank.  These tests run that reduction with two gloo ranks, and the
+reference arm's rule that only rank 0 runs and prints.
+"""
+import json
+import multiprocessing as mp
+import os
+import socket
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, ws, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        import bench
+        ms = bench._max_over_ranks(10.0 + 5.0 * rank, "cpu")   # rank 1 is the slow one
+        q.put((rank, ms, bench._job_rate(1000, ws, ms), bench._dist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_report_the_slowest_rank_and_all_units():
+    pytest.importorskip("torch")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        got = sorted(q.get(timeout=120) for _ in procs)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert [g[0] for g in got] == [0, 1]
+    for rank, ms, rate, dist_env in got:
+        assert ms == 15.0                              # max over ranks, seen by both
+        assert rate == pytest.approx(2 * 1000 / 0.015)  # both ranks' units over the slowest time
+        assert dist_env == (2, rank, rank)
+
+
+def test_job_rate_of_one_rank_is_units_over_time():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._job_rate(65536, 1, 1000.0) == pytest.approx(65536.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+
+    class Args:
+        steps, warmup, gpus = 1, 0, 2
+
+    assert bench.run_reference(Args()) == 0
+    assert capsys.readouterr().out == ""   # no work and no line on the other ranks
