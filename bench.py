@@ -161,8 +161,24 @@ def run_reference(args):
     return 0
 
 
+def _kernel_source_sha(src_text, anchors):
+    """Hash of the definitions that start at each anchor (up to the end of their
+    body): the captured kernel and the helpers it calls, not the whole file."""
+    parts = []
+    for a in anchors:
+        i = src_text.find(a)
+        if i < 0:
+            return None
+        j = src_text.find("\n}\n", i)
+        if j < 0:
+            return None
+        parts.append(src_text[i:j + 3])
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
 def _traffic_for(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if its kernel source is unchanged."""
+    """Per-launch DRAM bytes from the committed ncu summary, while the captured
+    kernel's source (and its helpers') is unchanged; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(p))
@@ -173,10 +189,11 @@ def _traffic_for(kernel):
         return None
     src = os.path.join(ROOT, "paper_2603_09381_gb300", "csrc", ent["source"])
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(src).read()
     except OSError:
         return None
-    return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
+    sha = _kernel_source_sha(text, ent["anchors"])
+    return ent["bytes_per_launch"] if sha is not None and sha == ent["source_sha"] else None
 
 
 FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",

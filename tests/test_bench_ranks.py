@@ -78,3 +78,20 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""   # no work and no line on the other ranks
+
+
+def test_traffic_record_follows_the_captured_kernel_only():
+    """The ncu traffic of a kernel stays valid while that kernel's source (and
+    its helpers') is unchanged, whatever else changes in its file."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    src = "int a;\n__global__ void k(int x) {\n  x += 1;\n}\nint b;\n"
+    base = bench._kernel_source_sha(src, ["__global__ void k("])
+    assert bench._kernel_source_sha(src.replace("int b;", "int c;"), ["__global__ void k("]) == base
+    assert bench._kernel_source_sha(src.replace("x += 1", "x += 2"), ["__global__ void k("]) != base
+    assert bench._kernel_source_sha(src, ["missing("]) is None
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    text = open(os.path.join(ROOT, "paper_2603_09381_gb300", "csrc", rec["dense_matvec64"]["source"])).read()
+    for a in rec["dense_matvec64"]["anchors"]:
+        assert a in text
