@@ -15,7 +15,8 @@ in two dimensions") they follow:
 
   geometry   -- boundary curves and Nystrom nodes (Sec. 2.2)
   quadrature -- Kress log-split weights, trigonometric differentiation
-                (the self-block quadrature, Sec. 2.2; reading A5 of DESIGN)
+                (the self-block quadrature of Sec. 2.2, in place of the paper's
+                zeta-corrected rule)
   kernels    -- fundamental solution and its normal derivatives (Sec. 2.1,
                 eqs. slp/dlp/d_slp/d_dlp)
   blocks     -- Nystrom blocks A_ij of PMCHWT (Omit) / (All) (Sec. 2.2)

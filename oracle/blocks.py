@@ -14,7 +14,8 @@ with S, D, D* by Kress's log-split rule and N by Maue's identity
   N phi = (1/|x'(t)|) d/dt S0[dphi/dtau] + k^2 n_x . S[n_y phi],
 discretised as  N = diag(1/|x'|) Dt S0 Dt + k^2 (S o n n^T)
 (S0: the single layer without the speed factor |x'(tau)|, Dt: trigonometric
-differentiation).  Readings A5-A7 of DESIGN.
+differentiation).  These quadratures replace the paper's zeta-corrected
+rule, identically on both sides of every parity check.
 
 Log split (Colton & Kress Sec. 3.6), t != tau, d = x(t) - x(tau), r = |d|:
   S-kernel * |x'(tau)| = M1 ln(4 sin^2((t-tau)/2)) + M2,

@@ -2,11 +2,11 @@
 ID of Cheng et al. 2005 computed by column-pivoted QR; the rank is decided
 adaptively from the diagonal of R against the threshold epsilon).
 
-Readings (DESIGN): the threshold is relative, a column is kept while
-|R_jj| > tol |R_11| (A10); trailing column norms are recomputed from scratch
+Where the paper is silent: the threshold is relative, a column is kept
+while |R_jj| > tol |R_11|; trailing column norms are recomputed from scratch
 at every step (no downdating); a column whose squared trailing norm is at
 least (1 - 1e-12) times the largest counts as tied, and among tied columns
-the lowest original index wins (A13).
+the lowest original index wins.
 
 Householder step (LAPACK zlarfg convention): for x = trailing part of the
 pivot column, alpha = x_0, beta = -sign(Re alpha) ||x||, tau = (beta - alpha)/beta,

@@ -3,7 +3,7 @@ derivatives (paper Sec. 2.1, eqs. slp, dlp, d_slp, d_dlp).
 
 The paper writes G = H_0^(1)(k|x-y|); the jump terms +-1/2 of its Burton-Miller
 system only hold for the standard normalisation, so the oracle uses
-G(x, y) = (i/4) H_0^(1)(k |x - y|)  (reading A1 of DESIGN).  With d = x - y,
+G(x, y) = (i/4) H_0^(1)(k |x - y|).  With d = x - y,
 r = |d|, z = k r:
 
   G             = (i/4) H0(z)

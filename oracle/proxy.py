@@ -16,7 +16,8 @@ Factor (upward, levels L..1):
     point for the Omit formulation;
   * ranks: each ID is decided by its own CPQR (cpqr.py); row group g and
     column group g (u-eq rows with q cols, q-eq rows with u cols) then share
-    k_g = max(row rank, column rank) so that A~ is square (reading A10);
+    k_g = max(row rank, column rank) so that A~ is square (the paper does not
+    say how unequal row and column ranks are reconciled);
   * A~_b = (R_b D_b^{-1} L_b)^{-1}  (Sec. 3, definition of A~_i); singular -> error.
 Top: D_root assembled like a parent from the level-1 boxes, partial-pivot LU.
 

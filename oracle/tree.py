@@ -2,7 +2,7 @@
 Sec. 3: each Gamma_j is a leaf cell; Sec. 4: the near field of a cell is its
 edge-adjacent neighbours; Sec. 4.4: cells indexed along the Morton Z-order).
 
-Readings (DESIGN A8, A9, A14, A15):
+Choices where the paper is silent:
   * inclusion j sits in grid cell (ix, iy) = round((c_j - origin) / spacing),
     origin = the smallest centre coordinates; the grid is padded to
     2^L x 2^L, L = ceil(log2(max(nx, ny))); empty boxes are dropped;
