@@ -17,7 +17,7 @@
  *    scaled normal derivative (paper Sec. 2.1, eqs. pressure and flux),
  *    N = sum_j 2 n_j.  Matrices and multi-RHS blocks are column-major.
  *  - Handles are owned by the library and released with the *_free calls
- *    (NULL-safe).  Factor handles are immutable after pm_factor.
+ *    (NULL-safe).  Factor handles are immutable after pm_factorize.
  *  - All compute runs on the current CUDA device; there is no CPU fallback.
  *    If no CUDA device is present the calls fail with PM_ERR_CUDA.
  */
@@ -35,7 +35,7 @@ typedef enum {
   PM_ERR_OOM = 2,           /* device or host allocation failed */
   PM_ERR_CUDA = 3,          /* CUDA runtime error (message names the call) */
   PM_ERR_SINGULAR = 4,      /* exactly singular pivot in an LU, or R A^{-1} L singular */
-  PM_ERR_NOT_CONVERGED = 5, /* reserved for iterative refinement */
+  PM_ERR_NOT_CONVERGED = 5, /* PM_MIXED: refinement stopped above refine_tol after max_refine steps */
   PM_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (tensor-core completion) */
   PM_ERR_GEOMETRY = 7,      /* inclusions not on a grid, two in one cell, ... */
   PM_ERR_UNSUPPORTED = 8    /* valid input the library does not handle yet */
@@ -54,8 +54,8 @@ enum { PM_FP64 = 0, PM_MIXED = 1 };
  *   PM_FOURIER: prm[0] = r0, prm[1..5] = a_2..a_6, prm[6..10] = phi_2..phi_6;
  *               r(t) = r0 (1 + sum_m a_m cos(m t + phi_m)),  rho = r(t) (cos t, sin t)
  * n_nodes: Nystrom nodes t_l = 2 pi l / n (paper Sec. 2.2), even, 16..4096.
- * k_in: interior wavenumber k^- (eps^- = (k^-/k^+)^2, eps^+ = 1).  Only real
- * k_in is supported by this build (complex -> PM_ERR_UNSUPPORTED). */
+ * k_in: interior wavenumber k^- (eps^- = (k^-/k^+)^2, eps^+ = 1); Re k_in > 0,
+ * Im k_in >= 0 (a lossy interior), else PM_ERR_INVALID_ARG. */
 typedef struct {
   int32_t shape;
   double cx, cy, rot;
@@ -93,8 +93,8 @@ typedef struct pm_factor pm_factor;
  *      complex128 operator out densely (N^2 x 16 bytes) when it fits in 60% of
  *      the free device memory, the dense operators of all live factorizations
  *      of the process stay within 40% of the device, and sum n_j <= 65535, so
- *      that each refinement step is one matrix product; PM_FLAG_NO_DENSE_OPERATOR keeps the
- *      on-the-fly operator instead.  PM_MIXED reduces every complex64 ID
+ *      that each refinement step is one matrix product (else, or with
+ *      PM_FLAG_NO_DENSE_OPERATOR, the operator is applied on the fly).  PM_MIXED reduces every complex64 ID
  *      input with at least twice as many rows as candidate columns to its
  *      triangular factor (unpivoted Householder QR) before the pivoted QR;
  *      PM_FLAG_NO_QR_FIRST pivots on the full input instead.  The trailing
@@ -152,8 +152,7 @@ typedef struct {
  * (paper Sec. 3 / Sec. 4: each inclusion a leaf cell, Morton order).
  * The problem struct and its inclusion array are copied; the caller keeps
  * ownership.  Errors: PM_ERR_INVALID_ARG (m < 1, bad shape, odd n_nodes ...),
- * PM_ERR_GEOMETRY (two inclusions rounding to one grid cell),
- * PM_ERR_UNSUPPORTED (complex k_in). */
+ * PM_ERR_GEOMETRY (two inclusions rounding to one grid cell). */
 pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out);
 
 /* Number of unknowns N = 2 sum n_j. */
@@ -174,12 +173,15 @@ pm_status pm_plane_wave_rhs(const pm_geometry* g, const double* angles, int32_t 
  * the multilevel proxy / interpolative-decomposition fast direct solver
  * (paper Sec. 3): self blocks, proxy IDs per cell (exterior kernel only),
  * compressed blocks A~_i = (R_i A_ii^{-1} L_i)^{-1}, recursive merge, top LU.
- * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_SINGULAR. */
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_SINGULAR,
+ * PM_ERR_TIMEOUT (opt-in tensor-core path only), PM_ERR_UNSUPPORTED. */
 pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_factor** out);
 
 /* Solve A phi = rhs for nrhs right-hand sides (paper Sec. 3: eq. compressed and
  * the recovery formula).  rhs and phi are N x nrhs column-major, device
- * pointers if on_device = 1, else host pointers; they may alias. */
+ * pointers if on_device = 1, else host pointers; they may alias.  PM_MIXED
+ * factors refine the solution (PM_ERR_NOT_CONVERGED if refine_tol is not
+ * reached). */
 pm_status pm_solve(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device);
 
 /* pm_solve that also reports the refinement outcome (info may be NULL). */
@@ -221,9 +223,11 @@ pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out);
 /* Per-kernel timing of a factorization made with flags & PM_FLAG_PROFILE
  * (no counterpart in the paper; measurement aid).  CUDA events bracket every
  * launch on the factorization's stream.  `work` is the algorithmic work of
- * all launches: real flops for cpqr_step, interp_solve, lu_*, getrs and
- * gemm_batched; matrix entries for gather_entries; node pairs for
- * self_pointwise.  Writes up to cap entries, *count = number available. */
+ * all launches: real flops for cpqr_step, interp_solve, lu_*, getrs,
+ * gemm_batched, qr_update32, dense_matvec64 and dense_offdiag64 (164 per node
+ * pair); bytes for cpqr_step32 (one read and write of every trailing entry);
+ * matrix entries for gather_entries; node pairs for self_pointwise.  Names
+ * ending in 32 are the complex64 instances.  Writes up to cap entries, *count = number available. */
 typedef struct {
   char name[32];
   int32_t launches;
