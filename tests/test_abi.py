@@ -50,3 +50,30 @@ def test_invalid_arguments_rejected_before_device_use():
     with pytest.raises(pm.PmError) as e:
         pm.Geometry(prob)
     assert e.value.status == 1
+
+
+def test_more_invalid_arguments_rejected_before_device_use():
+    """Argument checks at the C boundary come before any CUDA call, so they hold
+    on a machine without a GPU: each returns PM_ERR_INVALID_ARG (1) with a message."""
+    import ctypes as ct
+    from paper_2603_09381_gb300 import pmchwt as pm
+    from paper_2603_09381_gb300 import workloads as wl
+    lib = pm.load()
+    one = (ct.c_float * 2)(1.0, 0.0)
+    zero = (ct.c_float * 2)(0.0, 0.0)
+    buf = ct.c_void_p(16)   # never dereferenced: every call below fails its checks first
+    # tensor-core GEMM: leading dimensions below the matrix sizes, negative sizes, NULL scalars
+    assert lib.pm_gemm_c32(8, 8, 8, buf, 4, 0, buf, 8, 0, buf, 8, one, zero, None) == 1
+    assert lib.pm_gemm_c32(8, 16, 8, buf, 8, 0, buf, 8, 1, buf, 8, one, zero, None) == 1  # conj_b needs ldb >= n
+    assert lib.pm_gemm_c32(-1, 8, 8, buf, 8, 0, buf, 8, 0, buf, 8, one, zero, None) == 1
+    assert lib.pm_gemm_c32(8, 8, 8, buf, 8, 0, buf, 8, 0, buf, 8, None, zero, None) == 1
+    assert b"pm_gemm_c32" in lib.pm_last_error()
+    # NULL arguments and a non-positive inclusion count
+    out = ct.c_void_p()
+    assert lib.pm_build_geometry(None, ct.byref(out)) == 1
+    p, arr = pm.make_problem(wl.circle_grid(1, 1))
+    p.m = 0
+    assert lib.pm_build_geometry(ct.byref(p), ct.byref(out)) == 1
+    assert lib.pm_factorize(None, None, ct.byref(out)) == 1
+    assert lib.pm_solve(None, None, 1, None, 0) == 1
+    assert lib.pm_factor_stats(None, None) == 1
