@@ -89,3 +89,12 @@ def test_omit_and_all_agree_to_discretisation_error():
     A_all = dense.assemble(prob, "all")
     A_omit = dense.assemble(prob, "omit")
     assert np.linalg.norm((A_all - A_omit) @ a) < 1e-9 * np.linalg.norm(A_omit @ a)
+
+
+def test_uneven_node_counts_multipole():
+    """Each inclusion has its own n (its own offsets, weights and self block)."""
+    prob = wl.circle_grid(2, 2, n=96)
+    for inc, n in zip(prob["inclusions"], (80, 96, 112, 128)):
+        inc["n"] = n
+    assert dense.offsets(prob)[-1] == 2 * (80 + 96 + 112 + 128)
+    assert _mie_error(prob, angle=1.1) < 1e-10

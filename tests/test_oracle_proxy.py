@@ -51,3 +51,12 @@ def test_ragged_grid_and_multi_rhs():
     angs = [0.1, 2.0, 4.0]
     F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
     assert _rel(proxy.solve(fac, F), dense.solve(prob, angs)) < 1e-8
+
+
+def test_uneven_node_counts_match_dense():
+    prob = wl.star_grid(3, 3, n=64, seed=6)
+    for j, inc in enumerate(prob["inclusions"]):
+        inc["n"] = 48 + 16 * (j % 4)
+    fac = proxy.factor(prob, {"tol": 1e-10})
+    F = np.stack([dense.plane_wave(prob, a) for a in (0.2, 2.5)], 1)
+    assert _rel(proxy.solve(fac, F), dense.solve(prob, [0.2, 2.5])) < 3e-9
