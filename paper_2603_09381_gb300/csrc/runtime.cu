@@ -1234,8 +1234,9 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
 // Iterative refinement (mixed mode): x <- x + M^{-1} (b - A x) until the
 // relative residual of every column is below refine_tol.  With the dense
 // operator the first residual is an FP32 product, the later intermediate ones
-// float-float (~1e-13 relative) on the FP32 pipes; only FP64 residuals decide
-// convergence.
+// float-float (~1e-13 relative) on the FP32 pipes, or, once the residual is
+// small, the update r <- r - A dx with an FP32 product; only FP64 residuals
+// decide convergence.
 void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& ws, cudaStream_t st,
                    pm_solve_info* info) {
   const pm_geometry* g = F->g;
@@ -1269,6 +1270,23 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     CK(cudaGetLastError());
     return finish();
   };
+  std::vector<double> bnorm(nrhs, 1.0);
+  // r <- r - A dx (dx: the correction just added to x) with an FP32 product.
+  // Its rounding (~1e-6 of |A dx| ~ |r|) stays in the new residual and in x,
+  // so it is used only while 1e-6 |r| is far below refine_tol; the new
+  // residual goes to dx's buffer and the two buffers swap.
+  auto residual_update32 = [&]() {
+    dense_matvec32(F->dense64, (size_t)N, N, dX, N, Y, N, nrhs, st);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
+    residual64(R, Y, dX, N, nrhs, norms, st);
+    std::swap(R, dX);
+    CK(cudaMemcpyAsync(hn.data(), norms, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double worst = 0;
+    for (int r = 0; r < nrhs; ++r) worst = std::max(worst, std::sqrt(hn[2 * r]) / bnorm[r]);
+    return worst;
+  };
   auto precond = [&](const double2* rhs, double2* out, const std::vector<double>& colnorm) {
     for (int r = 0; r < nrhs; ++r) {
       double nr = colnorm[r] > 0 ? colnorm[r] : 1.0;
@@ -1283,7 +1301,10 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   CK(cudaMemsetAsync(Y, 0, sizeof(double2) * (size_t)N * nrhs, st));
   double res = finish();
   std::vector<double> cn(nrhs);
-  for (int r = 0; r < nrhs; ++r) cn[r] = std::sqrt(hn[2 * r]);
+  for (int r = 0; r < nrhs; ++r) {
+    cn[r] = std::sqrt(hn[2 * r]);
+    bnorm[r] = std::max(std::sqrt(hn[2 * r + 1]), 1e-300);
+  }
   int it = 0;
   const double tolr = F->opts.refine_tol > 0 ? F->opts.refine_tol : 1e-10;
   const int maxit = F->opts.max_refine > 0 ? F->opts.max_refine : 10;
@@ -1298,8 +1319,8 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
       // Refinement contracts the residual by a nearly constant factor; when
       // that trend says this step meets the tolerance, the residual is formed
       // in FP64 straight away (a wrong guess costs nothing: that residual
-      // drives the next step).  Otherwise float-float, confirmed in FP64 once
-      // it meets the tolerance.
+      // drives the next step).  Otherwise float-float or the FP32 update,
+      // confirmed in FP64 once it meets the tolerance.
       // (factor 2 of margin: a wrong guess costs a second FP64 product)
       const double rate = prev > 0 ? res / prev : 1.0;
       exact = res * rate <= 0.5 * tolr;
@@ -1311,7 +1332,8 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
       // error of an FP32 product; a smaller one is formed again in float-float
       r_new = residual_f32(X);
       if (r_new < 1e-4) r_new = residual_low(X);
-    } else r_new = residual_low(X);
+    } else if (1e-6 * res <= 0.05 * tolr) r_new = residual_update32();
+    else r_new = residual_low(X);
     if (!exact && r_new <= tolr) { r_new = residual(X); exact = true; }
     prev = res;
     res = r_new;
