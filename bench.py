@@ -119,6 +119,14 @@ def workload(name="star16"):
     return prob, opts, angs
 
 
+def _workload_config(nx, N, levels, precision, ws):
+    """The config object of the bench line; the reference arm reports the same one."""
+    return {"workload": f"{nx}x{nx} stars r=0.4(1+0.2cos5t), spacing 1, k0=2pi*20/16, k1=2k0, n=128, N={N}, "
+                        f"tol 1e-10, {levels} levels, 8 plane-wave RHS",
+            "precision": precision,
+            "l2": "inputs larger than L2 (factor working set > 1 GB)", "parallelism": f"replicas{ws}"}
+
+
 def cpu_oracle_sample(nx, reps=1):
     """Time the CPU oracle (factor + 8-RHS solve) on an nx x nx block of the same star recipe."""
     import numpy as np
@@ -141,6 +149,15 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    from paper_2603_09381_gb300 import workloads as wl
+    name = getattr(args, "workload", "star16")
+    if name not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the star-grid workloads only"}),
+              flush=True)
+        return 0
+    prob, _, _ = workload(name)
+    nxw = WORKLOADS[name]
+    levels = max(0, math.ceil(math.log2(nxw)))   # quadtree over the padded 2^L x 2^L grid
     # each step: the oracle on a 4x4 block (about 10-20 s); 2x2 if the run would exceed ~4 min
     nx = 4 if (args.steps + args.warmup) * 20 <= 240 else 2
     N, _ = cpu_oracle_sample(nx, reps=max(args.warmup, 0)) if args.warmup else (None, None)
@@ -151,11 +168,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": f"star grid {nx}x{nx} block of the 16x16 star recipe, n=128, tol 1e-10, 8 RHS",
-                       "l2": "n/a (CPU)"},
+            "config": _workload_config(nxw, wl.num_unknowns(prob), levels, getattr(args, "precision", "mixed"), ws),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"CPU oracle (NumPy/SciPy proxy solver), {nx}x{nx} stars, N={N}, "
-                                       f"factor + 8-RHS solve per step"},
+                             "sample": f"CPU oracle (NumPy/SciPy proxy solver) on a {nx}x{nx} block of the "
+                                       f"{nxw}x{nxw} workload, N={N}, factor + 8-RHS solve per step"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -373,11 +389,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+c128" if precision == pm.PM_MIXED else "c128",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOADS[args.workload]}x{WORKLOADS[args.workload]} stars "
-                                   f"r=0.4(1+0.2cos5t), spacing 1, k0=2pi*20/16, k1=2k0, n=128, N={N}, "
-                                   f"tol 1e-10, {st['levels']} levels, 8 plane-wave RHS",
-                       "precision": args.precision,
-                       "l2": "inputs larger than L2 (factor working set > 1 GB)", "parallelism": f"replicas{ws}"},
+            "config": _workload_config(WORKLOADS[args.workload], N, st["levels"], args.precision, ws),
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
             "refinement": info,
             "rank_predictor": {"used": model_ptr is not None, "cpqr_launches": st["cpqr_launches"],

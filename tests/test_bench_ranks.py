@@ -95,3 +95,26 @@ def test_traffic_record_follows_the_captured_kernel_only():
     text = open(os.path.join(ROOT, "paper_2603_09381_gb300", "csrc", rec["dense_matvec64"]["source"])).read()
     for a in rec["dense_matvec64"]["anchors"]:
         assert a in text
+
+
+def test_reference_arm_reports_the_workload_config(monkeypatch, capsys):
+    """The reference arm's line carries the same config object as the GPU arm's
+    line for the same workload; its bounded sample is described separately."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda nx, reps=1: (2 * 128 * nx * nx, [2.0] * reps))
+
+    class Args:
+        steps, warmup, gpus, workload, precision = 2, 1, 1, "star16", "mixed"
+
+    assert bench.run_reference(Args()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"] == bench._workload_config(16, 65536, 4, "mixed", 1)
+    assert line["value"] == pytest.approx(4096 / 2.0)
+    assert line["cpu_baseline"]["kind"] == "oracle" and "4x4 block" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
