@@ -77,3 +77,36 @@ def test_more_invalid_arguments_rejected_before_device_use():
     assert lib.pm_factorize(None, None, ct.byref(out)) == 1
     assert lib.pm_solve(None, None, 1, None, 0) == 1
     assert lib.pm_factor_stats(None, None) == 1
+
+
+def _bad(field, value):
+    def edit(prob):
+        inc = prob["inclusions"][0]
+        if field in ("k_out", "spacing"):
+            prob[field] = value
+        elif field == "prm0":
+            inc["prm"][0] = value
+        elif field == "prm5":
+            inc["prm"][5] = value
+        else:
+            inc[field] = value
+    return edit
+
+
+@pytest.mark.parametrize("field,value,word", [
+    ("shape", 4, "shape"), ("shape", -1, "shape"), ("n", 8, "n_nodes"), ("n", 4098, "n_nodes"),
+    ("n", 65, "n_nodes"), ("cx", float("nan"), "centre"), ("rot", float("inf"), "centre"),
+    ("prm0", 0.0, "size"), ("prm5", float("nan"), "shape parameter"), ("k_in", -2.0 + 0j, "positive real"),
+    ("k_in", 0.0 + 1j, "positive real"), ("k_in", 3.0 - 1e-3j, "Im"), ("k_out", 0.0, "k_out"),
+    ("k_out", float("nan"), "k_out"), ("spacing", -1.0, "spacing")])
+def test_each_invalid_descriptor_field_is_named(field, value, word):
+    """Every descriptor check of pm_build_geometry runs before the first CUDA
+    call: PM_ERR_INVALID_ARG and a message naming the field, with or without a GPU."""
+    from paper_2603_09381_gb300 import pmchwt as pm
+    from paper_2603_09381_gb300 import workloads as wl
+    prob = wl.circle_grid(2, 1)
+    _bad(field, value)(prob)
+    with pytest.raises(pm.PmError) as e:
+        pm.Geometry(prob)
+    assert e.value.status == 1
+    assert word in str(e.value)
