@@ -110,3 +110,24 @@ def test_each_invalid_descriptor_field_is_named(field, value, word):
         pm.Geometry(prob)
     assert e.value.status == 1
     assert word in str(e.value)
+
+
+def test_predictor_and_batch_entry_points_check_arguments_first():
+    """Sizes, counts, dtypes and NULL pointers are checked before any CUDA call."""
+    import ctypes as ct
+    from paper_2603_09381_gb300 import pmchwt as pm
+    lib = pm.load()
+    p = ct.c_void_p(16)          # never dereferenced: each call fails its checks first
+    assert lib.pm_mlp_forward(2, p, 4, p, p, None) == 1                     # dtype
+    assert lib.pm_mlp_forward(0, p, -1, p, p, None) == 1                    # batch size
+    assert lib.pm_mlp_forward(0, None, 4, p, p, None) == 1
+    assert lib.pm_mlp_loss_grad(0, p, 0, p, p, 1e-3, p, p, None) == 1        # empty batch
+    assert lib.pm_mlp_adam_step(1, p, p, p, p, 0, 1e-3, 0.9, 0.999, 1e-8, None) == 1   # step count from 1
+    assert lib.pm_mlp_train(p, 16, p, p, 0, 8, 1e-3, 0.0, 1, None, None) == 1          # no epochs
+    assert lib.pm_mlp_train(p, 16, p, p, 4, 0, 1e-3, 0.0, 1, None, None) == 1          # no batch
+    arr = (ct.c_void_p * 1)(16)
+    opts = pm.pm_factor_opts()
+    assert lib.pm_factor_batch(arr, 0, ct.byref(opts), arr, 1) == 1                      # empty batch
+    assert lib.pm_factor_batch(arr, 1, None, arr, 1) == 1
+    assert lib.pm_solve_batch(arr, 1, arr, 0, arr, 0, 1) == 1                            # no right-hand sides
+    assert b"pm_solve_batch" in lib.pm_last_error()
