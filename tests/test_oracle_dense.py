@@ -3,7 +3,6 @@ import math
 
 import numpy as np
 import pytest
-import scipy.special as sp
 
 from oracle import dense, geometry, mie
 from paper_2603_09381_gb300 import workloads as wl
@@ -25,20 +24,6 @@ def _mie_error(prob, angle=ANG):
         err.append(np.concatenate([q - qe, u - ue]))
         ref.append(np.concatenate([qe, ue]))
     return np.linalg.norm(np.concatenate(err)) / np.linalg.norm(np.concatenate(ref))
-
-
-def test_graf_addition_theorem():
-    k = 2 * math.pi
-    ci, cj = np.array([1.0, 0.3]), np.array([-0.2, 0.1])
-    M = 40
-    W = mie.translation_matrix(ci, cj, k, M)
-    ms = np.arange(-M, M + 1)
-    x = ci + 0.35 * np.array([math.cos(2.0), math.sin(2.0)])
-    dj, di = x - cj, x - ci
-    for m in [0, 1, -3, 7]:
-        lhs = sp.hankel1(m, k * np.hypot(*dj)) * np.exp(1j * m * math.atan2(dj[1], dj[0]))
-        rhs = np.sum(W[:, m + M] * sp.jv(ms, k * np.hypot(*di)) * np.exp(1j * ms * math.atan2(di[1], di[0])))
-        assert abs(lhs - rhs) < 1e-12
 
 
 def test_single_disk_mie():
