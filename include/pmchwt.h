@@ -103,7 +103,9 @@ typedef struct pm_factor pm_factor;
  *      slower today and, over the long row reductions, adds enough rounding
  *      error to raise the ranks at the complex64 threshold.
  * refine_tol: PM_MIXED: stop refining once every column's relative residual
- *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).
+ *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).  Intermediate residuals
+ *      may come from FP32 or float-float products of the stored operator;
+ *      the residual that ends the refinement is always formed in complex128.
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
  *      refine_tol returns PM_ERR_NOT_CONVERGED.
  * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 5e-6).
