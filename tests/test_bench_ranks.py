@@ -118,3 +118,28 @@ def test_reference_arm_reports_the_workload_config(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and "4x4 block" in line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_roofline_of_the_dominant_kernel():
+    """The roofline object names the kernel with the largest time and divides
+    its algorithmic work by its summed event time; FP64 kernels against the
+    nominal FP64 peak, the byte-counted FP32 CPQR against the copy bandwidth."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    steps = 2
+    prof = {"dense_matvec64": {"launches": 2, "ms": 400.0, "work": 2 * 2.75e11},
+            "qr_panel32": {"launches": 120, "ms": 150.0, "work": 0.0}}
+    r = bench._roofline(prof, steps)
+    assert r["kernel"] == "dense_matvec64" and r["launches_per_step"] == 1 and r["kernel_ms_per_step"] == 200.0
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(2.75e11 / 0.2 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_NOMINAL_TFLOPS)
+    assert r["traffic"] == json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))[
+        "dense_matvec64"]["bytes_per_launch"]
+    r = bench._roofline({"cpqr_step32": {"launches": 10, "ms": 50.0, "work": 1e11}}, 1)
+    peak, _ = bench._peaks()
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
+    assert r["achieved"] == pytest.approx(1e11 / 0.05 / 1e9) and r["frac"] == pytest.approx(r["achieved"] / peak)
+    t = bench._kernel_table(prof, steps)
+    assert list(t) == ["dense_matvec64", "qr_panel32"] and t["qr_panel32"] == {"launches": 60, "ms": 75.0}
