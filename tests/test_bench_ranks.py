@@ -143,3 +143,20 @@ def test_roofline_of_the_dominant_kernel():
     assert r["achieved"] == pytest.approx(1e11 / 0.05 / 1e9) and r["frac"] == pytest.approx(r["achieved"] / peak)
     t = bench._kernel_table(prof, steps)
     assert list(t) == ["dense_matvec64", "qr_panel32"] and t["qr_panel32"] == {"launches": 60, "ms": 75.0}
+
+
+def test_clock_summary_parses_samples():
+    """Median SM clock under load, the maximum clock and every throttle reason
+    seen active in the nvidia-smi samples."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    c.lines = ["0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line", "0, [N/A], 2070, 0, 0x0, a, b, c, d"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = []
+    assert c.summary()["sm_mhz"] is None
