@@ -1,9 +1,11 @@
-"""Multi-rank host logic of bench.py on the CPU (gloo, world size 2).
+"""Host logic of bench.py on the CPU.
 
 Each GPU of a multi-GPU run factors its own replica (no collective on the
 data path); the bench reports the slowest rank's time and counts the units
-of every rank.  These tests run that reduction with two gloo ranks, and the
-reference arm's rule that only rank 0 runs and prints.
+of every rank.  These tests run that reduction with two gloo ranks, the
+reference arm's rules (rank 0 only, the GPU arm's config), the roofline and
+kernel-table arithmetic, the traffic record's validity rule and the clock
+summary.
 """
 import json
 import multiprocessing as mp
