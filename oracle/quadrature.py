@@ -7,8 +7,8 @@
       int_0^{2pi} ln(4 sin^2((t - tau)/2)) f(tau) dtau  ~  sum_j R_j(t) f(t_j),
       R_j(t) = -(2 pi / M) sum_{m=1}^{M-1} cos(m (t - t_j)) / m
                - (pi / M^2) cos(M (t - t_j)).
-  The paper uses a zeta-corrected rule instead (Sec. 2.2); this build uses the
-  log-split rule in both the oracle and the CUDA path.
+  The paper uses a zeta-corrected rule instead (Sec. 2.2); the log-split rule
+  serves both the oracle and the CUDA path.
 * The trigonometric (Fourier) differentiation matrix on n equispaced nodes
   (n even): D_ij = 1/2 (-1)^(i-j) cot((t_i - t_j)/2), D_ii = 0 (Trefethen,
   Spectral Methods in MATLAB, ch. 3); used by Maue's form of N.
