@@ -102,10 +102,16 @@ typedef struct pm_factor pm_factor;
  *      moves them to the tensor cores (pm_gemm_c32's kernel), which is
  *      slower today and, over the long row reductions, adds enough rounding
  *      error to raise the ranks at the complex64 threshold.
+ *      PM_FLAG_FF_CONFIRM (PM_MIXED with the dense operator): the residual
+ *      that ends the refinement comes from a float-float product of the
+ *      stored operator whose sums are folded into FP64 every 16 columns
+ *      (worst-case error ~9e-13 of sum_j |a_ij| |x_j| per row, below that of
+ *      a sequential FP64 sum) instead of the FP64 product.
  * refine_tol: PM_MIXED: stop refining once every column's relative residual
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).  Intermediate residuals
  *      may come from FP32 or float-float products of the stored operator;
- *      the residual that ends the refinement is always formed in complex128.
+ *      the residual that ends the refinement is formed in complex128 (or, with
+ *      PM_FLAG_FF_CONFIRM, by the folded float-float product).
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
  *      refine_tol returns PM_ERR_NOT_CONVERGED.
  * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 5e-6).
@@ -236,7 +242,13 @@ typedef struct {
   double ms;
   double work;
 } pm_kernel_stat;
-enum { PM_FLAG_PROFILE = 1, PM_FLAG_NO_DENSE_OPERATOR = 2, PM_FLAG_NO_QR_FIRST = 4, PM_FLAG_TENSOR_CORES = 8 };
+enum {
+  PM_FLAG_PROFILE = 1,
+  PM_FLAG_NO_DENSE_OPERATOR = 2,
+  PM_FLAG_NO_QR_FIRST = 4,
+  PM_FLAG_TENSOR_CORES = 8,
+  PM_FLAG_FF_CONFIRM = 16
+};
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 
 /* ---- learned ID-rank predictor (no counterpart in the paper) ----------------

@@ -341,6 +341,66 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float4* __res
   }
 }
 
+// The float-float product with its (hi, lo) sums restarted every FFC_FOLD
+// columns and folded into FP64.  Within a group of m terms lo's own rounding
+// is at most ~(m^2/2 + 7m) u^2 sum |a||x| (u = 2^-24): with m = 16 about 9e-13
+// of sum_j |a_ij||x_j| per row, below the n 2^-53 worst case of a sequential
+// FP64 sum over a ~20,000-term segment, so this product can end the
+// refinement in place of the FP64 one.
+constexpr int FFC_FOLD = 16;
+template <int NR>
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __restrict__ A, size_t lda, int N,
+                                                              const double2* __restrict__ X, int ldx,
+                                                              double2* __restrict__ Y, int ldy, int seg) {
+  __shared__ float4 xs[NR][MV_KT];   // {hi(re), hi(im), lo(re), lo(im)} of x
+  const int row = blockIdx.x * MV_ROWS + threadIdx.x;
+  const int k0 = blockIdx.y * seg, k1 = min(N, k0 + seg);
+  double2 accd[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) accd[q] = make_double2(0.0, 0.0);
+  for (int kb = k0; kb < k1; kb += MV_KT) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NR * MV_KT; e += MV_ROWS) {
+      const int q = e / MV_KT, kk = e % MV_KT;
+      const double2 v = (kb + kk < k1) ? X[kb + kk + (size_t)q * ldx] : make_double2(0, 0);
+      xs[q][kk] = split4(v.x, v.y);
+    }
+    __syncthreads();
+    if (row < N) {
+      const int cnt = min(MV_KT, k1 - kb);
+      const float4* col = A + row + (size_t)kb * lda;
+      for (int kf = 0; kf < cnt; kf += FFC_FOLD) {
+        const int kend = min(cnt, kf + FFC_FOLD);
+        float rh[NR], rl[NR], ih[NR], il[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) { rh[q] = rl[q] = ih[q] = il[q] = 0.f; }
+        for (int kk = kf; kk < kend; ++kk) {
+          const float4 a = __ldg(col + (size_t)kk * lda);
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            const float4 x = xs[q][kk];
+            ff_mac(rh[q], rl[q], a.x, a.z, x.x, x.z, 1.f);
+            ff_mac(rh[q], rl[q], a.y, a.w, x.y, x.w, -1.f);
+            ff_mac(ih[q], il[q], a.x, a.z, x.y, x.w, 1.f);
+            ff_mac(ih[q], il[q], a.y, a.w, x.x, x.z, 1.f);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          accd[q].x += (double)rh[q] + (double)rl[q];
+          accd[q].y += (double)ih[q] + (double)il[q];
+        }
+      }
+    }
+  }
+  if (row >= N) return;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    atomicAdd(&Y[row + (size_t)q * ldy].x, accd[q].x);
+    atomicAdd(&Y[row + (size_t)q * ldy].y, accd[q].y);
+  }
+}
+
 __global__ void k_split_copy(const double2* __restrict__ src, int lds, float4* __restrict__ dst, size_t ldd, int m,
                              int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -536,6 +596,38 @@ void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int l
     else { launch_matvec_ff<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "dense_matvec_ff", 0.0);
+}
+
+template <int NR>
+void launch_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy,
+                       cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int rb = (N + MV_ROWS - 1) / MV_ROWS;
+  int segs = std::max(1, (sms * 12 + rb - 1) / rb);
+  int seg = (N + segs - 1) / segs;
+  seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
+  segs = (N + seg - 1) / seg;
+  k_dense_matvec_ffc<NR><<<dim3(rb, segs), MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  pm_launch_count_add(1);
+}
+
+void dense_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                      cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
+  KPROF_BEGIN(st);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    const double2* Xr = X + (size_t)r0 * ldx;
+    double2* Yr = Y + (size_t)r0 * ldy;
+    if (left >= 8) { launch_matvec_ffc<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec_ffc<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec_ffc<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec_ffc<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+  }
+  KPROF_END(st, "dense_matvec_ffc", 0.0);
 }
 
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st) {

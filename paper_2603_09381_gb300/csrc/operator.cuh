@@ -17,8 +17,9 @@ struct OpNodes {
 void apply_offdiag64(OpNodes nd, int total_nodes, double k0, const double2* X, int ldx, double2* Y, int ldy,
                      int nrhs, cudaStream_t st);
 // The dense operator is stored split: each complex entry a as float4
-// {hi(re), hi(im), lo(re), lo(im)} with hi = fl32(a), lo = fl32(a - hi), so
-// hi + lo represents the FP64 entry to ~4e-15 relative in 16 bytes.
+// {hi(re), hi(im), lo(re), lo(im)} with hi = a truncated to 24 significant
+// bits and lo the next 24 bits, so hi + lo is exact in FP64 and within 2^-47
+// of the entry, in 16 bytes.
 // Off-diagonal part written out densely (column-major, leading dimension lda);
 // same-inclusion pairs untouched (the caller copies the self blocks in).  One
 // Hankel evaluation per node pair fills the pair's 2 x 2 entries.
@@ -33,6 +34,11 @@ void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ld
 // sums; ~1e-13 relative, for refinement residuals.
 void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                      cudaStream_t st);
+// The float-float product with its sums folded into FP64 every 16 columns:
+// worst-case error ~9e-13 of sum_j |a_ij||x_j| per row, so it may decide the
+// convergence of the refinement (PM_FLAG_FF_CONFIRM).
+void dense_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+                      cudaStream_t st);
 // The same product with the hi parts in FP32 arithmetic (~1e-7 relative to
 // |A| |X|): the first refinement residual only.
 void dense_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,

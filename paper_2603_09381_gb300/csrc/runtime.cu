@@ -1256,8 +1256,17 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     for (int r = 0; r < nrhs; ++r) worst = std::max(worst, std::sqrt(hn[2 * r]) / std::max(std::sqrt(hn[2 * r + 1]), 1e-300));
     return worst;
   };
+  // The residual that can end the refinement: the FP64 product, or with
+  // PM_FLAG_FF_CONFIRM the float-float product folded into FP64 every 16
+  // columns (a smaller worst-case error bound on the FP32 pipes).
+  const bool ff_confirm = F->dense64 && (F->opts.flags & PM_FLAG_FF_CONFIRM);
   auto residual = [&](const double2* x) {
-    apply_operator64(F, x, nrhs, Y, ws, st);
+    if (ff_confirm) {
+      dense_matvec_ffc(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
+      CK(cudaGetLastError());
+    } else {
+      apply_operator64(F, x, nrhs, Y, ws, st);
+    }
     return finish();
   };
   auto residual_low = [&](const double2* x) {

@@ -64,6 +64,7 @@ PM_FLAG_PROFILE = 1
 PM_FLAG_NO_DENSE_OPERATOR = 2
 PM_FLAG_NO_QR_FIRST = 4
 PM_FLAG_TENSOR_CORES = 8
+PM_FLAG_FF_CONFIRM = 16
 _lib = None
 
 EXPORTS = {
@@ -206,7 +207,7 @@ class Geometry:
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
-                 qr_first=True, tensor_cores=False):
+                 qr_first=True, tensor_cores=False, ff_confirm=False):
         """rank_model: device pointer (int) of a trained predictor, or None."""
         lib = load()
         self.geom = geom
@@ -214,7 +215,8 @@ class Factor:
         o = pm_factor_opts(float(tol), float(proxy_factor), int(proxy_points), int(precision),
                            ct.c_void_p(stream) if stream else None,
                            (PM_FLAG_PROFILE if profile else 0) | (0 if dense_operator else PM_FLAG_NO_DENSE_OPERATOR)
-                           | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0),
+                           | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0)
+                           | (PM_FLAG_FF_CONFIRM if ff_confirm else 0),
                            float(refine_tol), int(max_refine), float(low_tol),
                            ct.c_void_p(rank_model) if rank_model else None)
         h = ct.c_void_p()
