@@ -228,14 +228,14 @@ def _peaks():
         return 6800.0, "fallback (recipe)"
 
 
-def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None):
+def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None, ff_confirm=False):
     """Warm-up, then `steps` timed factor + solve passes on the stream; returns per-step numbers."""
     import torch
     nrhs = len(angs)
 
     def step(profile):
         f = pm.Factor(g, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
-                      stream=stream.cuda_stream, profile=profile, rank_model=model_ptr)
+                      stream=stream.cuda_stream, profile=profile, rank_model=model_ptr, ff_confirm=ff_confirm)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         info = f.solve_device(F.data_ptr(), nrhs, X.data_ptr())
@@ -340,7 +340,7 @@ def run_ours(args):
         torch.distributed.barrier()
     with Clocks(local) as clk:
         ms, solve, prof_tot, st, info, launches = _timed(pm, g, prob, opts, angs, F, X, stream, precision,
-                                                        args.steps, args.warmup, model_ptr)
+                                                        args.steps, args.warmup, model_ptr, args.ff_confirm)
     if ws > 1:
         ms = _max_over_ranks(ms, "cuda")
         torch.distributed.barrier()
@@ -358,7 +358,7 @@ def run_ours(args):
     for _ in range(args.steps):
         g2 = pm.Geometry(prob)
         f2 = pm.Factor(g2, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
-                       stream=stream.cuda_stream, rank_model=model_ptr)
+                       stream=stream.cuda_stream, rank_model=model_ptr, ff_confirm=args.ff_confirm)
         inf2 = pm.pm_solve_info()
         pm._check(pm.load().pm_solve_ex(f2.h, rhs_host.data_ptr(), nrhs, out_host.data_ptr(), 0,
                                         pm.ct.byref(inf2)))
@@ -390,6 +390,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "c64+c128" if precision == pm.PM_MIXED else "c128",
             "data": "synthetic",
             "config": _workload_config(WORKLOADS[args.workload], N, st["levels"], args.precision, ws),
+            "refinement_confirm": "float-float, folded" if args.ff_confirm else "fp64",
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
             "refinement": info,
             "rank_predictor": {"used": model_ptr is not None, "cpqr_launches": st["cpqr_launches"],
@@ -463,6 +464,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-rank-model", action="store_true")
+    # the refinement ends on the folded float-float product instead of the FP64 one
+    ap.add_argument("--ff-confirm", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
