@@ -131,3 +131,39 @@ def test_predictor_and_batch_entry_points_check_arguments_first():
     assert lib.pm_factor_batch(arr, 1, None, arr, 1) == 1
     assert lib.pm_solve_batch(arr, 1, arr, 0, arr, 0, 1) == 1                            # no right-hand sides
     assert b"pm_solve_batch" in lib.pm_last_error()
+
+
+def test_factor_options_marshalling(monkeypatch):
+    """The binding's keyword options land in pm_factor_opts as the header
+    defines them (checked with a stand-in for the library)."""
+    import ctypes as ct
+    from paper_2603_09381_gb300 import pmchwt as pm
+    seen = {}
+
+    class FakeLib:
+        def pm_factorize(self, gh, optp, outp):
+            o = ct.cast(optp, ct.POINTER(pm.pm_factor_opts)).contents
+            seen.update({f: getattr(o, f) for f, _ in pm.pm_factor_opts._fields_})
+            return 0
+
+        def pm_factor_free(self, h):
+            pass
+
+    monkeypatch.setattr(pm, "load", lambda path=None: FakeLib())
+
+    class G:
+        h = ct.c_void_p(16)
+
+    cases = [({}, 0), ({"profile": True}, pm.PM_FLAG_PROFILE), ({"dense_operator": False}, pm.PM_FLAG_NO_DENSE_OPERATOR),
+             ({"qr_first": False}, pm.PM_FLAG_NO_QR_FIRST), ({"tensor_cores": True}, pm.PM_FLAG_TENSOR_CORES),
+             ({"ff_confirm": True}, pm.PM_FLAG_FF_CONFIRM),
+             ({"ff_confirm": True, "qr_first": False, "profile": True},
+              pm.PM_FLAG_FF_CONFIRM | pm.PM_FLAG_NO_QR_FIRST | pm.PM_FLAG_PROFILE)]
+    for kw, flags in cases:
+        seen.clear()
+        f = pm.Factor(G(), 1e-9, 1.7, 48, precision=pm.PM_MIXED, refine_tol=1e-11, max_refine=7, low_tol=4e-6, **kw)
+        f.h = None
+        assert seen["flags"] == flags, kw
+        assert (seen["tol"], seen["proxy_factor"], seen["proxy_points"], seen["precision"]) == (1e-9, 1.7, 48, 1)
+        assert (seen["refine_tol"], seen["max_refine"], seen["low_tol"]) == (1e-11, 7, 4e-6)
+        assert not seen["stream"] and not seen["rank_model"]
