@@ -60,3 +60,21 @@ def test_uneven_node_counts_match_dense():
     fac = proxy.factor(prob, {"tol": 1e-10})
     F = np.stack([dense.plane_wave(prob, a) for a in (0.2, 2.5)], 1)
     assert _rel(proxy.solve(fac, F), dense.solve(prob, [0.2, 2.5])) < 3e-9
+
+
+def test_full_rank_degenerates_to_the_dense_solve():
+    """With a threshold below rounding every ID keeps all of its indices: the
+    compressed system is the whole matrix and the solve is exact up to rounding."""
+    prob = wl.circle_grid(2, 2, n=32)
+    fac = proxy.factor(prob, {"tol": 1e-16, "proxy_points": 64})
+    assert fac["stats"]["K"] == fac["N"] == 256
+    x = proxy.solve(fac, dense.plane_wave(prob, 0.3))
+    assert _rel(x, dense.solve(prob, [0.3])[:, 0]) < 1e-13
+
+
+def test_loose_threshold_keeps_a_nonsingular_factorization():
+    prob = wl.circle_grid(2, 2, n=32)
+    fac = proxy.factor(prob, {"tol": 0.5, "proxy_points": 64})
+    assert 8 <= fac["stats"]["K"] < 64
+    x = proxy.solve(fac, dense.plane_wave(prob, 0.3))
+    assert np.all(np.isfinite(x)) and _rel(x, dense.solve(prob, [0.3])[:, 0]) < 1.0
