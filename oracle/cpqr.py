@@ -14,6 +14,17 @@ v = x / (alpha - beta) with v_0 = 1; H = I - tau v v^H satisfies
 H^H x = beta e_1, so the trailing columns are updated with H^H (conj(tau)).
 The ID T = R11^{-1} R12 does not depend on this phase convention.
 
+Decision margins (bookkeeping only, no effect on the arithmetic): every
+pivot choice and the rank decision compare floating-point norms against a
+threshold, so a second implementation that rounds differently can only
+disagree where a compared quantity lies within its rounding error of the
+threshold.  ``margin_pivot`` records, over all steps, the smallest distance
+|norm2_c - (1 - TIE) max| of any non-maximal candidate from the tie band's
+edge, measured in norms (|sqrt(norm2_c) - sqrt((1 - TIE) max)|), and
+``margin_rank`` the smallest |norm - tol |R_11|| over the kept steps and the
+stopping test; both in units of eps |R_11| (eps = 2^-52), the size of the
+rounding error a backward-stable QR leaves in a trailing column norm.
+
 Parity pinned by tests/test_oracle_cpqr.py: pivots equal brute-force greedy
 selection on tiny matrices; ID error on random low-rank matrices.
 """
@@ -21,6 +32,7 @@ import numpy as np
 import scipy.linalg as sla
 
 TIE = 1e-12
+EPS = 2.0 ** -52
 
 
 class CPQR:
@@ -49,6 +61,8 @@ class CPQR:
         self.ref = None
         self.rank = None
         self.rdiag = []
+        self.margin_pivot = np.inf
+        self.margin_rank = np.inf
 
     def _norms2(self):
         B = self.A[self.j:, self.j:]
@@ -57,6 +71,10 @@ class CPQR:
     def _step(self, norms2):
         j, A = self.j, self.A
         mx = norms2.max()
+        if self.ref and len(norms2) > 1:
+            others = np.delete(norms2, int(np.argmax(norms2)))
+            gap = np.min(np.abs(np.sqrt(others) - np.sqrt((1.0 - TIE) * mx))) / (EPS * self.ref)
+            self.margin_pivot = min(self.margin_pivot, gap)
         tied = np.nonzero(norms2 >= (1.0 - TIE) * mx)[0]
         p = j + tied[np.argmin(self.perm[j + tied])]
         if p != j:
@@ -81,6 +99,9 @@ class CPQR:
             norms2 = self._norms2()
             if self.ref is None:
                 self.ref = np.sqrt(norms2.max())
+            if self.ref > 0:
+                self.margin_rank = min(self.margin_rank, abs(np.sqrt(norms2.max()) - self.tol * self.ref)
+                                       / (EPS * self.ref))
             if not np.sqrt(norms2.max()) > self.tol * self.ref:
                 break
             self._step(norms2)

@@ -198,7 +198,8 @@ def factor(prob, opts):
                              "srows": np.concatenate(srows), "srgrp": np.concatenate(srgrp),
                              "scols": np.concatenate(scols), "scgrp": np.concatenate(scgrp),
                              "kg": kg, "skel": {key: (v[0], v[1].perm[:v[1].j].copy(), v[1].rank)
-                                                 for key, v in ids.items()}}
+                                                 for key, v in ids.items()},
+                             "margin": min(min(v[1].margin_pivot, v[1].margin_rank) for v in ids.values())}
             ranks_lev.append(kg)
         stats["ranks"][lev] = ranks_lev
     root = levels[0][0]

@@ -76,3 +76,26 @@ def test_rank_zero_matrix_and_stateful_extension():
     perm, R, _, _ = cp.cpqr(Z, 1e-8, max_steps=14)
     assert list(f.perm[:14]) == list(perm[:14])
     assert np.allclose(np.abs(np.diag(f.R[:, :14])), np.abs(np.diag(R[:, :14])), atol=1e-12)
+
+
+def test_decision_margins_flag_near_ties_only():
+    """The margins (bookkeeping for parity tests) are large for well separated
+    column norms and shrink to rounding size when a candidate sits at the tie
+    band's edge or a diagonal entry sits at the rank threshold."""
+    rng = np.random.default_rng(5)
+    Z = rng.standard_normal((40, 12)) + 1j * rng.standard_normal((40, 12))
+    Z *= np.logspace(0, -6, 12)[None, :]
+    f = cp.CPQR(Z, 1e-9)
+    f.find_rank()
+    assert f.margin_pivot > 1e6 and f.margin_rank > 1e6
+    # two orthogonal columns whose norms differ by exactly the tie band
+    Y = np.zeros((4, 2), dtype=complex)
+    Y[0, 0] = 1.0
+    Y[1, 1] = np.sqrt(1.0 - cp.TIE)
+    g = cp.CPQR(Y, 0.0)
+    g.find_rank()
+    assert g.margin_pivot < 10
+    # a column whose trailing norm equals tol |R_11|
+    X = np.diag([1.0, 1e-3, 1e-8]).astype(complex)
+    h = cp.CPQR(X, 1e-3)
+    assert h.find_rank() == 1 and h.margin_rank < 10

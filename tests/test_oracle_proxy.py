@@ -17,7 +17,20 @@ def test_small_circle_grid_matches_dense():
     fac = proxy.factor(prob, opts)
     F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
     assert _rel(proxy.solve(fac, F), dense.solve(prob, angs)) < 1e-11
-    assert fac["L"] == 1 and fac["stats"]["K"] <= 512
+    # 64 nodes per circle at 1e-12 keep every index: this case checks the
+    # algebra of eq. compressed and the recovery formula, not compression
+    assert fac["L"] == 1 and fac["stats"]["K"] == 512
+
+
+def test_single_level_compression_matches_dense():
+    """2 x 2 stars with 128 nodes at 1e-10: one compressed level that drops
+    almost a third of the unknowns and still solves to the threshold."""
+    prob = wl.star_grid(2, 2, n=128, seed=1)
+    fac = proxy.factor(prob, {"tol": 1e-10, "proxy_factor": 1.5})
+    assert fac["L"] == 1 and fac["stats"]["K"] < 0.75 * fac["N"]
+    angs = [0.3, 1.9]
+    F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
+    assert _rel(proxy.solve(fac, F), dense.solve(prob, angs)) < 30 * 1e-10
 
 
 def test_single_inclusion_degenerates_to_dense():
