@@ -120,7 +120,21 @@ typedef struct pm_factor pm_factor;
  *      CPQR of every level then runs up to the median predicted rank before its
  *      first rank check (host synchronisation) instead of checking every 16
  *      steps; IDs whose rank exceeds the prediction continue under the regular
- *      checks, so the factorization is the same with or without it. */
+ *      checks, so the factorization is the same with or without it.
+ * debug_flags: 0 in normal use.  Host-side fault injection for tests of the
+ *      failure paths (no counterpart in the paper); every injected fault is a
+ *      plain write of zeros or a changed host decision, never a device fault:
+ *      PM_DEBUG_SINGULAR_BLOCK zeroes the first leaf box's self block before
+ *        its LU (-> PM_ERR_SINGULAR, "diagonal block");
+ *      PM_DEBUG_SINGULAR_COMPRESSED zeroes R_b A_bb^{-1} L_b of the first leaf
+ *        box before its inversion (-> PM_ERR_SINGULAR, the failure that
+ *        Sec. 3 shows for the simplified Burton-Miller system);
+ *      PM_DEBUG_UNDERPREDICT replaces every predicted rank by 1 (with a
+ *        rank_model): every ID falls back to the adaptive checks, and the
+ *        factorization is unchanged;
+ *      PM_DEBUG_TC_NO_ARRIVE makes the tensor-core kernels (PM_FLAG_TENSOR_CORES)
+ *        wait, with a short bound, on a barrier that nothing arrives at
+ *        before they issue any work (-> PM_ERR_TIMEOUT). */
 typedef struct {
   double tol;
   double proxy_factor;
@@ -132,7 +146,14 @@ typedef struct {
   int32_t max_refine;
   double low_tol;
   const float* rank_model;
+  uint32_t debug_flags;
 } pm_factor_opts;
+enum {
+  PM_DEBUG_SINGULAR_BLOCK = 1,
+  PM_DEBUG_SINGULAR_COMPRESSED = 2,
+  PM_DEBUG_UNDERPREDICT = 4,
+  PM_DEBUG_TC_NO_ARRIVE = 8
+};
 
 /* Outcome of a refined solve (PM_MIXED): steps taken, the final largest
  * relative residual over the right-hand sides (-1 when not refined) and the
@@ -187,9 +208,11 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
 
 /* Solve A phi = rhs for nrhs right-hand sides (paper Sec. 3: eq. compressed and
  * the recovery formula).  rhs and phi are N x nrhs column-major, device
- * pointers if on_device = 1, else host pointers; they may alias.  PM_MIXED
- * factors refine the solution (PM_ERR_NOT_CONVERGED if refine_tol is not
- * reached). */
+ * pointers on the current device if on_device = 1 (anything else, e.g. a
+ * host pointer, -> PM_ERR_INVALID_ARG before any launch), else host
+ * pointers; they may alias.  A right-hand side with a NaN or infinite entry
+ * -> PM_ERR_INVALID_ARG, phi untouched.  PM_MIXED factors refine the
+ * solution (PM_ERR_NOT_CONVERGED if refine_tol is not reached). */
 pm_status pm_solve(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device);
 
 /* pm_solve that also reports the refinement outcome (info may be NULL). */
@@ -302,15 +325,26 @@ pm_status pm_gemm_c32(int32_t m, int32_t n, int32_t k, const void* A, int32_t ld
  * synchronise the device while the caller has work in flight, or because the
  * caller runs under its own device-memory manager or a fixed budget.
  *   out: caller-owned DEVICE buffer of (2 n_j)^2 pm_c64, column-major,
- *        on the current device; fully overwritten.
+ *        on the current device, which must be the device the geometry was
+ *        built on; fully overwritten.  A host pointer or another device's
+ *        memory -> PM_ERR_INVALID_ARG before any launch.
  * Scratch lives in a file-scope device array of 4 MiB + 64 KiB that every GPU
  * loading the library holds until the process exits; it limits n_j to 256
  * (larger n_j -> PM_ERR_INVALID_ARG, nothing written).  The first call on a
  * device looks up that array's device address; make it before any stream
- * capture.  Calls share the array and return only when their work on the
+ * capture.  The address is cached for the life of the process: it does not
+ * survive cudaDeviceReset or a reset of the primary context by the host
+ * application (call no further pm_self_block_noalloc after one).  Calls share the array and return only when their work on the
  * default stream has finished, so calls overlapping on the GPU (e.g. from
  * several host threads at once) race and must be serialised by the caller. */
 pm_status pm_self_block_noalloc(const pm_geometry* g, int32_t j, pm_c64* out);
+
+/* Peak arithmetic rates of the current device, measured by the library's
+ * own loop of independent fused multiply-adds (no counterpart in the paper;
+ * the denominators of the roofline fractions of the FP64 and FP32 kernels).
+ * which = 0: FP64 FMA, 1: FP32 FMA.  Runs about `ms_target` milliseconds on
+ * the default stream; *tflops receives 2 flops per FMA over the event time. */
+pm_status pm_measure_peak(int32_t which, double ms_target, double* tflops);
 
 void pm_factor_free(pm_factor* f);
 void pm_geometry_free(pm_geometry* g);

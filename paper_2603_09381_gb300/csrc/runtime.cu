@@ -116,6 +116,7 @@ struct Box {
 }  // namespace
 
 struct pm_geometry {
+  int device = 0;       // the CUDA device the geometry (and its factors) live on
   int m = 0;
   double k0 = 0, spacing = 1;
   int gnx = 0, gny = 0;
@@ -678,6 +679,7 @@ void process_level(pm_factor* F, int lev, double tol) {
         const int k = std::min(n, (int)std::ceil(frac * n + 2 + 0.02 * n));
         khat[4 * b + grp] = khat[4 * b + 2 + grp] = k;
       }
+    if (F->opts.debug_flags & PM_DEBUG_UNDERPREDICT) std::fill(khat.begin(), khat.end(), 1);   // injected
   }
   // 3a. complex64: tall inputs reduced to their triangular factor first, so
   // that the pivoted steps stream n instead of W rows
@@ -767,7 +769,8 @@ void process_level(pm_factor* F, int lev, double tol) {
             if (c == 0) continue;
             for (int l = 0; l < 3; ++l) {
               const int t0 = toff[l][s0], t1 = toff[l][s0 + c];
-              tc_gemm_batched(dg[l] + s0, dt[l] + s0, c, t1 - t0, terr, st, t0);
+              tc_gemm_batched(dg[l] + s0, dt[l] + s0, c, t1 - t0, terr, st, t0,
+                              (F->opts.debug_flags & PM_DEBUG_TC_NO_ARRIVE) != 0);
             }
           }
           qr_zero_lower<C>(dqp, nq, maxn, st);
@@ -973,6 +976,8 @@ void process_level(pm_factor* F, int lev, double tol) {
     CK(cudaGetLastError());
   }
   // 7. LU of D_b, X = D_b^{-1} L_b, Y = R_b X, A~_b = Y^{-1}
+  if ((F->opts.debug_flags & PM_DEBUG_SINGULAR_BLOCK) && lev == F->L && nb > 0)   // injected: zero self block
+    CK(cudaMemsetAsync(BF[0].D, 0, sizeof(C) * (size_t)BF[0].mb * BF[0].mb, st));
   std::vector<LuProb<C>> lu;
   for (int b = 0; b < nb; ++b) lu.push_back(LuProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, nullptr});
   lu_batch<C>(lu, scr, st, "diagonal block");
@@ -994,6 +999,8 @@ void process_level(pm_factor* F, int lev, double tol) {
     }
   }
   gy.run(scr, st);
+  if ((F->opts.debug_flags & PM_DEBUG_SINGULAR_COMPRESSED) && lev == F->L && nb > 0 && BF[0].kb > 0)
+    CK(cudaMemsetAsync(Y[0], 0, sizeof(C) * (size_t)BF[0].kb * BF[0].kb, st));   // injected: singular R A^-1 L
   std::vector<LuProb<C>> luy;
   std::vector<SolveProb<C>> svy;
   for (int b = 0; b < nb; ++b) {
@@ -1387,6 +1394,59 @@ void check_device() {
     fail(PM_ERR_CUDA, "no CUDA device available (this library has no CPU fallback)");
   }
 }
+
+// Device memory of the given device (or managed memory): anything else, such
+// as a host pointer or another GPU's buffer, is rejected before a kernel could
+// touch it.  cudaPointerGetAttributes allocates nothing.
+void require_device_ptr(const void* p, int device, const char* what) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    fail(PM_ERR_INVALID_ARG, std::string(what) + " is not a CUDA pointer");
+  }
+  if (!(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged))
+    fail(PM_ERR_INVALID_ARG, std::string(what) + " is not device memory (a host pointer?)");
+  if (a.type == cudaMemoryTypeDevice && a.device != device)
+    fail(PM_ERR_INVALID_ARG, std::string(what) + " lives on device " + std::to_string(a.device) + ", not on device " +
+                                 std::to_string(device));
+}
+
+void require_current_device(int device, const char* what) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != device)
+    fail(PM_ERR_INVALID_ARG, std::string(what) + ": the current device is " + std::to_string(dev) +
+                                 ", the geometry was built on device " + std::to_string(device));
+}
+
+// Sets *flag when any of the n doubles at x is NaN or infinite.
+__global__ void k_flag_nonfinite(const double* __restrict__ x, size_t n, int* flag) {
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1;
+}
+
+// Rejects right-hand sides holding a NaN or an infinity (host or device data).
+void require_finite_rhs(const pm_c64* rhs, size_t count, int on_device, Arena& ws, cudaStream_t st) {
+  if (!on_device) {
+    for (size_t i = 0; i < count; ++i)
+      if (!std::isfinite(rhs[i].re) || !std::isfinite(rhs[i].im))
+        fail(PM_ERR_INVALID_ARG, "right-hand side entry " + std::to_string(i) + " is not finite");
+    return;
+  }
+  int* flag = ws.get<int>(1);
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  const size_t n = 2 * count;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+  k_flag_nonfinite<<<std::max(blocks, 1), 256, 0, st>>>((const double*)rhs, n, flag);
+  pm_launch_count_add(1);
+  CK(cudaGetLastError());
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) fail(PM_ERR_INVALID_ARG, "a right-hand side entry is not finite");
+}
 }  // namespace
 
 extern "C" {
@@ -1413,6 +1473,7 @@ pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out) {
     }
     check_device();
     g = new pm_geometry();
+    CK(cudaGetDevice(&g->device));
     g->m = prob->m; g->k0 = prob->k_out; g->spacing = prob->spacing;
     g->gnx = prob->grid_nx; g->gny = prob->grid_ny;
     g->inc.assign(prob->inc, prob->inc + prob->m);
@@ -1473,6 +1534,10 @@ pm_status pm_plane_wave_rhs(const pm_geometry* g, const double* angles, int32_t 
     Arena ws;
     ws.min_block = 1 << 20;
     cudaStream_t st = 0;
+    if (on_device) {
+      require_current_device(g->device, "pm_plane_wave_rhs");
+      require_device_ptr(rhs, g->device, "rhs");
+    }
     std::vector<double> a(angles, angles + nrhs);
     double* da = upload(ws, a, st);
     Cd* F = on_device ? (Cd*)rhs : ws.get<Cd>((size_t)g->N * nrhs);
@@ -1607,7 +1672,14 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
   pm_factor* F = const_cast<pm_factor*>(Fc);
   return run_guarded("pm_solve", [&] {
     Arena ws;
+    ws.min_block = 1 << 20;
     const size_t bytes = sizeof(Cd) * (size_t)F->g->N * nrhs;
+    if (on_device) {
+      require_current_device(F->g->device, "pm_solve");
+      require_device_ptr(rhs, F->g->device, "rhs");
+      require_device_ptr(phi, F->g->device, "phi");
+    }
+    require_finite_rhs(rhs, (size_t)F->g->N * nrhs, on_device, ws, st);
     const Cd* drhs = (const Cd*)rhs;
     Cd* dphi = (Cd*)phi;
     if (!on_device) {
@@ -1991,6 +2063,8 @@ extern "C" pm_status pm_self_block_noalloc(const pm_geometry* g, int32_t j, pm_c
   }
   return run_guarded("pm_self_block_noalloc", [&] {
     cudaStream_t st = 0;
+    require_current_device(g->device, "pm_self_block_noalloc");
+    require_device_ptr(out, g->device, "out");
     char* base = noalloc_scratch();
     Cd* A = (Cd*)out;
     const int lda = 2 * n;

@@ -70,9 +70,9 @@ __device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, 
   *reinterpret_cast<float*>(lo + off) = to_tf32(x - h);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = WAIT_LIMIT) {
   const uint32_t a = smem_u32(bar);
-  for (int i = 0; i < WAIT_LIMIT; ++i) {
+  for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -92,7 +92,7 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd
 }
 
 __global__ void __launch_bounds__(TC_T) k_tc_gemm(const TcGemmProb* __restrict__ P, const int* __restrict__ tile_off,
-                                                  int nprob, int tile_base, int* err) {
+                                                  int nprob, int tile_base, int* err, int no_arrive) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int t = tile_base + (int)blockIdx.x;
   int lo_p = 0, hi_p = nprob;
@@ -106,10 +106,11 @@ __global__ void __launch_bounds__(TC_T) k_tc_gemm(const TcGemmProb* __restrict__
   const int m0 = (local % tiles_m) * TC_TM, n0 = (local / tiles_m) * TC_TN;
   const int tid = threadIdx.x, warp = tid >> 5;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * BUF);
-  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(sm + 2 * BUF + 16);
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(sm + 2 * BUF + 24);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[2])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -122,9 +123,11 @@ __global__ void __launch_bounds__(TC_T) k_tc_gemm(const TcGemmProb* __restrict__
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *s_taddr;
 
-  const int nchunks = (g.k + KC - 1) / KC;
-  uint32_t phase0 = 0, phase1 = 0;
   bool ok = true;
+  // timeout-path test: a barrier that nothing arrives at, waited on before any work is issued
+  if (no_arrive) ok = mbar_wait(&mbar[2], 0, 1 << 10);
+  const int nchunks = __syncthreads_and(ok ? 1 : 0) ? (g.k + KC - 1) / KC : 0;
+  uint32_t phase0 = 0, phase1 = 0;
   for (int c = 0; c < nchunks; ++c) {
     const int b = c & 1;
     unsigned char* Ahi = sm + b * BUF;
@@ -247,12 +250,12 @@ __global__ void __launch_bounds__(TC_T) k_tc_gemm(const TcGemmProb* __restrict__
 }  // namespace
 
 void tc_gemm_batched(const TcGemmProb* d_prob, const int* d_tile_off, int nprob, int total_tiles, int* d_err,
-                     cudaStream_t st, int tile_base) {
+                     cudaStream_t st, int tile_base, bool no_arrive) {
   if (nprob <= 0 || total_tiles <= 0) return;
   // the same value every time: idempotent across threads and devices
   cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   KPROF_BEGIN(st);
-  k_tc_gemm<<<total_tiles, TC_T, SMEM_BYTES, st>>>(d_prob, d_tile_off, nprob, tile_base, d_err);
+  k_tc_gemm<<<total_tiles, TC_T, SMEM_BYTES, st>>>(d_prob, d_tile_off, nprob, tile_base, d_err, no_arrive ? 1 : 0);
   pm_launch_count_add(1);
   KPROF_END(st, "tc_gemm32", 0.0);
 }

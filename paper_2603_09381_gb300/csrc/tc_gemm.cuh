@@ -25,5 +25,9 @@ inline int tc_tiles(int m, int n) { return ((m + TC_TM - 1) / TC_TM) * ((n + TC_
 // start at tile_base: then d_tile_off[0] == tile_base), total_tiles = the
 // tiles of the nprob problems; d_err: an int the kernel sets nonzero when a
 // wait on the tensor cores runs out (the launch's results are then invalid).
+// no_arrive (tests of the timeout path): every CTA first waits, with a bound
+// of about a millisecond, on a barrier that nothing arrives at, then skips
+// its tile, frees its tensor memory and sets *d_err, having issued no copy
+// and no MMA.
 void tc_gemm_batched(const TcGemmProb* d_prob, const int* d_tile_off, int nprob, int total_tiles, int* d_err,
-                     cudaStream_t st, int tile_base = 0);
+                     cudaStream_t st, int tile_base = 0, bool no_arrive = false);

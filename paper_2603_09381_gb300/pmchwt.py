@@ -42,7 +42,7 @@ class pm_factor_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("proxy_factor", ct.c_double), ("proxy_points", ct.c_int32),
                 ("precision", ct.c_int32), ("stream", ct.c_void_p), ("flags", ct.c_uint32),
                 ("refine_tol", ct.c_double), ("max_refine", ct.c_int32), ("low_tol", ct.c_double),
-                ("rank_model", ct.c_void_p)]
+                ("rank_model", ct.c_void_p), ("debug_flags", ct.c_uint32)]
 
 
 class pm_solve_info(ct.Structure):
@@ -65,6 +65,10 @@ PM_FLAG_NO_DENSE_OPERATOR = 2
 PM_FLAG_NO_QR_FIRST = 4
 PM_FLAG_TENSOR_CORES = 8
 PM_FLAG_FF_CONFIRM = 16
+PM_DEBUG_SINGULAR_BLOCK = 1
+PM_DEBUG_SINGULAR_COMPRESSED = 2
+PM_DEBUG_UNDERPREDICT = 4
+PM_DEBUG_TC_NO_ARRIVE = 8
 _lib = None
 
 EXPORTS = {
@@ -98,6 +102,7 @@ EXPORTS = {
     "pm_gemm_c32": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p,
                                ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_float),
                                ct.POINTER(ct.c_float), ct.c_void_p]),
+    "pm_measure_peak": (ct.c_int, [ct.c_int32, ct.c_double, ct.POINTER(ct.c_double)]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
     "pm_last_error": (ct.c_char_p, []),
@@ -148,6 +153,13 @@ def gemm_c32(m, n, k, A_ptr, lda, conj_a, B_ptr, ldb, conj_b, C_ptr, ldc, alpha=
     be = (ct.c_float * 2)(complex(beta).real, complex(beta).imag)
     _check(load().pm_gemm_c32(m, n, k, A_ptr, lda, int(conj_a), B_ptr, ldb, int(conj_b), C_ptr, ldc, al, be,
                               ct.c_void_p(stream) if stream else None))
+
+
+def measure_peak(which, ms_target=200.0):
+    """Peak TFLOP/s of the current device from the library's FMA loop: which 0 = FP64, 1 = FP32."""
+    v = ct.c_double()
+    _check(load().pm_measure_peak(int(which), float(ms_target), ct.byref(v)))
+    return v.value
 
 
 def launch_counter():
@@ -207,8 +219,9 @@ class Geometry:
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
-                 qr_first=True, tensor_cores=False, ff_confirm=False):
-        """rank_model: device pointer (int) of a trained predictor, or None."""
+                 qr_first=True, tensor_cores=False, ff_confirm=False, debug_flags=0):
+        """rank_model: device pointer (int) of a trained predictor, or None;
+        debug_flags: PM_DEBUG_* fault injection for failure-path tests (0 in normal use)."""
         lib = load()
         self.geom = geom
         self.last_info = None
@@ -218,7 +231,7 @@ class Factor:
                            | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0)
                            | (PM_FLAG_FF_CONFIRM if ff_confirm else 0),
                            float(refine_tol), int(max_refine), float(low_tol),
-                           ct.c_void_p(rank_model) if rank_model else None)
+                           ct.c_void_p(rank_model) if rank_model else None, int(debug_flags))
         h = ct.c_void_p()
         _check(lib.pm_factorize(geom.h, ct.byref(o), ct.byref(h)))
         self.h = h
@@ -318,7 +331,8 @@ def factor_batch(geoms, tol, precision=PM_FP64, workers=8, rank_model=None, **kw
     n = len(geoms)
     o = pm_factor_opts(float(tol), float(kw.get("proxy_factor", 1.5)), int(kw.get("proxy_points", 0)),
                        int(precision), None, 0, float(kw.get("refine_tol", 0.0)), int(kw.get("max_refine", 0)),
-                       float(kw.get("low_tol", 0.0)), ct.c_void_p(rank_model) if rank_model else None)
+                       float(kw.get("low_tol", 0.0)), ct.c_void_p(rank_model) if rank_model else None,
+                       int(kw.get("debug_flags", 0)))
     gh = (ct.c_void_p * n)(*[g.h.value for g in geoms])
     out = (ct.c_void_p * n)()
     _check(load().pm_factor_batch(gh, n, ct.byref(o), out, workers))

@@ -77,6 +77,16 @@ def test_more_invalid_arguments_rejected_before_device_use():
     assert lib.pm_factorize(None, None, ct.byref(out)) == 1
     assert lib.pm_solve(None, None, 1, None, 0) == 1
     assert lib.pm_factor_stats(None, None) == 1
+    # allocation-free self block: NULL geometry or output
+    assert lib.pm_self_block_noalloc(None, 0, buf) == 1
+    assert lib.pm_self_block_noalloc(None, 0, None) == 1
+    assert b"pm_self_block_noalloc" in lib.pm_last_error()
+    # peak measurement: unknown pipe, non-positive or excessive duration, NULL output
+    v = ct.c_double()
+    assert lib.pm_measure_peak(2, 10.0, ct.byref(v)) == 1
+    assert lib.pm_measure_peak(0, 0.0, ct.byref(v)) == 1
+    assert lib.pm_measure_peak(0, 1e6, ct.byref(v)) == 1
+    assert lib.pm_measure_peak(1, 10.0, None) == 1
 
 
 def _bad(field, value):

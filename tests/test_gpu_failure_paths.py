@@ -1,0 +1,135 @@
+"""Failure paths through the C ABI, driven by host-side fault injection.
+
+Every fault here is made on the host: a block overwritten with zeros before
+its LU (a plain memset), a changed host decision (the predicted ranks), a
+tensor-core wait on a barrier that nothing arrives at (bounded, before any
+work is issued), a non-finite right-hand side, a host pointer where device
+memory belongs.  None of them faults the GPU: after each the context stays
+usable, which the last step of every test checks by solving again.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense
+from paper_2603_09381_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_09381_gb300 import pmchwt
+    return pmchwt
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _still_solves(pm, prob):
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10)
+    return _rel(f.solve(g.plane_wave([0.5])), dense.solve(prob, [0.5])) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_singular_self_block_is_reported(pm, precision):
+    """A zero diagonal block: its LU meets an exactly zero pivot (paper Sec. 3
+    needs A_ii^{-1}) -> PM_ERR_SINGULAR, and no factor handle."""
+    prob = wl.circle_grid(2, 2, n=32)
+    g = pm.Geometry(prob)
+    prec = pm.PM_MIXED if precision == "mixed" else pm.PM_FP64
+    with pytest.raises(pm.PmError) as e:
+        pm.Factor(g, 1e-10, precision=prec, debug_flags=pm.PM_DEBUG_SINGULAR_BLOCK)
+    assert e.value.status == 4 and "diagonal block" in str(e.value)
+    assert _still_solves(pm, prob)
+
+
+def test_singular_compressed_block_is_reported(pm):
+    """R A^{-1} L exactly singular (the case Sec. 3 shows for the simplified
+    Burton-Miller system): A~ = (R A^{-1} L)^{-1} does not exist ->
+    PM_ERR_SINGULAR naming the compressed block."""
+    prob = wl.star_grid(2, 2, n=64, seed=1)
+    g = pm.Geometry(prob)
+    with pytest.raises(pm.PmError) as e:
+        pm.Factor(g, 1e-10, debug_flags=pm.PM_DEBUG_SINGULAR_COMPRESSED)
+    assert e.value.status == 4 and "R A^-1 L" in str(e.value)
+    assert _still_solves(pm, prob)
+
+
+def test_tensor_core_wait_that_runs_out_returns_timeout(pm):
+    """The tensor-core QR update waits, with a short bound, on a barrier that
+    nothing arrives at: the kernel frees its tensor memory, flags the error
+    and returns; the host reports PM_ERR_TIMEOUT and the context is usable."""
+    prob = wl.star_grid(2, 2, n=64, seed=1)
+    g = pm.Geometry(prob)
+    with pytest.raises(pm.PmError) as e:
+        pm.Factor(g, 1e-10, precision=pm.PM_MIXED, tensor_cores=True, debug_flags=pm.PM_DEBUG_TC_NO_ARRIVE)
+    assert e.value.status == 6
+    # the same factorization without the injected wait completes
+    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, tensor_cores=True)
+    F = g.plane_wave([0.5])
+    assert _rel(f.solve(F), dense.solve(prob, [0.5])) < 1e-8
+
+
+def test_forced_underprediction_falls_back_to_the_adaptive_rank(pm):
+    """Every predicted rank forced to 1: each ID exceeds its prediction and
+    falls back to the adaptive CPQR, which stays the judge of the rank, so the
+    factorization and the solution are those of the run without a predictor."""
+    from paper_2603_09381_gb300 import rank_predictor as rp
+    mdl = rp.load_model()
+    if mdl is None:
+        pytest.skip("no trained rank model in the package")
+    dm = rp.to_device(mdl)
+    prob = wl.star_grid(4, 4, n=64, seed=3)
+    g = pm.Geometry(prob)
+    f0 = pm.Factor(g, 1e-10)
+    f1 = pm.Factor(g, 1e-10, rank_model=dm.data_ptr(), debug_flags=pm.PM_DEBUG_UNDERPREDICT)
+    s0, s1 = f0.stats(), f1.stats()
+    assert s1["predictor_fallbacks"] > 0
+    assert s0["skeleton"] == s1["skeleton"] and s0["K"] == s1["K"]
+    F = g.plane_wave([0.4, 2.2])
+    assert np.array_equal(f0.solve(F), f1.solve(F))
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_non_finite_right_hand_side_is_rejected(pm, on_device):
+    import torch
+    prob = wl.circle_grid(2, 1, n=32)
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10)
+    F = g.plane_wave([0.3, 1.1])
+    F[5, 1] = complex(math.nan, 0.0)
+    if not on_device:
+        with pytest.raises(pm.PmError) as e:
+            f.solve(F)
+        assert e.value.status == 1 and "finite" in str(e.value)
+    else:
+        d = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+        d[0, 7] = complex(0.0, math.inf)
+        d[1, 5] = 1.0
+        out = torch.zeros_like(d)
+        with pytest.raises(pm.PmError) as e:
+            f.solve_device(d.data_ptr(), 2, out.data_ptr())
+        assert e.value.status == 1
+        torch.cuda.synchronize()
+        assert not bool(torch.any(out != 0))
+    F[5, 1] = 0.0
+    assert np.all(np.isfinite(f.solve(F)))
+
+
+def test_host_pointer_for_a_device_solve_is_rejected(pm):
+    prob = wl.circle_grid(2, 1, n=32)
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10)
+    host = np.ascontiguousarray(g.plane_wave([0.3]).T)
+    out = np.zeros_like(host)
+    with pytest.raises(pm.PmError) as e:
+        f.solve_device(host.ctypes.data, 1, out.ctypes.data)
+    assert e.value.status == 1 and "device memory" in str(e.value)
+    assert not np.any(out != 0)
+    assert _still_solves(pm, prob)

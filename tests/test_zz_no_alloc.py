@@ -42,7 +42,33 @@ def test_noalloc_rejects_blocks_above_the_scratch_limit():
     from paper_2603_09381_gb300 import pmchwt as pm
     prob = wl.circle_grid(1, 1, n=258)
     g = pm.Geometry(prob)
-    buf = torch.zeros(4, dtype=torch.complex128, device="cuda")
+    # a buffer of the full block size, so that a regression of the size check
+    # would still write inside it
+    buf = torch.zeros((2 * 258, 2 * 258), dtype=torch.complex128, device="cuda")
     with pytest.raises(pm.PmError) as e:
         g.self_block_noalloc(0, buf.data_ptr())
     assert e.value.status == 1 and "256" in str(e.value)
+    torch.cuda.synchronize()
+    assert not bool(torch.any(buf != 0))
+
+
+def test_noalloc_rejects_host_memory_and_bad_indices():
+    """A host buffer (the allocating sibling takes one, so the two are easy to
+    mix up) is refused before any launch, as is an inclusion index out of range."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_09381_gb300 import pmchwt as pm
+    prob = wl.circle_grid(2, 1, n=64)
+    g = pm.Geometry(prob)
+    host = np.zeros((128, 128), dtype=np.complex128)
+    with pytest.raises(pm.PmError) as e:
+        g.self_block_noalloc(0, host.ctypes.data)
+    assert e.value.status == 1 and "device memory" in str(e.value)
+    assert not np.any(host != 0)
+    buf = torch.zeros((128, 128), dtype=torch.complex128, device="cuda")
+    for j in (-1, 2):
+        with pytest.raises(pm.PmError) as e:
+            g.self_block_noalloc(j, buf.data_ptr())
+        assert e.value.status == 1
