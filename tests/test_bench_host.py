@@ -99,9 +99,10 @@ def test_traffic_record_follows_the_captured_kernel_only():
         assert a in text
 
 
-def test_reference_arm_reports_the_workload_config(monkeypatch, capsys):
-    """The reference arm's line carries the same config object as the GPU arm's
-    line for the same workload; its bounded sample is described separately."""
+def test_reference_arm_reports_the_block_it_ran(monkeypatch, capsys):
+    """The reference arm's config names the block the oracle actually timed (a
+    4 x 4 block of the recipe, N = 4,096), says which workload it is a block of,
+    and declares that it is not the GPU arm's config."""
     import sys
     sys.path.insert(0, ROOT)
     import bench
@@ -115,7 +116,10 @@ def test_reference_arm_reports_the_workload_config(monkeypatch, capsys):
     assert bench.run_reference(Args()) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference"
-    assert line["config"] == bench._workload_config(16, 65536, 4, "mixed", 1)
+    cfg = dict(line["config"])
+    assert cfg.pop("block_of") == bench._workload_config(16, 65536, 4, "mixed", 1)["workload"]
+    assert cfg == bench._workload_config(4, 4096, 2, "fp64", 1)
+    assert line["same_config_as_gpu_arm"] is False
     assert line["value"] == pytest.approx(4096 / 2.0)
     assert line["cpu_baseline"]["kind"] == "oracle" and "4x4 block" in line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
@@ -137,6 +141,12 @@ def test_roofline_of_the_dominant_kernel():
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(2.75e11 / 0.2 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_NOMINAL_TFLOPS)
+    # with measured FMA peaks the fraction is taken against them
+    rm = bench._roofline(prof, steps, {"fp64_tflops": 1.2, "fp32_tflops": 70.0})
+    assert rm["peak"] == 1.2 and rm["frac"] == pytest.approx(rm["achieved"] / 1.2) and "measured" in rm["peak_source"]
+    r32 = bench._roofline({"qr_update32": {"launches": 3, "ms": 10.0, "work": 3.5e11}}, 1, {"fp64_tflops": None,
+                                                                                          "fp32_tflops": 70.0})
+    assert r32["peak"] == 70.0 and r32["achieved"] == pytest.approx(35.0)
     assert r["traffic"] == json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))[
         "dense_matvec64"]["bytes_per_launch"]
     r = bench._roofline({"cpqr_step32": {"launches": 10, "ms": 50.0, "work": 1e11}}, 1)
