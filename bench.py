@@ -233,7 +233,7 @@ def _peaks():
         return 6800.0, "fallback (recipe)"
 
 
-def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None, ff_confirm=False,
+def _timed(pm, g, prob, opts, angs, F, X, stream, precision, steps, warmup, model_ptr=None, ff_confirm=True,
            profile=False):
     """Warm-up, then `steps` timed factor + solve passes on the stream; returns per-step numbers.
     With profile=True every launch is bracketed by CUDA events (the per-kernel table and the
@@ -288,25 +288,40 @@ def _kernel_table(prof_tot, steps):
     return out
 
 
-def measured_alu_peaks(pm):
+def _sm_max_mhz():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return 2070.0    # recipe table's maximum SM clock
+
+
+def measured_alu_peaks(pm, sm_max_mhz=None):
     """FP64 and FP32 FMA peaks of this GPU, measured now by the library's own FMA
-    loop (pm_measure_peak); None where the measurement failed."""
-    out = {}
-    for key, which in (("fp64_tflops", 0), ("fp32_tflops", 1)):
+    loop (pm_measure_peak), as run and scaled to the maximum SM clock (the clock
+    the solver's kernels run at, per the clock samples: a dense FMA loop draws
+    enough power to run below it).  The scaled figure is the roofline's
+    denominator; None where the measurement failed."""
+    mx = sm_max_mhz or _sm_max_mhz()
+    out = {"sm_max_mhz": mx}
+    for key, which in (("fp64", 0), ("fp32", 1)):
         try:
-            out[key] = max(pm.measure_peak(which, 150.0) for _ in range(3))
+            best = max((pm.measure_peak(which, 300.0) for _ in range(3)), key=lambda r: r[0] / max(r[1], 1.0))
+            tf, mhz = best
+            out[key + "_tflops_as_run"] = tf
+            out[key + "_loop_mhz"] = mhz
+            out[key + "_tflops"] = tf * mx / mhz if mhz > 0 else tf
         except Exception:   # noqa: BLE001 - a failed measurement falls back to the nominal figure
-            out[key] = None
+            out[key + "_tflops"] = None
     return out
 
 
 def _alu_peak(kind, peaks):
     if kind == "fp64":
         v = (peaks or {}).get("fp64_tflops")
-        return (v, "measured in this run (FP64 FMA loop, pm_measure_peak)") if v else \
+        return (v, "measured in this run (FP64 FMA loop, pm_measure_peak, scaled to the max SM clock)") if v else \
             (FP64_NOMINAL_TFLOPS, "nominal GB300 dense FP64 (recipe)")
     v = (peaks or {}).get("fp32_tflops")
-    return (v, "measured in this run (FP32 FMA loop, pm_measure_peak)") if v else \
+    return (v, "measured in this run (FP32 FMA loop, pm_measure_peak, scaled to the max SM clock)") if v else \
         (FP32_DERIVED_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz")
 
 
@@ -417,23 +432,23 @@ def run_ours(args):
         if mdl is not None:
             model_dev = rp.to_device(mdl)
             model_ptr = model_dev.data_ptr()
-    peaks = measured_alu_peaks(pm)
     if ws > 1:
         torch.distributed.barrier()
     # headline: no per-launch events inside the timed region
     with Clocks(local) as clk:
         ms, solve, _, st, info, launches = _timed(pm, g, prob, opts, angs, F, X, stream, precision,
-                                                 args.steps, args.warmup, model_ptr, args.ff_confirm)
+                                                 args.steps, args.warmup, model_ptr, not args.fp64_confirm)
     if ws > 1:
         ms = _max_over_ranks(ms, "cuda")
         torch.distributed.barrier()
     value = _job_rate(N, ws, ms)
     X_dev = X.cpu().numpy()
+    peaks = measured_alu_peaks(pm, clk.summary().get("sm_max_mhz"))   # after the timed region, GPU warm
     # per-kernel CUDA-event profile of the same step, in separate passes right after
     nprof = max(1, min(args.steps, 3))
     Xp = torch.zeros_like(F)
     ms_prof, _, prof_tot, _, _, _ = _timed(pm, g, prob, opts, angs, F, Xp, stream, precision, nprof, 0,
-                                           model_ptr, args.ff_confirm, profile=True)
+                                           model_ptr, not args.fp64_confirm, profile=True)
     del Xp
 
     # end to end through the public API with host buffers: descriptors and pinned
@@ -447,7 +462,7 @@ def run_ours(args):
     for _ in range(args.steps):
         g2 = pm.Geometry(prob)
         f2 = pm.Factor(g2, opts["tol"], opts["proxy_factor"], opts["proxy_points"], precision=precision,
-                       stream=stream.cuda_stream, rank_model=model_ptr, ff_confirm=args.ff_confirm)
+                       stream=stream.cuda_stream, rank_model=model_ptr, ff_confirm=not args.fp64_confirm)
         inf2 = pm.pm_solve_info()
         pm._check(pm.load().pm_solve_ex(f2.h, rhs_host.data_ptr(), nrhs, out_host.data_ptr(), 0,
                                         pm.ct.byref(inf2)))
@@ -486,7 +501,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "c64+c128" if precision == pm.PM_MIXED else "c128",
             "data": "synthetic",
             "config": _workload_config(WORKLOADS[args.workload], N, st["levels"], args.precision, ws),
-            "refinement_confirm": "float-float, folded" if args.ff_confirm else "fp64",
+            "refinement_confirm": "fp64" if args.fp64_confirm else "float-float folded into FP64 every 16 columns",
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
             "refinement": info,
             "rank_predictor": {"used": model_ptr is not None, "cpqr_launches": st["cpqr_launches"],
@@ -566,8 +581,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-rank-model", action="store_true")
-    # the refinement ends on the folded float-float product instead of the FP64 one
-    ap.add_argument("--ff-confirm", action="store_true")
+    # the refinement ends on the FP64 product instead of the folded float-float one
+    ap.add_argument("--fp64-confirm", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

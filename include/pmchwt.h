@@ -102,16 +102,18 @@ typedef struct pm_factor pm_factor;
  *      moves them to the tensor cores (pm_gemm_c32's kernel), which is
  *      slower today and, over the long row reductions, adds enough rounding
  *      error to raise the ranks at the complex64 threshold.
- *      PM_FLAG_FF_CONFIRM (PM_MIXED with the dense operator): the residual
- *      that ends the refinement comes from a float-float product of the
- *      stored operator whose sums are folded into FP64 every 16 columns
+ *      Confirming residual (PM_MIXED with the dense operator): by default the
+ *      residual that ends the refinement comes from a float-float product of
+ *      the stored operator whose sums are folded into FP64 every 16 columns
  *      (worst-case error ~9e-13 of sum_j |a_ij| |x_j| per row, below that of
- *      a sequential FP64 sum) instead of the FP64 product.
+ *      a sequential FP64 sum); PM_FLAG_FP64_CONFIRM forms it with the FP64
+ *      product instead.  PM_FLAG_FF_CONFIRM names the default and changes
+ *      nothing.
  * refine_tol: PM_MIXED: stop refining once every column's relative residual
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).  Intermediate residuals
  *      may come from FP32 or float-float products of the stored operator;
- *      the residual that ends the refinement is formed in complex128 (or, with
- *      PM_FLAG_FF_CONFIRM, by the folded float-float product).
+ *      the residual that ends the refinement is formed by the folded
+ *      float-float product (or, with PM_FLAG_FP64_CONFIRM, in complex128).
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
  *      refine_tol returns PM_ERR_NOT_CONVERGED.
  * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 5e-6).
@@ -270,7 +272,8 @@ enum {
   PM_FLAG_NO_DENSE_OPERATOR = 2,
   PM_FLAG_NO_QR_FIRST = 4,
   PM_FLAG_TENSOR_CORES = 8,
-  PM_FLAG_FF_CONFIRM = 16
+  PM_FLAG_FF_CONFIRM = 16,
+  PM_FLAG_FP64_CONFIRM = 32
 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 
@@ -343,8 +346,12 @@ pm_status pm_self_block_noalloc(const pm_geometry* g, int32_t j, pm_c64* out);
  * own loop of independent fused multiply-adds (no counterpart in the paper;
  * the denominators of the roofline fractions of the FP64 and FP32 kernels).
  * which = 0: FP64 FMA, 1: FP32 FMA.  Runs about `ms_target` milliseconds on
- * the default stream; *tflops receives 2 flops per FMA over the event time. */
-pm_status pm_measure_peak(int32_t which, double ms_target, double* tflops);
+ * the default stream; *tflops receives 2 flops per FMA over the event time,
+ * *sm_mhz (may be NULL) the SM clock the loop ran at (clock64 cycles of the
+ * longest CTA over that time), so that the rate can be scaled to another
+ * clock.  Errors: PM_ERR_INVALID_ARG (which, ms_target outside (0, 10000],
+ * NULL tflops), PM_ERR_CUDA. */
+pm_status pm_measure_peak(int32_t which, double ms_target, double* tflops, double* sm_mhz);
 
 void pm_factor_free(pm_factor* f);
 void pm_geometry_free(pm_geometry* g);

@@ -1263,10 +1263,11 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     for (int r = 0; r < nrhs; ++r) worst = std::max(worst, std::sqrt(hn[2 * r]) / std::max(std::sqrt(hn[2 * r + 1]), 1e-300));
     return worst;
   };
-  // The residual that can end the refinement: the FP64 product, or with
-  // PM_FLAG_FF_CONFIRM the float-float product folded into FP64 every 16
-  // columns (a smaller worst-case error bound on the FP32 pipes).
-  const bool ff_confirm = F->dense64 && (F->opts.flags & PM_FLAG_FF_CONFIRM);
+  // The residual that can end the refinement: the float-float product folded
+  // into FP64 every 16 columns (a smaller worst-case error bound than a
+  // sequential FP64 sum, on the FP32 pipes), or with PM_FLAG_FP64_CONFIRM the
+  // FP64 product.
+  const bool ff_confirm = F->dense64 && !(F->opts.flags & PM_FLAG_FP64_CONFIRM);
   auto residual = [&](const double2* x) {
     if (ff_confirm) {
       dense_matvec_ffc(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);

@@ -65,6 +65,7 @@ PM_FLAG_NO_DENSE_OPERATOR = 2
 PM_FLAG_NO_QR_FIRST = 4
 PM_FLAG_TENSOR_CORES = 8
 PM_FLAG_FF_CONFIRM = 16
+PM_FLAG_FP64_CONFIRM = 32
 PM_DEBUG_SINGULAR_BLOCK = 1
 PM_DEBUG_SINGULAR_COMPRESSED = 2
 PM_DEBUG_UNDERPREDICT = 4
@@ -102,7 +103,7 @@ EXPORTS = {
     "pm_gemm_c32": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p,
                                ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_float),
                                ct.POINTER(ct.c_float), ct.c_void_p]),
-    "pm_measure_peak": (ct.c_int, [ct.c_int32, ct.c_double, ct.POINTER(ct.c_double)]),
+    "pm_measure_peak": (ct.c_int, [ct.c_int32, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
     "pm_last_error": (ct.c_char_p, []),
@@ -156,10 +157,11 @@ def gemm_c32(m, n, k, A_ptr, lda, conj_a, B_ptr, ldb, conj_b, C_ptr, ldc, alpha=
 
 
 def measure_peak(which, ms_target=200.0):
-    """Peak TFLOP/s of the current device from the library's FMA loop: which 0 = FP64, 1 = FP32."""
-    v = ct.c_double()
-    _check(load().pm_measure_peak(int(which), float(ms_target), ct.byref(v)))
-    return v.value
+    """(TFLOP/s, SM MHz during the loop) of the library's FMA loop on the current
+    device: which 0 = FP64, 1 = FP32."""
+    v, mhz = ct.c_double(), ct.c_double()
+    _check(load().pm_measure_peak(int(which), float(ms_target), ct.byref(v), ct.byref(mhz)))
+    return v.value, mhz.value
 
 
 def launch_counter():
@@ -219,8 +221,10 @@ class Geometry:
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
-                 qr_first=True, tensor_cores=False, ff_confirm=False, debug_flags=0):
+                 qr_first=True, tensor_cores=False, ff_confirm=True, debug_flags=0):
         """rank_model: device pointer (int) of a trained predictor, or None;
+        ff_confirm: the refinement ends on the folded float-float product (default) or,
+        with False, on the FP64 product (PM_FLAG_FP64_CONFIRM);
         debug_flags: PM_DEBUG_* fault injection for failure-path tests (0 in normal use)."""
         lib = load()
         self.geom = geom
@@ -229,7 +233,7 @@ class Factor:
                            ct.c_void_p(stream) if stream else None,
                            (PM_FLAG_PROFILE if profile else 0) | (0 if dense_operator else PM_FLAG_NO_DENSE_OPERATOR)
                            | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0)
-                           | (PM_FLAG_FF_CONFIRM if ff_confirm else 0),
+                           | (0 if ff_confirm else PM_FLAG_FP64_CONFIRM),
                            float(refine_tol), int(max_refine), float(low_tol),
                            ct.c_void_p(rank_model) if rank_model else None, int(debug_flags))
         h = ct.c_void_p()

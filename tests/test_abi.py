@@ -83,10 +83,10 @@ def test_more_invalid_arguments_rejected_before_device_use():
     assert b"pm_self_block_noalloc" in lib.pm_last_error()
     # peak measurement: unknown pipe, non-positive or excessive duration, NULL output
     v = ct.c_double()
-    assert lib.pm_measure_peak(2, 10.0, ct.byref(v)) == 1
-    assert lib.pm_measure_peak(0, 0.0, ct.byref(v)) == 1
-    assert lib.pm_measure_peak(0, 1e6, ct.byref(v)) == 1
-    assert lib.pm_measure_peak(1, 10.0, None) == 1
+    assert lib.pm_measure_peak(2, 10.0, ct.byref(v), None) == 1
+    assert lib.pm_measure_peak(0, 0.0, ct.byref(v), None) == 1
+    assert lib.pm_measure_peak(0, 1e6, ct.byref(v), None) == 1
+    assert lib.pm_measure_peak(1, 10.0, None, None) == 1
 
 
 def _bad(field, value):
@@ -166,9 +166,9 @@ def test_factor_options_marshalling(monkeypatch):
 
     cases = [({}, 0), ({"profile": True}, pm.PM_FLAG_PROFILE), ({"dense_operator": False}, pm.PM_FLAG_NO_DENSE_OPERATOR),
              ({"qr_first": False}, pm.PM_FLAG_NO_QR_FIRST), ({"tensor_cores": True}, pm.PM_FLAG_TENSOR_CORES),
-             ({"ff_confirm": True}, pm.PM_FLAG_FF_CONFIRM),
-             ({"ff_confirm": True, "qr_first": False, "profile": True},
-              pm.PM_FLAG_FF_CONFIRM | pm.PM_FLAG_NO_QR_FIRST | pm.PM_FLAG_PROFILE)]
+             ({"ff_confirm": False}, pm.PM_FLAG_FP64_CONFIRM),
+             ({"ff_confirm": False, "qr_first": False, "profile": True},
+              pm.PM_FLAG_FP64_CONFIRM | pm.PM_FLAG_NO_QR_FIRST | pm.PM_FLAG_PROFILE)]
     for kw, flags in cases:
         seen.clear()
         f = pm.Factor(G(), 1e-9, 1.7, 48, precision=pm.PM_MIXED, refine_tol=1e-11, max_refine=7, low_tol=4e-6, **kw)

@@ -1,5 +1,5 @@
-"""GPU parity of the refinement ended by the folded float-float product
-(PM_FLAG_FF_CONFIRM) instead of the FP64 product."""
+"""GPU parity of the refinement ended by the folded float-float product (the
+default) and by the FP64 product (PM_FLAG_FP64_CONFIRM)."""
 import numpy as np
 import pytest
 
@@ -17,12 +17,13 @@ def pm():
     return pmchwt
 
 
-def test_float_float_confirmation_matches_the_oracle(pm):
+@pytest.mark.parametrize("ff_confirm", [True, False])
+def test_confirming_residual_matches_the_oracle(pm, ff_confirm):
     prob = wl.star_grid(4, 4, n=64, seed=1)
     angs = [0.3, 1.9, 4.4]
     g = pm.Geometry(prob)
     F = g.plane_wave(angs)
-    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, ff_confirm=True)
+    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, ff_confirm=ff_confirm)
     phi = f.solve(F)
     info = f.last_info
     assert 1 <= info["iterations"] <= 6 and info["residual"] <= 1e-10
