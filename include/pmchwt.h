@@ -108,7 +108,14 @@ typedef struct pm_factor pm_factor;
  *      (worst-case error ~9e-13 of sum_j |a_ij| |x_j| per row, below that of
  *      a sequential FP64 sum); PM_FLAG_FP64_CONFIRM forms it with the FP64
  *      product instead.  PM_FLAG_FF_CONFIRM names the default and changes
- *      nothing.
+ *      nothing.  PM_FLAG_NO_AUTOTUNE: the call tunes no batched-GEMM tile
+ *      shape (classes tuned before keep their choice; see pm_autotune_table).
+ *      Solve graphs: the compressed inverse (PM_FP64) and the mixed
+ *      preconditioner are launch sequences fixed by the factorization; the
+ *      second time a factor applies one for a given right-hand-side count it
+ *      captures the launches into a CUDA graph (kept with the factor) and
+ *      replays it from then on; PM_FLAG_NO_GRAPHS (or PM_FLAG_PROFILE) keeps
+ *      every application eager.  Solves of one factor are serialised.
  * refine_tol: PM_MIXED: stop refining once every column's relative residual
  *      ||b - A x|| / ||b|| <= refine_tol (0 -> 1e-10).  Intermediate residuals
  *      may come from FP32 or float-float products of the stored operator;
@@ -177,6 +184,8 @@ typedef struct {
   int32_t rank_checks;      /* device-to-host rank checks (host synchronisations) */
   int32_t predictor_fallbacks;  /* IDs whose rank exceeded the predicted bound */
   double ms_level[16];      /* wall time of each compressed level (index = level) */
+  int32_t graph_captures;   /* solve graphs captured so far (one per kind and right-hand-side count) */
+  int32_t graph_launches;   /* solve graph replays so far */
 } pm_stats;
 
 /* Build node geometry on the device (paper Sec. 2.2) and the quadtree
@@ -222,13 +231,21 @@ pm_status pm_solve_ex(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c6
                       pm_solve_info* info);
 
 /* Many independent problems (no counterpart in the paper; the paper factors
- * one system at a time).  pm_factor_batch factors g[0..count) with `workers`
- * host threads (0 -> 8), each driving its own CUDA stream, so the problems'
- * kernels overlap on the GPU; out[i] receives each handle (all NULL on
- * error, which names the failing problem).  opts->stream is ignored; the
- * returned handles run later pm_solve calls on the default stream.
+ * one system at a time).  pm_factor_batch splits g[0..count) into `workers`
+ * groups (0 -> 4; each problem, in descending order of N^1.5, joins the group
+ * with the least work so far).  The problems of a group are factored
+ * together in shared launches: one gather, one batched QR / CPQR step, one
+ * batched LU and GEMM per phase for all of their boxes, step s taking level
+ * L_i - s of every problem i (leaves first, whatever the depths), then all
+ * top-level systems in one batched LU; each group runs on its own host
+ * thread and CUDA stream, so groups overlap.  workers = count gives one
+ * problem per group (no shared launches).  Every problem's result equals
+ * its pm_factorize.  out[i] receives each handle (all NULL on error).
+ * opts->stream is ignored and PM_FLAG_PROFILE cleared; the returned handles
+ * run later pm_solve calls on the default stream.
  * pm_solve_batch solves each factor for its own right-hand sides rhs[i] ->
- * phi[i] (N_i x nrhs each), concurrently in the same way. */
+ * phi[i] (N_i x nrhs each) with `workers` host threads (0 -> 8), one CUDA
+ * stream each. */
 pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_factor_opts* opts, pm_factor** out,
                           int32_t workers);
 pm_status pm_solve_batch(const pm_factor* const* f, int32_t count, const pm_c64* const* rhs, int32_t nrhs,
@@ -273,7 +290,9 @@ enum {
   PM_FLAG_NO_QR_FIRST = 4,
   PM_FLAG_TENSOR_CORES = 8,
   PM_FLAG_FF_CONFIRM = 16,
-  PM_FLAG_FP64_CONFIRM = 32
+  PM_FLAG_FP64_CONFIRM = 32,
+  PM_FLAG_NO_AUTOTUNE = 64,
+  PM_FLAG_NO_GRAPHS = 128
 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 
@@ -301,6 +320,24 @@ pm_status pm_mlp_adam_step(int32_t dtype, void* theta, const void* grad, void* m
  * one mean loss per epoch, or NULL. */
 pm_status pm_mlp_train(void* theta, int32_t nsamples, const float* X, const float* T, int32_t epochs, int32_t batch,
                        double lr, double lam, uint64_t seed, double* loss_history, void* stream);
+
+/* The batched-GEMM autotuner's choices (no counterpart in the paper).  The
+ * complex GEMMs of the factorization and the solve run one kernel over a list
+ * of products; its output tile is chosen per class of batch (device, complex
+ * size in bytes, ceil log2 of the largest m, of the largest n, of the mean k,
+ * of the number of products) among 32x32, 64x64, 64x32, 128x8 and 64x16.
+ * The first batch of a class whose outputs are write-only times every shape
+ * once (CUDA events, after a warm-up launch) and keeps the fastest; the
+ * choice is cached per process.  All shapes accumulate over k in the same
+ * order, so the choice changes no result.  Writes up to cap entries (ms: the
+ * measured time of each shape in the order above), *count = entries known. */
+typedef struct {
+  int32_t device, complex_bytes, log2_m, log2_n, log2_k, log2_count;
+  int32_t tm, tn;      /* chosen output tile */
+  float ms[8];
+  int64_t uses;        /* batches of the class run so far */
+} pm_tune_entry;
+pm_status pm_autotune_table(pm_tune_entry* out, int32_t cap, int32_t* count);
 
 /* Number of CUDA kernel launches this library has made in this process
  * (no counterpart in the paper; measurement aid). */

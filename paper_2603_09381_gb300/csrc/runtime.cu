@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 #include <type_traits>
@@ -80,10 +81,22 @@ struct Arena {
   ~Arena() { release(); }
 };
 
+// While a solve plan is being captured into a CUDA graph, descriptor uploads
+// must not become graph nodes (they read pageable host memory that is gone
+// when the graph replays): they go, synchronously, through this side stream
+// into plan-owned device memory that the graph's kernels then read.
+thread_local cudaStream_t g_capture_side = nullptr;
+
 template <class T>
 T* upload(Arena& a, const std::vector<T>& v, cudaStream_t st) {
   T* d = a.get<T>(std::max<size_t>(v.size(), 1));
-  if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  if (v.empty()) return d;
+  if (g_capture_side) {
+    CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, g_capture_side));
+    CK(cudaStreamSynchronize(g_capture_side));
+  } else {
+    CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
   return d;
 }
 
@@ -191,7 +204,30 @@ struct pm_factor {
   int* d_iq = nullptr;
   float4* dense64 = nullptr;    // the whole FP64 operator, N x N, split hi/lo, when it fits the memory budget
   size_t dense_bytes = 0;
+  // CUDA graphs of the compressed inverse (FP64) or the mixed preconditioner,
+  // one per right-hand-side count; solves of one factor are serialised by plan_mu
+  std::mutex plan_mu;
+  std::map<std::pair<int, int>, std::unique_ptr<struct SolvePlan>> plans;   // (kind, nrhs)
+  int graph_launches = 0, graph_captures = 0;
   ~pm_factor();
+};
+
+// A captured solve: plan-owned input / output / scale buffers, the arena of
+// the captured launches (descriptors and workspace, never reused by anything
+// else), and the instantiated graph.
+struct SolvePlan {
+  int uses = 0;
+  Arena io, ws;
+  double2* in = nullptr;
+  double2* out = nullptr;
+  double* scal = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~SolvePlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    if (side) cudaStreamDestroy(side);
+  }
 };
 
 namespace {
@@ -376,13 +412,16 @@ struct GatherBatch {
   std::vector<int> tile_off{0};
   std::vector<int> codes;                 // all target / source lists
   std::vector<std::pair<size_t, size_t>> lists;  // (tgt offset, src offset) per prob
-  void add(C* out, int ld, int M, int N, const std::vector<int>& tgt, const std::vector<int>& src, int trans) {
+  // code_off: added to every packed code (the problem's first point in a joint
+  // point table, times 2); k: the problem's exterior wavenumber (0: run()'s k0)
+  void add(C* out, int ld, int M, int N, const std::vector<int>& tgt, const std::vector<int>& src, int trans,
+           int code_off = 0, double k = 0.0) {
     if (M <= 0 || N <= 0) return;
     size_t to = codes.size();
-    codes.insert(codes.end(), tgt.begin(), tgt.end());
+    for (int c : tgt) codes.push_back(c + code_off);
     size_t so = codes.size();
-    codes.insert(codes.end(), src.begin(), src.end());
-    probs.push_back(GatherProb<C>{out, ld, M, N, nullptr, nullptr, trans});
+    for (int c : src) codes.push_back(c + code_off);
+    probs.push_back(GatherProb<C>{out, ld, M, N, nullptr, nullptr, trans, k});
     lists.push_back({to, so});
     tile_off.push_back(tile_off.back() + gather_tiles(M, N));
   }
@@ -405,6 +444,38 @@ struct GatherBatch {
   }
 };
 
+// Autotuner of the batched GEMM's output tile (no counterpart in the paper).
+// Batches are classed by (device, precision, ceil log2 of the largest m, of
+// the largest n, of the mean k, of the problem count).  The first
+// write-only batch of a class (every C overwritten, no C aliasing an
+// operand, so running it again gives the same result) times every tile shape
+// once after a warm-up launch with CUDA events and keeps the fastest; later
+// batches of the class use it.  All shapes sum over k in the same order, so
+// the choice changes speed only, never a result.  A class not tuned yet runs
+// the 32 x 32 shape.
+struct TuneKey {
+  int dev, bytes, lm, ln, lk, lc;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, bytes, lm, ln, lk, lc) < std::tie(o.dev, o.bytes, o.lm, o.ln, o.lk, o.lc);
+  }
+};
+struct TuneEntry {
+  int shape = 0;
+  float ms[GEMM_NSHAPES] = {};
+  long long uses = 0;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+thread_local bool g_tune_off = false;    // PM_FLAG_NO_AUTOTUNE of the running call
+
+int ceil_log2(double x) { return x <= 1 ? 0 : (int)std::ceil(std::log2(x)); }
+
+struct TuneScope {   // the running call's PM_FLAG_NO_AUTOTUNE, restored on exit
+  bool prev;
+  explicit TuneScope(bool off) : prev(g_tune_off) { g_tune_off = off; }
+  ~TuneScope() { g_tune_off = prev; }
+};
+
 template <class C>
 struct GemmBatch {
   std::vector<GemmDesc<C>> d;
@@ -418,11 +489,56 @@ struct GemmBatch {
     d.push_back(GemmDesc<C>{m, n, k, A, lda, B, ldb, Cp, ldc, alpha, beta, beta_zero});
     off.push_back(off.back() + gemm_tiles(m, n));
   }
+  std::vector<int> offsets(int shape) const {
+    std::vector<int> o{0};
+    for (auto& x : d) o.push_back(o.back() + gemm_tiles_shape(shape, x.m, x.n));
+    return o;
+  }
   void run(Arena& scr, cudaStream_t st) {
     if (d.empty()) return;
     auto* dd = upload(scr, d, st);
-    int* dof = upload(scr, off, st);
-    la_gemm_batched<C>(dd, dof, (int)d.size(), off.back(), st);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int mm = 0, mn = 0;
+    double ks = 0;
+    bool write_only = true;
+    for (auto& x : d) {
+      mm = std::max(mm, x.m); mn = std::max(mn, x.n); ks += x.k;
+      write_only = write_only && x.beta_zero && (const void*)x.Cm != (const void*)x.A && (const void*)x.Cm != (const void*)x.B;
+    }
+    const TuneKey key{dev, (int)sizeof(C), ceil_log2(mm), ceil_log2(mn), ceil_log2(ks / d.size()), ceil_log2((double)d.size())};
+    int shape = 0;
+    bool tune = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) { shape = it->second.shape; it->second.uses++; }
+      else tune = write_only && !g_tune_off && !g_kprof && !g_capture_side;
+    }
+    if (tune) {
+      TuneEntry e;
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a)); CK(cudaEventCreate(&b));
+      for (int sh = 0; sh < GEMM_NSHAPES; ++sh) {
+        const std::vector<int> o = offsets(sh);
+        int* dof = upload(scr, o, st);
+        la_gemm_batched_shape<C>(sh, dd, dof, (int)d.size(), o.back(), st);   // warm-up
+        CK(cudaEventRecord(a, st));
+        la_gemm_batched_shape<C>(sh, dd, dof, (int)d.size(), o.back(), st);
+        CK(cudaEventRecord(b, st));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(&e.ms[sh], a, b));
+        if (e.ms[sh] < e.ms[e.shape]) e.shape = sh;
+      }
+      cudaEventDestroy(a); cudaEventDestroy(b);
+      e.uses = 1;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune.emplace(key, e);   // the result is in C: every shape wrote the same values
+    } else {
+      const std::vector<int> o = shape == 0 ? off : offsets(shape);
+      int* dof = upload(scr, o, st);
+      la_gemm_batched_shape<C>(shape, dd, dof, (int)d.size(), o.back(), st);
+    }
     if (g_kprof) {
       double f = 0;
       for (auto& x : d) f += 8.0 * x.m * x.n * x.k;
@@ -501,7 +617,7 @@ struct Timer {
 // Cc: the children's arithmetic, Cp: the parent's.
 template <class Cc, class Cp>
 void merge_children(pm_factor* F, const std::vector<BoxF<Cc>>& kids, const Box& box, BoxF<Cp>& bf,
-                    GatherBatch<Cp>& gb, CopyBatch<Cc, Cp>& cb) {
+                    GatherBatch<Cp>& gb, CopyBatch<Cc, Cp>& cb, int code_off = 0) {
   bf.rows.clear(); bf.rgrp.clear(); bf.cols.clear(); bf.cgrp.clear(); bf.child_off.clear();
   for (int c : box.children) {
     bf.child_off.push_back((int)bf.rows.size());
@@ -526,7 +642,7 @@ void merge_children(pm_factor* F, const std::vector<BoxF<Cc>>& kids, const Box& 
       } else {
         std::vector<int> scodes(kb.scols.size());
         for (size_t i = 0; i < kb.scols.size(); ++i) scodes[i] = g->code_of(kb.scols[i]);
-        gb.add(dst, bf.mb, ka.kb, kb.kb, tcodes, scodes, 0);
+        gb.add(dst, bf.mb, ka.kb, kb.kb, tcodes, scodes, 0, code_off, g->k0);
       }
     }
   }
@@ -553,61 +669,142 @@ PointsDev make_points(const pm_geometry* g, const std::vector<Box>& boxes, Arena
   return P;
 }
 
-template <class C>
-void process_level(pm_factor* F, int lev, double tol) {
-  const pm_geometry* g = F->g;
-  cudaStream_t st = F->st;
-  Arena& scr = F->scratch;
-  scr.reset();
-  const auto& boxes = F->tree[lev];
-  auto& LV = levels_of<C>(F);
-  auto& BF = LV[lev];
-  const int nb = (int)boxes.size();
-  BF.assign(nb, BoxF<C>());
-  Timer t_asm(st);
-  // 1. active sets and diagonal blocks
-  if (lev == F->L) {
-    std::vector<int> incl(nb), lda(nb);
-    std::vector<C*> A(nb);
-    for (int b = 0; b < nb; ++b) {
-      int j = boxes[b].leaves[0];
-      int n = g->inc[j].n_nodes;
-      BoxF<C>& bf = BF[b];
-      bf.mb = 2 * n;
-      for (int i = 0; i < 2 * n; ++i) {
-        bf.rows.push_back(g->row_off[j] + i);
-        bf.rgrp.push_back(i >= n);
+// One level of one problem's factorization; several jobs (independent
+// problems, possibly at different depths of their trees) are processed in
+// shared launches.
+struct LevelJob {
+  pm_factor* F;
+  int lev;
+};
+
+// Points of several problems in one table: problem j's nodes, then the proxy
+// points of its boxes at its job's level (none with `proxies` false), from
+// point base[j] on; poff[j][b] = box b's first proxy relative to the problem's
+// proxy block.
+PointsDev make_points_joint(const std::vector<LevelJob>& jobs, bool proxies, Arena& scr, cudaStream_t st,
+                            std::vector<int>& base, std::vector<std::vector<int>>& poff) {
+  const int nj = (int)jobs.size();
+  base.assign(nj, 0);
+  poff.assign(nj, {});
+  std::vector<std::vector<ProxyBoxDev>> pb(nj);
+  std::vector<int> nprox(nj, 0);
+  size_t np = 0;
+  for (int j = 0; j < nj; ++j) {
+    const pm_geometry* g = jobs[j].F->g;
+    base[j] = (int)np;
+    if (proxies) {
+      const auto& boxes = jobs[j].F->tree[jobs[j].lev];
+      poff[j].assign(boxes.size(), 0);
+      for (size_t b = 0; b < boxes.size(); ++b) {
+        poff[j][b] = nprox[j];
+        pb[j].push_back(ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, nprox[j]});
+        nprox[j] += boxes[b].p;
       }
-      bf.cols = bf.rows; bf.cgrp = bf.rgrp;
-      bf.D = F->arena.get<C>((size_t)bf.mb * bf.mb);
-      incl[b] = j; A[b] = bf.D; lda[b] = bf.mb;
     }
-    assemble_self<C>(g, incl, A, lda, scr, st);
-  } else {
-    GatherBatch<C> gb; CopyBatch<C, C> cb;
-    for (int b = 0; b < nb; ++b) merge_children<C, C>(F, LV[lev + 1], boxes[b], BF[b], gb, cb);
-    std::vector<int> dummy;
-    PointsDev P0 = make_points(g, {}, scr, st, dummy);
-    gb.run(scr, P0, g->k0, st);
-    cb.run(scr, st);
+    np += (size_t)g->total_nodes + nprox[j];
   }
-  // 2. proxy points and ID inputs: per box 4 IDs (row u-eq, row q-eq, col q, col u)
-  std::vector<int> poff;
-  PointsDev P = make_points(g, boxes, scr, st, poff);
+  if (np > (size_t)(1 << 30)) fail(PM_ERR_UNSUPPORTED, "more than 2^30 points in one launch");
+  PointsDev P;
+  P.x = scr.get<double>(np); P.y = scr.get<double>(np); P.nx = scr.get<double>(np);
+  P.ny = scr.get<double>(np); P.w = scr.get<double>(np);
+  for (int j = 0; j < nj; ++j) {
+    const pm_geometry* g = jobs[j].F->g;
+    const size_t o = base[j];
+    PointsDev Pj{P.x + o, P.y + o, P.nx + o, P.ny + o, P.w + o};
+    geom_points_from_nodes(g->nodes, Pj, g->total_nodes, st);
+    if (nprox[j] > 0) {
+      auto* dpb = upload(scr, pb[j], st);
+      geom_proxy_points(dpb, (int)pb[j].size(), Pj, nprox[j], g->total_nodes, st);
+    }
+  }
+  CK(cudaGetLastError());
+  return P;
+}
+
+template <class C>
+void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t st, double tol) {
+  scr.reset();
+  const int nj = (int)jobs.size();
+  const pm_factor_opts& O = jobs[0].F->opts;   // the jobs of one call share their options
+  // boxes of all jobs, flattened: global box gb = jb_off[j] + b
+  std::vector<int> jb_off(nj + 1, 0);
+  for (int j = 0; j < nj; ++j) {
+    const int nbj = (int)jobs[j].F->tree[jobs[j].lev].size();
+    levels_of<C>(jobs[j].F)[jobs[j].lev].assign(nbj, BoxF<C>());
+    jb_off[j + 1] = jb_off[j] + nbj;
+  }
+  const int nb = jb_off[nj];
+  std::vector<int> job_of(nb);
+  for (int j = 0; j < nj; ++j)
+    for (int b = jb_off[j]; b < jb_off[j + 1]; ++b) job_of[b] = j;
+  auto BFx = [&](int x) -> BoxF<C>& {
+    const LevelJob& J = jobs[job_of[x]];
+    return levels_of<C>(J.F)[J.lev][x - jb_off[job_of[x]]];
+  };
+  auto BOX = [&](int x) -> const Box& {
+    const LevelJob& J = jobs[job_of[x]];
+    return J.F->tree[J.lev][x - jb_off[job_of[x]]];
+  };
+  auto GEO = [&](int x) -> const pm_geometry* { return jobs[job_of[x]].F->g; };
+  Timer t_asm(st);
+  // one point table for the level: every job's nodes and its boxes' proxy points
+  std::vector<int> pt_base;
+  std::vector<std::vector<int>> poff;
+  PointsDev P = make_points_joint(jobs, true, scr, st, pt_base, poff);
+  // 1. active sets and diagonal blocks
+  {
+    GatherBatch<C> gm; CopyBatch<C, C> cm;
+    for (int j = 0; j < nj; ++j) {
+      pm_factor* F = jobs[j].F;
+      const int lev = jobs[j].lev;
+      const pm_geometry* g = F->g;
+      auto& LV = levels_of<C>(F);
+      auto& BF = LV[lev];
+      const auto& boxes = F->tree[lev];
+      const int nbj = (int)boxes.size();
+      if (lev == F->L) {
+        std::vector<int> incl(nbj), lda(nbj);
+        std::vector<C*> A(nbj);
+        for (int b = 0; b < nbj; ++b) {
+          int i0 = boxes[b].leaves[0];
+          int n = g->inc[i0].n_nodes;
+          BoxF<C>& bf = BF[b];
+          bf.mb = 2 * n;
+          for (int i = 0; i < 2 * n; ++i) {
+            bf.rows.push_back(g->row_off[i0] + i);
+            bf.rgrp.push_back(i >= n);
+          }
+          bf.cols = bf.rows; bf.cgrp = bf.rgrp;
+          bf.D = F->arena.get<C>((size_t)bf.mb * bf.mb);
+          incl[b] = i0; A[b] = bf.D; lda[b] = bf.mb;
+        }
+        assemble_self<C>(g, incl, A, lda, scr, st);
+      } else {
+        for (int b = 0; b < nbj; ++b) merge_children<C, C>(F, LV[lev + 1], boxes[b], BF[b], gm, cm, 2 * pt_base[j]);
+      }
+    }
+    gm.run(scr, P, 0.0, st);
+    cm.run(scr, st);
+  }
+  // 2. ID inputs: per box 4 IDs (row u-eq, row q-eq, col q, col u)
   const int nid = 4 * nb;
   std::vector<int> W(nid), nn(nid);
   std::vector<C*> Z(nid);
   std::vector<std::vector<int>> pos(nid);
   GatherBatch<C> gb;
   for (int b = 0; b < nb; ++b) {
-    const Box& box = boxes[b];
-    const BoxF<C>& bf = BF[b];
+    const int jj = job_of[b], lb = b - jb_off[jj];
+    const pm_geometry* g = GEO(b);
+    const Box& box = BOX(b);
+    const BoxF<C>& bf = BFx(b);
+    const auto& BFj = levels_of<C>(jobs[jj].F)[jobs[jj].lev];
+    const int co = 2 * pt_base[jj];
     std::vector<int> ncols, nrows;
     for (int o : box.near) {
-      for (int c : BF[o].cols) ncols.push_back(g->code_of(c));
-      for (int r : BF[o].rows) nrows.push_back(g->code_of(r));
+      for (int c : BFj[o].cols) ncols.push_back(g->code_of(c));
+      for (int r : BFj[o].rows) nrows.push_back(g->code_of(r));
     }
-    const int pbase = g->total_nodes + poff[b];
+    const int pbase = g->total_nodes + poff[jj][lb];
     std::vector<int> pcols, prows;
     for (int grp = 0; grp < 2; ++grp)
       for (int s = 0; s < box.p; ++s) { pcols.push_back((pbase + s) * 2 + grp); prows.push_back((pbase + s) * 2 + grp); }
@@ -620,7 +817,7 @@ void process_level(pm_factor* F, int lev, double tol) {
       src.insert(src.end(), pcols.begin(), pcols.end());
       W[id] = (int)src.size(); nn[id] = (int)tgt.size();
       Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
-      gb.add(Z[id], W[id], W[id], nn[id], tgt, src, 1);
+      gb.add(Z[id], W[id], W[id], nn[id], tgt, src, 1, co, g->k0);
       // column ID of group grp: Z[w, c] = A(target w, column c), targets = near rows + proxy
       id = 4 * b + 2 + grp;
       std::vector<int> srcc;
@@ -629,33 +826,36 @@ void process_level(pm_factor* F, int lev, double tol) {
       tg.insert(tg.end(), prows.begin(), prows.end());
       W[id] = (int)tg.size(); nn[id] = (int)srcc.size();
       Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
-      gb.add(Z[id], W[id], W[id], nn[id], tg, srcc, 0);
+      gb.add(Z[id], W[id], W[id], nn[id], tg, srcc, 0, co, g->k0);
     }
   }
-  gb.run(scr, P, g->k0, st);
-  F->stats.ms_assemble += t_asm.stop();
+  gb.run(scr, P, 0.0, st);
+  const double ms_asm = t_asm.stop();
+  for (const auto& J : jobs) J.F->stats.ms_assemble += ms_asm;
   Timer t_id(st);
   // features of every (box, group) for the learned rank predictor
   std::vector<float> feat(2 * (size_t)nb * MLP_IN);
   for (int b = 0; b < nb; ++b) {
+    const pm_geometry* g = GEO(b);
+    const Box& box = BOX(b);
     double kin = 0;
-    for (int j : boxes[b].leaves) kin += g->inc[j].k_in.re;
-    kin /= std::max<size_t>(boxes[b].leaves.size(), 1);
+    for (int j : box.leaves) kin += g->inc[j].k_in.re;
+    kin /= std::max<size_t>(box.leaves.size(), 1);
     for (int grp = 0; grp < 2; ++grp) {
       float* f = &feat[(2 * (size_t)b + grp) * MLP_IN];
       f[0] = (float)std::log((double)std::max(nn[4 * b + grp], 1));
       f[1] = (float)std::log((double)std::max(W[4 * b + grp], 1));
       f[2] = (float)std::log((double)std::max(W[4 * b + 2 + grp], 1));
-      f[3] = (float)(g->k0 * boxes[b].r_cell);
+      f[3] = (float)(g->k0 * box.r_cell);
       f[4] = (float)std::log10(tol);
-      f[5] = (float)std::log2((double)boxes[b].leaves.size());
+      f[5] = (float)std::log2((double)box.leaves.size());
       f[6] = (float)grp;
       f[7] = (float)(kin / g->k0);
     }
   }
   std::vector<int> khat;   // predicted rank bound per ID (empty: no predictor)
-  if (F->opts.rank_model) {
-    const float* mdl = F->opts.rank_model;   // theta | mean (8) | std (8), device
+  if (O.rank_model) {
+    const float* mdl = O.rank_model;   // theta | mean (8) | std (8), device
     std::vector<float> musd(2 * MLP_IN);
     CK(cudaMemcpyAsync(musd.data(), mdl + MLP_NPARAM, sizeof(float) * 2 * MLP_IN, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -679,13 +879,13 @@ void process_level(pm_factor* F, int lev, double tol) {
         const int k = std::min(n, (int)std::ceil(frac * n + 2 + 0.02 * n));
         khat[4 * b + grp] = khat[4 * b + 2 + grp] = k;
       }
-    if (F->opts.debug_flags & PM_DEBUG_UNDERPREDICT) std::fill(khat.begin(), khat.end(), 1);   // injected
+    if (O.debug_flags & PM_DEBUG_UNDERPREDICT) std::fill(khat.begin(), khat.end(), 1);   // injected
   }
   // 3a. complex64: tall inputs reduced to their triangular factor first, so
   // that the pivoted steps stream n instead of W rows
   std::vector<int> We(W);   // rows the pivoted QR runs on (leading dimension stays W)
   if constexpr (std::is_same<C, float2>::value) {
-    if (!(F->opts.flags & PM_FLAG_NO_QR_FIRST)) {
+    if (!(O.flags & PM_FLAG_NO_QR_FIRST)) {
       std::vector<QrProb<C>> qp;
       int maxn = 0;
       double fl = 0;
@@ -703,7 +903,7 @@ void process_level(pm_factor* F, int lev, double tol) {
         const int nq = (int)qp.size();
         C* tws = scr.get<C>((size_t)nq * QR_NB * QR_NB);
         for (int q = 0; q < nq; ++q) qp[q].T = tws + (size_t)q * QR_NB * QR_NB;
-        if (!(F->opts.flags & PM_FLAG_TENSOR_CORES)) {
+        if (!(O.flags & PM_FLAG_TENSOR_CORES)) {
           int maxW = 0;
           for (int q = 0; q < nq; ++q) {
             qp[q].mrb = (qp[q].W + QR_RB - 1) / QR_RB;
@@ -770,7 +970,7 @@ void process_level(pm_factor* F, int lev, double tol) {
             for (int l = 0; l < 3; ++l) {
               const int t0 = toff[l][s0], t1 = toff[l][s0 + c];
               tc_gemm_batched(dg[l] + s0, dt[l] + s0, c, t1 - t0, terr, st, t0,
-                              (F->opts.debug_flags & PM_DEBUG_TC_NO_ARRIVE) != 0);
+                              (O.debug_flags & PM_DEBUG_TC_NO_ARRIVE) != 0);
             }
           }
           qr_zero_lower<C>(dqp, nq, maxn, st);
@@ -835,14 +1035,14 @@ void process_level(pm_factor* F, int lev, double tol) {
   }
   for (int t = 0; t < maxT; ++t) {
     cpqr_step<C>(dcp, dch, nch, t, ctr + t, st, tall);
-    F->stats.cpqr_launches++;
+    for (const auto& J : jobs) J.F->stats.cpqr_launches++;
     const bool check = khat.empty() ? ((t % 16 == 15) || t == maxT - 1)
                                     : (t == first_check || (t > first_check && ((t - first_check) % 16 == 0)) ||
                                        t == maxT - 1);
     if (check) {
       CK(cudaMemcpyAsync(hr.data(), rank, nid * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      F->stats.rank_checks++;
+      for (const auto& J : jobs) J.F->stats.rank_checks++;
       int pending = 0;
       for (int i = 0; i < nid; ++i) if (hr[i] < 0 && t + 1 < cp[i].target) ++pending;
       if (pending == 0) break;
@@ -854,7 +1054,7 @@ void process_level(pm_factor* F, int lev, double tol) {
   std::vector<int> r(nid);
   for (int i = 0; i < nid; ++i) r[i] = hr[i] >= 0 ? hr[i] : cp[i].target;
   if (!khat.empty())
-    for (int i = 0; i < nid; ++i) F->stats.predictor_fallbacks += r[i] > khat[i];   // rank above the predicted bound
+    for (int i = 0; i < nid; ++i) jobs[job_of[i / 4]].F->stats.predictor_fallbacks += r[i] > khat[i];   // above the bound
   // 4. pair ranks k_g = max(row rank, column rank); extend the shorter factorization
   std::vector<int> kk(nid);
   int maxExt = 0;
@@ -863,7 +1063,7 @@ void process_level(pm_factor* F, int lev, double tol) {
       int ir = 4 * b + grp, ic = 4 * b + 2 + grp;
       int k = std::min(std::max(r[ir], r[ic]), std::min(cp[ir].target, cp[ic].target));
       kk[ir] = kk[ic] = k;
-      BF[b].kg[grp] = k;
+      BFx(b).kg[grp] = k;
     }
   for (int i = 0; i < nid; ++i) {
     cp[i].mode = CPQR_EXTEND;
@@ -874,17 +1074,18 @@ void process_level(pm_factor* F, int lev, double tol) {
   if (maxExt > 0) {
     dcp = upload(scr, cp, st);
     for (int t = 0; t < maxExt; ++t) cpqr_step<C>(dcp, dch, nch, t, ctr + maxT + t, st, tall);
-    F->stats.cpqr_launches += maxExt;
+    for (const auto& J : jobs) J.F->stats.cpqr_launches += maxExt;
     CK(cudaGetLastError());
   }
   // training data for the rank predictor: features -> (row rank, column rank) / n
   for (int b = 0; b < nb; ++b)
     for (int grp = 0; grp < 2; ++grp) {
       const float* f = &feat[(2 * (size_t)b + grp) * MLP_IN];
-      F->rank_X.insert(F->rank_X.end(), f, f + MLP_IN);
+      pm_factor* Fb = jobs[job_of[b]].F;
+      Fb->rank_X.insert(Fb->rank_X.end(), f, f + MLP_IN);
       const double n = std::max(nn[4 * b + grp], 1);
-      F->rank_T.push_back((float)(r[4 * b + grp] / n));
-      F->rank_T.push_back((float)(r[4 * b + 2 + grp] / n));
+      Fb->rank_T.push_back((float)(r[4 * b + grp] / n));
+      Fb->rank_T.push_back((float)(r[4 * b + 2 + grp] / n));
     }
   {
     // the unchosen columns follow the pivots, ascending (defines the column order of T)
@@ -929,7 +1130,8 @@ void process_level(pm_factor* F, int lev, double tol) {
     interp_solve<C>(dip, (int)ip.size(), maxcols, st);
     CK(cudaGetLastError());
   }
-  F->stats.ms_id += t_id.stop();
+  const double ms_id = t_id.stop();
+  for (const auto& J : jobs) J.F->stats.ms_id += ms_id;
   Timer t_sc(st);
   // 6. skeleton lists, L (into X) and R
   std::vector<ScatterProb<C>> sp;
@@ -937,12 +1139,13 @@ void process_level(pm_factor* F, int lev, double tol) {
   std::vector<size_t> posref;
   int maxe = 0;
   for (int b = 0; b < nb; ++b) {
-    BoxF<C>& bf = BF[b];
+    BoxF<C>& bf = BFx(b);
+    Arena& ar = jobs[job_of[b]].F->arena;
     bf.kb = bf.kg[0] + bf.kg[1];
-    bf.X = F->arena.get<C>((size_t)std::max(bf.mb, 1) * std::max(bf.kb, 1));
-    bf.Rm = F->arena.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.mb, 1));
-    bf.At = F->arena.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
-    bf.ipiv = F->arena.get<int>(std::max(bf.mb, 1));
+    bf.X = ar.get<C>((size_t)std::max(bf.mb, 1) * std::max(bf.kb, 1));
+    bf.Rm = ar.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.mb, 1));
+    bf.At = ar.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
+    bf.ipiv = ar.get<int>(std::max(bf.mb, 1));
     CK(cudaMemsetAsync(bf.X, 0, sizeof(C) * (size_t)bf.mb * bf.kb, st));
     CK(cudaMemsetAsync(bf.Rm, 0, sizeof(C) * (size_t)bf.mb * bf.kb, st));
     int off = 0;
@@ -976,20 +1179,23 @@ void process_level(pm_factor* F, int lev, double tol) {
     CK(cudaGetLastError());
   }
   // 7. LU of D_b, X = D_b^{-1} L_b, Y = R_b X, A~_b = Y^{-1}
-  if ((F->opts.debug_flags & PM_DEBUG_SINGULAR_BLOCK) && lev == F->L && nb > 0)   // injected: zero self block
-    CK(cudaMemsetAsync(BF[0].D, 0, sizeof(C) * (size_t)BF[0].mb * BF[0].mb, st));
+  // injected (tests): the first leaf box's self block zeroed
+  const bool first_is_leaf = nb > 0 && jobs[0].lev == jobs[0].F->L;
+  if ((O.debug_flags & PM_DEBUG_SINGULAR_BLOCK) && first_is_leaf)
+    CK(cudaMemsetAsync(BFx(0).D, 0, sizeof(C) * (size_t)BFx(0).mb * BFx(0).mb, st));
   std::vector<LuProb<C>> lu;
-  for (int b = 0; b < nb; ++b) lu.push_back(LuProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, nullptr});
+  for (int b = 0; b < nb; ++b) lu.push_back(LuProb<C>{BFx(b).D, BFx(b).mb, BFx(b).mb, BFx(b).ipiv, nullptr});
   lu_batch<C>(lu, scr, st, "diagonal block");
   std::vector<SolveProb<C>> sv;
-  for (int b = 0; b < nb; ++b) sv.push_back(SolveProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, BF[b].X, BF[b].mb, BF[b].kb});
+  for (int b = 0; b < nb; ++b)
+    sv.push_back(SolveProb<C>{BFx(b).D, BFx(b).mb, BFx(b).mb, BFx(b).ipiv, BFx(b).X, BFx(b).mb, BFx(b).kb});
   solve_batch<C>(sv, scr, st);
   GemmBatch<C> gy;
   std::vector<C*> Y(nb);
   std::vector<int*> ypiv(nb);
   std::vector<CopyProb<C, C>> idp;
   for (int b = 0; b < nb; ++b) {
-    BoxF<C>& bf = BF[b];
+    BoxF<C>& bf = BFx(b);
     Y[b] = scr.get<C>((size_t)std::max(bf.kb, 1) * std::max(bf.kb, 1));
     ypiv[b] = scr.get<int>(std::max(bf.kb, 1));
     gy.add(bf.kb, bf.kb, bf.mb, bf.Rm, bf.kb, bf.X, bf.mb, Y[b], bf.kb, cone<C>(), czero_h<C>(), 1);
@@ -999,54 +1205,78 @@ void process_level(pm_factor* F, int lev, double tol) {
     }
   }
   gy.run(scr, st);
-  if ((F->opts.debug_flags & PM_DEBUG_SINGULAR_COMPRESSED) && lev == F->L && nb > 0 && BF[0].kb > 0)
-    CK(cudaMemsetAsync(Y[0], 0, sizeof(C) * (size_t)BF[0].kb * BF[0].kb, st));   // injected: singular R A^-1 L
+  if ((O.debug_flags & PM_DEBUG_SINGULAR_COMPRESSED) && first_is_leaf && BFx(0).kb > 0)
+    CK(cudaMemsetAsync(Y[0], 0, sizeof(C) * (size_t)BFx(0).kb * BFx(0).kb, st));   // injected: singular R A^-1 L
   std::vector<LuProb<C>> luy;
   std::vector<SolveProb<C>> svy;
   for (int b = 0; b < nb; ++b) {
-    if (BF[b].kb <= 0) continue;
-    luy.push_back(LuProb<C>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], nullptr});
-    svy.push_back(SolveProb<C>{Y[b], BF[b].kb, BF[b].kb, ypiv[b], BF[b].At, BF[b].kb, BF[b].kb});
+    const BoxF<C>& bf = BFx(b);
+    if (bf.kb <= 0) continue;
+    luy.push_back(LuProb<C>{Y[b], bf.kb, bf.kb, ypiv[b], nullptr});
+    svy.push_back(SolveProb<C>{Y[b], bf.kb, bf.kb, ypiv[b], bf.At, bf.kb, bf.kb});
   }
   lu_batch<C>(luy, scr, st, "R A^-1 L (compressed block)");
   solve_batch<C>(svy, scr, st);
-  F->stats.ms_schur += t_sc.stop();
-  int sk = 0;
-  for (auto& bf : BF) sk += bf.kb;
-  if (lev < 16) F->stats.skeleton[lev] = sk;
+  const double ms_sc = t_sc.stop();
+  for (const auto& J : jobs) {
+    J.F->stats.ms_schur += ms_sc;
+    int sk = 0;
+    for (auto& bf : levels_of<C>(J.F)[J.lev]) sk += bf.kb;
+    if (J.lev < 16) J.F->stats.skeleton[J.lev] = sk;
+  }
 }
 
-// Top-level system in FP64 from the level-1 boxes (arithmetic Cc), or the
-// single inclusion's self block.
+template <class C>
+void process_level(pm_factor* F, int lev, double tol) {
+  process_levels<C>({LevelJob{F, lev}}, F->scratch, F->st, tol);
+}
+
+// Top-level systems in FP64 from the level-1 boxes (arithmetic Cc), or the
+// single inclusion's self block, of one or more factorizations: one gather,
+// one copy and one batched LU for all of them.
 template <class Cc>
-void factor_top(pm_factor* F) {
-  const pm_geometry* g = F->g;
-  cudaStream_t st = F->st;
-  Arena& scr = F->scratch;
+void factor_tops(const std::vector<pm_factor*>& Fs, Arena& scr, cudaStream_t st) {
   scr.reset();
   Timer t(st);
-  BoxF<double2>& rt = F->root;
-  if (F->L == 0) {
-    int j = F->tree[0][0].leaves[0];
-    int n = g->inc[j].n_nodes;
-    rt.mb = 2 * n;
-    for (int i = 0; i < 2 * n; ++i) { rt.rows.push_back(g->row_off[j] + i); rt.rgrp.push_back(i >= n); }
-    rt.cols = rt.rows; rt.cgrp = rt.rgrp;
-    rt.D = F->arena.get<double2>((size_t)rt.mb * rt.mb);
-    assemble_self<double2>(g, {j}, {rt.D}, {rt.mb}, scr, st);
-  } else {
-    GatherBatch<double2> gb; CopyBatch<Cc, double2> cb;
-    merge_children<Cc, double2>(F, levels_of<Cc>(F)[1], F->tree[0][0], rt, gb, cb);
-    std::vector<int> dummy;
-    PointsDev P0 = make_points(g, {}, scr, st, dummy);
-    gb.run(scr, P0, g->k0, st);
-    cb.run(scr, st);
+  std::vector<LevelJob> jobs;
+  for (pm_factor* F : Fs) jobs.push_back(LevelJob{F, 0});
+  std::vector<int> base;
+  std::vector<std::vector<int>> poff;
+  PointsDev P = make_points_joint(jobs, false, scr, st, base, poff);
+  GatherBatch<double2> gb;
+  CopyBatch<Cc, double2> cb;
+  std::vector<LuProb<double2>> lu;
+  for (size_t i = 0; i < Fs.size(); ++i) {
+    pm_factor* F = Fs[i];
+    const pm_geometry* g = F->g;
+    BoxF<double2>& rt = F->root;
+    if (F->L == 0) {
+      int j = F->tree[0][0].leaves[0];
+      int n = g->inc[j].n_nodes;
+      rt.mb = 2 * n;
+      for (int r = 0; r < 2 * n; ++r) { rt.rows.push_back(g->row_off[j] + r); rt.rgrp.push_back(r >= n); }
+      rt.cols = rt.rows; rt.cgrp = rt.rgrp;
+      rt.D = F->arena.get<double2>((size_t)rt.mb * rt.mb);
+      assemble_self<double2>(g, {j}, {rt.D}, {rt.mb}, scr, st);
+    } else {
+      merge_children<Cc, double2>(F, levels_of<Cc>(F)[1], F->tree[0][0], rt, gb, cb, 2 * base[i]);
+    }
+    rt.ipiv = F->arena.get<int>(std::max(rt.mb, 1));
+    lu.push_back(LuProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, nullptr});
   }
-  rt.ipiv = F->arena.get<int>(std::max(rt.mb, 1));
-  std::vector<LuProb<double2>> lu{LuProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, nullptr}};
+  gb.run(scr, P, 0.0, st);
+  cb.run(scr, st);
   lu_batch<double2>(lu, scr, st, "top-level system");
-  F->stats.K = rt.mb;
-  F->stats.ms_top += t.stop();
+  const double ms = t.stop();
+  for (pm_factor* F : Fs) {
+    F->stats.K = F->root.mb;
+    F->stats.ms_top += ms;
+  }
+}
+
+template <class Cc>
+void factor_top(pm_factor* F) {
+  factor_tops<Cc>({F}, F->scratch, F->st);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1209,6 +1439,70 @@ void apply_inverse_mixed(pm_factor* F, const double2* rhs, int nrhs, double2* ph
   CK(cudaGetLastError());
 }
 
+// phi = M^{-1} rhs through the factor's plan for (kind, nrhs): kind 0 the
+// compressed inverse of an FP64 factorization, kind 1 the mixed
+// preconditioner with per-column scales h_scale (2 nrhs host values: scale,
+// unscale).  The first use runs the launches eagerly in the plan's arena
+// (sizing it); the second captures the same launches into a CUDA graph on
+// the plan's stream, with descriptor uploads done synchronously on a side
+// stream into the arena, and instantiates it; later uses replay the graph on
+// `st`.  The caller holds F->plan_mu; the body synchronises nothing.
+void run_planned(pm_factor* F, int kind, const double2* rhs, int nrhs, double2* phi, const double* h_scale,
+                 cudaStream_t st) {
+  const int N = F->g->N;
+  auto& up = F->plans[std::make_pair(kind, nrhs)];
+  if (!up) up.reset(new SolvePlan());
+  SolvePlan& P = *up;
+  P.uses++;
+  const size_t bytes = sizeof(double2) * (size_t)N * nrhs;
+  if (!P.in) {
+    P.io.min_block = 1 << 20;
+    P.in = P.io.get<double2>((size_t)N * nrhs);
+    P.out = P.io.get<double2>((size_t)N * nrhs);
+    P.scal = P.io.get<double>(2 * (size_t)nrhs);
+  }
+  CK(cudaMemcpyAsync(P.in, rhs, bytes, cudaMemcpyDeviceToDevice, st));
+  if (kind == 1) CK(cudaMemcpyAsync(P.scal, h_scale, 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+  auto body = [&](cudaStream_t s2) {
+    if (kind == 0) apply_inverse64(F, P.in, nrhs, P.out, P.ws, s2);
+    else apply_inverse_mixed(F, P.in, nrhs, P.out, P.scal, P.scal + nrhs, P.ws, s2);
+  };
+  const bool graphs = !F->profiling && !(F->opts.flags & PM_FLAG_NO_GRAPHS);
+  if (!P.exec && graphs && P.uses >= 2) {
+    if (!P.cap) CK(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
+    if (!P.side) CK(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(st));   // the eager run that used the arena has finished
+    P.ws.reset();                    // the same launches again: the arena allocates nothing new
+    CK(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeRelaxed));
+    g_capture_side = P.side;
+    cudaGraph_t graph = nullptr;
+    try {
+      body(P.cap);
+    } catch (...) {
+      g_capture_side = nullptr;
+      cudaStreamEndCapture(P.cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    g_capture_side = nullptr;
+    CK(cudaStreamEndCapture(P.cap, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&P.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) P.exec = nullptr;
+    CK(e);
+    F->graph_captures++;
+  }
+  if (P.exec) {
+    CK(cudaGraphLaunch(P.exec, st));
+    F->graph_launches++;
+  } else {
+    P.ws.reset();
+    body(st);
+  }
+  CK(cudaMemcpyAsync(phi, P.out, bytes, cudaMemcpyDeviceToDevice, st));
+}
+
 // Y = A X with the FP64 operator (self blocks + on-the-fly off-diagonal kernels).
 void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Arena& ws, cudaStream_t st) {
   const pm_geometry* g = F->g;
@@ -1310,8 +1604,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
       hs[r] = 1.0 / nr;
       hs[nrhs + r] = nr;
     }
-    CK(cudaMemcpyAsync(scal, hs.data(), 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-    apply_inverse_mixed(F, rhs, nrhs, out, scal, scal + nrhs, ws, st);
+    run_planned(F, 1, rhs, nrhs, out, hs.data(), st);
   };
   // x0 = 0, r0 = b (no operator application needed)
   CK(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)N * nrhs, st));
@@ -1450,6 +1743,134 @@ void require_finite_rhs(const pm_c64* rhs, size_t count, int on_device, Arena& w
 }
 }  // namespace
 
+namespace {
+
+// Option checks shared by pm_factorize and pm_factor_batch (sets g_err).
+bool check_factor_opts(const pm_factor_opts* opts, const char* where) {
+  const std::string w(where);
+  if (!(opts->tol > 0 && opts->tol < 1)) { g_err = w + ": tol must be in (0, 1)"; return false; }
+  if (opts->proxy_factor != 0 && !(opts->proxy_factor > 1)) { g_err = w + ": proxy_factor must be > 1"; return false; }
+  if (opts->proxy_points < 0 || opts->proxy_points > 100000) { g_err = w + ": bad proxy_points"; return false; }
+  if (opts->precision != PM_FP64 && opts->precision != PM_MIXED) { g_err = w + ": unsupported precision"; return false; }
+  if (opts->precision == PM_MIXED && (opts->low_tol < 0 || opts->low_tol >= 1 || opts->refine_tol < 0 || opts->max_refine < 0)) {
+    g_err = w + ": bad refinement options";
+    return false;
+  }
+  return true;
+}
+
+// Options, tree and proxy plan of a new factorization; returns the ID threshold.
+double setup_factor(pm_factor* F, const pm_geometry* g, const pm_factor_opts* opts) {
+  F->g = g;
+  F->opts = *opts;
+  if (F->opts.proxy_factor == 0) F->opts.proxy_factor = 1.5;
+  F->st = (cudaStream_t)opts->stream;
+  F->L = g->L;
+  F->precision = opts->precision;
+  F->tree = g->levels;
+  // the FP32 factorization of the mixed mode cannot resolve tolerances far below FP32 precision
+  const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 5e-6)
+                                                 : opts->tol;
+  pm_factor_opts popts = F->opts;
+  popts.tol = id_tol;
+  plan_proxies(g, F->tree, &popts);
+  F->stats.levels = F->L;
+  F->stats.N = g->N;
+  F->profiling = (opts->flags & 1u) != 0;
+  if (F->precision == PM_FP64) F->lev64.assign(F->L + 1, {});
+  else F->lev32.assign(F->L + 1, {});
+  return id_tol;
+}
+
+// The levels of several factorizations (same precision and options) in shared
+// launches: step s processes level L_i - s of every problem i that has one, so
+// problems of different depths meet at their leaves first; then all top-level
+// systems at once.  One factorization is the group of one.
+template <class C>
+void factor_group_t(std::vector<pm_factor*>& Fs, double id_tol, Arena& scr, cudaStream_t st) {
+  int Lmax = 0;
+  for (pm_factor* F : Fs) Lmax = std::max(Lmax, F->L);
+  for (int s = 0; s < Lmax; ++s) {
+    std::vector<LevelJob> jobs;
+    for (pm_factor* F : Fs)
+      if (F->L - s >= 1) jobs.push_back(LevelJob{F, F->L - s});
+    Timer tl(st);
+    process_levels<C>(jobs, scr, st, id_tol);
+    const double ms = tl.stop();
+    for (auto& J : jobs)
+      if (J.lev < 16) J.F->stats.ms_level[J.lev] = ms;
+  }
+  factor_tops<C>(Fs, scr, st);
+}
+
+void factor_group(std::vector<pm_factor*>& Fs, double id_tol, Arena& scr, cudaStream_t st) {
+  if (Fs.empty()) return;
+  if (Fs[0]->precision == PM_FP64) factor_group_t<double2>(Fs, id_tol, scr, st);
+  else factor_group_t<float2>(Fs, id_tol, scr, st);
+}
+
+// Mixed mode, after the complex64 levels: the FP64 self blocks, index maps and
+// (when it fits) the dense FP64 operator of the refinement residual.
+void finish_mixed(pm_factor* F) {
+  const pm_geometry* g = F->g;
+  const pm_factor_opts* opts = &F->opts;
+  // FP64 self blocks and index maps for the refinement residual
+  F->scratch.reset();
+  std::vector<int> incl(g->m), lda(g->m);
+  F->self64.resize(g->m);
+  for (int j = 0; j < g->m; ++j) {
+    incl[j] = j;
+    lda[j] = 2 * g->inc[j].n_nodes;
+    F->self64[j] = F->arena.get<double2>((size_t)lda[j] * lda[j]);
+  }
+  assemble_self<double2>(g, incl, F->self64, lda, F->scratch, F->st);
+  std::vector<int> iu(g->total_nodes), iq(g->total_nodes);
+  for (int j = 0; j < g->m; ++j)
+    for (int l = 0; l < g->inc[j].n_nodes; ++l) {
+      iu[g->node_off[j] + l] = g->row_off[j] + l;
+      iq[g->node_off[j] + l] = g->row_off[j] + g->inc[j].n_nodes + l;
+    }
+  F->d_iu = upload(F->arena, iu, F->st);
+  F->d_iq = upload(F->arena, iq, F->st);
+  // With room in HBM, write the FP64 operator out once: each refinement step
+  // is then a skinny FP64 GEMM instead of a Hankel evaluation per node pair.
+  // Budget: 60% of the free memory, and all dense operators held in the
+  // process at most 40% of the device; otherwise (or if the allocation
+  // fails) the refinement applies the operator on the fly.
+  const size_t need = sizeof(float4) * (size_t)g->N * g->N;
+  if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535) {
+    std::lock_guard<std::mutex> lk(g_dense_mu);
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    if (need <= fr / 10 * 6 && g_dense_held + need <= tot / 10 * 4) {
+      if (cudaMalloc(&F->dense64, need) == cudaSuccess) {
+        F->dense_bytes = need;
+        g_dense_held += need;
+      } else {
+        F->dense64 = nullptr;
+        cudaGetLastError();   // clear the failed allocation's error
+      }
+    }
+  }
+  if (F->dense64) {
+    OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
+    assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense64, (size_t)g->N, F->st);
+    if (g_kprof) {
+      double pairs = (double)g->total_nodes * g->total_nodes;
+      for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
+      g_kprof->add_flops("dense_offdiag64", pairs * 164.0);
+    }
+    for (int j = 0; j < g->m; ++j) {
+      const int m2 = 2 * g->inc[j].n_nodes;
+      split_copy(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, (size_t)g->N, m2,
+                 m2, F->st);
+    }
+    CK(cudaGetLastError());
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* pm_last_error(void) { return g_err.c_str(); }
@@ -1552,107 +1973,20 @@ pm_status pm_plane_wave_rhs(const pm_geometry* g, const double* angles, int32_t 
 pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_factor** out) {
   if (!g || !opts || !out) { g_err = "pm_factorize: NULL argument"; return PM_ERR_INVALID_ARG; }
   *out = nullptr;
-  if (!(opts->tol > 0 && opts->tol < 1)) { g_err = "pm_factorize: tol must be in (0, 1)"; return PM_ERR_INVALID_ARG; }
-  if (opts->proxy_factor != 0 && !(opts->proxy_factor > 1)) { g_err = "pm_factorize: proxy_factor must be > 1"; return PM_ERR_INVALID_ARG; }
-  if (opts->proxy_points < 0 || opts->proxy_points > 100000) { g_err = "pm_factorize: bad proxy_points"; return PM_ERR_INVALID_ARG; }
-  if (opts->precision != PM_FP64 && opts->precision != PM_MIXED) { g_err = "pm_factorize: unsupported precision"; return PM_ERR_UNSUPPORTED; }
-  if (opts->precision == PM_MIXED && (opts->low_tol < 0 || opts->low_tol >= 1 || opts->refine_tol < 0 || opts->max_refine < 0)) {
-    g_err = "pm_factorize: bad refinement options";
-    return PM_ERR_INVALID_ARG;
-  }
+  if (!check_factor_opts(opts, "pm_factorize")) return opts->precision != PM_FP64 && opts->precision != PM_MIXED
+                                                          ? PM_ERR_UNSUPPORTED : PM_ERR_INVALID_ARG;
   pm_factor* F = new pm_factor();
   pm_status s = run_guarded("pm_factorize", [&] {
-    F->g = g;
-    F->opts = *opts;
-    if (F->opts.proxy_factor == 0) F->opts.proxy_factor = 1.5;
-    F->st = (cudaStream_t)opts->stream;
-    F->L = g->L;
-    F->precision = opts->precision;
-    F->tree = g->levels;
-    // the FP32 factorization of the mixed mode cannot resolve tolerances far below FP32 precision
-    const double id_tol = F->precision == PM_MIXED ? std::max(opts->tol, opts->low_tol > 0 ? opts->low_tol : 5e-6)
-                                                   : opts->tol;
-    pm_factor_opts popts = F->opts;
-    popts.tol = id_tol;
-    plan_proxies(g, F->tree, &popts);
-    F->stats.levels = F->L;
-    F->stats.N = g->N;
-    F->profiling = (opts->flags & 1u) != 0;
+    TuneScope ts((opts->flags & PM_FLAG_NO_AUTOTUNE) != 0);
+    const double id_tol = setup_factor(F, g, opts);
     struct ProfScope {
       explicit ProfScope(KProf* p) { g_kprof = p; }
       ~ProfScope() { g_kprof = nullptr; }
     } scope(F->profiling ? &F->prof : nullptr);
     Timer tt(F->st);
-    if (F->precision == PM_FP64) {
-      F->lev64.assign(F->L + 1, {});
-      for (int l = F->L; l >= 1; --l) {
-        Timer tl(F->st);
-        process_level<double2>(F, l, id_tol);
-        if (l < 16) F->stats.ms_level[l] = tl.stop(); else tl.stop();
-      }
-      factor_top<double2>(F);
-    } else {
-      F->lev32.assign(F->L + 1, {});
-      for (int l = F->L; l >= 1; --l) {
-        Timer tl(F->st);
-        process_level<float2>(F, l, id_tol);
-        if (l < 16) F->stats.ms_level[l] = tl.stop(); else tl.stop();
-      }
-      factor_top<float2>(F);
-      // FP64 self blocks and index maps for the refinement residual
-      F->scratch.reset();
-      std::vector<int> incl(g->m), lda(g->m);
-      F->self64.resize(g->m);
-      for (int j = 0; j < g->m; ++j) {
-        incl[j] = j;
-        lda[j] = 2 * g->inc[j].n_nodes;
-        F->self64[j] = F->arena.get<double2>((size_t)lda[j] * lda[j]);
-      }
-      assemble_self<double2>(g, incl, F->self64, lda, F->scratch, F->st);
-      std::vector<int> iu(g->total_nodes), iq(g->total_nodes);
-      for (int j = 0; j < g->m; ++j)
-        for (int l = 0; l < g->inc[j].n_nodes; ++l) {
-          iu[g->node_off[j] + l] = g->row_off[j] + l;
-          iq[g->node_off[j] + l] = g->row_off[j] + g->inc[j].n_nodes + l;
-        }
-      F->d_iu = upload(F->arena, iu, F->st);
-      F->d_iq = upload(F->arena, iq, F->st);
-      // With room in HBM, write the FP64 operator out once: each refinement step
-      // is then a skinny FP64 GEMM instead of a Hankel evaluation per node pair.
-      // Budget: 60% of the free memory, and all dense operators held in the
-      // process at most 40% of the device; otherwise (or if the allocation
-      // fails) the refinement applies the operator on the fly.
-      const size_t need = sizeof(float4) * (size_t)g->N * g->N;
-      if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535) {
-        std::lock_guard<std::mutex> lk(g_dense_mu);
-        size_t fr = 0, tot = 0;
-        CK(cudaMemGetInfo(&fr, &tot));
-        if (need <= fr / 10 * 6 && g_dense_held + need <= tot / 10 * 4) {
-          if (cudaMalloc(&F->dense64, need) == cudaSuccess) {
-            F->dense_bytes = need;
-            g_dense_held += need;
-          } else {
-            F->dense64 = nullptr;
-            cudaGetLastError();   // clear the failed allocation's error
-          }
-        }
-      }
-      if (F->dense64) {
-        OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
-        assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense64, (size_t)g->N, F->st);
-        if (g_kprof) {
-          double pairs = (double)g->total_nodes * g->total_nodes;
-          for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
-          g_kprof->add_flops("dense_offdiag64", pairs * 164.0);
-        }
-        for (int j = 0; j < g->m; ++j) {
-          const int m2 = 2 * g->inc[j].n_nodes;
-          split_copy(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, (size_t)g->N, m2,
-                     m2, F->st);
-        }
-        CK(cudaGetLastError());
-      }
-    }
+    std::vector<pm_factor*> one{F};
+    factor_group(one, id_tol, F->scratch, F->st);
+    if (F->precision == PM_MIXED) finish_mixed(F);
     F->stats.ms_total = tt.stop();
     if (F->profiling) F->prof.collect();
     F->scratch.release();
@@ -1672,6 +2006,7 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
   }
   pm_factor* F = const_cast<pm_factor*>(Fc);
   return run_guarded("pm_solve", [&] {
+    TuneScope ts((F->opts.flags & PM_FLAG_NO_AUTOTUNE) != 0);
     Arena ws;
     ws.min_block = 1 << 20;
     const size_t bytes = sizeof(Cd) * (size_t)F->g->N * nrhs;
@@ -1697,7 +2032,8 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
       explicit ProfScope(KProf* p) { g_kprof = p; }
       ~ProfScope() { g_kprof = nullptr; }
     } scope(F->profiling ? &F->prof : nullptr);
-    if (F->precision == PM_FP64) apply_inverse64(F, drhs, nrhs, dphi, ws, st);
+    std::lock_guard<std::mutex> plan_lock(F->plan_mu);   // solves of one factor share its graphs
+    if (F->precision == PM_FP64) run_planned(F, 0, drhs, nrhs, dphi, nullptr, st);
     else solve_refined(F, drhs, nrhs, dphi, ws, st, info);
     if (!on_device) CK(cudaMemcpyAsync(phi, dphi, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1751,12 +2087,50 @@ pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_f
                           int32_t workers) {
   if (!g || !opts || !out || count < 1) { g_err = "pm_factor_batch: bad argument"; return PM_ERR_INVALID_ARG; }
   for (int i = 0; i < count; ++i) out[i] = nullptr;
-  pm_status s = run_batch(count, workers > 0 ? workers : 8, [&](int i, cudaStream_t st) {
-    pm_factor_opts o = *opts;
-    o.stream = st;
-    pm_status r = pm_factorize(g[i], &o, &out[i]);
-    if (out[i]) out[i]->st = nullptr;   // the worker streams end with the batch
-    return r;
+  for (int i = 0; i < count; ++i)
+    if (!g[i]) { g_err = "pm_factor_batch: NULL geometry " + std::to_string(i); return PM_ERR_INVALID_ARG; }
+  if (!check_factor_opts(opts, "pm_factor_batch"))
+    return opts->precision != PM_FP64 && opts->precision != PM_MIXED ? PM_ERR_UNSUPPORTED : PM_ERR_INVALID_ARG;
+  // groups: problems in descending order of work (~N^1.5), each to the group
+  // with the least work so far; a group's levels share launches
+  const int ng = std::max(1, std::min(workers > 0 ? workers : 4, count));
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  auto work = [&](int i) { return std::pow((double)g[i]->N, 1.5); };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  std::vector<std::vector<int>> groups(ng);
+  std::vector<double> load(ng, 0.0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    groups[k].push_back(i);
+    load[k] += work(i);
+  }
+  for (auto& grp : groups) std::sort(grp.begin(), grp.end());
+  pm_status s = run_batch(ng, ng, [&](int k, cudaStream_t st) {
+    return run_guarded("pm_factor_batch", [&] {
+      TuneScope ts((opts->flags & PM_FLAG_NO_AUTOTUNE) != 0);
+      std::vector<pm_factor*> Fs;
+      double id_tol = 0;
+      pm_factor_opts o = *opts;
+      o.stream = st;
+      o.flags &= ~(uint32_t)PM_FLAG_PROFILE;   // per-kernel profiles are per factorization
+      for (int i : groups[k]) {
+        out[i] = new pm_factor();
+        id_tol = setup_factor(out[i], g[i], &o);
+        Fs.push_back(out[i]);
+      }
+      Timer tt(st);
+      Arena scr;
+      factor_group(Fs, id_tol, scr, st);
+      scr.release();
+      for (pm_factor* F : Fs)
+        if (F->precision == PM_MIXED) { finish_mixed(F); F->scratch.release(); }
+      const double ms = tt.stop();
+      for (pm_factor* F : Fs) {
+        F->stats.ms_total = ms;
+        F->st = nullptr;   // the worker streams end with the batch
+      }
+    });
   });
   if (s != PM_OK) {
     for (int i = 0; i < count; ++i) { delete out[i]; out[i] = nullptr; }
@@ -1775,6 +2149,8 @@ pm_status pm_solve_batch(const pm_factor* const* f, int32_t count, const pm_c64*
 pm_status pm_factor_stats(const pm_factor* F, pm_stats* out) {
   if (!F || !out) { g_err = "pm_factor_stats: NULL argument"; return PM_ERR_INVALID_ARG; }
   *out = F->stats;
+  out->graph_captures = F->graph_captures;
+  out->graph_launches = F->graph_launches;
   return PM_OK;
 }
 
@@ -2000,6 +2376,26 @@ pm_status pm_gemm_c32(int32_t m, int32_t n, int32_t k, const void* A, int32_t ld
     CK(cudaStreamSynchronize(st));
     if (herr) fail(PM_ERR_TIMEOUT, "a wait on the tensor cores ran out");
   });
+}
+
+pm_status pm_autotune_table(pm_tune_entry* out, int32_t cap, int32_t* count) {
+  if (!count || cap < 0 || (cap > 0 && !out)) { g_err = "pm_autotune_table: bad argument"; return PM_ERR_INVALID_ARG; }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int i = 0;
+  for (const auto& kv : g_tune) {
+    if (i < cap) {
+      pm_tune_entry& e = out[i];
+      std::memset(&e, 0, sizeof(e));
+      e.device = kv.first.dev; e.complex_bytes = kv.first.bytes;
+      e.log2_m = kv.first.lm; e.log2_n = kv.first.ln; e.log2_k = kv.first.lk; e.log2_count = kv.first.lc;
+      e.tm = kGemmShapes[kv.second.shape].tm; e.tn = kGemmShapes[kv.second.shape].tn;
+      for (int sh = 0; sh < GEMM_NSHAPES && sh < 8; ++sh) e.ms[sh] = kv.second.ms[sh];
+      e.uses = kv.second.uses;
+    }
+    ++i;
+  }
+  *count = i;
+  return PM_OK;
 }
 
 pm_status pm_launch_counter(uint64_t* out) {
