@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256) k_gather(const GatherProb<C>* __restrict_
   if (i >= g.M || j >= g.N) return;
   int tc = g.trans ? g.tgt[j] : g.tgt[i];
   int sc = g.trans ? g.src[i] : g.src[j];
-  g.out[i + (size_t)j * g.ld] = omit_entry<C>(P, tc, sc, k);
+  g.out[i + (size_t)j * g.ld] = omit_entry<C>(P, tc, sc, g.k != 0.0 ? g.k : k);
 }
 
 }  // namespace

@@ -30,6 +30,8 @@ struct GatherProb {        // out[i + j ld] = A(t, s): t = tgt[trans ? j : i], s
   const int* tgt;          // packed point*2 + row group (0 u-eq, 1 q-eq)
   const int* src;          // packed point*2 + column group (0 q, 1 u)
   int trans;
+  double k;                // exterior wavenumber of this problem's kernels (0: the launch's k0);
+                           // lets problems of different frequencies share one launch
 };
 
 struct ProxyBoxDev { double cx, cy, R; int p; int point_off; };

@@ -79,6 +79,75 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const GemmDesc<C>* __restr
                local % tiles_m, local / tiles_m);
 }
 
+// The same product with a TM x TN output tile, each of the 256 threads
+// holding MR x NR outputs (TM / MR by TN / NR threads).  Every output
+// accumulates over k in the same order as gemm_tile (chunks of TK, each in
+// order), so all tile shapes give bit-identical results; the autotuner picks
+// among them by speed alone.
+template <typename C, int TM, int TN, int MR, int NR>
+__global__ void __launch_bounds__(256) k_gemm_batched_t(const GemmDesc<C>* __restrict__ d,
+                                                        const int* __restrict__ tile_off, int nprob) {
+  constexpr int TX = TM / MR, TY = TN / NR;
+  static_assert(TX * TY == 256, "256 threads per tile");
+  __shared__ C As[TK][TM + 1];
+  __shared__ C Bs[TK][TN + 1];
+  const int t = blockIdx.x;
+  int lo = 0, hi = nprob;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_off[mid] <= t) lo = mid; else hi = mid;
+  }
+  const GemmDesc<C> g = d[lo];
+  if (g.m <= 0 || g.n <= 0) return;
+  const int local = t - tile_off[lo];
+  const int tiles_m = (g.m + TM - 1) / TM;
+  const int r0 = (local % tiles_m) * TM, c0 = (local / tiles_m) * TN;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  C acc[MR][NR];
+#pragma unroll
+  for (int a = 0; a < MR; ++a)
+#pragma unroll
+    for (int b = 0; b < NR; ++b) acc[a][b] = czero<C>();
+  for (int l0 = 0; l0 < g.k; l0 += TK) {
+    for (int e = tid; e < TM * TK; e += 256) {
+      const int i = e % TM, l = e / TM;
+      const int gi = r0 + i, gl = l0 + l;
+      As[l][i] = (gi < g.m && gl < g.k) ? g.A[gi + (size_t)gl * g.lda] : czero<C>();
+    }
+    for (int e = tid; e < TN * TK; e += 256) {
+      const int l = e % TK, j = e / TK;
+      const int gl = l0 + l, gj = c0 + j;
+      Bs[l][j] = (gl < g.k && gj < g.n) ? g.B[gl + (size_t)gj * g.ldb] : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < TK; ++l) {
+      C av[MR], bv[NR];
+#pragma unroll
+      for (int a = 0; a < MR; ++a) av[a] = As[l][tx + TX * a];
+#pragma unroll
+      for (int b = 0; b < NR; ++b) bv[b] = Bs[l][ty + TY * b];
+#pragma unroll
+      for (int a = 0; a < MR; ++a)
+#pragma unroll
+        for (int b = 0; b < NR; ++b) cfma(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < MR; ++a)
+#pragma unroll
+    for (int b = 0; b < NR; ++b) {
+      const int gi = r0 + tx + TX * a, gj = c0 + ty + TY * b;
+      if (gi < g.m && gj < g.n) {
+        C* p = g.Cm + gi + (size_t)gj * g.ldc;
+        C v = g.alpha * acc[a][b];
+        if (!g.beta_zero) v = v + g.beta * (*p);
+        *p = v;
+      }
+    }
+}
+
 // ---- LU with partial pivoting (blocked, right-looking) ---------------------------------
 
 __device__ __forceinline__ double2 shfl_c(double2 v, int src) {
@@ -525,6 +594,24 @@ void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob
   KPROF_END(st, kname<C>("gemm_batched", "gemm_batched32"), 0.0);
 }
 
+const GemmShape kGemmShapes[GEMM_NSHAPES] = {{32, 32}, {64, 64}, {64, 32}, {128, 8}, {64, 16}};
+
+template <typename C>
+void la_gemm_batched_shape(int shape, const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob, int total_tiles,
+                           cudaStream_t st) {
+  if (nprob <= 0 || total_tiles <= 0) return;
+  KPROF_BEGIN(st);
+  switch (shape) {
+    case 1: k_gemm_batched_t<C, 64, 64, 4, 4><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob); break;
+    case 2: k_gemm_batched_t<C, 64, 32, 4, 2><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob); break;
+    case 3: k_gemm_batched_t<C, 128, 8, 4, 1><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob); break;
+    case 4: k_gemm_batched_t<C, 64, 16, 2, 2><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob); break;
+    default: k_gemm_batched<C><<<total_tiles, 256, 0, st>>>(d_desc, d_tile_off, nprob); break;
+  }
+  pm_launch_count_add(1);
+  KPROF_END(st, kname<C>("gemm_batched", "gemm_batched32"), 0.0);
+}
+
 constexpr int LU_NB = 16;
 static_assert(LU_NB <= MAXNB, "LU panel wider than the kernels' shared tiles");
 constexpr int RS_NB = 32;
@@ -634,6 +721,8 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
   KPROF_END(st, kname<C>("getrs", "getrs32"), fl);
 }
 
+template void la_gemm_batched_shape<double2>(int, const GemmDesc<double2>*, const int*, int, int, cudaStream_t);
+template void la_gemm_batched_shape<float2>(int, const GemmDesc<float2>*, const int*, int, int, cudaStream_t);
 template void la_gemm_batched<double2>(const GemmDesc<double2>*, const int*, int, int, cudaStream_t);
 template void la_gemm_batched<float2>(const GemmDesc<float2>*, const int*, int, int, cudaStream_t);
 template void la_getrf_batched<double2>(const LuProb<double2>*, int, int, const int*, cudaStream_t);

@@ -42,3 +42,17 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
 
 // tiles of a GEMM problem for the 32 x 32 output tiling
 inline int gemm_tiles(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
+
+// Output tile shapes of the batched GEMM (shape 0 is la_gemm_batched's 32 x 32).
+// All shapes sum over k in the same order, so they give bit-identical results.
+struct GemmShape { int tm, tn; };
+constexpr int GEMM_NSHAPES = 5;
+extern const GemmShape kGemmShapes[GEMM_NSHAPES];
+inline int gemm_tiles_shape(int shape, int m, int n) {
+  const GemmShape s = kGemmShapes[shape];
+  return ((m + s.tm - 1) / s.tm) * ((n + s.tn - 1) / s.tn);
+}
+// d_tile_off: prefix sums of gemm_tiles_shape(shape, m, n) over the problems.
+template <typename C>
+void la_gemm_batched_shape(int shape, const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob, int total_tiles,
+                           cudaStream_t st);

@@ -53,7 +53,14 @@ class pm_stats(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("N", ct.c_int32), ("K", ct.c_int32), ("skeleton", ct.c_int32 * 16),
                 ("ms_assemble", ct.c_double), ("ms_id", ct.c_double), ("ms_schur", ct.c_double),
                 ("ms_top", ct.c_double), ("ms_total", ct.c_double), ("cpqr_launches", ct.c_int32),
-                ("rank_checks", ct.c_int32), ("predictor_fallbacks", ct.c_int32), ("ms_level", ct.c_double * 16)]
+                ("rank_checks", ct.c_int32), ("predictor_fallbacks", ct.c_int32), ("ms_level", ct.c_double * 16),
+                ("graph_captures", ct.c_int32), ("graph_launches", ct.c_int32)]
+
+
+class pm_tune_entry(ct.Structure):
+    _fields_ = [("device", ct.c_int32), ("complex_bytes", ct.c_int32), ("log2_m", ct.c_int32),
+                ("log2_n", ct.c_int32), ("log2_k", ct.c_int32), ("log2_count", ct.c_int32), ("tm", ct.c_int32),
+                ("tn", ct.c_int32), ("ms", ct.c_float * 8), ("uses", ct.c_int64)]
 
 
 class pm_kernel_stat(ct.Structure):
@@ -66,6 +73,8 @@ PM_FLAG_NO_QR_FIRST = 4
 PM_FLAG_TENSOR_CORES = 8
 PM_FLAG_FF_CONFIRM = 16
 PM_FLAG_FP64_CONFIRM = 32
+PM_FLAG_NO_AUTOTUNE = 64
+PM_FLAG_NO_GRAPHS = 128
 PM_DEBUG_SINGULAR_BLOCK = 1
 PM_DEBUG_SINGULAR_COMPRESSED = 2
 PM_DEBUG_UNDERPREDICT = 4
@@ -91,6 +100,7 @@ EXPORTS = {
     "pm_self_block": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_factor_profile": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_launch_counter": (ct.c_int, [ct.POINTER(ct.c_uint64)]),
+    "pm_autotune_table": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_factor_rank_data": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_mlp_forward": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "pm_mlp_loss_grad": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_double,
@@ -164,6 +174,17 @@ def measure_peak(which, ms_target=200.0):
     return v.value, mhz.value
 
 
+def autotune_table():
+    """The batched-GEMM autotuner's cached choices: one dict per batch class."""
+    cnt = ct.c_int32()
+    _check(load().pm_autotune_table(None, 0, ct.byref(cnt)))
+    arr = (pm_tune_entry * max(cnt.value, 1))()
+    _check(load().pm_autotune_table(arr, cnt.value, ct.byref(cnt)))
+    return [{"device": e.device, "complex_bytes": e.complex_bytes, "log2_m": e.log2_m, "log2_n": e.log2_n,
+             "log2_k": e.log2_k, "log2_count": e.log2_count, "tile": (e.tm, e.tn), "ms": list(e.ms)[:5],
+             "uses": e.uses} for e in arr[: cnt.value]]
+
+
 def launch_counter():
     v = ct.c_uint64()
     _check(load().pm_launch_counter(ct.byref(v)))
@@ -221,7 +242,7 @@ class Geometry:
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
-                 qr_first=True, tensor_cores=False, ff_confirm=True, debug_flags=0):
+                 qr_first=True, tensor_cores=False, ff_confirm=True, debug_flags=0, autotune=True, graphs=True):
         """rank_model: device pointer (int) of a trained predictor, or None;
         ff_confirm: the refinement ends on the folded float-float product (default) or,
         with False, on the FP64 product (PM_FLAG_FP64_CONFIRM);
@@ -233,7 +254,8 @@ class Factor:
                            ct.c_void_p(stream) if stream else None,
                            (PM_FLAG_PROFILE if profile else 0) | (0 if dense_operator else PM_FLAG_NO_DENSE_OPERATOR)
                            | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0)
-                           | (0 if ff_confirm else PM_FLAG_FP64_CONFIRM),
+                           | (0 if ff_confirm else PM_FLAG_FP64_CONFIRM) | (0 if autotune else PM_FLAG_NO_AUTOTUNE)
+                           | (0 if graphs else PM_FLAG_NO_GRAPHS),
                            float(refine_tol), int(max_refine), float(low_tol),
                            ct.c_void_p(rank_model) if rank_model else None, int(debug_flags))
         h = ct.c_void_p()
@@ -246,7 +268,8 @@ class Factor:
         return {"levels": s.levels, "N": s.N, "K": s.K, "skeleton": list(s.skeleton)[: s.levels + 1],
                 "ms_assemble": s.ms_assemble, "ms_id": s.ms_id, "ms_schur": s.ms_schur, "ms_top": s.ms_top,
                 "ms_total": s.ms_total, "cpqr_launches": s.cpqr_launches, "rank_checks": s.rank_checks,
-                "predictor_fallbacks": s.predictor_fallbacks, "ms_level": list(s.ms_level)[: s.levels + 1]}
+                "predictor_fallbacks": s.predictor_fallbacks, "ms_level": list(s.ms_level)[: s.levels + 1],
+                "graph_captures": s.graph_captures, "graph_launches": s.graph_launches}
 
     def rank_data(self):
         """(X, T): features (n x 8) and adaptive ranks / n_g (n x 2) of every box and group."""

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "pmchwt.h")
 
 STRUCTS = ["pm_c64", "pm_inclusion", "pm_problem", "pm_factor_opts", "pm_solve_info", "pm_stats",
-           "pm_kernel_stat"]
+           "pm_kernel_stat", "pm_tune_entry"]
 
 
 def _c_layout():
