@@ -1,7 +1,9 @@
 """Solve graphs: the second application of a factor's compressed inverse (or
 of the mixed preconditioner) for a right-hand-side count is captured into a
-CUDA graph, later ones replay it, and the results equal eager launches bit
-for bit."""
+CUDA graph, later ones replay it, and the results equal eager launches: bit
+for bit in FP64; in the mixed mode to 1e-11, since the refinement's dense
+products add column-split partial sums with FP64 atomics (mixed solves
+reproduce to ~1e-13 from run to run)."""
 import numpy as np
 import pytest
 
@@ -48,9 +50,11 @@ def test_mixed_refinement_replays_the_preconditioner_graph(pm):
     x = f.solve(F)
     it = f.last_info["iterations"]
     st = f.stats()
-    assert it >= 3
+    assert it >= 3 and it == eager.last_info["iterations"]
     assert st["graph_captures"] == 1 and st["graph_launches"] == it - 1
-    assert np.array_equal(x, ref)
+    assert np.linalg.norm(x - ref) < 1e-11 * np.linalg.norm(ref)
     x2 = f.solve(F)    # a second solve replays from its first application
-    assert np.array_equal(x2, ref)
-    assert f.stats()["graph_launches"] == 2 * it - 1
+    it2 = f.last_info["iterations"]
+    assert np.linalg.norm(x2 - ref) < 1e-11 * np.linalg.norm(ref)
+    assert f.stats()["graph_launches"] == it - 1 + it2
+    assert np.linalg.norm(ref - dense.solve(prob, [0.7, 3.3])) < 1e-8 * np.linalg.norm(ref)
