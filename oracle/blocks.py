@@ -27,8 +27,20 @@ Log split (Colton & Kress Sec. 3.6), t != tau, d = x(t) - x(tau), r = |d|:
       L1* = (k/4pi) J1(kr) (n_x.d)/r |x'(tau)|,  L2*(t,t) = (1/4pi) (n.x'')/|x'|
   matrix entry = R(t_i - t_j) * (log coefficient) + (2 pi/n) * (smooth part).
 
+Burton-Miller (eq. bm_bie), unknowns per inclusion [u_i; q_i], rows
+[exterior equation; interior equation], alpha = i / k+, I the identity:
+  self:  [[D+ - I/2 + alpha N+,  -eps+ S+ - alpha eps+ (D*+ + I/2)],
+          [D- + I/2,             -eps- S-]]
+  i != j: [[D+ + alpha N+,  -eps+ (S+ + alpha D*+)],
+           [D-,              -eps- S-]]   (interior kernel of the source inclusion)
+  right-hand side [-(u^I + alpha q^I); 0].
+The simplified Burton-Miller system drops the interior terms of the
+off-diagonal blocks (their lower blocks are zero), the case Sec. 3 shows to
+make R A^{-1} L singular.
+
 Parity pinned by tests/test_oracle_blocks.py (circle eigenvalues, Calderon
-identities on stars / ellipses, Green's formula between two curves).
+identities on stars / ellipses, Green's formula between two curves) and, for
+the Burton-Miller blocks, by the disk series of tests/test_oracle_dense.py.
 """
 import math
 
@@ -115,3 +127,27 @@ def all_block(nt, ns, k_out, k_in_src, eps_out, eps_in_src):
     Sm, Dm, Dsm, Nm = offdiag_operators(nt, ns, k_in_src)
     return np.block([[-(eps_out * Sp + eps_in_src * Sm), Dp + Dm],
                      [-(Dsp + Dsm), Np / eps_out + Nm / eps_in_src]])
+
+
+def bm_self_block(nd, k_out, k_in, eps_out, eps_in):
+    """A_ii (2n x 2n) of the Burton-Miller system, unknowns [u; q]."""
+    Sp, Dp, Dsp, Np = self_operators(nd, k_out)
+    Sm, Dm, Dsm, Nm = self_operators(nd, k_in)
+    n = nd["n"]
+    eye = np.eye(n)
+    a = 1j / k_out
+    return np.block([[Dp - eye / 2 + a * Np, -eps_out * Sp - a * eps_out * (Dsp + eye / 2)],
+                     [Dm + eye / 2, -eps_in * Sm]])
+
+
+def bm_block(nt, ns, k_out, k_in_src, eps_out, eps_in_src, simplified=False):
+    """A_ij (i != j) of the Burton-Miller system (unknowns [u; q]); with
+    simplified=True the interior (lower) blocks are dropped."""
+    Sp, Dp, Dsp, Np = offdiag_operators(nt, ns, k_out)
+    a = 1j / k_out
+    upper = [Dp + a * Np, -eps_out * (Sp + a * Dsp)]
+    if simplified:
+        z = np.zeros_like(Sp)
+        return np.block([upper, [z, z]])
+    Sm, Dm, Dsm, Nm = offdiag_operators(nt, ns, k_in_src)
+    return np.block([upper, [Dm, -eps_in_src * Sm]])

@@ -49,6 +49,25 @@ def assemble(prob, formulation="omit", nds=None):
     return A
 
 
+def assemble_bm(prob, nds=None, simplified=False):
+    """The Burton-Miller system (eq. bm_bie): unknowns [u_i; q_i] and rows
+    [exterior; interior] per inclusion (blocks.bm_self_block / bm_block)."""
+    nds = nds if nds is not None else all_nodes(prob)
+    m = len(nds)
+    off = offsets(prob)
+    A = np.zeros((off[-1], off[-1]), dtype=np.complex128)
+    k0 = prob["k_out"]
+    for i in range(m):
+        for j in range(m):
+            if i == j:
+                blk = blocks.bm_self_block(nds[i], k0, prob["inclusions"][i]["k_in"], EPS_OUT, eps_in(prob, i))
+            else:
+                blk = blocks.bm_block(nds[i], nds[j], k0, prob["inclusions"][j]["k_in"], EPS_OUT, eps_in(prob, j),
+                                      simplified)
+            A[off[i]:off[i + 1], off[j]:off[j + 1]] = blk
+    return A
+
+
 def plane_wave(prob, angle, nds=None):
     """Right-hand side f = [-u^I_i; -q^I_i] per inclusion for incidence angle ``angle``."""
     nds = nds if nds is not None else all_nodes(prob)
@@ -62,11 +81,41 @@ def plane_wave(prob, angle, nds=None):
     return np.concatenate(parts)
 
 
+def bm_rhs(prob, f):
+    """The Burton-Miller right-hand side [-(u^I + alpha q^I); 0] per inclusion
+    from the PMCHWT one f = [-u^I; -q^I] (alpha = i / k+)."""
+    f = np.asarray(f)
+    a = 1j / prob["k_out"]
+    out = np.zeros_like(f)
+    off = offsets(prob)
+    for j, inc in enumerate(prob["inclusions"]):
+        n = inc["n"]
+        out[off[j]:off[j] + n] = f[off[j]:off[j] + n] + a * f[off[j] + n:off[j] + 2 * n]
+    return out
+
+
+def bm_to_pmchwt_order(prob, x):
+    """[u_i; q_i] per inclusion -> [q_i; u_i] (the PMCHWT unknown order)."""
+    x = np.asarray(x)
+    out = np.empty_like(x)
+    off = offsets(prob)
+    for j, inc in enumerate(prob["inclusions"]):
+        n = inc["n"]
+        out[off[j]:off[j] + n] = x[off[j] + n:off[j] + 2 * n]
+        out[off[j] + n:off[j] + 2 * n] = x[off[j]:off[j] + n]
+    return out
+
+
 def solve(prob, angles, formulation="omit"):
-    """phi (2N x nrhs) of the conventional BIEM for plane waves at ``angles``."""
+    """phi (2N x nrhs, [q_i; u_i] per inclusion) of the conventional BIEM for
+    plane waves at ``angles``; formulation "omit", "all" or "bm"."""
     nds = all_nodes(prob)
-    A = assemble(prob, formulation, nds)
     F = np.stack([plane_wave(prob, a, nds) for a in angles], 1)
+    if formulation == "bm":
+        A = assemble_bm(prob, nds)
+        X = sla.lu_solve(sla.lu_factor(A), bm_rhs(prob, F))
+        return bm_to_pmchwt_order(prob, X)
+    A = assemble(prob, formulation, nds)
     lu = sla.lu_factor(A)
     return sla.lu_solve(lu, F)
 

@@ -34,10 +34,12 @@ import scipy.linalg as sla
 
 from . import cpqr as cp
 from . import tree as tr
-from .dense import EPS_OUT, offsets
+from .dense import EPS_OUT, bm_rhs, bm_to_pmchwt_order, offsets
 from .geometry import all_nodes, eps_in
 from .kernels import kernel_values
-from .blocks import self_block
+from .blocks import bm_self_block, self_block
+
+FORMS = ("omit", "all", "bm", "bm_simplified")
 
 
 class SingularError(RuntimeError):
@@ -55,6 +57,11 @@ class _Index:
         self.X = np.concatenate([nd["x"] for nd in nds])
         self.NRM = np.concatenate([nd["nrm"] for nd in nds])
         self.W = np.concatenate([nd["w"] for nd in nds])
+        self.k_in = [inc["k_in"] for inc in prob["inclusions"]]
+        self.eps_in = [eps_in(prob, j) for j in range(len(prob["inclusions"]))]
+
+    def incl_of_node(self, node):
+        return np.searchsorted(self.node_off, np.asarray(node), side="right") - 1
 
     def decode(self, g):
         g = np.asarray(g)
@@ -65,51 +72,164 @@ class _Index:
         return node, grp
 
 
-def _combine(S, D, Ds, N, rg, cg, w):
-    """Omit off-diagonal entry for row group rg (0: u-eq, 1: q-eq) and column group cg (0: q, 1: u)."""
-    val = np.where(rg == 0, np.where(cg == 0, -EPS_OUT * S, D),
-                   np.where(cg == 0, -Ds, N / EPS_OUT))
+def _combine(S, D, Ds, N, rg, cg, w, eps=EPS_OUT):
+    """Omit off-diagonal entry for row group rg (0: u-eq, 1: q-eq) and column group cg (0: q, 1: u)
+    (with eps = eps- and interior kernel values: the interior terms of PMCHWT (All))."""
+    val = np.where(rg == 0, np.where(cg == 0, -eps * S, D),
+                   np.where(cg == 0, -Ds, N / eps))
     return val * w
 
 
-def entries(ix, k0, rows, cols):
-    """A(rows, cols) for rows and cols on different inclusions (exterior kernel only)."""
+def _combine_bm(Sp, Dp, Dsp, Np, Sm, Dm, rg, cg, w, k0, eps_in, simplified=False):
+    """Burton-Miller off-diagonal entry: row group rg (0: exterior eq., 1: interior
+    eq.), column group cg (0: u, 1: q); exterior kernel values Sp..Np, interior Sm, Dm."""
+    a = 1j / k0
+    ext = np.where(cg == 0, Dp + a * Np, -EPS_OUT * (Sp + a * Dsp))
+    inner = 0.0 if simplified else np.where(cg == 0, Dm, -eps_in * Sm)
+    return np.where(rg == 0, ext, inner) * w
+
+
+def _kvals(xt, nt, xs, ns, k):
+    return kernel_values(xt, nt, xs, ns, k)
+
+
+def entries(ix, k0, rows, cols, form="omit"):
+    """A(rows, cols) for rows and cols on different inclusions: PMCHWT (Omit,
+    exterior kernel only), PMCHWT (All) or Burton-Miller (plain or simplified),
+    interior terms with the source inclusion's k- and eps-."""
     rn, rg = ix.decode(rows)
     cn, cg = ix.decode(cols)
-    S, D, Ds, N = kernel_values(ix.X[rn][:, None, :], ix.NRM[rn][:, None, :],
-                                ix.X[cn][None, :, :], ix.NRM[cn][None, :, :], k0)
-    return _combine(S, D, Ds, N, rg[:, None], cg[None, :], ix.W[cn][None, :])
+    xt, nt = ix.X[rn][:, None, :], ix.NRM[rn][:, None, :]
+    xs, ns = ix.X[cn][None, :, :], ix.NRM[cn][None, :, :]
+    w = ix.W[cn][None, :]
+    Sp, Dp, Dsp, Np = _kvals(xt, nt, xs, ns, k0)
+    if form == "omit":
+        return _combine(Sp, Dp, Dsp, Np, rg[:, None], cg[None, :], w)
+    jin = ix.incl_of_node(cn)
+    out = np.zeros((len(rn), len(cn)), dtype=np.complex128)
+    for j in np.unique(jin):          # interior terms: the source inclusion's k- and eps-
+        sel = jin == j
+        kin, ein = ix.k_in[j], ix.eps_in[j]
+        if form == "all":
+            Sm, Dm, Dsm, Nm = _kvals(xt, nt, xs[:, sel], ns[:, sel], kin)
+            out[:, sel] = (_combine(Sp[:, sel], Dp[:, sel], Dsp[:, sel], Np[:, sel], rg[:, None], cg[None, sel],
+                                    w[:, sel])
+                           + _combine(Sm, Dm, Dsm, Nm, rg[:, None], cg[None, sel], w[:, sel], ein))
+        elif form in ("bm", "bm_simplified"):
+            Sm, Dm, _, _ = _kvals(xt, nt, xs[:, sel], ns[:, sel], kin)
+            out[:, sel] = _combine_bm(Sp[:, sel], Dp[:, sel], Dsp[:, sel], Np[:, sel], Sm, Dm, rg[:, None],
+                                      cg[None, sel], w[:, sel], k0, ein, form == "bm_simplified")
+        else:
+            raise ValueError(form)
+    return out
 
 
-def proxy_row_block(ix, k0, rows, box):
-    """Rows of the box against the proxy boundary's 2p densities (q then u)."""
+def _box_interior(ix, box):
+    """k- and eps- of the box's inclusions (the interior proxy family of PMCHWT
+    (All) and Burton-Miller assumes one interior medium per box)."""
+    j = box["leaves"][0]
+    return ix.k_in[j], ix.eps_in[j]
+
+
+def proxy_row_block(ix, k0, rows, box, form="omit"):
+    """Rows of the box against the proxy boundary's densities: Omit 2p (q then
+    u, exterior kernel); All 4p (the exterior family, then the same with the
+    interior kernel); Burton-Miller 2p (u then q, the proxy circle treated as an
+    inclusion of the box's interior medium)."""
     px, pn, pw = tr.proxy_points(box)
     p = len(pw)
     rn, rg = ix.decode(rows)
-    S, D, Ds, N = kernel_values(ix.X[rn][:, None, :], ix.NRM[rn][:, None, :],
-                                px[None, :, :], pn[None, :, :], k0)
+    xt, nt = ix.X[rn][:, None, :], ix.NRM[rn][:, None, :]
+    w = np.concatenate([pw, pw])[None, :]
+    cg = np.repeat([0, 1], p)[None, :]
+    two = lambda vals: [np.concatenate([a, a], 1) for a in vals]
+    Sp, Dp, Dsp, Np = two(kernel_values(xt, nt, px[None, :, :], pn[None, :, :], k0))
+    if form == "omit":
+        return _combine(Sp, Dp, Dsp, Np, rg[:, None], cg, w)
+    kin, ein = _box_interior(ix, box)
+    Sm, Dm, Dsm, Nm = two(kernel_values(xt, nt, px[None, :, :], pn[None, :, :], kin))
+    if form == "all":
+        return np.concatenate([_combine(Sp, Dp, Dsp, Np, rg[:, None], cg, w),
+                               _combine(Sm, Dm, Dsm, Nm, rg[:, None], cg, w, ein)], 1)
+    return _combine_bm(Sp, Dp, Dsp, Np, Sm, Dm, rg[:, None], cg, w, k0, ein, form == "bm_simplified")
+
+
+def proxy_col_block(ix, k0, box, cols, form="omit"):
+    """The proxy boundary's equations against the box's columns (the same
+    families as proxy_row_block, the proxy circle as the target inclusion)."""
+    px, pn, _ = tr.proxy_points(box)
+    p = len(px)
+    cn, cg = ix.decode(cols)
+    xs, ns = ix.X[cn][None, :, :], ix.NRM[cn][None, :, :]
+    w = ix.W[cn][None, :]
+    rg = np.repeat([0, 1], p)[:, None]
+    two = lambda vals: [np.concatenate([a, a], 0) for a in vals]
+    Sp, Dp, Dsp, Np = two(kernel_values(px[:, None, :], pn[:, None, :], xs, ns, k0))
+    if form == "omit":
+        return _combine(Sp, Dp, Dsp, Np, rg, cg[None, :], w)
+    jin = ix.incl_of_node(cn)
+    if form == "all":
+        parts = []
+        out_m = np.zeros((2 * p, len(cn)), dtype=np.complex128)
+        for j in np.unique(jin):
+            sel = jin == j
+            Sm, Dm, Dsm, Nm = two(kernel_values(px[:, None, :], pn[:, None, :], xs[:, sel], ns[:, sel], ix.k_in[j]))
+            out_m[:, sel] = _combine(Sm, Dm, Dsm, Nm, rg, cg[None, sel], w[:, sel], ix.eps_in[j])
+        return np.concatenate([_combine(Sp, Dp, Dsp, Np, rg, cg[None, :], w), out_m], 0)
+    out = np.zeros((2 * p, len(cn)), dtype=np.complex128)
+    for j in np.unique(jin):
+        sel = jin == j
+        Sm, Dm, _, _ = two(kernel_values(px[:, None, :], pn[:, None, :], xs[:, sel], ns[:, sel], ix.k_in[j]))
+        out[:, sel] = _combine_bm(Sp[:, sel], Dp[:, sel], Dsp[:, sel], Np[:, sel], Sm, Dm, rg, cg[None, sel],
+                                  w[:, sel], k0, ix.eps_in[j], form == "bm_simplified")
+    return out
+
+
+def heldout_row_block(ix, k0, rows, box):
+    """Rows of the box against the held-out ring's densities (q then u)."""
+    px, pn, pw = tr.heldout_points(box)
+    p = len(pw)
+    rn, rg = ix.decode(rows)
+    S, D, Ds, N = kernel_values(ix.X[rn][:, None, :], ix.NRM[rn][:, None, :], px[None, :, :], pn[None, :, :], k0)
     S, D, Ds, N = (np.concatenate([a, a], 1) for a in (S, D, Ds, N))
     cg = np.repeat([0, 1], p)[None, :]
     return _combine(S, D, Ds, N, rg[:, None], cg, np.concatenate([pw, pw])[None, :])
 
 
-def proxy_col_block(ix, k0, box, cols):
-    """The proxy boundary's 2p equations (u-eq then q-eq) against the box's columns."""
-    px, pn, _ = tr.proxy_points(box)
+def heldout_col_block(ix, k0, box, cols):
+    """The held-out ring's equations (u-eq then q-eq) against the box's columns."""
+    px, pn, _ = tr.heldout_points(box)
     p = len(px)
     cn, cg = ix.decode(cols)
-    S, D, Ds, N = kernel_values(px[:, None, :], pn[:, None, :],
-                                ix.X[cn][None, :, :], ix.NRM[cn][None, :, :], k0)
+    S, D, Ds, N = kernel_values(px[:, None, :], pn[:, None, :], ix.X[cn][None, :, :], ix.NRM[cn][None, :, :], k0)
     S, D, Ds, N = (np.concatenate([a, a], 0) for a in (S, D, Ds, N))
     rg = np.repeat([0, 1], p)[:, None]
     return _combine(S, D, Ds, N, rg, cg[None, :], ix.W[cn][None, :])
 
 
+def id_heldout_error(H, perm, k, T):
+    """Relative error ||H[:, J] - H[:, S] T||_F / ||H||_F of an ID (skeleton S =
+    perm[:k], the rest J = perm[k:], T = R11^{-1} R12) on a held-out block H
+    whose columns are the ID's candidates (no counterpart in the paper: the
+    a posteriori check of a proxy count)."""
+    E = H[:, perm[k:]] - H[:, perm[:k]] @ T
+    return float(np.linalg.norm(E) / max(np.linalg.norm(H), 1e-300))
+
+
 def factor(prob, opts):
+    """opts: tol, proxy_factor, proxy_points, proxy_scale, proxy_check and
+    formulation ("omit" (default), "all", "bm", "bm_simplified").  PMCHWT
+    (All) and Burton-Miller need the interior kernel in the proxies too: the
+    closed-form proxy count then uses the largest wavenumber."""
+    form = opts.get("formulation", "omit")
+    if form not in FORMS:
+        raise ValueError(form)
     nds = all_nodes(prob)
     ix = _Index(prob, nds)
     k0 = float(prob["k_out"])
     tol = float(opts["tol"])
+    if form != "omit":
+        opts = dict(opts, k_rule=max([k0] + [abs(complex(inc["k_in"]).real) for inc in prob["inclusions"]]))
     tree = tr.build(prob, nds, opts)
     L = tree["L"]
     levels = tree["levels"]
@@ -121,7 +241,8 @@ def factor(prob, opts):
         j = box["leaves"][0]
         rows = off[j] + np.arange(2 * ix.n[j])
         grp = np.repeat([0, 1], ix.n[j])
-        D = self_block(nds[j], k0, prob["inclusions"][j]["k_in"], EPS_OUT, eps_in(prob, j))
+        blk = bm_self_block if form.startswith("bm") else self_block
+        D = blk(nds[j], k0, prob["inclusions"][j]["k_in"], EPS_OUT, eps_in(prob, j))
         return rows, grp, rows.copy(), grp.copy(), D
 
     def merge(lev, box):
@@ -138,7 +259,7 @@ def factor(prob, opts):
                 if a == b:
                     D[ro[a]:ro[a + 1], ro[b]:ro[b + 1]] = da["At"]
                 else:
-                    D[ro[a]:ro[a + 1], ro[b]:ro[b + 1]] = entries(ix, k0, da["srows"], db["scols"])
+                    D[ro[a]:ro[a + 1], ro[b]:ro[b + 1]] = entries(ix, k0, da["srows"], db["scols"], form)
         return rows, rgrp, cols, cgrp, D
 
     for lev in range(L, 0, -1):
@@ -154,12 +275,12 @@ def factor(prob, opts):
             ids = {}
             for g in (0, 1):
                 rpos = np.nonzero(rgrp == g)[0]
-                Mr = np.concatenate([entries(ix, k0, rows[rpos], near_cols),
-                                     proxy_row_block(ix, k0, rows[rpos], box)], 1)
+                Mr = np.concatenate([entries(ix, k0, rows[rpos], near_cols, form),
+                                     proxy_row_block(ix, k0, rows[rpos], box, form)], 1)
                 ids["r", g] = (rpos, cp.CPQR(Mr.T, tol))
                 cpos = np.nonzero(cgrp == g)[0]
-                Mc = np.concatenate([entries(ix, k0, near_rows, cols[cpos]),
-                                     proxy_col_block(ix, k0, box, cols[cpos])], 0)
+                Mc = np.concatenate([entries(ix, k0, near_rows, cols[cpos], form),
+                                     proxy_col_block(ix, k0, box, cols[cpos], form)], 0)
                 ids["c", g] = (cpos, cp.CPQR(Mc, tol))
             kg = []
             for g in (0, 1):
@@ -168,6 +289,18 @@ def factor(prob, opts):
                 fr.extend(k)
                 fc.extend(k)
                 kg.append(k)
+            check = None
+            if opts.get("proxy_check"):
+                # held-out ring check of every ID: rows (resp. columns) of the box
+                # against the held-out ring, interpolated through the ID
+                check = 0.0
+                for g in (0, 1):
+                    rpos, f = ids["r", g]
+                    H = heldout_row_block(ix, k0, rows[rpos], box).T
+                    check = max(check, id_heldout_error(H, f.perm, kg[g], cp.interp_matrix(f.R, kg[g])))
+                    cpos, f = ids["c", g]
+                    H = heldout_col_block(ix, k0, box, cols[cpos])
+                    check = max(check, id_heldout_error(H, f.perm, kg[g], cp.interp_matrix(f.R, kg[g])))
             kb = sum(kg)
             Lm = np.zeros((len(rows), kb), dtype=np.complex128)
             Rm = np.zeros((kb, len(cols)), dtype=np.complex128)
@@ -176,15 +309,21 @@ def factor(prob, opts):
             for g in (0, 1):
                 k = kg[g]
                 rpos, f = ids["r", g]
-                perm, T = f.perm, cp.interp_matrix(f.R, k)
-                Lm[rpos[perm[:k]], o + np.arange(k)] = 1.0
-                Lm[np.ix_(rpos[perm[k:]], o + np.arange(k))] = T.T
+                perm = f.perm
+                # an exactly zero ID input (no far field at all, e.g. the interior
+                # rows of the simplified Burton-Miller system): zero interpolation
+                if f.ref:
+                    T = cp.interp_matrix(f.R, k)
+                    Lm[rpos[perm[:k]], o + np.arange(k)] = 1.0
+                    Lm[np.ix_(rpos[perm[k:]], o + np.arange(k))] = T.T
                 srows.append(rows[rpos[perm[:k]]])
                 srgrp.append(np.full(k, g))
                 cpos, f = ids["c", g]
-                perm, T = f.perm, cp.interp_matrix(f.R, k)
-                Rm[o + np.arange(k), cpos[perm[:k]]] = 1.0
-                Rm[np.ix_(o + np.arange(k), cpos[perm[k:]])] = T
+                perm = f.perm
+                if f.ref:
+                    T = cp.interp_matrix(f.R, k)
+                    Rm[o + np.arange(k), cpos[perm[:k]]] = 1.0
+                    Rm[np.ix_(o + np.arange(k), cpos[perm[k:]])] = T
                 scols.append(cols[cpos[perm[:k]]])
                 scgrp.append(np.full(k, g))
                 o += k
@@ -199,7 +338,8 @@ def factor(prob, opts):
                              "scols": np.concatenate(scols), "scgrp": np.concatenate(scgrp),
                              "kg": kg, "skel": {key: (v[0], v[1].perm[:v[1].j].copy(), v[1].rank)
                                                  for key, v in ids.items()},
-                             "margin": min(min(v[1].margin_pivot, v[1].margin_rank) for v in ids.values())}
+                             "margin": min(min(v[1].margin_pivot, v[1].margin_rank) for v in ids.values()),
+                             "check": check}
             ranks_lev.append(kg)
         stats["ranks"][lev] = ranks_lev
     root = levels[0][0]
@@ -209,15 +349,25 @@ def factor(prob, opts):
         rows, _, cols, _, Droot = merge(0, root)
     stats["K"] = Droot.shape[0]
     return {"L": L, "tree": tree, "data": data, "root_lu": sla.lu_factor(Droot),
-            "root_rows": rows, "root_cols": cols, "N": int(off[-1]), "stats": stats}
+            "root_rows": rows, "root_cols": cols, "N": int(off[-1]), "stats": stats, "form": form, "prob": prob}
 
 
 def solve(fac, F):
-    """phi = A^{-1} F (F: 2N x nrhs) through the compressed factorization."""
+    """phi = A^{-1} F (F: 2N x nrhs) through the compressed factorization.
+    F is the PMCHWT right-hand side [-u^I; -q^I] per inclusion and phi is
+    returned as [q; u] per inclusion for every formulation (Burton-Miller maps
+    F to its own right-hand side and reorders its [u; q] unknowns)."""
     F = np.asarray(F, dtype=np.complex128)
     vec = F.ndim == 1
     if vec:
         F = F[:, None]
+    if fac.get("form", "omit").startswith("bm"):
+        x = _solve_system(fac, bm_rhs(fac["prob"], F))
+        return _ret(bm_to_pmchwt_order(fac["prob"], x), vec)
+    return _ret(_solve_system(fac, F), vec)
+
+
+def _solve_system(fac, F):
     L, data, levels = fac["L"], fac["data"], fac["tree"]["levels"]
     up = {}
     for lev in range(L, 0, -1):
@@ -231,7 +381,7 @@ def solve(fac, F):
             ft = d["At"] @ (d["R"] @ g)
             up[lev, bi] = (g, ft)
     if L == 0:
-        return _ret(sla.lu_solve(fac["root_lu"], F[fac["root_rows"]]), vec)
+        return sla.lu_solve(fac["root_lu"], F[fac["root_rows"]])
     froot = np.concatenate([up[1, c][1] for c in levels[0][0]["children"]])
     x = {(0, 0): sla.lu_solve(fac["root_lu"], froot)}
     phi = np.zeros((fac["N"], F.shape[1]), dtype=np.complex128)
@@ -250,7 +400,7 @@ def solve(fac, F):
                 x[lev, c] = xc
                 if lev == L:
                     phi[d["cols"]] = xc
-    return _ret(phi, vec)
+    return phi
 
 
 def _ret(a, vec):

@@ -10,7 +10,9 @@ Choices where the paper is silent:
   * r_cell = largest distance from the box centre to any node of the box's
     inclusions; the proxy circle has radius R_p = f r_cell (f = 1.5) and p
     equispaced points, p = opts["proxy_points"] if positive, otherwise
-    p = max(32, 8 ceil((2 k0 R_p + c)/8)), c = ceil(ln(1/tol)/ln f);
+    p = max(32, 8 ceil((2 k0 R_p + c)/8)), c = ceil(ln(1/tol)/ln f); with
+    opts["proxy_scale"] = s != 1 the count is max(16, 8 ceil(s p / 8)) (the
+    rule's count stays in box["p_rule"]);
   * near(b) = edge-adjacent boxes of the same level, plus every box that has a
     node closer than R_p to b's centre (so all far nodes lie outside the
     proxy circle), in Morton order;
@@ -43,7 +45,7 @@ def build(prob, nds, opts):
     L = 0 if side <= 1 else int(math.ceil(math.log2(side)))
     factor = float(opts.get("proxy_factor", 1.5))
     tol = float(opts["tol"])
-    k0 = float(prob["k_out"])
+    k0 = float(opts.get("k_rule", prob["k_out"]))   # the largest wavenumber the proxies must resolve
     levels = {}
     # leaves
     keys = [(int(a), int(b)) for a, b in ij]
@@ -72,6 +74,12 @@ def build(prob, nds, opts):
             pp = int(opts.get("proxy_points", 0) or 0)
             if pp <= 0:
                 pp = max(32, 8 * math.ceil((2 * k0 * b["R_p"] + ctol) / 8))
+                b["p_rule"] = pp
+                pscale = float(opts.get("proxy_scale", 1.0) or 1.0)
+                if pscale != 1.0:
+                    pp = max(16, 8 * math.ceil(pscale * pp / 8))
+            else:
+                b["p_rule"] = pp
             b["p"] = pp
         for bi, b in enumerate(boxes):
             near = []
@@ -89,6 +97,18 @@ def build(prob, nds, opts):
                     near.append(bj)
             b["near"] = near
     return {"L": L, "levels": levels, "origin": origin}
+
+
+def heldout_points(box):
+    """The held-out ring of the proxy adequacy check: as many points as the
+    proxy circle on the same circle, turned by half their spacing (the
+    midpoints between proxy points)."""
+    p = box["p"]
+    th = 2 * math.pi * (np.arange(p) + 0.5) / p
+    nrm = np.stack([np.cos(th), np.sin(th)], -1)
+    x = box["center"] + box["R_p"] * nrm
+    w = np.full(p, 2 * math.pi * box["R_p"] / p)
+    return x, nrm, w
 
 
 def proxy_points(box):

@@ -10,8 +10,8 @@ from paper_2603_09381_gb300 import workloads as wl
 ANG = math.radians(30.0)
 
 
-def _mie_error(prob, angle=ANG):
-    phi = dense.solve(prob, [angle])[:, 0]
+def _mie_error(prob, angle=ANG, formulation="omit"):
+    phi = dense.solve(prob, [angle], formulation)[:, 0]
     k0 = prob["k_out"]
     inc0 = prob["inclusions"][0]
     k1, a = inc0["k_in"], inc0["prm"][0]
@@ -83,3 +83,25 @@ def test_uneven_node_counts_multipole():
         inc["n"] = n
     assert dense.offsets(prob)[-1] == 2 * (80 + 96 + 112 + 128)
     assert _mie_error(prob, angle=1.1) < 1e-10
+
+
+@pytest.mark.parametrize("n,bound", [(64, 6e-10), (96, 1e-10)])
+def test_burton_miller_matches_the_multipole_solution(n, bound):
+    """The Burton-Miller system (eq. bm_bie: alpha = i/k+, the +-1/2 jump terms
+    of G = (i/4) H0, unknowns [u; q], right-hand side [-(u^I + alpha q^I); 0])
+    solves the same 2 x 2 disk problem: a wrong sign of a jump term or of
+    alpha would miss the Foldy-Lax solution by O(1)."""
+    assert _mie_error(wl.circle_grid(2, 2, n=n), formulation="bm") < bound
+    assert _mie_error(wl.circle_grid(1, 1, n=64), formulation="bm") < 1e-12
+
+
+def test_burton_miller_rhs_map_and_unknown_order():
+    prob = wl.circle_grid(2, 1, n=16)
+    f = np.arange(64) + 1j * np.arange(64)[::-1]
+    b = dense.bm_rhs(prob, f)
+    a = 1j / prob["k_out"]
+    assert np.allclose(b[:16], f[:16] + a * f[16:32]) and not b[16:32].any()
+    assert np.allclose(b[32:48], f[32:48] + a * f[48:64]) and not b[48:].any()
+    x = np.arange(64.0)
+    y = dense.bm_to_pmchwt_order(prob, x)
+    assert np.array_equal(y[:16], x[16:32]) and np.array_equal(y[16:32], x[:16])

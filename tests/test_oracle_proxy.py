@@ -91,3 +91,28 @@ def test_loose_threshold_keeps_a_nonsingular_factorization():
     assert 8 <= fac["stats"]["K"] < 64
     x = proxy.solve(fac, dense.plane_wave(prob, 0.3))
     assert np.all(np.isfinite(x)) and _rel(x, dense.solve(prob, [0.3])[:, 0]) < 1.0
+
+
+@pytest.mark.parametrize("form", ["all", "bm"])
+def test_other_formulations_match_their_dense_solve(form):
+    """PMCHWT (All) and Burton-Miller through the proxy solver: the proxies
+    carry the interior kernel too (All: a second density family; BM: its own
+    entries on the proxy circle), so the compressed solve reproduces the
+    formulation's dense solve: exactly with every index kept, within the
+    threshold when it compresses."""
+    prob, opts, angs = wl.config_fp64_small()
+    F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
+    fac = proxy.factor(prob, dict(opts, formulation=form))
+    assert _rel(proxy.solve(fac, F), dense.solve(prob, angs, form)) < 1e-12
+    stars = wl.star_grid(2, 2, n=128, seed=1, k_out=5.0, k_ratio=5 ** 0.5)
+    fac = proxy.factor(stars, {"tol": 1e-10, "formulation": form})
+    assert fac["stats"]["K"] < fac["N"]
+    F = np.stack([dense.plane_wave(stars, a) for a in angs], 1)
+    assert _rel(proxy.solve(fac, F), dense.solve(stars, angs, form)) < 30 * 1e-10
+
+
+def test_simplified_burton_miller_compressed_block_is_singular():
+    """Sec. 3: without the off-diagonal interior terms the interior rows see no
+    far field, their interpolation vanishes and R A^{-1} L is singular."""
+    with pytest.raises(proxy.SingularError):
+        proxy.factor(wl.circle_grid(2, 2), {"tol": 1e-10, "formulation": "bm_simplified"})
