@@ -107,23 +107,30 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-WORKLOADS = {"star16": 16, "star8": 8, "star4": 4}
+WORKLOADS = {"star16": 16, "star8": 8, "star4": 4, "fourier64": 64}
 
 
 def workload(name="star16"):
     """The 16x16 star grid (default); star8 / star4 are smaller blocks of the same
-    recipe, used only for profiler captures."""
+    recipe, used only for profiler captures; fourier64 is the 64x64 grid of
+    random smooth shapes (N = 1,048,576, k0 = 5, tol 1e-9)."""
     from paper_2603_09381_gb300 import workloads as wl
+    if name == "fourier64":
+        return wl.config_fourier64()
     nx = WORKLOADS[name]
     prob, opts, angs = wl.config_star16(nx, nx)
     return prob, opts, angs
 
 
-def _workload_config(nx, N, levels, precision, ws):
+def _workload_config(nx, N, levels, precision, ws, name="star"):
     """The config object of the bench line; the reference arm reports the same one."""
-    return {"workload": f"{nx}x{nx} stars r=0.4(1+0.2cos5t), spacing 1, k0=2pi*20/16, k1=2k0, n=128, N={N}, "
-                        f"tol 1e-10, {levels} levels, 8 plane-wave RHS",
-            "precision": precision,
+    if name == "fourier64":
+        desc = (f"{nx}x{nx} random smooth shapes r=0.4(1+sum a_m cos(m t+phi_m)), a_m~U(0,0.04), spacing 1, k0=5, "
+                f"k1/k0~U(1.5,3), n=128, N={N}, tol 1e-9, {levels} levels, 8 plane-wave RHS")
+    else:
+        desc = (f"{nx}x{nx} stars r=0.4(1+0.2cos5t), spacing 1, k0=2pi*20/16, k1=2k0, n=128, N={N}, "
+                f"tol 1e-10, {levels} levels, 8 plane-wave RHS")
+    return {"workload": desc, "precision": precision,
             "l2": "inputs larger than L2 (factor working set > 1 GB)", "parallelism": f"replicas{ws}"}
 
 
@@ -151,7 +158,7 @@ def run_reference(args):
         return 0
     from paper_2603_09381_gb300 import workloads as wl
     name = getattr(args, "workload", "star16")
-    if name not in WORKLOADS:
+    if name not in WORKLOADS or name == "fourier64":
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the star-grid workloads only"}),
               flush=True)
         return 0
@@ -503,7 +510,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+c128" if precision == pm.PM_MIXED else "c128",
             "data": "synthetic",
-            "config": _workload_config(WORKLOADS[args.workload], N, st["levels"], args.precision, ws),
+            "config": _workload_config(WORKLOADS[args.workload], N, st["levels"], args.precision, ws, args.workload),
             "refinement_confirm": "fp64" if args.fp64_confirm else "float-float folded into FP64 every 16 columns",
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
             "refinement": info,

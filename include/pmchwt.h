@@ -65,7 +65,12 @@ typedef struct {
 } pm_inclusion;
 
 /* m inclusions on a grid of spacing `spacing` (paper Sec. 4: inclusions on a
- * regular grid, each one a leaf cell).  k_out = k^+ = omega (eps^+ = 1). */
+ * regular grid, each one a leaf cell), or with spacing = 0 anywhere (Sec.
+ * 4.4's general arrangements): the quadtree then covers the bounding square
+ * of the centres, deep enough (up to 20 levels) for one centre per finest
+ * cell, a leaf's proxy circle around its inclusion and a parent's around its
+ * cell; the near lists keep every inclusion with a node inside a box's proxy
+ * circle.  Inclusions must not overlap.  k_out = k^+ = omega (eps^+ = 1). */
 typedef struct {
   int32_t m;
   const pm_inclusion* inc;
@@ -124,12 +129,42 @@ typedef struct pm_factor pm_factor;
  * max_refine: PM_MIXED: refinement steps at most (0 -> 10); not reaching
  *      refine_tol returns PM_ERR_NOT_CONVERGED.
  * low_tol: PM_MIXED: ID threshold of the complex64 levels (0 -> 5e-6).
- * rank_model: NULL, or a trained rank predictor on the device (float32:
- *      PM_MLP_NPARAM weights, then 8 feature means and 8 feature scales); the
- *      CPQR of every level then runs up to the median predicted rank before its
- *      first rank check (host synchronisation) instead of checking every 16
- *      steps; IDs whose rank exceeds the prediction continue under the regular
- *      checks, so the factorization is the same with or without it.
+ * rank_model: NULL, or a trained predictor on the device (float32:
+ *      PM_MLP_NPARAM weights, then 8 feature means and 8 feature scales) whose
+ *      two outputs per box and index group are the ID rank / n_g and the
+ *      fraction of the rule's proxy count the box needs.  Ranks: the CPQR of
+ *      every level runs up to the median predicted rank before its first rank
+ *      check (host synchronisation) instead of checking every 16 steps; IDs
+ *      whose rank exceeds the prediction continue under the regular checks.
+ *      Proxy counts (when proxy_points = 0): each box gets
+ *      max(16, 8 ceil(s p_rule / 8)) points, s = min(1, max(0.25, predicted
+ *      fraction + 0.1)); in PM_FP64 every box below the rule is judged by the
+ *      held-out check below, and a box that fails is redone with the rule's
+ *      count (pm_stats.proxy_fallbacks); in PM_MIXED the refinement against
+ *      the complex128 operator judges the result (the check runs only with
+ *      PM_FLAG_PROXY_CHECK).
+ * proxy_scale: 0 or 1 -> the rule's proxy count; s in (0, 1) -> every box
+ *      gets max(16, 8 ceil(s p_rule / 8)) points (proxy_points = 0 only).
+ *      With PM_FLAG_PROXY_CHECK every ID is then checked a posteriori on a
+ *      held-out ring: the box's proxy count of points on the proxy circle,
+ *      turned by half their spacing; with H the kernel block between that
+ *      ring and the ID's candidates, the check passes when
+ *      ||H_J - H_S T||_F <= 200 tol ||H||_F (S the skeleton, J the rest,
+ *      T the interpolation matrix).  No counterpart in the paper.
+ * formulation: PM_FORM_* (0: PMCHWT (Omit)).  PMCHWT (All) and Burton-Miller
+ *      need proxies for the interior kernel as well: PMCHWT (All) uses two
+ *      families of proxy densities (exterior and interior kernel), Burton-
+ *      Miller its own entries with the proxy circle as an inclusion; the
+ *      closed-form proxy count then uses max(k+, k-).  These run in PM_FP64
+ *      with one real interior wavenumber for all inclusions (else
+ *      PM_ERR_UNSUPPORTED).  For every formulation pm_solve takes the PMCHWT
+ *      right-hand side [-u^I; -q^I] and returns [q; u] per inclusion
+ *      (Burton-Miller maps it to [-(u^I + alpha q^I); 0] and reorders its
+ *      [u; q] unknowns).
+ * scratch_gb: device memory for the ID inputs of one step of the levels
+ *      (0 -> 35% of the memory free when the step starts).  A level whose
+ *      boxes need more runs in consecutive chunks of boxes, each within the
+ *      budget (pm_stats.level_chunks); results do not depend on the chunks.
  * debug_flags: 0 in normal use.  Host-side fault injection for tests of the
  *      failure paths (no counterpart in the paper); every injected fault is a
  *      plain write of zeros or a changed host decision, never a device fault:
@@ -156,7 +191,17 @@ typedef struct {
   double low_tol;
   const float* rank_model;
   uint32_t debug_flags;
+  double proxy_scale;
+  int32_t formulation;
+  double scratch_gb;
 } pm_factor_opts;
+/* Boundary integral formulations (paper Sec. 2.1): PMCHWT (Omit), eq.
+ * pmchwt_omit_bie, the default; PMCHWT (All), eq. pmchwt_all_bie (interior
+ * potentials kept in the off-diagonal blocks); Burton-Miller, eq. bm_bie
+ * (alpha = i/k+), and its simplified form without the off-diagonal interior
+ * terms, which the fast solver cannot use: its R A^{-1} L is singular
+ * (Sec. 3), reported as PM_ERR_SINGULAR. */
+enum { PM_FORM_OMIT = 0, PM_FORM_ALL = 1, PM_FORM_BM = 2, PM_FORM_BM_SIMPLIFIED = 3 };
 enum {
   PM_DEBUG_SINGULAR_BLOCK = 1,
   PM_DEBUG_SINGULAR_COMPRESSED = 2,
@@ -186,6 +231,10 @@ typedef struct {
   double ms_level[16];      /* wall time of each compressed level (index = level) */
   int32_t graph_captures;   /* solve graphs captured so far (one per kind and right-hand-side count) */
   int32_t graph_launches;   /* solve graph replays so far */
+  int32_t proxy_checked;    /* boxes whose IDs ran the held-out proxy check */
+  int32_t proxy_fallbacks;  /* boxes redone with the rule's proxy count after failing it */
+  int64_t id_rows;          /* sum over all IDs of their input rows (near + proxy), the work measure of the IDs */
+  int32_t level_chunks;     /* chunks of boxes the levels ran in (one per level when the scratch fits) */
 } pm_stats;
 
 /* Build node geometry on the device (paper Sec. 2.2) and the quadtree
@@ -270,6 +319,27 @@ pm_status pm_matrix_entries(const pm_geometry* g, const int32_t* rows, int32_t M
  * (paper Sec. 2.2: Kress log-split quadrature for S, D, D*; Maue's form of N). */
 pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out);
 
+/* Fields represented by a boundary solution phi (N x nrhs, [q_j; u_j] per
+ * inclusion, as pm_solve returns it): Green's representation over all
+ * boundaries with the trapezoid rule, u^s(x) = sum_j int [dG/dn_y u -
+ * G eps+ q] ds, G = (i/4) H0(k+ |x - y|) (the incident wave adds nothing
+ * outside the inclusions).  No counterpart in the paper's text, which uses
+ * the boundary solutions only; the paper's Sec. 4.3 frequency study reuses
+ * them.
+ * pm_far_field: the far-field pattern u_inf(xhat), u^s(x) = e^{i k r}/sqrt(r)
+ *      (u_inf + O(1/r)), at directions xhat = (cos a, sin a) for the ndir
+ *      host angles: out[d + c ndir].
+ * pm_scattered_field: u^s at npts host points (xy: x, y pairs), which must
+ *      lie outside the inclusions and a few node spacings from every
+ *      boundary for trapezoid accuracy: out[p + c npts].
+ * phi and out are device pointers of the geometry's device if on_device = 1,
+ * else host buffers.  Errors: PM_ERR_INVALID_ARG (NULL, sizes, non-finite
+ * directions or points, host pointer for on_device = 1), PM_ERR_CUDA. */
+pm_status pm_far_field(const pm_geometry* g, const pm_c64* phi, int32_t nrhs, int32_t on_device, const double* angles,
+                       int32_t ndir, pm_c64* out);
+pm_status pm_scattered_field(const pm_geometry* g, const pm_c64* phi, int32_t nrhs, int32_t on_device,
+                             const double* xy, int32_t npts, pm_c64* out);
+
 /* Per-kernel timing of a factorization made with flags & PM_FLAG_PROFILE
  * (no counterpart in the paper; measurement aid).  CUDA events bracket every
  * launch on the factorization's stream.  `work` is the algorithmic work of
@@ -292,7 +362,8 @@ enum {
   PM_FLAG_FF_CONFIRM = 16,
   PM_FLAG_FP64_CONFIRM = 32,
   PM_FLAG_NO_AUTOTUNE = 64,
-  PM_FLAG_NO_GRAPHS = 128
+  PM_FLAG_NO_GRAPHS = 128,
+  PM_FLAG_PROXY_CHECK = 256
 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 
@@ -306,8 +377,15 @@ pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap
  * the host arrays of pm_factor_rank_data / pm_mlp_train's X, T and
  * loss_history are device pointers; dtype 0 = float32, 1 = float64. */
 enum { PM_MLP_NPARAM = 4866 };
-/* Training samples recorded by a factorization: X (count x 8), T (count x 2), host. */
+/* Training samples recorded by a factorization, two per box (index groups
+ * 0, 1), in level order L..1 and Morton order: X (count x 8) the features,
+ * T (count x 2) = (max(row rank, column rank) / n_g, proxy count used / the
+ * rule's count), host buffers. */
 pm_status pm_factor_rank_data(const pm_factor* f, float* X, float* T, int32_t cap, int32_t* count);
+/* For the same samples: the held-out check's ratio ||H_J - H_S T|| /
+ * (tol ||H||) of the box (largest over its four IDs; -1 where it did not run)
+ * and whether the box was redone with the rule's proxy count (0 / 1). */
+pm_status pm_factor_proxy_data(const pm_factor* f, float* ratio, int32_t* redone, int32_t cap, int32_t* count);
 pm_status pm_mlp_forward(int32_t dtype, const void* theta, int32_t B, const void* X, void* Y, void* stream);
 /* loss (1 value) and gradient (PM_MLP_NPARAM) of a batch, overwritten. */
 pm_status pm_mlp_loss_grad(int32_t dtype, const void* theta, int32_t B, const void* X, const void* T, double lam,

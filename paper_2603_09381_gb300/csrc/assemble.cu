@@ -82,7 +82,7 @@ __global__ void k_proxy_points(const ProxyBoxDev* __restrict__ box, int nbox, Po
   while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (box[mid].point_off <= g) lo = mid; else hi = mid; }
   const ProxyBoxDev b = box[lo];
   int s = g - b.point_off;
-  double th = 2 * PI * s / b.p;
+  double th = 2 * PI * (s + b.phase) / b.p;
   double c, sn; sincos(th, &sn, &c);
   int q = off + g;
   p.x[q] = b.cx + b.R * c; p.y[q] = b.cy + b.R * sn;
@@ -165,7 +165,7 @@ __device__ __forceinline__ void kress_entries(const SelfGeo& q, double2 k, doubl
 template <typename C>
 __global__ void __launch_bounds__(256) k_self_pointwise(const InclDev* __restrict__ inc, NodesDev nd, double k0,
                                                         C* const* __restrict__ Aptr, const int* __restrict__ ldA,
-                                                        C* const* __restrict__ Cptr) {
+                                                        C* const* __restrict__ Cptr, int bm) {
   typedef typename real_of<C>::type R;
   const int j = blockIdx.y;
   const InclDev c = inc[j];
@@ -198,6 +198,24 @@ __global__ void __launch_bounds__(256) k_self_pointwise(const InclDev* __restric
   C* A = Aptr[j];
   const size_t lda = ldA[j];
   const int i = q.i, l = q.l;
+  if (bm) {
+    // Burton-Miller (eps+ = 1, alpha = i/k+): [[D+ - I/2 + alpha N+, -S+ - alpha (D*+ + I/2)],
+    // [D- + I/2, -eps- S-]]; here the pointwise part of alpha N+ (alpha k+^2 S+ o nn), the
+    // Maue part alpha diag(1/|x'|) Dt S0+ Dt follows through the middle factor alpha S0+
+    const double half = (i == l) ? 0.5 : 0.0;
+    const double2 al = make_double2(0.0, 1.0 / k0);
+    const double a0 = k0 * k0 * nn;
+    const double2 aN = zmul(al, make_double2(a0 * Sp.x, a0 * Sp.y));
+    A[i + (size_t)l * lda] = mk((R)(Dp.x - half + aN.x), (R)(Dp.y + aN.y));
+    const double2 aT = zmul(al, make_double2(Tp.x + half, Tp.y));
+    A[i + (size_t)(n + l) * lda] = mk((R)(-Sp.x - aT.x), (R)(-Sp.y - aT.y));
+    A[n + i + (size_t)l * lda] = mk((R)(Dm.x + half), (R)Dm.y);
+    const double2 eS = zmul(em, Sm);
+    A[n + i + (size_t)(n + l) * lda] = mk((R)(-eS.x), (R)(-eS.y));
+    const double2 aS = zmul(al, make_double2(Sp.x / q.spl, Sp.y / q.spl));
+    Cptr[j][i + (size_t)l * n] = mk((R)aS.x, (R)aS.y);
+    return;
+  }
   // [[-(e+ S+ + e- S-), D+ + D-], [-(D*+ + D*-), k+^2/e+ S+ o nn + k-^2/e- S- o nn (+ Maue part)]]
   const double2 eS = zmul(em, Sm);
   A[i + (size_t)l * lda] = mk((R)(-(Sp.x + eS.x)), (R)(-(Sp.y + eS.y)));
@@ -313,6 +331,69 @@ __device__ __forceinline__ float2 omit_entry<float2>(const PointsDev& P, int t, 
   return make_float2(-Him * f, Hre * f);
 }
 
+// The four trapezoid-rule kernels S, D, D*, N (times the source weight) between
+// point t and point s for wavenumber k (G = (i/4) H0(k r)).
+__device__ __forceinline__ void kernels4(const PointsDev& P, int pt, int ps, double k, double2& S, double2& D,
+                                         double2& Ds, double2& N) {
+  const double dx = P.x[pt] - P.x[ps], dy = P.y[pt] - P.y[ps];
+  const double r = sqrt(dx * dx + dy * dy);
+  const double z = k * r, w = P.w[ps];
+  double J0, Y0, J1, Y1;
+  if (z < HK_ZA) { J0 = j0(z); Y0 = y0(z); J1 = j1(z); Y1 = y1(z); }
+  else hankel01(z, J0, Y0, J1, Y1);
+  const double a = (P.nx[pt] * dx + P.ny[pt] * dy) / r, b = (P.nx[ps] * dx + P.ny[ps] * dy) / r;
+  const double nn = P.nx[pt] * P.nx[ps] + P.ny[pt] * P.ny[ps];
+  const double f = 0.25 * k * w;
+  S = make_double2(-0.25 * Y0 * w, 0.25 * J0 * w);       // (i/4) H0 w
+  D = make_double2(-Y1 * b * f, J1 * b * f);               // (ik/4) H1 b w
+  Ds = make_double2(Y1 * a * f, -J1 * a * f);              // -(ik/4) H1 a w
+  const double c0 = k * a * b, c1 = (nn - 2 * a * b) / r;
+  N = make_double2(-(c0 * Y0 + c1 * Y1) * f, (c0 * J0 + c1 * J1) * f);
+}
+
+// Entry of the PMCHWT (All), Burton-Miller or interior-family systems (FP64).
+__device__ double2 form_entry(const PointsDev& P, int t, int s, const GatherProb<double2>& g, double k) {
+  const int pt = t >> 1, rg = t & 1, ps = s >> 1, cg = s & 1;
+  const double dx = P.x[pt] - P.x[ps], dy = P.y[pt] - P.y[ps];
+  if (!(dx * dx + dy * dy > 0)) return make_double2(0, 0);
+  auto omit_like = [&](double kk, double eps) {
+    double2 S, D, Ds, N;
+    kernels4(P, pt, ps, kk, S, D, Ds, N);
+    if (rg == 0) return cg == 0 ? make_double2(-eps * S.x, -eps * S.y) : D;
+    return cg == 0 ? make_double2(-Ds.x, -Ds.y) : make_double2(N.x / eps, N.y / eps);
+  };
+  if (g.mode == GATHER_INTERIOR) return omit_like(g.k_in, g.eps_in);
+  if (g.mode == GATHER_ALL) {
+    const double2 e = omit_like(k, 1.0), i2 = omit_like(g.k_in, g.eps_in);
+    return make_double2(e.x + i2.x, e.y + i2.y);
+  }
+  // Burton-Miller
+  if (rg == 1) {
+    if (g.mode == GATHER_BM_SIMPLIFIED) return make_double2(0, 0);
+    double2 S, D, Ds, N;
+    kernels4(P, pt, ps, g.k_in, S, D, Ds, N);
+    return cg == 0 ? D : make_double2(-g.eps_in * S.x, -g.eps_in * S.y);
+  }
+  double2 S, D, Ds, N;
+  kernels4(P, pt, ps, k, S, D, Ds, N);
+  const double ia = 1.0 / k;   // alpha = i / k
+  if (cg == 0) return make_double2(D.x - ia * N.y, D.y + ia * N.x);            // D + alpha N
+  return make_double2(-(S.x - ia * Ds.y), -(S.y + ia * Ds.x));                 // -(S + alpha D*)
+}
+
+template <typename C>
+__device__ __forceinline__ C gather_entry(const PointsDev& P, int t, int s, const GatherProb<C>& g, double k);
+template <>
+__device__ __forceinline__ double2 gather_entry<double2>(const PointsDev& P, int t, int s,
+                                                         const GatherProb<double2>& g, double k) {
+  return g.mode == GATHER_OMIT ? omit_entry<double2>(P, t, s, k) : form_entry(P, t, s, g, k);
+}
+template <>
+__device__ __forceinline__ float2 gather_entry<float2>(const PointsDev& P, int t, int s, const GatherProb<float2>& g,
+                                                       double k) {
+  return omit_entry<float2>(P, t, s, k);   // the complex64 path is PMCHWT (Omit) only
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_gather(const GatherProb<C>* __restrict__ prob, const int* __restrict__ tile_off,
                                                 int nprob, PointsDev P, double k) {
@@ -327,7 +408,7 @@ __global__ void __launch_bounds__(256) k_gather(const GatherProb<C>* __restrict_
   if (i >= g.M || j >= g.N) return;
   int tc = g.trans ? g.tgt[j] : g.tgt[i];
   int sc = g.trans ? g.src[i] : g.src[j];
-  g.out[i + (size_t)j * g.ld] = omit_entry<C>(P, tc, sc, g.k != 0.0 ? g.k : k);
+  g.out[i + (size_t)j * g.ld] = gather_entry<C>(P, tc, sc, g, g.k != 0.0 ? g.k : k);
 }
 
 }  // namespace
@@ -361,11 +442,11 @@ void plane_wave_rhs(const InclDev* d_inc, NodesDev nodes, int total, double k0, 
 
 template <typename C>
 void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, double k0, C* const* d_A,
-                    const int* d_lda, C* const* d_Cm, cudaStream_t st) {
+                    const int* d_lda, C* const* d_Cm, cudaStream_t st, int bm) {
   if (m <= 0) return;
   dim3 g((maxn * maxn + 255) / 256, m);
   KPROF_BEGIN(st);
-  k_self_pointwise<C><<<g, 256, 0, st>>>(d_inc, nodes, k0, d_A, d_lda, d_Cm);
+  k_self_pointwise<C><<<g, 256, 0, st>>>(d_inc, nodes, k0, d_A, d_lda, d_Cm, bm);
   pm_launch_count_add(1);
   KPROF_END(st, kname<C>("self_pointwise", "self_pointwise32"), 0.0);
 }
@@ -396,13 +477,13 @@ void gather_assemble(const GatherProb<C>* d_prob, const int* d_tile_off, int npr
 
 template void plane_wave_rhs<double2>(const InclDev*, NodesDev, int, double, const double*, int, double2*, int, cudaStream_t);
 template void self_pointwise<double2>(const InclDev*, int, int, NodesDev, double, double2* const*, const int*,
-                                      double2* const*, cudaStream_t);
+                                      double2* const*, cudaStream_t, int);
 template void diff_matrices<double2>(int, double2*, cudaStream_t);
 template void scaled_diff<double2>(const InclDev*, int, int, NodesDev, double2* const*, cudaStream_t);
 template void gather_assemble<double2>(const GatherProb<double2>*, const int*, int, int, PointsDev, double, cudaStream_t);
 
 template void self_pointwise<float2>(const InclDev*, int, int, NodesDev, double, float2* const*, const int*,
-                                     float2* const*, cudaStream_t);
+                                     float2* const*, cudaStream_t, int);
 template void diff_matrices<float2>(int, float2*, cudaStream_t);
 template void scaled_diff<float2>(const InclDev*, int, int, NodesDev, float2* const*, cudaStream_t);
 template void gather_assemble<float2>(const GatherProb<float2>*, const int*, int, int, PointsDev, double, cudaStream_t);

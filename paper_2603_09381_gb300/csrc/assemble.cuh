@@ -32,9 +32,24 @@ struct GatherProb {        // out[i + j ld] = A(t, s): t = tgt[trans ? j : i], s
   int trans;
   double k;                // exterior wavenumber of this problem's kernels (0: the launch's k0);
                            // lets problems of different frequencies share one launch
+  int mode;                // entries (complex128 only beyond GATHER_OMIT): see GatherMode
+  double k_in, eps_in;     // interior wavenumber and eps- (real) of the interior terms
 };
 
-struct ProxyBoxDev { double cx, cy, R; int p; int point_off; };
+// Entry formulas of the gather, packed codes point*2 + group:
+//  GATHER_OMIT   PMCHWT (Omit), rows (0 u-eq, 1 q-eq) x columns (0 q, 1 u):
+//                [[-eps+ S+, D+], [-D*+, N+/eps+]]
+//  GATHER_ALL    PMCHWT (All): Omit plus [[-eps- S-, D-], [-D*-, N-/eps-]]
+//  GATHER_BM     Burton-Miller, rows (0 exterior, 1 interior eq.) x columns (0 u, 1 q):
+//                [[D+ + alpha N+, -eps+ (S+ + alpha D*+)], [D-, -eps- S-]], alpha = i/k+
+//  GATHER_BM_SIMPLIFIED  the same without the interior row (zeros)
+//  GATHER_INTERIOR  the Omit layout with the interior kernel and eps-: the
+//                interior proxy family of PMCHWT (All)
+enum GatherMode { GATHER_OMIT = 0, GATHER_ALL = 1, GATHER_BM = 2, GATHER_BM_SIMPLIFIED = 3, GATHER_INTERIOR = 4 };
+
+// p points at angles 2 pi (s + phase) / p (phase 0: the proxy circle; 0.5: the
+// held-out ring of the proxy check)
+struct ProxyBoxDev { double cx, cy, R; int p; int point_off; double phase; };
 
 void geom_nodes(const InclDev* d_inc, NodesDev nodes, int total_nodes, const InclDev* h_inc, cudaStream_t st);
 void geom_points_from_nodes(NodesDev nodes, PointsDev pts, int total_nodes, cudaStream_t st);
@@ -45,9 +60,12 @@ void plane_wave_rhs(const InclDev* d_inc, NodesDev nodes, int total_nodes, doubl
                     int nrhs, C* F, int ldf, cudaStream_t st);
 // Self blocks, pointwise part: writes the S, D, D* blocks and the k^2 S o nn term
 // of A_jj (2n x 2n, leading dim lda), and the Maue middle factor Cm (n x n).
+// bm != 0: the Burton-Miller self block (unknowns [u; q], rows [exterior;
+// interior]); the Maue middle factor is then alpha S0+ and its product goes to
+// the (exterior, u) block.  Otherwise the PMCHWT self block.
 template <typename C>
 void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, double k0, C* const* d_A,
-                    const int* d_lda, C* const* d_Cm, cudaStream_t st);
+                    const int* d_lda, C* const* d_Cm, cudaStream_t st, int bm = 0);
 // Trigonometric differentiation matrix Dt (n x n) and diag(1/|x'|) Dt for an inclusion.
 template <typename C>
 void diff_matrices(int n, C* Dt, cudaStream_t st);

@@ -20,6 +20,7 @@
 #include "cpqr.cuh"
 #include "tc_gemm.cuh"
 #include "dense_la.cuh"
+#include "field.cuh"
 #include "mlp.cuh"
 #include "operator.cuh"
 #include "prof.cuh"
@@ -73,6 +74,11 @@ struct Arena {
   }
   template <class T> T* get(size_t n) { return (T*)alloc(n * sizeof(T)); }
   void reset() { cur = 0; off = 0; }
+  size_t capacity() const {
+    size_t c = 0;
+    for (auto& b : blks) c += b.size;
+    return c;
+  }
   void release() {
     for (auto& b : blks) cudaFree(b.p);
     blks.clear();
@@ -123,6 +129,8 @@ struct Box {
   std::vector<int> children;  // indices into the level below
   double cx = 0, cy = 0, r_cell = 0, R_p = 0;
   int p = 0;
+  int p_rule = 0;        // the closed-form proxy count (or the fixed one)
+  bool locked = false;   // proxy count fixed to p_rule after a failed held-out check
   std::vector<int> near;
 };
 
@@ -144,6 +152,7 @@ struct pm_geometry {
   // quadtree (paper Sec. 3; grid cells padded to 2^L x 2^L, Morton order)
   int L = 0;
   double ox = 0, oy = 0;
+  bool general = false;   // spacing 0: an arbitrary arrangement, cells of the centres' bounding square
   std::vector<std::vector<Box>> levels;  // levels[l], l = 0..L
 
   // global index -> packed point code (node * 2 + group)
@@ -198,6 +207,9 @@ struct pm_factor {
   bool profiling = false;
   // learned rank predictor: features and adaptive ranks of every (box, group)
   std::vector<float> rank_X, rank_T;
+  // per (box, group) sample: held-out proxy check ratio (-1: not run), box redone with the rule
+  std::vector<float> proxy_ratio;
+  std::vector<int> proxy_redone;
   // mixed mode: FP64 self blocks (operator for the refinement residual)
   std::vector<double2*> self64;
   int* d_iu = nullptr;
@@ -253,22 +265,51 @@ namespace {
 
 void build_tree(pm_geometry* g, const pm_factor_opts* o) {
   // grid indices
-  double ox = 1e300, oy = 1e300;
-  for (auto& c : g->inc) { ox = std::min(ox, c.cx); oy = std::min(oy, c.cy); }
-  g->ox = ox; g->oy = oy;
-  const double s = g->spacing;
-  std::vector<int> ix(g->m), iy(g->m);
-  int side = 1;
-  std::map<std::pair<int, int>, int> seen;
-  for (int j = 0; j < g->m; ++j) {
-    ix[j] = (int)std::lround((g->inc[j].cx - ox) / s);
-    iy[j] = (int)std::lround((g->inc[j].cy - oy) / s);
-    if (ix[j] < 0 || iy[j] < 0 || ix[j] > (1 << 20) || iy[j] > (1 << 20)) fail(PM_ERR_GEOMETRY, "grid index out of range");
-    if (!seen.emplace(std::make_pair(ix[j], iy[j]), j).second) fail(PM_ERR_GEOMETRY, "two inclusions share a grid cell");
-    side = std::max(side, std::max(ix[j], iy[j]) + 1);
+  double ox = 1e300, oy = 1e300, mx = -1e300, my = -1e300;
+  for (auto& c : g->inc) {
+    ox = std::min(ox, c.cx); oy = std::min(oy, c.cy);
+    mx = std::max(mx, c.cx); my = std::max(my, c.cy);
   }
+  g->ox = ox; g->oy = oy;
+  std::vector<int> ix(g->m), iy(g->m);
   int L = 0;
-  while ((1 << L) < side) ++L;
+  if (g->general) {
+    // the centres' bounding square (side = the larger extent, widened by
+    // 1 + 2^-30) in 2^L x 2^L cells, L the smallest depth up to 20 that puts
+    // every centre in a cell of its own
+    const double ext = std::max(mx - ox, my - oy);
+    g->spacing = 1.0;
+    if (g->m > 1 && ext > 0) {
+      const double side = ext * (1.0 + std::ldexp(1.0, -30));
+      bool ok = false;
+      for (L = 1; L <= 20 && !ok; ++L) {
+        const double cell = side / (double)(1 << L);
+        std::map<std::pair<int, int>, int> seen;
+        ok = true;
+        for (int j = 0; j < g->m && ok; ++j) {
+          ix[j] = (int)std::floor((g->inc[j].cx - ox) / cell);
+          iy[j] = (int)std::floor((g->inc[j].cy - oy) / cell);
+          ok = seen.emplace(std::make_pair(ix[j], iy[j]), j).second;
+        }
+        if (ok) { g->spacing = cell; break; }
+      }
+      if (!ok) fail(PM_ERR_GEOMETRY, "inclusion centres too close to separate");
+    } else {
+      for (int j = 0; j < g->m; ++j) ix[j] = iy[j] = 0;
+    }
+  } else {
+    const double s = g->spacing;
+    int side = 1;
+    std::map<std::pair<int, int>, int> seen;
+    for (int j = 0; j < g->m; ++j) {
+      ix[j] = (int)std::lround((g->inc[j].cx - ox) / s);
+      iy[j] = (int)std::lround((g->inc[j].cy - oy) / s);
+      if (ix[j] < 0 || iy[j] < 0 || ix[j] > (1 << 20) || iy[j] > (1 << 20)) fail(PM_ERR_GEOMETRY, "grid index out of range");
+      if (!seen.emplace(std::make_pair(ix[j], iy[j]), j).second) fail(PM_ERR_GEOMETRY, "two inclusions share a grid cell");
+      side = std::max(side, std::max(ix[j], iy[j]) + 1);
+    }
+    while ((1 << L) < side) ++L;
+  }
   g->L = L;
   g->levels.assign(L + 1, {});
   std::vector<int> order(g->m);
@@ -295,17 +336,33 @@ void build_tree(pm_geometry* g, const pm_factor_opts* o) {
   (void)o;
 }
 
+// Proxy count for a fraction s of the rule's count: max(16, 8 ceil(s p / 8)).
+int proxy_count(double s, int p_rule) { return std::max(16, 8 * (int)std::ceil(s * p_rule / 8.0)); }
+
 // Proxy circles and near lists (depend on the tolerance and the proxy options).
 void plan_proxies(const pm_geometry* g, std::vector<std::vector<Box>>& levels, const pm_factor_opts* o) {
   const double f = o->proxy_factor > 0 ? o->proxy_factor : 1.5;
   const int ctol = (int)std::ceil(std::log(1.0 / o->tol) / std::log(f));
+  // PMCHWT (All) and Burton-Miller proxies carry the interior kernel too: the
+  // closed-form count resolves the largest wavenumber
+  double krule = g->k0;
+  if (o->formulation != PM_FORM_OMIT)
+    for (const auto& c : g->inc) krule = std::max(krule, c.k_in.re);
   const double s = g->spacing;
   for (int l = 0; l <= g->L; ++l) {
     const double scale = std::ldexp(1.0, g->L - l);
     auto& boxes = levels[l];
     for (auto& b : boxes) {
-      b.cx = g->ox + s * (b.bx * scale + (scale - 1) / 2.0);
-      b.cy = g->oy + s * (b.by * scale + (scale - 1) / 2.0);
+      if (!g->general) {
+        b.cx = g->ox + s * (b.bx * scale + (scale - 1) / 2.0);
+        b.cy = g->oy + s * (b.by * scale + (scale - 1) / 2.0);
+      } else if (l == g->L) {   // a leaf's proxy circle around its inclusion
+        b.cx = g->inc[b.leaves[0]].cx;
+        b.cy = g->inc[b.leaves[0]].cy;
+      } else {                  // a parent's around its cell
+        b.cx = g->ox + s * (b.bx * scale + scale / 2.0);
+        b.cy = g->oy + s * (b.by * scale + scale / 2.0);
+      }
       double r = 0;
       for (int j : b.leaves)
         for (int q = g->node_off[j]; q < g->node_off[j + 1]; ++q)
@@ -313,7 +370,13 @@ void plan_proxies(const pm_geometry* g, std::vector<std::vector<Box>>& levels, c
       b.r_cell = r;
       b.R_p = f * r;
       int p = o->proxy_points;
-      if (p <= 0) p = std::max(32, 8 * (int)std::ceil((2 * g->k0 * b.R_p + ctol) / 8.0));
+      if (p <= 0) {
+        p = std::max(32, 8 * (int)std::ceil((2 * krule * b.R_p + ctol) / 8.0));
+        b.p_rule = p;
+        if (o->proxy_scale > 0 && o->proxy_scale != 1.0) p = proxy_count(o->proxy_scale, p);
+      } else {
+        b.p_rule = p;
+      }
       b.p = p;
     }
     for (int i = 0; i < (int)boxes.size(); ++i) {
@@ -354,9 +417,10 @@ void upload_inclusions(pm_geometry* g) {
 }
 
 // Self blocks A_jj of the listed inclusions into A[i] (leading dims lda[i]).
+// bm: the Burton-Miller self blocks (the Maue product goes to the (exterior, u) block).
 template <class C>
 void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std::vector<C*>& A,
-                   const std::vector<int>& lda, Arena& scr, cudaStream_t st) {
+                   const std::vector<int>& lda, Arena& scr, cudaStream_t st, int bm = 0) {
   const int m = (int)incl.size();
   if (m == 0) return;
   std::vector<InclDev> sub(m);
@@ -381,7 +445,7 @@ void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std
   int* dlda = upload(scr, lda, st);
   C** dC = upload(scr, Cm, st);
   C** dD = upload(scr, DtS, st);
-  self_pointwise<C>(d_sub, m, maxn, g->nodes, g->k0, dA, dlda, dC, st);
+  self_pointwise<C>(d_sub, m, maxn, g->nodes, g->k0, dA, dlda, dC, st, bm);
   if (g_kprof) {
     double e = 0;
     for (auto& c : sub) e += (double)c.n * c.n;
@@ -395,7 +459,8 @@ void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std
   for (int i = 0; i < m; ++i) {
     int n = sub[i].n;
     d1[i] = GemmDesc<C>{n, n, n, Cm[i], n, dts[n], n, E[i], n, cone<C>(), czero_h<C>(), 1};
-    d2[i] = GemmDesc<C>{n, n, n, DtS[i], n, E[i], n, A[i] + n + (size_t)n * lda[i], lda[i], cone<C>(), cone<C>(), 0};
+    C* tgt = bm ? A[i] : A[i] + n + (size_t)n * lda[i];
+    d2[i] = GemmDesc<C>{n, n, n, DtS[i], n, E[i], n, tgt, lda[i], cone<C>(), cone<C>(), 0};
     off1[i + 1] = off1[i] + gemm_tiles(n, n);
     off2[i + 1] = off2[i] + gemm_tiles(n, n);
   }
@@ -408,6 +473,8 @@ void assemble_self(const pm_geometry* g, const std::vector<int>& incl, const std
 
 template <class C>
 struct GatherBatch {
+  int mode = GATHER_OMIT;          // entry formula of the products added from now on
+  double k_in = 0, eps_in = 1;     // interior wavenumber and eps- (real) of the non-Omit formulas
   std::vector<GatherProb<C>> probs;
   std::vector<int> tile_off{0};
   std::vector<int> codes;                 // all target / source lists
@@ -421,7 +488,7 @@ struct GatherBatch {
     for (int c : tgt) codes.push_back(c + code_off);
     size_t so = codes.size();
     for (int c : src) codes.push_back(c + code_off);
-    probs.push_back(GatherProb<C>{out, ld, M, N, nullptr, nullptr, trans, k});
+    probs.push_back(GatherProb<C>{out, ld, M, N, nullptr, nullptr, trans, k, mode, k_in, eps_in});
     lists.push_back({to, so});
     tile_off.push_back(tile_off.back() + gather_tiles(M, N));
   }
@@ -615,9 +682,9 @@ struct Timer {
 
 // Active sets and D_b of a parent (or the root) from its children's compressed blocks.
 // Cc: the children's arithmetic, Cp: the parent's.
+// Active sets of a parent (or the root): its children's skeletons, in order.
 template <class Cc, class Cp>
-void merge_children(pm_factor* F, const std::vector<BoxF<Cc>>& kids, const Box& box, BoxF<Cp>& bf,
-                    GatherBatch<Cp>& gb, CopyBatch<Cc, Cp>& cb, int code_off = 0) {
+void active_sets(const std::vector<BoxF<Cc>>& kids, const Box& box, BoxF<Cp>& bf) {
   bf.rows.clear(); bf.rgrp.clear(); bf.cols.clear(); bf.cgrp.clear(); bf.child_off.clear();
   for (int c : box.children) {
     bf.child_off.push_back((int)bf.rows.size());
@@ -628,6 +695,12 @@ void merge_children(pm_factor* F, const std::vector<BoxF<Cc>>& kids, const Box& 
     bf.cgrp.insert(bf.cgrp.end(), k.scgrp.begin(), k.scgrp.end());
   }
   bf.mb = (int)bf.rows.size();
+}
+
+template <class Cc, class Cp>
+void merge_children(pm_factor* F, const std::vector<BoxF<Cc>>& kids, const Box& box, BoxF<Cp>& bf,
+                    GatherBatch<Cp>& gb, CopyBatch<Cc, Cp>& cb, int code_off = 0) {
+  active_sets<Cc, Cp>(kids, box, bf);
   bf.D = F->arena.get<Cp>((size_t)std::max(bf.mb, 1) * std::max(bf.mb, 1));
   const pm_geometry* g = F->g;
   for (size_t a = 0; a < box.children.size(); ++a) {
@@ -655,7 +728,7 @@ PointsDev make_points(const pm_geometry* g, const std::vector<Box>& boxes, Arena
   std::vector<ProxyBoxDev> pb(boxes.size());
   for (size_t b = 0; b < boxes.size(); ++b) {
     proxy_off[b] = total_proxy;
-    pb[b] = ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, total_proxy};
+    pb[b] = ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, total_proxy, 0.0};
     total_proxy += boxes[b].p;
   }
   const size_t np = (size_t)g->total_nodes + total_proxy;
@@ -672,36 +745,56 @@ PointsDev make_points(const pm_geometry* g, const std::vector<Box>& boxes, Arena
 // One level of one problem's factorization; several jobs (independent
 // problems, possibly at different depths of their trees) are processed in
 // shared launches.
+// boxes [b0, b1) of the level (b1 < 0: to the last); the call with b0 = 0 also
+// sets up the active sets of all of the level's boxes (the near lists of later
+// chunks read them)
 struct LevelJob {
   pm_factor* F;
   int lev;
+  int b0 = 0, b1 = -1;
 };
 
-// Points of several problems in one table: problem j's nodes, then the proxy
-// points of its boxes at its job's level (none with `proxies` false), from
-// point base[j] on; poff[j][b] = box b's first proxy relative to the problem's
-// proxy block.
+// Points of several problems in one table: every problem's nodes first
+// (problem j's from nbase[j]), then, per problem from pbase[j], the proxy
+// points of its boxes at its job's level (box b's first at pbase[j] +
+// poff[j][b]) and, with hoff, each box's held-out ring (its proxy count,
+// turned half a spacing; first at pbase[j] + hoff[j][b]).  Node positions do
+// not depend on the proxy counts.
 PointsDev make_points_joint(const std::vector<LevelJob>& jobs, bool proxies, Arena& scr, cudaStream_t st,
-                            std::vector<int>& base, std::vector<std::vector<int>>& poff) {
+                            std::vector<int>& nbase, std::vector<int>& pbase, std::vector<std::vector<int>>& poff,
+                            std::vector<std::vector<int>>* hoff = nullptr) {
   const int nj = (int)jobs.size();
-  base.assign(nj, 0);
+  nbase.assign(nj, 0);
+  pbase.assign(nj, 0);
   poff.assign(nj, {});
+  if (hoff) hoff->assign(nj, {});
   std::vector<std::vector<ProxyBoxDev>> pb(nj);
   std::vector<int> nprox(nj, 0);
   size_t np = 0;
   for (int j = 0; j < nj; ++j) {
-    const pm_geometry* g = jobs[j].F->g;
-    base[j] = (int)np;
+    nbase[j] = (int)np;
+    np += (size_t)jobs[j].F->g->total_nodes;
+  }
+  for (int j = 0; j < nj; ++j) {
+    pbase[j] = (int)np;
     if (proxies) {
       const auto& boxes = jobs[j].F->tree[jobs[j].lev];
       poff[j].assign(boxes.size(), 0);
       for (size_t b = 0; b < boxes.size(); ++b) {
         poff[j][b] = nprox[j];
-        pb[j].push_back(ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, nprox[j]});
+        pb[j].push_back(ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, nprox[j], 0.0});
         nprox[j] += boxes[b].p;
       }
+      if (hoff) {
+        (*hoff)[j].assign(boxes.size(), 0);
+        for (size_t b = 0; b < boxes.size(); ++b) {
+          (*hoff)[j][b] = nprox[j];
+          pb[j].push_back(ProxyBoxDev{boxes[b].cx, boxes[b].cy, boxes[b].R_p, boxes[b].p, nprox[j], 0.5});
+          nprox[j] += boxes[b].p;
+        }
+      }
     }
-    np += (size_t)g->total_nodes + nprox[j];
+    np += nprox[j];
   }
   if (np > (size_t)(1 << 30)) fail(PM_ERR_UNSUPPORTED, "more than 2^30 points in one launch");
   PointsDev P;
@@ -709,51 +802,108 @@ PointsDev make_points_joint(const std::vector<LevelJob>& jobs, bool proxies, Are
   P.ny = scr.get<double>(np); P.w = scr.get<double>(np);
   for (int j = 0; j < nj; ++j) {
     const pm_geometry* g = jobs[j].F->g;
-    const size_t o = base[j];
-    PointsDev Pj{P.x + o, P.y + o, P.nx + o, P.ny + o, P.w + o};
-    geom_points_from_nodes(g->nodes, Pj, g->total_nodes, st);
+    const size_t o = nbase[j];
+    geom_points_from_nodes(g->nodes, PointsDev{P.x + o, P.y + o, P.nx + o, P.ny + o, P.w + o}, g->total_nodes, st);
     if (nprox[j] > 0) {
+      const size_t q = pbase[j];
       auto* dpb = upload(scr, pb[j], st);
-      geom_proxy_points(dpb, (int)pb[j].size(), Pj, nprox[j], g->total_nodes, st);
+      geom_proxy_points(dpb, (int)pb[j].size(), PointsDev{P.x + q, P.y + q, P.nx + q, P.ny + q, P.w + q}, nprox[j], 0,
+                        st);
     }
   }
   CK(cudaGetLastError());
   return P;
 }
 
+// Entry formula of the off-diagonal blocks of a factorization's formulation,
+// and its interior medium (one real k- for all inclusions off PMCHWT (Omit)).
+int gather_mode_of(const pm_factor_opts& O) {
+  switch (O.formulation) {
+    case PM_FORM_ALL: return GATHER_ALL;
+    case PM_FORM_BM: return GATHER_BM;
+    case PM_FORM_BM_SIMPLIFIED: return GATHER_BM_SIMPLIFIED;
+    default: return GATHER_OMIT;
+  }
+}
 template <class C>
-void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t st, double tol) {
+void set_form(GatherBatch<C>& gb, const pm_factor* F) {
+  gb.mode = gather_mode_of(F->opts);
+  gb.k_in = F->g->inc[0].k_in.re;
+  gb.eps_in = (gb.k_in / F->g->k0) * (gb.k_in / F->g->k0);
+}
+
+// Squared Frobenius norms of many column-major blocks: out[i] += sum |A_i|^2.
+struct SqNormProb { const void* A; int ld; int m; int n; double* out; };
+template <class C>
+__global__ void __launch_bounds__(256) k_sqnorm(const SqNormProb* __restrict__ P) {
+  const SqNormProb p = P[blockIdx.y];
+  const C* A = (const C*)p.A;
+  double acc = 0;
+  for (int j = blockIdx.x; j < p.n; j += gridDim.x)
+    for (int i = threadIdx.x; i < p.m; i += 256) acc += (double)abs2(A[i + (size_t)j * p.ld]);
+  acc = warp_sum(acc);
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    atomicAdd(p.out, t);
+  }
+}
+
+template <class C>
+void sqnorm_batch(const std::vector<SqNormProb>& probs, Arena& scr, cudaStream_t st) {
+  if (probs.empty()) return;
+  auto* d = upload(scr, probs, st);
+  k_sqnorm<C><<<dim3(64, (unsigned)probs.size()), 256, 0, st>>>(d);
+  pm_launch_count_add(1);
+  CK(cudaGetLastError());
+}
+
+// Held-out proxy check bound: an ID passes while ||H_J - H_S T|| <= PROXY_CHECK_BOUND tol ||H||.
+constexpr double PROXY_CHECK_BOUND = 200.0;
+
+// failed (optional): receives (job, box) of every box whose predicted proxy
+// count failed the held-out check; the call then returns before the Schur
+// steps, and the caller redoes the level with those boxes at the rule's count.
+template <class C>
+void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t st, double tol,
+                    std::vector<std::pair<int, int>>* failed = nullptr) {
   scr.reset();
   const int nj = (int)jobs.size();
   const pm_factor_opts& O = jobs[0].F->opts;   // the jobs of one call share their options
-  // boxes of all jobs, flattened: global box gb = jb_off[j] + b
-  std::vector<int> jb_off(nj + 1, 0);
+  // boxes of all jobs (each job's range [b0, b1)), flattened: global box
+  // gb = jb_off[j] + (b - b0[j])
+  std::vector<int> jb_off(nj + 1, 0), jb0(nj), jb1(nj);
   for (int j = 0; j < nj; ++j) {
     const int nbj = (int)jobs[j].F->tree[jobs[j].lev].size();
-    levels_of<C>(jobs[j].F)[jobs[j].lev].assign(nbj, BoxF<C>());
-    jb_off[j + 1] = jb_off[j] + nbj;
+    jb0[j] = jobs[j].b0;
+    jb1[j] = jobs[j].b1 < 0 ? nbj : std::min(jobs[j].b1, nbj);
+    if (jb0[j] == 0) levels_of<C>(jobs[j].F)[jobs[j].lev].assign(nbj, BoxF<C>());
+    jb_off[j + 1] = jb_off[j] + (jb1[j] - jb0[j]);
   }
   const int nb = jb_off[nj];
   std::vector<int> job_of(nb);
   for (int j = 0; j < nj; ++j)
     for (int b = jb_off[j]; b < jb_off[j + 1]; ++b) job_of[b] = j;
+  auto lbox = [&](int x) { return x - jb_off[job_of[x]] + jb0[job_of[x]]; };   // box index within its level
   auto BFx = [&](int x) -> BoxF<C>& {
     const LevelJob& J = jobs[job_of[x]];
-    return levels_of<C>(J.F)[J.lev][x - jb_off[job_of[x]]];
+    return levels_of<C>(J.F)[J.lev][lbox(x)];
   };
   auto BOX = [&](int x) -> const Box& {
     const LevelJob& J = jobs[job_of[x]];
-    return J.F->tree[J.lev][x - jb_off[job_of[x]]];
+    return J.F->tree[J.lev][lbox(x)];
   };
   auto GEO = [&](int x) -> const pm_geometry* { return jobs[job_of[x]].F->g; };
   Timer t_asm(st);
-  // one point table for the level: every job's nodes and its boxes' proxy points
-  std::vector<int> pt_base;
-  std::vector<std::vector<int>> poff;
-  PointsDev P = make_points_joint(jobs, true, scr, st, pt_base, poff);
-  // 1. active sets and diagonal blocks
+  // node positions in the level's point table (the proxy points follow all nodes)
+  std::vector<int> nbase(nj, 0);
+  for (int j = 1; j < nj; ++j) nbase[j] = nbase[j - 1] + jobs[j - 1].F->g->total_nodes;
+  // 1. active sets and diagonal blocks (the merges' gathers run once the points exist)
+  GatherBatch<C> gm; CopyBatch<C, C> cm;
   {
-    GatherBatch<C> gm; CopyBatch<C, C> cm;
     for (int j = 0; j < nj; ++j) {
       pm_factor* F = jobs[j].F;
       const int lev = jobs[j].lev;
@@ -763,77 +913,54 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
       const auto& boxes = F->tree[lev];
       const int nbj = (int)boxes.size();
       if (lev == F->L) {
-        std::vector<int> incl(nbj), lda(nbj);
-        std::vector<C*> A(nbj);
-        for (int b = 0; b < nbj; ++b) {
-          int i0 = boxes[b].leaves[0];
-          int n = g->inc[i0].n_nodes;
-          BoxF<C>& bf = BF[b];
-          bf.mb = 2 * n;
-          for (int i = 0; i < 2 * n; ++i) {
-            bf.rows.push_back(g->row_off[i0] + i);
-            bf.rgrp.push_back(i >= n);
+        if (jb0[j] == 0)
+          for (int b = 0; b < nbj; ++b) {   // active sets of every box of the level
+            int i0 = boxes[b].leaves[0];
+            int n = g->inc[i0].n_nodes;
+            BoxF<C>& bf = BF[b];
+            bf.mb = 2 * n;
+            for (int i = 0; i < 2 * n; ++i) {
+              bf.rows.push_back(g->row_off[i0] + i);
+              bf.rgrp.push_back(i >= n);
+            }
+            bf.cols = bf.rows; bf.cgrp = bf.rgrp;
           }
-          bf.cols = bf.rows; bf.cgrp = bf.rgrp;
+        std::vector<int> incl, lda;
+        std::vector<C*> A;
+        for (int b = jb0[j]; b < jb1[j]; ++b) {
+          BoxF<C>& bf = BF[b];
           bf.D = F->arena.get<C>((size_t)bf.mb * bf.mb);
-          incl[b] = i0; A[b] = bf.D; lda[b] = bf.mb;
+          incl.push_back(boxes[b].leaves[0]); A.push_back(bf.D); lda.push_back(bf.mb);
         }
-        assemble_self<C>(g, incl, A, lda, scr, st);
+        assemble_self<C>(g, incl, A, lda, scr, st, F->opts.formulation >= PM_FORM_BM);
       } else {
-        for (int b = 0; b < nbj; ++b) merge_children<C, C>(F, LV[lev + 1], boxes[b], BF[b], gm, cm, 2 * pt_base[j]);
+        if (jb0[j] == 0)
+          for (int b = 0; b < nbj; ++b) active_sets<C, C>(LV[lev + 1], boxes[b], BF[b]);
+        set_form(gm, F);
+        for (int b = jb0[j]; b < jb1[j]; ++b)
+          merge_children<C, C>(F, LV[lev + 1], boxes[b], BF[b], gm, cm, 2 * nbase[j]);
       }
     }
-    gm.run(scr, P, 0.0, st);
-    cm.run(scr, st);
   }
-  // 2. ID inputs: per box 4 IDs (row u-eq, row q-eq, col q, col u)
   const int nid = 4 * nb;
-  std::vector<int> W(nid), nn(nid);
-  std::vector<C*> Z(nid);
-  std::vector<std::vector<int>> pos(nid);
-  GatherBatch<C> gb;
+  // 1b. candidate counts, input rows at the rule's proxy count and the learned
+  // predictor's features of every (box, group); the predictor may then lower
+  // the boxes' proxy counts before the proxy points are made
+  std::vector<int> nn(nid), Wr(nid);
   for (int b = 0; b < nb; ++b) {
-    const int jj = job_of[b], lb = b - jb_off[jj];
-    const pm_geometry* g = GEO(b);
+    const int jj = job_of[b];
     const Box& box = BOX(b);
     const BoxF<C>& bf = BFx(b);
     const auto& BFj = levels_of<C>(jobs[jj].F)[jobs[jj].lev];
-    const int co = 2 * pt_base[jj];
-    std::vector<int> ncols, nrows;
-    for (int o : box.near) {
-      for (int c : BFj[o].cols) ncols.push_back(g->code_of(c));
-      for (int r : BFj[o].rows) nrows.push_back(g->code_of(r));
-    }
-    const int pbase = g->total_nodes + poff[jj][lb];
-    std::vector<int> pcols, prows;
-    for (int grp = 0; grp < 2; ++grp)
-      for (int s = 0; s < box.p; ++s) { pcols.push_back((pbase + s) * 2 + grp); prows.push_back((pbase + s) * 2 + grp); }
+    int ncol = 0, nrow = 0;
+    for (int o : box.near) { ncol += (int)BFj[o].cols.size(); nrow += (int)BFj[o].rows.size(); }
     for (int grp = 0; grp < 2; ++grp) {
-      // row ID of group grp: Z[w, c] = A(row c, source w), sources = near columns + proxy
-      int id = 4 * b + grp;
-      std::vector<int> tgt;
-      for (int i = 0; i < bf.mb; ++i) if (bf.rgrp[i] == grp) { pos[id].push_back(i); tgt.push_back(g->code_of(bf.rows[i])); }
-      std::vector<int> src = ncols;
-      src.insert(src.end(), pcols.begin(), pcols.end());
-      W[id] = (int)src.size(); nn[id] = (int)tgt.size();
-      Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
-      gb.add(Z[id], W[id], W[id], nn[id], tgt, src, 1, co, g->k0);
-      // column ID of group grp: Z[w, c] = A(target w, column c), targets = near rows + proxy
-      id = 4 * b + 2 + grp;
-      std::vector<int> srcc;
-      for (int i = 0; i < bf.mb; ++i) if (bf.cgrp[i] == grp) { pos[id].push_back(i); srcc.push_back(g->code_of(bf.cols[i])); }
-      std::vector<int> tg = nrows;
-      tg.insert(tg.end(), prows.begin(), prows.end());
-      W[id] = (int)tg.size(); nn[id] = (int)srcc.size();
-      Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
-      gb.add(Z[id], W[id], W[id], nn[id], tg, srcc, 0, co, g->k0);
+      nn[4 * b + grp] = (int)std::count(bf.rgrp.begin(), bf.rgrp.end(), grp);
+      nn[4 * b + 2 + grp] = (int)std::count(bf.cgrp.begin(), bf.cgrp.end(), grp);
+      Wr[4 * b + grp] = ncol + 2 * box.p_rule;
+      Wr[4 * b + 2 + grp] = nrow + 2 * box.p_rule;
     }
   }
-  gb.run(scr, P, 0.0, st);
-  const double ms_asm = t_asm.stop();
-  for (const auto& J : jobs) J.F->stats.ms_assemble += ms_asm;
-  Timer t_id(st);
-  // features of every (box, group) for the learned rank predictor
   std::vector<float> feat(2 * (size_t)nb * MLP_IN);
   for (int b = 0; b < nb; ++b) {
     const pm_geometry* g = GEO(b);
@@ -844,8 +971,8 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
     for (int grp = 0; grp < 2; ++grp) {
       float* f = &feat[(2 * (size_t)b + grp) * MLP_IN];
       f[0] = (float)std::log((double)std::max(nn[4 * b + grp], 1));
-      f[1] = (float)std::log((double)std::max(W[4 * b + grp], 1));
-      f[2] = (float)std::log((double)std::max(W[4 * b + 2 + grp], 1));
+      f[1] = (float)std::log((double)std::max(Wr[4 * b + grp], 1));
+      f[2] = (float)std::log((double)std::max(Wr[4 * b + 2 + grp], 1));
       f[3] = (float)(g->k0 * box.r_cell);
       f[4] = (float)std::log10(tol);
       f[5] = (float)std::log2((double)box.leaves.size());
@@ -854,7 +981,9 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
     }
   }
   std::vector<int> khat;   // predicted rank bound per ID (empty: no predictor)
-  if (O.rank_model) {
+  bool lowered = false;    // some box runs below the rule's proxy count
+  for (int b = 0; b < nb; ++b) lowered = lowered || BOX(b).p < BOX(b).p_rule;
+  if (O.rank_model && O.formulation == PM_FORM_OMIT) {   // trained on PMCHWT (Omit) factorizations
     const float* mdl = O.rank_model;   // theta | mean (8) | std (8), device
     std::vector<float> musd(2 * MLP_IN);
     CK(cudaMemcpyAsync(musd.data(), mdl + MLP_NPARAM, sizeof(float) * 2 * MLP_IN, cudaMemcpyDeviceToHost, st));
@@ -871,16 +1000,97 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
     CK(cudaMemcpyAsync(yp.data(), dy, sizeof(float) * yp.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     khat.assign(nid, 0);
-    for (int b = 0; b < nb; ++b)
+    for (int b = 0; b < nb; ++b) {
+      double pfrac = 0;
       for (int grp = 0; grp < 2; ++grp) {
         const float* y = &yp[(2 * (size_t)b + grp) * MLP_OUT];
         const int n = nn[4 * b + grp];
-        const double frac = std::min(1.0, std::max(0.0, (double)std::max(y[0], y[1])));
+        const double frac = std::min(1.0, std::max(0.0, (double)y[0]));
         const int k = std::min(n, (int)std::ceil(frac * n + 2 + 0.02 * n));
         khat[4 * b + grp] = khat[4 * b + 2 + grp] = k;
+        pfrac = std::max(pfrac, (double)y[1]);
       }
+      // learned proxy count, unless the count is fixed or the box failed the check before
+      Box& box = jobs[job_of[b]].F->tree[jobs[job_of[b]].lev][lbox(b)];
+      if (O.proxy_points == 0 && !box.locked) {
+        box.p = std::min(box.p_rule, proxy_count(std::min(1.0, std::max(0.25, pfrac + 0.1)), box.p_rule));
+        lowered = lowered || box.p < box.p_rule;
+      }
+    }
     if (O.debug_flags & PM_DEBUG_UNDERPREDICT) std::fill(khat.begin(), khat.end(), 1);   // injected
   }
+  // the held-out proxy check: asked for, or the judge of lowered counts in FP64
+  const bool check_on = O.formulation == PM_FORM_OMIT &&
+                        ((O.flags & PM_FLAG_PROXY_CHECK) ||
+                         (lowered && O.rank_model && O.precision == PM_FP64 && O.proxy_points == 0));
+  // one point table for the level: every job's nodes, then its boxes' proxy points (and held-out rings)
+  std::vector<int> pbase;
+  std::vector<std::vector<int>> poff, hoff;
+  PointsDev P = make_points_joint(jobs, true, scr, st, nbase, pbase, poff, check_on ? &hoff : nullptr);
+  gm.run(scr, P, 0.0, st);
+  cm.run(scr, st);
+  // 2. ID inputs: per box 4 IDs (row u-eq, row q-eq, col q, col u)
+  std::vector<int> W(nid);
+  std::vector<C*> Z(nid);
+  std::vector<std::vector<int>> pos(nid);
+  GatherBatch<C> gb;
+  for (int b = 0; b < nb; ++b) {
+    const int jj = job_of[b], lb = lbox(b);
+    const pm_geometry* g = GEO(b);
+    const Box& box = BOX(b);
+    const BoxF<C>& bf = BFx(b);
+    const auto& BFj = levels_of<C>(jobs[jj].F)[jobs[jj].lev];
+    const int co = 2 * nbase[jj];
+    std::vector<int> ncols, nrows;
+    for (int o : box.near) {
+      for (int c : BFj[o].cols) ncols.push_back(g->code_of(c) + co);
+      for (int r : BFj[o].rows) nrows.push_back(g->code_of(r) + co);
+    }
+    const int pb0 = pbase[jj] + poff[jj][lb];   // absolute point index of the box's first proxy
+    std::vector<int> pcols, prows;
+    for (int grp = 0; grp < 2; ++grp)
+      for (int s = 0; s < box.p; ++s) { pcols.push_back((pb0 + s) * 2 + grp); prows.push_back((pb0 + s) * 2 + grp); }
+    // rows of the ID inputs: near entries of the formulation, then the proxy
+    // densities (PMCHWT (All): an exterior and an interior family)
+    const pm_factor* Fj = jobs[jj].F;
+    const int form = Fj->opts.formulation;
+    const int nfam = form == PM_FORM_ALL ? 2 : 1;
+    auto add_proxies = [&](C* Zp, int ld, int n_cand, const std::vector<int>& cand, const std::vector<int>& prox,
+                           int trans) {
+      for (int fam = 0; fam < nfam; ++fam) {
+        set_form(gb, Fj);
+        if (form == PM_FORM_ALL) gb.mode = fam == 0 ? GATHER_OMIT : GATHER_INTERIOR;
+        C* out = Zp + (size_t)fam * prox.size();
+        if (trans) gb.add(out, ld, (int)prox.size(), n_cand, cand, prox, 1, 0, g->k0);
+        else gb.add(out, ld, (int)prox.size(), n_cand, prox, cand, 0, 0, g->k0);
+      }
+    };
+    for (int grp = 0; grp < 2; ++grp) {
+      // row ID of group grp: Z[w, c] = A(row c, source w), sources = near columns + proxy
+      int id = 4 * b + grp;
+      std::vector<int> tgt;
+      for (int i = 0; i < bf.mb; ++i) if (bf.rgrp[i] == grp) { pos[id].push_back(i); tgt.push_back(g->code_of(bf.rows[i]) + co); }
+      W[id] = (int)(ncols.size() + nfam * pcols.size());
+      Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
+      set_form(gb, Fj);
+      gb.add(Z[id], W[id], (int)ncols.size(), nn[id], tgt, ncols, 1, 0, g->k0);
+      add_proxies(Z[id] + ncols.size(), W[id], nn[id], tgt, pcols, 1);
+      // column ID of group grp: Z[w, c] = A(target w, column c), targets = near rows + proxy
+      id = 4 * b + 2 + grp;
+      std::vector<int> srcc;
+      for (int i = 0; i < bf.mb; ++i) if (bf.cgrp[i] == grp) { pos[id].push_back(i); srcc.push_back(g->code_of(bf.cols[i]) + co); }
+      W[id] = (int)(nrows.size() + nfam * prows.size());
+      Z[id] = scr.get<C>((size_t)W[id] * std::max(nn[id], 1));
+      set_form(gb, Fj);
+      gb.add(Z[id], W[id], (int)nrows.size(), nn[id], nrows, srcc, 0, 0, g->k0);
+      add_proxies(Z[id] + nrows.size(), W[id], nn[id], srcc, prows, 0);
+    }
+  }
+  gb.run(scr, P, 0.0, st);
+  for (int i = 0; i < nid; ++i) jobs[job_of[i / 4]].F->stats.id_rows += W[i];
+  const double ms_asm = t_asm.stop();
+  for (const auto& J : jobs) J.F->stats.ms_assemble += ms_asm;
+  Timer t_id(st);
   // 3a. complex64: tall inputs reduced to their triangular factor first, so
   // that the pivoted steps stream n instead of W rows
   std::vector<int> We(W);   // rows the pivoted QR runs on (leading dimension stays W)
@@ -1050,7 +1260,14 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hr.data(), rank, nid * sizeof(int), cudaMemcpyDeviceToHost, st));
+  // an exactly zero ID input (no far field at all: the interior rows of the
+  // simplified Burton-Miller system) gets a zero interpolation, not an
+  // identity on arbitrary pivots
+  std::vector<double> href(nid);
+  CK(cudaMemcpyAsync(href.data(), ref, nid * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  std::vector<char> zero_in(nid);
+  for (int i = 0; i < nid; ++i) zero_in[i] = nn[i] > 0 && !(href[i] > 0);
   std::vector<int> r(nid);
   for (int i = 0; i < nid; ++i) r[i] = hr[i] >= 0 ? hr[i] : cp[i].target;
   if (!khat.empty())
@@ -1077,15 +1294,20 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
     for (const auto& J : jobs) J.F->stats.cpqr_launches += maxExt;
     CK(cudaGetLastError());
   }
-  // training data for the rank predictor: features -> (row rank, column rank) / n
+  // training data for the predictor: features -> (max(row rank, column rank) / n,
+  // proxy count used / the rule's); the held-out check's ratio is filled in below
+  std::vector<size_t> rec0(nj);
+  for (int j = 0; j < nj; ++j) rec0[j] = jobs[j].F->proxy_ratio.size();
   for (int b = 0; b < nb; ++b)
     for (int grp = 0; grp < 2; ++grp) {
       const float* f = &feat[(2 * (size_t)b + grp) * MLP_IN];
       pm_factor* Fb = jobs[job_of[b]].F;
       Fb->rank_X.insert(Fb->rank_X.end(), f, f + MLP_IN);
       const double n = std::max(nn[4 * b + grp], 1);
-      Fb->rank_T.push_back((float)(r[4 * b + grp] / n));
-      Fb->rank_T.push_back((float)(r[4 * b + 2 + grp] / n));
+      Fb->rank_T.push_back((float)(std::max(r[4 * b + grp], r[4 * b + 2 + grp]) / n));
+      Fb->rank_T.push_back((float)BOX(b).p / (float)std::max(BOX(b).p_rule, 1));
+      Fb->proxy_ratio.push_back(-1.f);
+      Fb->proxy_redone.push_back(BOX(b).locked ? 1 : 0);
     }
   {
     // the unchosen columns follow the pivots, ascending (defines the column order of T)
@@ -1120,7 +1342,7 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
   int maxcols = 0;
   for (int i = 0; i < nid; ++i) {
     int k = kk[i], n = nn[i];
-    if (k <= 0 || n - k <= 0) continue;
+    if (k <= 0 || n - k <= 0 || zero_in[i]) continue;
     T[i] = scr.get<C>((size_t)k * (n - k));
     ip.push_back(InterpProb<C>{Z[i], W[i], n, k, perm + noff[i], rdiag + noff[i], T[i], k});
     maxcols = std::max(maxcols, n - k);
@@ -1129,6 +1351,71 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
     auto* dip = upload(scr, ip, st);
     interp_solve<C>(dip, (int)ip.size(), maxcols, st);
     CK(cudaGetLastError());
+  }
+  // 5b. held-out proxy check: each ID's candidates against its box's held-out
+  // ring, gathered in pivot order so that H = [H_S | H_J]; then H_J -= H_S T
+  // and ratio = ||H_J|| / (tol ||H||) (no counterpart in the paper)
+  if (check_on) {
+    GatherBatch<C> gh;
+    GemmBatch<C> ge;
+    std::vector<SqNormProb> nref, nerr;
+    double* sums = scr.get<double>(2 * (size_t)nid);
+    CK(cudaMemsetAsync(sums, 0, 2 * (size_t)nid * sizeof(double), st));
+    std::vector<C*> H(nid, nullptr);
+    std::vector<int> Wh(nid, 0);
+    for (int b = 0; b < nb; ++b) {
+      const int jj = job_of[b], lb = lbox(b);
+      const pm_geometry* g = GEO(b);
+      const Box& box = BOX(b);
+      const BoxF<C>& bf = BFx(b);
+      const int co = 2 * nbase[jj];
+      const int h0 = pbase[jj] + hoff[jj][lb];
+      std::vector<int> ring;
+      for (int grp = 0; grp < 2; ++grp)
+        for (int s2 = 0; s2 < box.p; ++s2) ring.push_back((h0 + s2) * 2 + grp);
+      for (int q = 0; q < 4; ++q) {
+        const int id = 4 * b + q;
+        const int n = nn[id], k = kk[id];
+        if (n <= 0) continue;
+        const bool row_id = q < 2;
+        std::vector<int> cand(n);
+        for (int j2 = 0; j2 < n; ++j2) {
+          const int pos_i = pos[id][hperm[noff[id] + j2]];
+          cand[j2] = g->code_of(row_id ? bf.rows[pos_i] : bf.cols[pos_i]) + co;
+        }
+        Wh[id] = (int)ring.size();
+        H[id] = scr.get<C>((size_t)Wh[id] * n);
+        if (row_id) gh.add(H[id], Wh[id], Wh[id], n, cand, ring, 1, 0, g->k0);
+        else gh.add(H[id], Wh[id], Wh[id], n, ring, cand, 0, 0, g->k0);
+        nref.push_back(SqNormProb{H[id], Wh[id], Wh[id], n, sums + 2 * id});
+        if (k > 0 && n - k > 0)
+          ge.add(Wh[id], n - k, k, H[id], Wh[id], T[id], k, H[id] + (size_t)k * Wh[id], Wh[id], cmone<C>(), cone<C>(), 0);
+        if (n - k > 0) nerr.push_back(SqNormProb{H[id] + (size_t)k * Wh[id], Wh[id], Wh[id], n - k, sums + 2 * id + 1});
+      }
+    }
+    gh.run(scr, P, 0.0, st);
+    sqnorm_batch<C>(nref, scr, st);
+    ge.run(scr, st);
+    sqnorm_batch<C>(nerr, scr, st);
+    std::vector<double> hs(2 * (size_t)nid);
+    CK(cudaMemcpyAsync(hs.data(), sums, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < nb; ++b) {
+      double ratio = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int id = 4 * b + q;
+        if (nn[id] <= 0) continue;
+        const double ref = hs[2 * id], err = hs[2 * id + 1];
+        ratio = std::max(ratio, ref > 0 ? std::sqrt(err / ref) / tol : 0.0);
+      }
+      const int jj = job_of[b];
+      pm_factor* Fb = jobs[jj].F;
+      Fb->stats.proxy_checked++;
+      for (int grp = 0; grp < 2; ++grp) Fb->proxy_ratio[rec0[jj] + 2 * (b - jb_off[jj]) + grp] = (float)ratio;
+      const Box& box = BOX(b);
+      if (failed && ratio > PROXY_CHECK_BOUND && box.p < box.p_rule) failed->push_back({jj, lbox(b)});
+    }
+    if (failed && !failed->empty()) return;   // the caller redoes the level
   }
   const double ms_id = t_id.stop();
   for (const auto& J : jobs) J.F->stats.ms_id += ms_id;
@@ -1160,6 +1447,7 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
       }
       for (int side = 0; side < 2; ++side) {
         int id = side == 0 ? ir : ic;
+        if (zero_in[id]) continue;   // zero interpolation: the block of X (L) or R stays zero
         size_t po = posall.size();
         posall.insert(posall.end(), pos[id].begin(), pos[id].end());
         ScatterProb<C> sc{side == 0 ? bf.X : bf.Rm, side == 0 ? bf.mb : bf.kb, off, side == 0,
@@ -1240,9 +1528,9 @@ void factor_tops(const std::vector<pm_factor*>& Fs, Arena& scr, cudaStream_t st)
   Timer t(st);
   std::vector<LevelJob> jobs;
   for (pm_factor* F : Fs) jobs.push_back(LevelJob{F, 0});
-  std::vector<int> base;
+  std::vector<int> base, pbase;
   std::vector<std::vector<int>> poff;
-  PointsDev P = make_points_joint(jobs, false, scr, st, base, poff);
+  PointsDev P = make_points_joint(jobs, false, scr, st, base, pbase, poff);
   GatherBatch<double2> gb;
   CopyBatch<Cc, double2> cb;
   std::vector<LuProb<double2>> lu;
@@ -1257,8 +1545,9 @@ void factor_tops(const std::vector<pm_factor*>& Fs, Arena& scr, cudaStream_t st)
       for (int r = 0; r < 2 * n; ++r) { rt.rows.push_back(g->row_off[j] + r); rt.rgrp.push_back(r >= n); }
       rt.cols = rt.rows; rt.cgrp = rt.rgrp;
       rt.D = F->arena.get<double2>((size_t)rt.mb * rt.mb);
-      assemble_self<double2>(g, {j}, {rt.D}, {rt.mb}, scr, st);
+      assemble_self<double2>(g, {j}, {rt.D}, {rt.mb}, scr, st, F->opts.formulation >= PM_FORM_BM);
     } else {
+      set_form(gb, F);
       merge_children<Cc, double2>(F, levels_of<Cc>(F)[1], F->tree[0][0], rt, gb, cb, 2 * base[i]);
     }
     rt.ipiv = F->arena.get<int>(std::max(rt.mb, 1));
@@ -1713,6 +2002,33 @@ void require_current_device(int device, const char* what) {
                                  ", the geometry was built on device " + std::to_string(device));
 }
 
+// Burton-Miller right-hand side from the PMCHWT one, per inclusion and column:
+// [f_u + alpha f_q; 0] with f = [f_u; f_q] = [-u^I; -q^I], alpha = i / k+.
+__global__ void k_bm_rhs(const InclDev* __restrict__ inc, const int* __restrict__ incl, int total, double k0,
+                         const double2* __restrict__ f, double2* __restrict__ b, int N, int nrhs) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (q >= total || c >= nrhs) return;
+  const InclDev d = inc[incl[q]];
+  const int l = q - d.node_off;
+  const double2 fu = f[d.row_off + l + (size_t)c * N], fq = f[d.row_off + d.n + l + (size_t)c * N];
+  b[d.row_off + l + (size_t)c * N] = make_double2(fu.x - fq.y / k0, fu.y + fq.x / k0);
+  b[d.row_off + d.n + l + (size_t)c * N] = make_double2(0.0, 0.0);
+}
+
+// [u; q] per inclusion (Burton-Miller unknowns) -> [q; u] (the PMCHWT order).
+__global__ void k_bm_order(const InclDev* __restrict__ inc, const int* __restrict__ incl, int total,
+                           const double2* __restrict__ x, double2* __restrict__ phi, int N, int nrhs) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (q >= total || c >= nrhs) return;
+  const InclDev d = inc[incl[q]];
+  const int l = q - d.node_off;
+  const size_t o = (size_t)c * N + d.row_off;
+  phi[o + l] = x[o + d.n + l];
+  phi[o + d.n + l] = x[o + l];
+}
+
 // Sets *flag when any of the n doubles at x is NaN or infinite.
 __global__ void k_flag_nonfinite(const double* __restrict__ x, size_t n, int* flag) {
   int bad = 0;
@@ -1756,11 +2072,22 @@ bool check_factor_opts(const pm_factor_opts* opts, const char* where) {
     g_err = w + ": bad refinement options";
     return false;
   }
+  if (opts->formulation < PM_FORM_OMIT || opts->formulation > PM_FORM_BM_SIMPLIFIED) {
+    g_err = w + ": unknown formulation";
+    return false;
+  }
+  if (!(opts->proxy_scale >= 0 && opts->proxy_scale <= 1)) { g_err = w + ": proxy_scale must be in [0, 1]"; return false; }
   return true;
 }
 
 // Options, tree and proxy plan of a new factorization; returns the ID threshold.
 double setup_factor(pm_factor* F, const pm_geometry* g, const pm_factor_opts* opts) {
+  if (opts->formulation != PM_FORM_OMIT) {
+    if (opts->precision != PM_FP64) fail(PM_ERR_UNSUPPORTED, "PMCHWT (All) and Burton-Miller run in PM_FP64 only");
+    for (const auto& c : g->inc)
+      if (c.k_in.im != 0 || c.k_in.re != g->inc[0].k_in.re)
+        fail(PM_ERR_UNSUPPORTED, "PMCHWT (All) and Burton-Miller need one real interior wavenumber for all inclusions");
+  }
   F->g = g;
   F->opts = *opts;
   if (F->opts.proxy_factor == 0) F->opts.proxy_factor = 1.5;
@@ -1786,19 +2113,97 @@ double setup_factor(pm_factor* F, const pm_geometry* g, const pm_factor_opts* op
 // launches: step s processes level L_i - s of every problem i that has one, so
 // problems of different depths meet at their leaves first; then all top-level
 // systems at once.  One factorization is the group of one.
+// Scratch bytes a box's IDs take when its level runs (four inputs of W rows
+// and about mb/2 candidates each, with the workspaces of the QR, the CPQR and
+// the interpolation matrices), estimated before the level's active sets exist.
+template <class C>
+double box_scratch_bytes(pm_factor* F, int lev, int b) {
+  auto mb_of = [&](int bb) -> double {
+    const Box& x = F->tree[lev][bb];
+    if (lev == F->L) return 2.0 * F->g->inc[x.leaves[0]].n_nodes;
+    double m = 0;
+    for (int c : x.children) m += levels_of<C>(F)[lev + 1][c].kb;
+    return m;
+  };
+  const Box& box = F->tree[lev][b];
+  double near = 0;
+  for (int o : box.near) near += mb_of(o);
+  const double W = near + (F->opts.formulation == PM_FORM_ALL ? 4.0 : 2.0) * box.p_rule;
+  return 1.5 * sizeof(C) * 2.0 * W * mb_of(b);
+}
+
+// The jobs' boxes in consecutive chunks whose scratch estimates stay within
+// budget bytes (a box larger than the budget runs alone).
+template <class C>
+std::vector<std::vector<LevelJob>> plan_chunks(const std::vector<LevelJob>& jobs, double budget) {
+  std::vector<std::vector<LevelJob>> chunks(1);
+  double acc = 0;
+  for (const LevelJob& J : jobs) {
+    const int nbj = (int)J.F->tree[J.lev].size();
+    for (int b = 0; b < nbj; ++b) {
+      const double bytes = box_scratch_bytes<C>(J.F, J.lev, b);
+      if (acc > 0 && acc + bytes > budget) { chunks.emplace_back(); acc = 0; }
+      auto& cur = chunks.back();
+      if (!cur.empty() && cur.back().F == J.F && cur.back().b1 == b) cur.back().b1 = b + 1;
+      else cur.push_back(LevelJob{J.F, J.lev, b, b + 1});
+      acc += bytes;
+    }
+  }
+  return chunks;
+}
+
 template <class C>
 void factor_group_t(std::vector<pm_factor*>& Fs, double id_tol, Arena& scr, cudaStream_t st) {
   int Lmax = 0;
   for (pm_factor* F : Fs) Lmax = std::max(Lmax, F->L);
   for (int s = 0; s < Lmax; ++s) {
-    std::vector<LevelJob> jobs;
+    std::vector<LevelJob> level_jobs;
     for (pm_factor* F : Fs)
-      if (F->L - s >= 1) jobs.push_back(LevelJob{F, F->L - s});
+      if (F->L - s >= 1) level_jobs.push_back(LevelJob{F, F->L - s});
     Timer tl(st);
-    process_levels<C>(jobs, scr, st, id_tol);
+    // scratch budget: opts.scratch_gb, else 35% of the device memory free now.
+    // The scratch blocks of the previous step go back first: sized for its
+    // boxes, they would otherwise stay allocated beside the larger ones the
+    // next level's boxes need.
+    if (s > 0) {
+      CK(cudaStreamSynchronize(st));
+      scr.release();
+    }
+    double budget = Fs[0]->opts.scratch_gb * 1e9;
+    if (!(budget > 0)) {
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      budget = 0.35 * (double)fr;
+    }
+    const auto chunks = plan_chunks<C>(level_jobs, budget);
+    for (const auto& jobs : chunks) {
+      std::vector<std::pair<int, int>> failed;
+      std::vector<size_t> nx(jobs.size()), nt(jobs.size()), np(jobs.size());
+      for (size_t j = 0; j < jobs.size(); ++j) {
+        nx[j] = jobs[j].F->rank_X.size(); nt[j] = jobs[j].F->rank_T.size(); np[j] = jobs[j].F->proxy_ratio.size();
+      }
+      process_levels<C>(jobs, scr, st, id_tol, &failed);
+      if (!failed.empty()) {
+        // boxes whose learned proxy count failed the held-out check: the rule's
+        // count from now on, and the level again (its samples recorded afresh)
+        for (auto& fb : failed) {
+          Box& box = jobs[fb.first].F->tree[jobs[fb.first].lev][fb.second];
+          box.p = box.p_rule;
+          box.locked = true;
+          jobs[fb.first].F->stats.proxy_fallbacks++;
+        }
+        for (size_t j = 0; j < jobs.size(); ++j) {
+          pm_factor* F = jobs[j].F;
+          F->rank_X.resize(nx[j]); F->rank_T.resize(nt[j]);
+          F->proxy_ratio.resize(np[j]); F->proxy_redone.resize(np[j]);
+        }
+        process_levels<C>(jobs, scr, st, id_tol, nullptr);
+      }
+    }
     const double ms = tl.stop();
-    for (auto& J : jobs)
+    for (auto& J : level_jobs)
       if (J.lev < 16) J.F->stats.ms_level[J.lev] = ms;
+    for (auto* F : Fs) F->stats.level_chunks += (int)chunks.size();
   }
   factor_tops<C>(Fs, scr, st);
 }
@@ -1882,7 +2287,8 @@ pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out) {
   pm_status s = run_guarded("pm_build_geometry", [&] {
     if (prob->m < 1 || !prob->inc) fail(PM_ERR_INVALID_ARG, "need m >= 1 inclusions");
     if (!(prob->k_out > 0) || !std::isfinite(prob->k_out)) fail(PM_ERR_INVALID_ARG, "k_out must be positive");
-    if (!(prob->spacing > 0)) fail(PM_ERR_INVALID_ARG, "spacing must be positive");
+    if (!(prob->spacing >= 0) || !std::isfinite(prob->spacing))
+      fail(PM_ERR_INVALID_ARG, "spacing must be positive, or 0 for an arbitrary arrangement");
     for (int j = 0; j < prob->m; ++j) {
       const pm_inclusion& c = prob->inc[j];
       if (c.shape < 0 || c.shape > 3) fail(PM_ERR_INVALID_ARG, "unknown shape");
@@ -1897,6 +2303,7 @@ pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out) {
     g = new pm_geometry();
     CK(cudaGetDevice(&g->device));
     g->m = prob->m; g->k0 = prob->k_out; g->spacing = prob->spacing;
+    g->general = prob->spacing == 0;
     g->gnx = prob->grid_nx; g->gny = prob->grid_ny;
     g->inc.assign(prob->inc, prob->inc + prob->m);
     g->node_off.assign(g->m + 1, 0); g->row_off.assign(g->m + 1, 0);
@@ -2033,8 +2440,24 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
       ~ProfScope() { g_kprof = nullptr; }
     } scope(F->profiling ? &F->prof : nullptr);
     std::lock_guard<std::mutex> plan_lock(F->plan_mu);   // solves of one factor share its graphs
-    if (F->precision == PM_FP64) run_planned(F, 0, drhs, nrhs, dphi, nullptr, st);
-    else solve_refined(F, drhs, nrhs, dphi, ws, st, info);
+    if (F->precision == PM_FP64 && F->opts.formulation >= PM_FORM_BM) {
+      // Burton-Miller: its own right-hand side, then its [u; q] unknowns reordered
+      const pm_geometry* g = F->g;
+      Cd* b = ws.get<Cd>((size_t)g->N * nrhs);
+      Cd* x = ws.get<Cd>((size_t)g->N * nrhs);
+      const dim3 grid((g->total_nodes + 255) / 256, nrhs);
+      k_bm_rhs<<<grid, 256, 0, st>>>(g->d_inc, g->nodes.incl, g->total_nodes, g->k0, drhs, b, g->N, nrhs);
+      pm_launch_count_add(1);
+      CK(cudaGetLastError());
+      run_planned(F, 0, b, nrhs, x, nullptr, st);
+      k_bm_order<<<grid, 256, 0, st>>>(g->d_inc, g->nodes.incl, g->total_nodes, x, dphi, g->N, nrhs);
+      pm_launch_count_add(1);
+      CK(cudaGetLastError());
+    } else if (F->precision == PM_FP64) {
+      run_planned(F, 0, drhs, nrhs, dphi, nullptr, st);
+    } else {
+      solve_refined(F, drhs, nrhs, dphi, ws, st, info);
+    }
     if (!on_device) CK(cudaMemcpyAsync(phi, dphi, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (F->profiling) F->prof.collect();
@@ -2206,6 +2629,56 @@ pm_status pm_matrix_entries(const pm_geometry* g, const int32_t* rows, int32_t M
   });
 }
 
+namespace {
+// Shared body of pm_far_field / pm_scattered_field: pts holds ndir angles
+// (far) or npts points as x, y pairs (near).
+pm_status field_impl(const char* where, bool far, const pm_geometry* g, const pm_c64* phi, int32_t nrhs,
+                     int32_t on_device, const double* pts, int32_t npts, pm_c64* out) {
+  if (!g || !phi || !pts || !out || nrhs < 1 || npts < 1) {
+    g_err = std::string(where) + ": bad argument";
+    return PM_ERR_INVALID_ARG;
+  }
+  const int nv = far ? npts : 2 * npts;
+  for (int i = 0; i < nv; ++i)
+    if (!std::isfinite(pts[i])) { g_err = std::string(where) + ": non-finite direction or point"; return PM_ERR_INVALID_ARG; }
+  return run_guarded(where, [&] {
+    Arena ws;
+    ws.min_block = 1 << 20;
+    cudaStream_t st = 0;
+    const size_t nphi = (size_t)g->N * nrhs, nout = (size_t)npts * nrhs;
+    const Cd* dphi = (const Cd*)phi;
+    Cd* dout = (Cd*)out;
+    if (on_device) {
+      require_current_device(g->device, where);
+      require_device_ptr(phi, g->device, "phi");
+      require_device_ptr(out, g->device, "out");
+    } else {
+      Cd* a = ws.get<Cd>(nphi);
+      CK(cudaMemcpyAsync(a, phi, nphi * sizeof(Cd), cudaMemcpyHostToDevice, st));
+      dphi = a;
+      dout = ws.get<Cd>(nout);
+    }
+    std::vector<double> hp(pts, pts + nv);
+    double* dp = upload(ws, hp, st);
+    if (far) far_field(g->d_inc, g->nodes, g->total_nodes, g->k0, dphi, g->N, nrhs, dp, npts, dout, st);
+    else scattered_field(g->d_inc, g->nodes, g->total_nodes, g->k0, dphi, g->N, nrhs, dp, npts, dout, st);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(out, dout, nout * sizeof(Cd), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  });
+}
+}  // namespace
+
+pm_status pm_far_field(const pm_geometry* g, const pm_c64* phi, int32_t nrhs, int32_t on_device, const double* angles,
+                       int32_t ndir, pm_c64* out) {
+  return field_impl("pm_far_field", true, g, phi, nrhs, on_device, angles, ndir, out);
+}
+
+pm_status pm_scattered_field(const pm_geometry* g, const pm_c64* phi, int32_t nrhs, int32_t on_device,
+                             const double* xy, int32_t npts, pm_c64* out) {
+  return field_impl("pm_scattered_field", false, g, phi, nrhs, on_device, xy, npts, out);
+}
+
 pm_status pm_self_block(const pm_geometry* g, int32_t j, pm_c64* out) {
   if (!g || !out || j < 0 || j >= g->m) { g_err = "pm_self_block: bad argument"; return PM_ERR_INVALID_ARG; }
   return run_guarded("pm_self_block", [&] {
@@ -2244,6 +2717,17 @@ pm_status pm_factor_rank_data(const pm_factor* F, float* X, float* T, int32_t ca
     if (X) std::memcpy(X + (size_t)i * MLP_IN, &F->rank_X[(size_t)i * MLP_IN], sizeof(float) * MLP_IN);
     if (T) std::memcpy(T + (size_t)i * MLP_OUT, &F->rank_T[(size_t)i * MLP_OUT], sizeof(float) * MLP_OUT);
   }
+  return PM_OK;
+}
+
+pm_status pm_factor_proxy_data(const pm_factor* F, float* ratio, int32_t* redone, int32_t cap, int32_t* count) {
+  if (!F || !count || cap < 0 || (cap > 0 && (!ratio || !redone))) {
+    g_err = "pm_factor_proxy_data: bad argument";
+    return PM_ERR_INVALID_ARG;
+  }
+  const int n = (int)F->proxy_ratio.size();
+  *count = n;
+  for (int i = 0; i < n && i < cap; ++i) { ratio[i] = F->proxy_ratio[i]; redone[i] = F->proxy_redone[i]; }
   return PM_OK;
 }
 

@@ -16,6 +16,10 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA"
           5: "PM_ERR_NOT_CONVERGED", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_GEOMETRY", 8: "PM_ERR_UNSUPPORTED"}
 PM_FP64 = 0
 PM_MIXED = 1
+PM_FORM_OMIT = 0
+PM_FORM_ALL = 1
+PM_FORM_BM = 2
+PM_FORM_BM_SIMPLIFIED = 3
 
 
 class PmError(RuntimeError):
@@ -42,7 +46,8 @@ class pm_factor_opts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("proxy_factor", ct.c_double), ("proxy_points", ct.c_int32),
                 ("precision", ct.c_int32), ("stream", ct.c_void_p), ("flags", ct.c_uint32),
                 ("refine_tol", ct.c_double), ("max_refine", ct.c_int32), ("low_tol", ct.c_double),
-                ("rank_model", ct.c_void_p), ("debug_flags", ct.c_uint32)]
+                ("rank_model", ct.c_void_p), ("debug_flags", ct.c_uint32), ("proxy_scale", ct.c_double),
+                ("formulation", ct.c_int32), ("scratch_gb", ct.c_double)]
 
 
 class pm_solve_info(ct.Structure):
@@ -54,7 +59,8 @@ class pm_stats(ct.Structure):
                 ("ms_assemble", ct.c_double), ("ms_id", ct.c_double), ("ms_schur", ct.c_double),
                 ("ms_top", ct.c_double), ("ms_total", ct.c_double), ("cpqr_launches", ct.c_int32),
                 ("rank_checks", ct.c_int32), ("predictor_fallbacks", ct.c_int32), ("ms_level", ct.c_double * 16),
-                ("graph_captures", ct.c_int32), ("graph_launches", ct.c_int32)]
+                ("graph_captures", ct.c_int32), ("graph_launches", ct.c_int32), ("proxy_checked", ct.c_int32),
+                ("proxy_fallbacks", ct.c_int32), ("id_rows", ct.c_int64), ("level_chunks", ct.c_int32)]
 
 
 class pm_tune_entry(ct.Structure):
@@ -75,6 +81,7 @@ PM_FLAG_FF_CONFIRM = 16
 PM_FLAG_FP64_CONFIRM = 32
 PM_FLAG_NO_AUTOTUNE = 64
 PM_FLAG_NO_GRAPHS = 128
+PM_FLAG_PROXY_CHECK = 256
 PM_DEBUG_SINGULAR_BLOCK = 1
 PM_DEBUG_SINGULAR_COMPRESSED = 2
 PM_DEBUG_UNDERPREDICT = 4
@@ -98,10 +105,15 @@ EXPORTS = {
                                       ct.POINTER(ct.c_int32)]),
     "pm_matrix_entries": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "pm_self_block": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "pm_far_field": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
+                                ct.c_void_p]),
+    "pm_scattered_field": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
+                                      ct.c_void_p]),
     "pm_factor_profile": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_launch_counter": (ct.c_int, [ct.POINTER(ct.c_uint64)]),
     "pm_autotune_table": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_factor_rank_data": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "pm_factor_proxy_data": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "pm_mlp_forward": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "pm_mlp_loss_grad": (ct.c_int, [ct.c_int32, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_double,
                                     ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -229,6 +241,27 @@ class Geometry:
         _check(load().pm_self_block(self.h, j, out.ctypes.data))
         return out.T  # column-major -> row-major view
 
+    def far_field(self, phi, angles):
+        """u_inf at directions angles for host solutions phi (N,) or (N, nrhs)."""
+        phi = np.asarray(phi, dtype=np.complex128)
+        vec = phi.ndim == 1
+        P = np.ascontiguousarray((phi[:, None] if vec else phi).T)
+        ang = np.ascontiguousarray(angles, dtype=np.float64)
+        out = np.zeros((P.shape[0], len(ang)), dtype=np.complex128)
+        _check(load().pm_far_field(self.h, P.ctypes.data, P.shape[0], 0, ang.ctypes.data, len(ang), out.ctypes.data))
+        return out[0] if vec else out.T
+
+    def scattered_field(self, phi, points):
+        """u^s at points (P x 2) for host solutions phi (N,) or (N, nrhs)."""
+        phi = np.asarray(phi, dtype=np.complex128)
+        vec = phi.ndim == 1
+        P = np.ascontiguousarray((phi[:, None] if vec else phi).T)
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        out = np.zeros((P.shape[0], len(pts)), dtype=np.complex128)
+        _check(load().pm_scattered_field(self.h, P.ctypes.data, P.shape[0], 0, pts.ctypes.data, len(pts),
+                                         out.ctypes.data))
+        return out[0] if vec else out.T
+
     def self_block_noalloc(self, j, out_ptr):
         """A_jj into a caller-owned device buffer, with no device allocation."""
         _check(load().pm_self_block_noalloc(self.h, j, out_ptr))
@@ -242,7 +275,8 @@ class Geometry:
 class Factor:
     def __init__(self, geom, tol, proxy_factor=1.5, proxy_points=0, precision=PM_FP64, stream=None,
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
-                 qr_first=True, tensor_cores=False, ff_confirm=True, debug_flags=0, autotune=True, graphs=True):
+                 qr_first=True, tensor_cores=False, ff_confirm=True, debug_flags=0, autotune=True, graphs=True,
+                 proxy_scale=0.0, proxy_check=False, formulation=PM_FORM_OMIT, scratch_gb=0.0):
         """rank_model: device pointer (int) of a trained predictor, or None;
         ff_confirm: the refinement ends on the folded float-float product (default) or,
         with False, on the FP64 product (PM_FLAG_FP64_CONFIRM);
@@ -255,9 +289,10 @@ class Factor:
                            (PM_FLAG_PROFILE if profile else 0) | (0 if dense_operator else PM_FLAG_NO_DENSE_OPERATOR)
                            | (0 if qr_first else PM_FLAG_NO_QR_FIRST) | (PM_FLAG_TENSOR_CORES if tensor_cores else 0)
                            | (0 if ff_confirm else PM_FLAG_FP64_CONFIRM) | (0 if autotune else PM_FLAG_NO_AUTOTUNE)
-                           | (0 if graphs else PM_FLAG_NO_GRAPHS),
+                           | (0 if graphs else PM_FLAG_NO_GRAPHS) | (PM_FLAG_PROXY_CHECK if proxy_check else 0),
                            float(refine_tol), int(max_refine), float(low_tol),
-                           ct.c_void_p(rank_model) if rank_model else None, int(debug_flags))
+                           ct.c_void_p(rank_model) if rank_model else None, int(debug_flags), float(proxy_scale),
+                           int(formulation), float(scratch_gb))
         h = ct.c_void_p()
         _check(lib.pm_factorize(geom.h, ct.byref(o), ct.byref(h)))
         self.h = h
@@ -269,16 +304,30 @@ class Factor:
                 "ms_assemble": s.ms_assemble, "ms_id": s.ms_id, "ms_schur": s.ms_schur, "ms_top": s.ms_top,
                 "ms_total": s.ms_total, "cpqr_launches": s.cpqr_launches, "rank_checks": s.rank_checks,
                 "predictor_fallbacks": s.predictor_fallbacks, "ms_level": list(s.ms_level)[: s.levels + 1],
-                "graph_captures": s.graph_captures, "graph_launches": s.graph_launches}
+                "graph_captures": s.graph_captures, "graph_launches": s.graph_launches,
+                "proxy_checked": s.proxy_checked, "proxy_fallbacks": s.proxy_fallbacks, "id_rows": s.id_rows,
+                "level_chunks": s.level_chunks}
 
     def rank_data(self):
-        """(X, T): features (n x 8) and adaptive ranks / n_g (n x 2) of every box and group."""
+        """(X, T): features (n x 8) and, per box and group, (max(row rank, column rank) / n_g,
+        proxy count used / the rule's count) (n x 2)."""
         cnt = ct.c_int32()
         _check(load().pm_factor_rank_data(self.h, None, None, 0, ct.byref(cnt)))
         X = np.zeros((cnt.value, 8), dtype=np.float32)
         T = np.zeros((cnt.value, 2), dtype=np.float32)
         _check(load().pm_factor_rank_data(self.h, X.ctypes.data, T.ctypes.data, cnt.value, ct.byref(cnt)))
         return X, T
+
+    def proxy_data(self):
+        """(ratio, redone) per sample of rank_data(): the held-out proxy check's
+        ||H_J - H_S T|| / (tol ||H||) of the box (-1: not run) and whether the
+        box was redone with the rule's proxy count."""
+        cnt = ct.c_int32()
+        _check(load().pm_factor_proxy_data(self.h, None, None, 0, ct.byref(cnt)))
+        r = np.zeros(cnt.value, dtype=np.float32)
+        d = np.zeros(cnt.value, dtype=np.int32)
+        _check(load().pm_factor_proxy_data(self.h, r.ctypes.data, d.ctypes.data, cnt.value, ct.byref(cnt)))
+        return r, d
 
     def profile(self):
         cnt = ct.c_int32()
@@ -346,6 +395,7 @@ class _Handle:
         self.geom, self.h, self.last_info = geom, h, None
 
     stats = Factor.stats
+    proxy_data = Factor.proxy_data
     solve = Factor.solve
     solve_device = Factor.solve_device
     skeleton = Factor.skeleton
@@ -359,7 +409,8 @@ def factor_batch(geoms, tol, precision=PM_FP64, workers=8, rank_model=None, **kw
     o = pm_factor_opts(float(tol), float(kw.get("proxy_factor", 1.5)), int(kw.get("proxy_points", 0)),
                        int(precision), None, 0, float(kw.get("refine_tol", 0.0)), int(kw.get("max_refine", 0)),
                        float(kw.get("low_tol", 0.0)), ct.c_void_p(rank_model) if rank_model else None,
-                       int(kw.get("debug_flags", 0)))
+                       int(kw.get("debug_flags", 0)), float(kw.get("proxy_scale", 0.0)),
+                       int(kw.get("formulation", PM_FORM_OMIT)), float(kw.get("scratch_gb", 0.0)))
     gh = (ct.c_void_p * n)(*[g.h.value for g in geoms])
     out = (ct.c_void_p * n)()
     _check(load().pm_factor_batch(gh, n, ct.byref(o), out, workers))

@@ -1,5 +1,8 @@
-"""Learned ID-rank predictor: harvest (features, ranks) from factorizations,
-train the MLP with the library's own kernels, save / load the model.
+"""Learned ID-rank and proxy-count predictor: harvest (features, targets) from
+factorizations, train the MLP with the library's own kernels, save / load the
+model.  Targets per box and index group: the adaptive ID rank / n_g, and the
+smallest fraction of the closed-form proxy count that passes the library's
+held-out proxy check.
 
 Marshalling only: factorizations, training steps and inference run in the
 CUDA library (pm_factorize records the samples; pm_mlp_train trains).
@@ -45,15 +48,37 @@ def training_problems():
     return out
 
 
-def harvest(problems, precision=pm.PM_FP64):
+def harvest(problems, precision=pm.PM_FP64, ladder=(1.0, 0.7, 0.5, 0.35, 0.25), bound=200.0):
+    """(X, T) of every box and index group of the problems' factorizations.
+
+    T[:, 0]: max(row rank, column rank) / n_g at the rule's proxy count.
+    T[:, 1]: the smallest fraction s of the rule's proxy count on the ladder
+    such that the box passes the held-out proxy check (ratio <= bound) at s
+    and at every larger fraction of the ladder, from one factorization per
+    fraction with the check on.  Features come from the rule's run (they use
+    the rule's input sizes in every run)."""
     X, T = [], []
     for prob, tol in problems:
         g = pm.Geometry(prob)
-        f = pm.Factor(g, tol, precision=precision)
-        x, t = f.rank_data()
+        x = t = None
+        ok = None
+        label = None
+        for s in sorted(ladder, reverse=True):
+            f = pm.Factor(g, tol, precision=precision, proxy_scale=s, proxy_check=True)
+            xs, ts = f.rank_data()
+            ratio, _ = f.proxy_data()
+            if x is None:
+                x, t = xs, ts.copy()
+                ok = np.ones(len(xs), dtype=bool)
+                label = np.full(len(xs), float(s), dtype=np.float32)
+            if len(xs) == len(x):
+                ok &= (ratio >= 0) & (ratio <= bound)
+                label[ok] = s
+            del f
+        t[:, 1] = label
         X.append(x)
         T.append(t)
-        del f, g
+        del g
     return np.concatenate(X), np.concatenate(T)
 
 
@@ -88,11 +113,15 @@ def to_device(model):
 
 
 if __name__ == "__main__":
+    # python -m paper_2603_09381_gb300.rank_predictor [output.npy]: harvest the
+    # training problems' ranks and proxy-check outcomes, train, save
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import __graft_entry__
     __graft_entry__.build()
-    X, T = harvest(training_problems())
+    out = sys.argv[1] if len(sys.argv) > 1 else MODEL_PATH
+    X, T = harvest(training_problems(), ladder=(1.0, 0.6, 0.35))
     model, hist = train(X, T)
-    save(model)
-    print(f"samples {len(X)}  loss first {hist[0]:.4f} last {hist[-1]:.5f}  -> {MODEL_PATH}")
+    save(model, out)
+    print(f"samples {len(X)}  proxy label mean {T[:, 1].mean():.3f}  loss first {hist[0]:.4f} "
+          f"last {hist[-1]:.5f}  -> {out}")

@@ -111,6 +111,28 @@ def ellipse_batch(count=64, seed=3, m_lo=4, m_hi=400, spacing=1.0, n_lo=64, n_hi
     return probs
 
 
+def random_arrangement(m, seed=6, box=4.0, min_gap=0.12, n=96, k_out=2 * math.pi, k_ratio=2.0):
+    """m ellipses (semi-axes ~ U(0.2, 0.4), orientation ~ U[0, pi)) at random
+    positions in a box x box square, not on a grid (spacing 0): centres drawn
+    one by one and kept when the bounding circles stay min_gap apart."""
+    rng = np.random.default_rng(seed)
+    inc, cs, rs = [], [], []
+    tries = 0
+    while len(inc) < m:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place the inclusions")
+        a, b = rng.uniform(0.2, 0.4, size=2)
+        c = rng.uniform(0.0, box, size=2)
+        r = max(a, b)
+        if any(np.hypot(*(c - c2)) < r + r2 + min_gap for c2, r2 in zip(cs, rs)):
+            continue
+        cs.append(c)
+        rs.append(r)
+        inc.append(_inclusion(SHAPE_ELLIPSE, c[0], c[1], rng.uniform(0.0, math.pi), [a, b], n, k_ratio * k_out))
+    return {"k_out": float(k_out), "inclusions": inc, "grid_nx": 0, "grid_ny": 0, "spacing": 0.0}
+
+
 def plane_wave_angles(count, seed=2):
     """Incidence angles ~ U[0, 2 pi) for multi-RHS solves."""
     return np.random.default_rng(seed).uniform(0.0, 2 * math.pi, size=count).tolist()
@@ -129,6 +151,15 @@ def config_star16(nx=16, ny=16, n=128):
     """16x16 stars, k0 = 2 pi 20/16, k1 = 2 k0, n=128 (N=65,536), tol 1e-10, 8 RHS."""
     prob = star_grid(nx, ny, n=n, seed=1)
     opts = {"tol": 1e-10, "proxy_points": 0, "proxy_factor": 1.5}
+    return prob, opts, plane_wave_angles(8, seed=2)
+
+
+def config_fourier64(nx=64, ny=64, n=128):
+    """64x64 random smooth shapes r = 0.4 (1 + sum_{m=2..6} a_m cos(m t + phi_m)),
+    a_m ~ U(0, 0.04), per-inclusion k1/k0 ~ U(1.5, 3) (seed 4), k0 = 5,
+    n = 128 (N = 1,048,576), tol 1e-9, 8 RHS."""
+    prob = fourier_grid(nx, ny, n=n, seed=4, k_out=5.0)
+    opts = {"tol": 1e-9, "proxy_points": 0, "proxy_factor": 1.5}
     return prob, opts, plane_wave_angles(8, seed=2)
 
 

@@ -262,3 +262,51 @@ def test_mixed_dense_and_on_the_fly_operators_agree(pm):
     assert _rel(xa, xb) < 1e-9
     ref = dense.solve(prob, [0.9, 3.1])
     assert _rel(xa, ref) < 1e-8
+
+
+def test_levels_in_chunks_reproduce_the_unchunked_factorization(pm):
+    """A scratch budget too small for one box per launch makes every level run
+    box by box (the way the 64 x 64 grid's upper levels fit in memory); the
+    complex128 factorization is the same bit for bit."""
+    prob = wl.star_grid(4, 4, n=64, seed=1)
+    g = pm.Geometry(prob)
+    F = g.plane_wave([0.3, 2.9])
+    whole = pm.Factor(g, 1e-10)
+    chunked = pm.Factor(g, 1e-10, scratch_gb=1e-6)
+    sw, sc = whole.stats(), chunked.stats()
+    assert sw["level_chunks"] == sw["levels"]
+    assert sc["level_chunks"] == 16 + 4          # one chunk per box at both levels
+    assert (sw["K"], sw["skeleton"]) == (sc["K"], sc["skeleton"])
+    assert np.array_equal(whole.solve(F), chunked.solve(F))
+    for lev in (1, 2):
+        for b in range(4 if lev == 1 else 16):
+            assert all(np.array_equal(x, y) for x, y in zip(whole.skeleton(lev, b), chunked.skeleton(lev, b)))
+    # mixed mode: the chunked complex64 levels still precondition the refinement to 1e-10
+    m = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, scratch_gb=1e-6)
+    x = m.solve(F)
+    assert m.last_info["residual"] <= 1e-10
+    assert _rel(x, dense.solve(prob, [0.3, 2.9])) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_arbitrary_arrangement_matches_the_oracle(pm, precision):
+    """20 ellipses at random positions (spacing 0, Sec. 4.4's general
+    arrangements): the same automatic quadtree as the oracle (same depth,
+    boxes and compressed size in FP64) and the solution within the
+    threshold of the dense solve."""
+    prob = wl.random_arrangement(20, seed=6)
+    g = pm.Geometry(prob)
+    prec = pm.PM_MIXED if precision == "mixed" else pm.PM_FP64
+    f = pm.Factor(g, 1e-10, precision=prec)
+    angs = [0.3, 2.2]
+    phi = f.solve(g.plane_wave(angs))
+    ref = dense.solve(prob, angs)
+    fo = proxy.factor(prob, {"tol": 1e-10})
+    assert f.stats()["levels"] == fo["L"]
+    if precision == "fp64":
+        assert _rel(phi, ref) < 30 * 1e-10
+        F = np.stack([dense.plane_wave(prob, a) for a in angs], 1)
+        assert _rel(phi, proxy.solve(fo, F)) < 30 * 1e-10
+        print(f"random arrangement: K={f.stats()['K']} (oracle {fo['stats']['K']})")
+    else:
+        assert f.last_info["residual"] <= 1e-10 and _rel(phi, ref) < 1e-8

@@ -71,24 +71,48 @@ def test_training_fits_a_smooth_map(pm):
     assert np.sqrt(np.mean((dY.cpu().numpy() - T) ** 2)) < 0.03
 
 
-def test_predictor_gain_without_changing_the_factorization(pm):
-    """Trained on the solver's own rank data, the network presizes the CPQR of a
-    held-out problem: same ranks and solution, fewer host rank checks."""
+def test_predictor_presizes_ranks_and_proxy_counts(pm):
+    """Trained on the solver's own ranks and held-out proxy-check outcomes, the
+    network presizes a held-out problem's factorization.  With a fixed proxy
+    count the ranks and the solution are those of the run without it and the
+    host rank checks drop; with learned proxy counts the ID inputs shrink, the
+    compressed system is no larger, and the solution stays within the
+    solver's tolerance of the rule's (PM_FP64: every lowered box judged by
+    the held-out check, failures redone with the rule's count)."""
     from paper_2603_09381_gb300 import rank_predictor as rp
-    train_probs = [(wl.star_grid(4, 4, n=128, seed=s), 1e-10) for s in (1, 2, 3)] + \
-                  [(wl.star_grid(8, 8, n=64, seed=4), 1e-10), (wl.fourier_grid(4, 4, n=128, seed=5), 1e-10)]
-    X, T = rp.harvest(train_probs)
+    from oracle import dense
+    train_probs = [(wl.star_grid(4, 4, n=64, seed=s), tol) for s in (1, 2) for tol in (1e-10, 1e-6)] + \
+                  [(wl.fourier_grid(4, 4, n=128, seed=5), 1e-10), (wl.star_grid(8, 8, n=64, seed=4), 1e-10)]
+    X, T = rp.harvest(train_probs, ladder=(1.0, 0.6, 0.35))
+    assert X.shape[1] == 8 and np.all((T[:, 1] > 0) & (T[:, 1] <= 1))
     model, _ = rp.train(X, T, epochs=300, batch=32, lr=2e-3, lam=4.0)
-    held = wl.fourier_grid(8, 8, n=128, seed=21)
-    g = pm.Geometry(held)
-    f0 = pm.Factor(g, 1e-10)
     dm = rp.to_device(model)
-    f1 = pm.Factor(g, 1e-10, rank_model=dm.data_ptr())
+    held = wl.fourier_grid(4, 4, n=128, seed=21)
+    g = pm.Geometry(held)
+    F = g.plane_wave([0.4, 2.2])
+    # 1. ranks only (fixed proxy count): the same factorization, fewer host syncs
+    f0 = pm.Factor(g, 1e-10, proxy_points=96)
+    f1 = pm.Factor(g, 1e-10, proxy_points=96, rank_model=dm.data_ptr())
     s0, s1 = f0.stats(), f1.stats()
     assert s0["skeleton"] == s1["skeleton"] and s0["K"] == s1["K"]
-    F = g.plane_wave([0.4, 2.2])
     assert np.array_equal(f0.solve(F), f1.solve(F))
     assert s1["rank_checks"] < s0["rank_checks"]
-    print(f"rank checks {s0['rank_checks']} -> {s1['rank_checks']}, CPQR launches {s0['cpqr_launches']} -> "
-          f"{s1['cpqr_launches']}, fallbacks {s1['predictor_fallbacks']}, "
-          f"factor ms {s0['ms_total']:.1f} -> {s1['ms_total']:.1f}")
+    # 2. learned proxy counts
+    ref = dense.solve(held, [0.4, 2.2])
+    res = {}
+    for prec in (pm.PM_FP64, pm.PM_MIXED):
+        rule = pm.Factor(g, 1e-10, precision=prec)
+        lrn = pm.Factor(g, 1e-10, precision=prec, rank_model=dm.data_ptr())
+        sr, sl = rule.stats(), lrn.stats()
+        xr, xl = rule.solve(F), lrn.solve(F)
+        assert np.linalg.norm(xl - ref) <= 30 * 1e-10 * np.linalg.norm(ref) + np.linalg.norm(xr - ref)
+        assert sl["K"] <= sr["K"]
+        if sl["proxy_fallbacks"] == 0:
+            assert sl["id_rows"] < sr["id_rows"]
+        if prec == pm.PM_FP64:
+            assert sl["proxy_checked"] > 0
+        res[prec] = (sr, sl)
+        print(f"precision {prec}: id_rows {sr['id_rows']} -> {sl['id_rows']}, K {sr['K']} -> {sl['K']}, "
+              f"proxy checks {sl['proxy_checked']}, fallbacks {sl['proxy_fallbacks']}, "
+              f"factor ms {sr['ms_total']:.1f} -> {sl['ms_total']:.1f}, rank checks {sr['rank_checks']} -> "
+              f"{sl['rank_checks']}")
