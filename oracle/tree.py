@@ -7,6 +7,10 @@ Choices where the paper is silent:
     origin = the smallest centre coordinates; the grid is padded to
     2^L x 2^L, L = ceil(log2(max(nx, ny))); empty boxes are dropped;
   * a level-l box has centre origin + spacing (b 2^(L-l) + (2^(L-l) - 1)/2);
+  * spacing 0 (an arbitrary arrangement, Sec. 4.4's general layouts): the
+    quadtree of the centres' bounding square, deep enough for one centre per
+    cell (auto_cells); a leaf's centre is its inclusion's centre, a parent's
+    the centre of its cell;
   * r_cell = largest distance from the box centre to any node of the box's
     inclusions; the proxy circle has radius R_p = f r_cell (f = 1.5) and p
     equispaced points, p = opts["proxy_points"] if positive, otherwise
@@ -34,15 +38,37 @@ def morton(bx, by):
     return code
 
 
+def auto_cells(cent):
+    """Cells of an arbitrary arrangement (spacing 0): the bounding square of the
+    centres (side E, the larger extent, widened by a factor 1 + 2^-30) in
+    2^L x 2^L cells, L the smallest depth (up to 20) at which no two centres
+    share a cell; cell indices floor((c - origin) / (E / 2^L))."""
+    origin = cent.min(0)
+    ext = float(np.max(cent.max(0) - origin))
+    if len(cent) == 1 or ext == 0.0:
+        return origin, 1.0, 0, np.zeros((len(cent), 2), dtype=np.int64)
+    side = ext * (1.0 + 2.0 ** -30)
+    for L in range(1, 21):
+        cell = side / (1 << L)
+        ij = np.floor((cent - origin) / cell).astype(np.int64)
+        if len({(int(a), int(b)) for a, b in ij}) == len(ij):
+            return origin, cell, L, ij
+    raise ValueError("inclusion centres too close to separate")
+
+
 def build(prob, nds, opts):
     cent = np.array([[inc["cx"], inc["cy"]] for inc in prob["inclusions"]])
     s = float(prob["spacing"])
-    origin = cent.min(0)
-    ij = np.rint((cent - origin) / s).astype(np.int64)
-    if len({(int(a), int(b)) for a, b in ij}) != len(ij):
-        raise ValueError("two inclusions share a grid cell")
-    side = int(ij.max()) + 1
-    L = 0 if side <= 1 else int(math.ceil(math.log2(side)))
+    general = s == 0.0      # arbitrary arrangement: quadtree over the centres' bounding square
+    if general:
+        origin, s, L, ij = auto_cells(cent)
+    else:
+        origin = cent.min(0)
+        ij = np.rint((cent - origin) / s).astype(np.int64)
+        if len({(int(a), int(b)) for a, b in ij}) != len(ij):
+            raise ValueError("two inclusions share a grid cell")
+        side = int(ij.max()) + 1
+        L = 0 if side <= 1 else int(math.ceil(math.log2(side)))
     factor = float(opts.get("proxy_factor", 1.5))
     tol = float(opts["tol"])
     k0 = float(opts.get("k_rule", prob["k_out"]))   # the largest wavenumber the proxies must resolve
@@ -66,7 +92,12 @@ def build(prob, nds, opts):
     for lev, boxes in levels.items():
         scale = 2 ** (L - lev)
         for b in boxes:
-            c = origin + s * (np.array(b["key"], dtype=np.float64) * scale + (scale - 1) / 2.0)
+            if not general:
+                c = origin + s * (np.array(b["key"], dtype=np.float64) * scale + (scale - 1) / 2.0)
+            elif lev == L:
+                c = cent[b["leaves"][0]].copy()     # a leaf's proxy circle around its inclusion
+            else:
+                c = origin + s * (np.array(b["key"], dtype=np.float64) * scale + scale / 2.0)
             pts = np.concatenate([nds[j]["x"] for j in b["leaves"]])
             b["center"] = c
             b["r_cell"] = float(np.max(np.hypot(*(pts - c).T)))

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpmchwt.so")
-SOURCES = ["assemble.cu", "cpqr.cu", "dense_la.cu", "mlp.cu", "operator.cu", "peaks.cu", "qr.cu", "runtime.cu",
+SOURCES = ["assemble.cu", "cpqr.cu", "dense_la.cu", "field.cu", "mlp.cu", "operator.cu", "peaks.cu", "qr.cu", "runtime.cu",
            "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -1,0 +1,84 @@
+"""Scattered and far fields of the GPU solutions, and a frequency sweep (the
+study of the paper's Sec. 4.3: compressed size against frequency).
+
+The field kernels evaluate the oracle's formulas (oracle/field.py) on the
+same solution vector, so they must agree to rounding; the single disk's
+fields must match the Mie series, and lossless configurations must satisfy
+the optical theorem at every frequency of the sweep.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, field, mie
+from paper_2603_09381_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_09381_gb300 import pmchwt
+    return pmchwt
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_field_kernels_match_the_oracle_formulas(pm):
+    prob = wl.star_grid(4, 4, n=64, seed=2)
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10)
+    angs = [0.3, 2.0, 4.1]
+    phi = f.solve(g.plane_wave(angs))
+    th = np.linspace(0, 2 * np.pi, 91)
+    ff = g.far_field(phi, th)
+    for c in range(len(angs)):
+        assert _rel(ff[:, c], field.far_field(prob, phi[:, c], th)) < 1e-13
+    rng = np.random.default_rng(1)
+    pts = np.stack([rng.uniform(-2, 5, 30), rng.uniform(4.0, 6.0, 30)], -1)   # above the grid
+    us = g.scattered_field(phi, pts)
+    for c in range(len(angs)):
+        assert _rel(us[:, c], field.scattered_field(prob, phi[:, c], pts)) < 1e-12
+
+
+def test_single_disk_far_field_matches_mie(pm):
+    prob = wl.circle_grid(1, 1, n=64)
+    angle = 0.7
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-12)
+    phi = f.solve(g.plane_wave([angle]))[:, 0]
+    inc = prob["inclusions"][0]
+    k0, k1, a = prob["k_out"], inc["k_in"], inc["prm"][0]
+    M = int(math.ceil(max(k0, k1) * a)) + 30
+    am = mie.t_matrix(a, k0, k1, (k1 / k0) ** 2, M) * mie.incident_coeffs((0.0, 0.0), k0, angle, M)
+    th = np.linspace(0, 2 * np.pi, 37)
+    m = np.arange(-M, M + 1)
+    exact = math.sqrt(2 / (math.pi * k0)) * np.exp(-0.25j * math.pi) * (np.exp(1j * np.outer(th, m)) @ (am * (-1j) ** m))
+    assert np.max(np.abs(g.far_field(phi, th) - exact)) < 1e-10 * np.max(np.abs(exact))
+
+
+def test_frequency_sweep_compressed_size_and_energy(pm):
+    """Sec. 4.3: one star grid at omega = 1, 2, 4, 8 (eps- = 5), one
+    factorization per frequency.  The compressed size grows with omega D, and
+    every solution conserves energy (lossless: scattered power = extinction)."""
+    K = []
+    for omega in (1.0, 2.0, 4.0, 8.0):
+        prob = wl.star_grid(4, 4, n=128, seed=1, k_out=omega, k_ratio=5 ** 0.5, spacing=1.6)
+        g = pm.Geometry(prob)
+        f = pm.Factor(g, 1e-9)
+        angle = 0.0
+        phi = f.solve(g.plane_wave([angle]))[:, 0]
+        th = 2 * np.pi * np.arange(512) / 512
+        uf = g.far_field(phi, th)
+        scattered = np.sum(np.abs(uf) ** 2) * 2 * np.pi / 512
+        fwd = g.far_field(phi, np.array([angle]))[0]
+        extinction = -math.sqrt(8 * math.pi / omega) * (np.exp(0.25j * math.pi) * fwd).real
+        assert abs(scattered - extinction) < 1e-6 * scattered, omega
+        K.append(f.stats()["K"])
+    print("omega 1, 2, 4, 8 -> K", K)
+    assert K == sorted(K) and K[-1] > K[0]

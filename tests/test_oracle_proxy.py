@@ -116,3 +116,13 @@ def test_simplified_burton_miller_compressed_block_is_singular():
     far field, their interpolation vanishes and R A^{-1} L is singular."""
     with pytest.raises(proxy.SingularError):
         proxy.factor(wl.circle_grid(2, 2), {"tol": 1e-10, "formulation": "bm_simplified"})
+
+
+def test_arbitrary_arrangement_matches_dense():
+    """Inclusions placed at random, not on a grid (Sec. 4.4): the automatic
+    quadtree with containment-based near lists solves to the threshold."""
+    prob = wl.random_arrangement(20, seed=6)
+    fac = proxy.factor(prob, {"tol": 1e-10})
+    assert fac["L"] >= 2 and fac["stats"]["K"] < fac["N"]
+    F = np.stack([dense.plane_wave(prob, a) for a in (0.3, 2.2)], 1)
+    assert _rel(proxy.solve(fac, F), dense.solve(prob, [0.3, 2.2])) < 30 * 1e-10

@@ -57,3 +57,28 @@ def test_padding_and_ragged_grid():
     assert len(t["levels"][2]) == 6
     assert len(t["levels"][1]) == 2
     assert sorted(len(b["leaves"]) for b in t["levels"][1]) == [2, 4]
+
+
+def test_arbitrary_arrangement_tree():
+    """spacing 0: the bounding square of the centres at the smallest depth that
+    gives every centre its own cell; leaves centred on their inclusions; every
+    node of a non-near box outside the proxy circle at every level."""
+    prob = wl.random_arrangement(20, seed=6)
+    nds = geometry.all_nodes(prob)
+    cent = np.array([[i["cx"], i["cy"]] for i in prob["inclusions"]])
+    origin, cell, L, ij = tree.auto_cells(cent)
+    assert len({tuple(x) for x in ij}) == 20 and ij.min() >= 0 and ij.max() < 2 ** L
+    coarser = np.floor((cent - origin) / (2 * cell)).astype(int)
+    assert len({tuple(x) for x in coarser}) < 20            # one level less would not separate them
+    t = tree.build(prob, nds, {"tol": 1e-10})
+    assert t["L"] == L
+    for b in t["levels"][L]:
+        assert np.allclose(b["center"], cent[b["leaves"][0]])
+    for lev in range(1, L + 1):
+        boxes = t["levels"][lev]
+        for bi, b in enumerate(boxes):
+            for bj, o in enumerate(boxes):
+                if bj == bi or bj in b["near"]:
+                    continue
+                pts = np.concatenate([nds[j]["x"] for j in o["leaves"]])
+                assert np.min(np.hypot(*(pts - b["center"]).T)) >= b["R_p"]
