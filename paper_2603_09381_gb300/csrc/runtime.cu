@@ -74,11 +74,6 @@ struct Arena {
   }
   template <class T> T* get(size_t n) { return (T*)alloc(n * sizeof(T)); }
   void reset() { cur = 0; off = 0; }
-  size_t capacity() const {
-    size_t c = 0;
-    for (auto& b : blks) c += b.size;
-    return c;
-  }
   void release() {
     for (auto& b : blks) cudaFree(b.p);
     blks.clear();
