@@ -36,7 +36,7 @@ typedef enum {
   PM_ERR_CUDA = 3,          /* CUDA runtime error (message names the call) */
   PM_ERR_SINGULAR = 4,      /* exactly singular pivot in an LU, or R A^{-1} L singular */
   PM_ERR_NOT_CONVERGED = 5, /* PM_MIXED: refinement stopped above refine_tol after max_refine steps */
-  PM_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (tensor-core completion) */
+  PM_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (tensor-core completion, chained solve) */
   PM_ERR_GEOMETRY = 7,      /* inclusions not on a grid, two in one cell, ... */
   PM_ERR_UNSUPPORTED = 8    /* valid input the library does not handle yet */
 } pm_status;
@@ -178,7 +178,11 @@ typedef struct pm_factor pm_factor;
  *        factorization is unchanged;
  *      PM_DEBUG_TC_NO_ARRIVE makes the tensor-core kernels (PM_FLAG_TENSOR_CORES)
  *        wait, with a short bound, on a barrier that nothing arrives at
- *        before they issue any work (-> PM_ERR_TIMEOUT). */
+ *        before they issue any work (-> PM_ERR_TIMEOUT);
+ *      PM_DEBUG_SOLVE_NO_FLAG makes the chained top-level triangular solves
+ *        (one launch per triangle, used for at most 8 right-hand sides) wait,
+ *        with a 1 ms bound, on a flag that nothing sets before any work
+ *        (-> PM_ERR_TIMEOUT from pm_solve / pm_solve_ex). */
 typedef struct {
   double tol;
   double proxy_factor;
@@ -206,7 +210,8 @@ enum {
   PM_DEBUG_SINGULAR_BLOCK = 1,
   PM_DEBUG_SINGULAR_COMPRESSED = 2,
   PM_DEBUG_UNDERPREDICT = 4,
-  PM_DEBUG_TC_NO_ARRIVE = 8
+  PM_DEBUG_TC_NO_ARRIVE = 8,
+  PM_DEBUG_SOLVE_NO_FLAG = 16
 };
 
 /* Outcome of a refined solve (PM_MIXED): steps taken, the final largest
@@ -272,7 +277,10 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
  * host pointer, -> PM_ERR_INVALID_ARG before any launch), else host
  * pointers; they may alias.  A right-hand side with a NaN or infinite entry
  * -> PM_ERR_INVALID_ARG, phi untouched.  PM_MIXED factors refine the
- * solution (PM_ERR_NOT_CONVERGED if refine_tol is not reached). */
+ * solution (PM_ERR_NOT_CONVERGED if refine_tol is not reached).  With at
+ * most 8 right-hand sides the top-level triangular solves run as one chained
+ * launch per triangle whose cross-block waits are bounded: PM_ERR_TIMEOUT if
+ * one ran out (phi then invalid; the factor stays usable). */
 pm_status pm_solve(const pm_factor* f, const pm_c64* rhs, int32_t nrhs, pm_c64* phi, int32_t on_device);
 
 /* pm_solve that also reports the refinement outcome (info may be NULL). */

@@ -427,23 +427,27 @@ __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuProb<C>* __restric
   for (int i = 0; i < MB; ++i) if (i < jb) col[p + i] = v[i];
 }
 
-// Trailing update A22 -= L21 * U12.
+// Trailing update A22 -= L21 * U12 on the trailing columns [p+jb+lo, p+jb+hi)
+// (all of them: lo = 0, hi >= m).  Every entry is the same sum whatever the
+// column range, so a split update gives the same bits as the whole one.
 template <typename C>
-__global__ void __launch_bounds__(256) k_lu_update(const LuProb<C>* __restrict__ P, int p, int nb) {
+__global__ void __launch_bounds__(256) k_lu_update(const LuProb<C>* __restrict__ P, int p, int nb, int lo, int hi) {
   const LuProb<C> pr = P[blockIdx.y];
   const int m = pr.m;
   if (p >= m) return;
   const int jb = min(nb, m - p);
   const int mt = m - p - jb;
   if (mt <= 0) return;
-  const int tiles_m = (mt + TB - 1) / TB;
+  const int c0 = p + jb + lo, c1 = p + jb + min(hi, mt);
+  if (c1 <= c0) return;
+  const int tiles_m = (mt + TB - 1) / TB, tiles_n = (c1 - c0 + TB - 1) / TB;
   const int t = blockIdx.x;
-  if (t >= tiles_m * tiles_m) return;
+  if (t >= tiles_m * tiles_n) return;
   C* A = pr.A;
   const size_t ld = pr.ld;
   C mone = mk((typename real_of<C>::type)-1, (typename real_of<C>::type)0);
-  gemm_tile<C>(mt, mt, jb, A + (p + jb) + p * ld, pr.ld, A + p + (p + jb) * ld, pr.ld,
-               A + (p + jb) + (p + jb) * ld, pr.ld, mone, mk((typename real_of<C>::type)1, (typename real_of<C>::type)0),
+  gemm_tile<C>(mt, c1 - c0, jb, A + (p + jb) + p * ld, pr.ld, A + p + c0 * ld, pr.ld,
+               A + (p + jb) + c0 * ld, pr.ld, mone, mk((typename real_of<C>::type)1, (typename real_of<C>::type)0),
                0, t % tiles_m, t / tiles_m);
 }
 
@@ -582,6 +586,144 @@ __global__ void __launch_bounds__(128) k_getrs_update_thin(const SolveProb<C>* _
   *out = *out - (acc0 + acc1);
 }
 
+// One triangle of a single large LU solve with at most 8 right-hand sides as
+// ONE launch: a chain of RS_NB-row blocks, one CTA per block.  Each CTA
+// takes a ticket from a counter (so a CTA only ever waits on CTAs that took
+// a smaller ticket and are therefore already running: no co-residency is
+// assumed), maps it to its block (lower: top down; upper: bottom up), and
+// subtracts the products of the blocks it depends on in the same order and
+// with the same two-chain sums as k_getrs_update_thin, each as soon as that
+// block's flag is up; then it solves its diagonal block as k_getrs_diag
+// does, stores the result and raises its own flag.  Results are therefore
+// bit-identical to the launch-per-block sequence, without ~4 launches per
+// block on the critical path.  Every wait is bounded (TS_WAIT_NS); a wait
+// that runs out sets *err and the shared abort word, and every CTA then
+// leaves without writing.
+// sync: [0] ticket, [1] abort, [2, 2 + nblk) flags; zeroed before the launch.
+// no_flag (failure-path tests): every CTA first waits, with a 1 ms bound, on
+// `never`, which nothing sets.
+constexpr long long TS_WAIT_NS = 2000000000ll;   // 2 s per wait
+__device__ __forceinline__ unsigned long long ts_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ts_load_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void ts_store_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <typename C>
+__global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restrict__ P, int lower, int* sync,
+                                                    int* err, const int* never, int no_flag) {
+  typedef typename real_of<C>::type R;
+  constexpr int NB = 32;
+  __shared__ C sl[NB][NB + 1];   // the off-diagonal block of the current dependency, [col][row]
+  __shared__ C sx[NB][8];        // its solved rows
+  __shared__ C sa[NB][NB + 1];   // the diagonal block
+  __shared__ int s_t, s_stop;
+  const SolveProb<C> pr = P[0];
+  const int m = pr.m, nrhs = pr.nrhs;
+  const int nblk = (m + NB - 1) / NB;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_t = atomicAdd(&sync[0], 1);
+    s_stop = 0;
+    if (no_flag) {
+      const unsigned long long t0 = ts_now();
+      while (ts_load_acquire(never) == 0) {
+        if (ts_load_acquire(&sync[1]) != 0) break;
+        if ((long long)(ts_now() - t0) > 1000000ll) { atomicExch(err, 1); atomicExch(&sync[1], 1); break; }
+        __nanosleep(64);
+      }
+      s_stop = 1;
+    }
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int t = s_t;
+  if (t >= nblk) return;
+  const int b = lower ? t : nblk - 1 - t;
+  const int r0 = b * NB, jb = min(NB, m - r0);
+  const size_t ld = pr.ld;
+  int* flags = sync + 2;
+  for (int e = tid; e < jb * jb; e += 256) {
+    const int r = e % jb, c = e / jb;
+    sa[r][c] = pr.A[r0 + r + (size_t)(r0 + c) * ld];
+  }
+  // this thread's entry (row i, right-hand side q) of the block being solved
+  const int i = tid & 31, q = tid >> 5;
+  const bool mine = i < jb && q < nrhs;
+  C x = mine ? pr.B[r0 + i + (size_t)q * pr.ldb] : czero<C>();
+  const int ndep = lower ? b : nblk - 1 - b;
+  for (int d = 0; d < ndep; ++d) {
+    const int j = lower ? d : nblk - 1 - d;
+    const int c0 = j * NB, jbj = min(NB, m - c0);
+    // the coefficients do not depend on the flag: load them first
+    for (int e = tid; e < jb * jbj; e += 256) {
+      const int r = e % jb, c = e / jb;
+      sl[c][r] = pr.A[r0 + r + (size_t)(c0 + c) * ld];
+    }
+    if (tid == 0) {
+      const unsigned long long t0 = ts_now();
+      while (ts_load_acquire(&flags[j]) == 0) {
+        if (ts_load_acquire(&sync[1]) != 0) { s_stop = 1; break; }
+        if ((long long)(ts_now() - t0) > TS_WAIT_NS) {
+          atomicExch(err, 1);
+          atomicExch(&sync[1], 1);
+          s_stop = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+    for (int e = tid; e < jbj * nrhs; e += 256) {
+      const int l = e % jbj, qq = e / jbj;
+      sx[l][qq] = __ldcg(pr.B + c0 + l + (size_t)qq * pr.ldb);
+    }
+    __syncthreads();
+    if (mine) {
+      C acc0 = czero<C>(), acc1 = czero<C>();
+      int l = 0;
+      for (; l + 1 < jbj; l += 2) {
+        cfma(acc0, sl[l][i], sx[l][q]);
+        cfma(acc1, sl[l + 1][i], sx[l + 1][q]);
+      }
+      if (l < jbj) cfma(acc0, sl[l][i], sx[l][q]);
+      x = x - (acc0 + acc1);
+    }
+    __syncthreads();   // sl and sx are refilled next
+  }
+  // the diagonal block: warp q solves right-hand side q, lane r holds row r
+  if (mine) sx[i][q] = x;
+  __syncthreads();
+  if (warp < nrhs) {
+    const C dinv = (!lower && lane < jb) ? cdiv(mk((R)1, (R)0), sa[lane][lane]) : czero<C>();
+    C y = lane < jb ? sx[lane][warp] : czero<C>();
+    if (lower) {
+      for (int c = 0; c < jb - 1; ++c) {
+        const C yc = shfl_c(y, c);
+        if (lane > c && lane < jb) cfms(y, sa[lane][c], yc);
+      }
+    } else {
+      for (int c = jb - 1; c >= 0; --c) {
+        if (lane == c) y = y * dinv;
+        const C yc = shfl_c(y, c);
+        if (lane < c) cfms(y, sa[lane][c], yc);
+      }
+    }
+    if (lane < jb) pr.B[r0 + lane + (size_t)warp * pr.ldb] = y;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ts_store_release(&flags[b], 1);
+}
+
 }  // namespace
 
 template <typename C>
@@ -616,40 +758,116 @@ constexpr int LU_NB = 16;
 static_assert(LU_NB <= MAXNB, "LU panel wider than the kernels' shared tiles");
 constexpr int RS_NB = 32;
 
+// Flop counts of step p (panel, unit-lower solve of U12, trailing GEMM) for the profiler.
+inline void lu_step_flops(const int* h_m, int nprob, int p, double& fp, double& fs, double& fu) {
+  fp = fs = fu = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const int m = h_m[i];
+    if (p >= m) continue;
+    const double jb = std::min(LU_NB, m - p), rest = m - p - jb, h = m - p;
+    fp += 8.0 * (h * jb * jb / 2);
+    fs += 8.0 * rest * jb * jb / 2;
+    fu += 8.0 * rest * rest * jb;
+  }
+}
+
+template <typename C>
+void launch_panel_cluster(const LuProb<C>* d_prob, int nprob, int p, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nprob * 8);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 8;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_lu_panel_cluster<C, 256>, d_prob, p, LU_NB);
+}
+
+// A few large matrices (the top-level LU) with look-ahead: step p's update
+// of the next panel's LU_NB columns runs first, on a high-priority stream
+// with the panels, and the rest of the trailing update on a low-priority
+// stream, so that panel p+1 (latency-bound, on one 8-CTA cluster) overlaps
+// the bulk of update p instead of leaving the other SMs idle.  Step p+1's
+// interchanges wait for that update.  The kernels and their arithmetic are
+// those of the plain sequence (identical bits).
+template <typename C>
+void la_getrf_lookahead(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st) {
+  int pr_lo = 0, pr_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&pr_lo, &pr_hi);
+  cudaStream_t sp = nullptr, su = nullptr;
+  cudaStreamCreateWithPriority(&sp, cudaStreamNonBlocking, pr_hi);
+  cudaStreamCreateWithPriority(&su, cudaStreamNonBlocking, pr_lo);
+  cudaEvent_t e_fork, e_next, e_rest;
+  cudaEventCreateWithFlags(&e_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&e_next, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&e_rest, cudaEventDisableTiming);
+  cudaEventRecord(e_fork, st);
+  cudaStreamWaitEvent(sp, e_fork, 0);
+  cudaStreamWaitEvent(su, e_fork, 0);
+  bool rest_pending = false;
+  for (int p = 0; p < maxm; p += LU_NB) {
+    double fp, fs, fu;
+    lu_step_flops(h_m, nprob, p, fp, fs, fu);
+    KPROF_BEGIN(sp);
+    launch_panel_cluster<C>(d_prob, nprob, p, sp);
+    pm_launch_count_add(1);
+    KPROF_END(sp, kname<C>("lu_panel", "lu_panel32"), fp);
+    if (rest_pending) cudaStreamWaitEvent(sp, e_rest, 0);
+    dim3 g1((maxm + 255) / 256, nprob);
+    KPROF_BEGIN(sp);
+    k_lu_swap_trsm<C><<<g1, 256, 0, sp>>>(d_prob, p, LU_NB);
+    pm_launch_count_add(1);
+    KPROF_END(sp, kname<C>("lu_swap_trsm", "lu_swap_trsm32"), fs);
+    rest_pending = false;
+    const int mt = maxm - p - LU_NB;
+    if (mt <= 0) continue;
+    const int nrest = mt - LU_NB;
+    if (nrest > 0) cudaEventRecord(e_next, sp);   // interchanges and U12 of step p are done
+    const int tiles_m = (mt + TB - 1) / TB;
+    const double fn = fu * std::min(1.0, (double)LU_NB / mt);
+    KPROF_BEGIN(sp);
+    k_lu_update<C><<<dim3(tiles_m, nprob), 256, 0, sp>>>(d_prob, p, LU_NB, 0, LU_NB);
+    pm_launch_count_add(1);
+    KPROF_END(sp, kname<C>("lu_update", "lu_update32"), fn);
+    if (nrest > 0) {
+      cudaStreamWaitEvent(su, e_next, 0);
+      dim3 g2(tiles_m * ((nrest + TB - 1) / TB), nprob);
+      KPROF_BEGIN(su);
+      k_lu_update<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
+      pm_launch_count_add(1);
+      KPROF_END(su, kname<C>("lu_update", "lu_update32"), fu - fn);
+      cudaEventRecord(e_rest, su);
+      rest_pending = true;
+    }
+  }
+  cudaEventRecord(e_next, sp);
+  cudaEventRecord(e_rest, su);
+  cudaStreamWaitEvent(st, e_next, 0);
+  cudaStreamWaitEvent(st, e_rest, 0);
+  cudaEventDestroy(e_fork);
+  cudaEventDestroy(e_next);
+  cudaEventDestroy(e_rest);
+  cudaStreamDestroy(sp);
+  cudaStreamDestroy(su);
+}
+
 template <typename C>
 void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st) {
   if (nprob <= 0 || maxm <= 0) return;
+  if (nprob <= 8 && maxm >= 2048) {
+    la_getrf_lookahead<C>(d_prob, nprob, maxm, h_m, st);
+    return;
+  }
   for (int p = 0; p < maxm; p += LU_NB) {
     double fp = 0, fs = 0, fu = 0;
-    if (g_kprof) {
-      for (int i = 0; i < nprob; ++i) {
-        int m = h_m[i];
-        if (p >= m) continue;
-        double jb = std::min(LU_NB, m - p), rest = m - p - jb, h = m - p;
-        fp += 8.0 * (h * jb * jb / 2);          // panel: rank-1 updates inside the panel
-        fs += 8.0 * rest * jb * jb / 2;          // unit-lower solve of U12
-        fu += 8.0 * rest * rest * jb;            // trailing GEMM
-      }
-    }
+    if (g_kprof) lu_step_flops(h_m, nprob, p, fp, fs, fu);
     KPROF_BEGIN(st);
-    if (nprob <= 8 && maxm >= 2048) {
-      // a few large matrices (the top-level LU): a cluster of 8 CTAs each
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(nprob * 8);
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = 0;
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = 8;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      cudaLaunchKernelEx(&cfg, k_lu_panel_cluster<C, 256>, d_prob, p, LU_NB);
-    } else {
-      k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
-    }
+    k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
     KPROF_END(st, kname<C>("lu_panel", "lu_panel32"), fp);
     dim3 g1((maxm + 255) / 256, nprob);
@@ -662,16 +880,18 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
       int tiles = ((mt + TB - 1) / TB);
       dim3 g2(tiles * tiles, nprob);
       KPROF_BEGIN(st);
-      k_lu_update<C><<<g2, 256, 0, st>>>(d_prob, p, LU_NB);
+      k_lu_update<C><<<g2, 256, 0, st>>>(d_prob, p, LU_NB, 0, 1 << 30);
       pm_launch_count_add(1);
       KPROF_END(st, kname<C>("lu_update", "lu_update32"), fu);
     }
   }
 }
 
+int la_getrs_sync_ints(int maxm) { return 2 * (2 + (maxm + RS_NB - 1) / RS_NB) + 1; }
+
 template <typename C>
 void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
-                      const int* h_rhs, cudaStream_t st) {
+                      const int* h_rhs, cudaStream_t st, int* d_sync, int* d_err, int debug_no_flag) {
   if (nprob <= 0 || maxm <= 0 || maxrhs <= 0) return;
   double fl = 0;
   if (g_kprof)
@@ -688,6 +908,17 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
     k_getrs_swap<C><<<gsw, 128, 0, st>>>(d_prob);
   }
   pm_launch_count_add(1);
+  if (d_sync && d_err && nprob == 1 && maxrhs <= 8 && maxm > RS_NB) {
+    // one large matrix, few right-hand sides: each triangle as one chained launch
+    const int nblk = (maxm + RS_NB - 1) / RS_NB;
+    cudaMemsetAsync(d_sync, 0, sizeof(int) * la_getrs_sync_ints(maxm), st);
+    const int* never = d_sync + 2 * (2 + nblk);
+    k_trsv_chain<C><<<nblk, 256, 0, st>>>(d_prob, 1, d_sync, d_err, never, debug_no_flag);
+    k_trsv_chain<C><<<nblk, 256, 0, st>>>(d_prob, 0, d_sync + 2 + nblk, d_err, never, debug_no_flag);
+    pm_launch_count_add(2);
+    KPROF_END(st, kname<C>("getrs", "getrs32"), fl);
+    return;
+  }
   dim3 gs((maxrhs + DG_RHS - 1) / DG_RHS, nprob);
   const int tiles_n = (maxrhs + TB - 1) / TB;
   for (int p = 0; p < maxm; p += RS_NB) {
@@ -727,5 +958,7 @@ template void la_gemm_batched<double2>(const GemmDesc<double2>*, const int*, int
 template void la_gemm_batched<float2>(const GemmDesc<float2>*, const int*, int, int, cudaStream_t);
 template void la_getrf_batched<double2>(const LuProb<double2>*, int, int, const int*, cudaStream_t);
 template void la_getrf_batched<float2>(const LuProb<float2>*, int, int, const int*, cudaStream_t);
-template void la_getrs_batched<double2>(const SolveProb<double2>*, int, int, int, const int*, const int*, cudaStream_t);
-template void la_getrs_batched<float2>(const SolveProb<float2>*, int, int, int, const int*, const int*, cudaStream_t);
+template void la_getrs_batched<double2>(const SolveProb<double2>*, int, int, int, const int*, const int*, cudaStream_t,
+                                        int*, int*, int);
+template void la_getrs_batched<float2>(const SolveProb<float2>*, int, int, int, const int*, const int*, cudaStream_t,
+                                       int*, int*, int);

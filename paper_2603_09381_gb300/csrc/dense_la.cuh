@@ -36,9 +36,17 @@ void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob
 // h_m: host copy of the matrix sizes (flop accounting for the optional profiler)
 template <typename C>
 void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st);
+// d_sync / d_err (optional, device): for one matrix with at most 8
+// right-hand sides each triangle runs as one chained launch (k_trsv_chain);
+// d_sync holds la_getrs_sync_ints(maxm) ints (zeroed by the call) and
+// *d_err is set to 1 if one of its bounded waits runs out (results invalid).
+// debug_no_flag (failure-path tests): the chained launches first wait, with
+// a 1 ms bound, on a flag that nothing sets.
+int la_getrs_sync_ints(int maxm);
 template <typename C>
 void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
-                      const int* h_rhs, cudaStream_t st);
+                      const int* h_rhs, cudaStream_t st, int* d_sync = nullptr, int* d_err = nullptr,
+                      int debug_no_flag = 0);
 
 // tiles of a GEMM problem for the 32 x 32 output tiling
 inline int gemm_tiles(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }

@@ -216,6 +216,8 @@ struct pm_factor {
   std::mutex plan_mu;
   std::map<std::pair<int, int>, std::unique_ptr<struct SolvePlan>> plans;   // (kind, nrhs)
   int graph_launches = 0, graph_captures = 0;
+  // set by a bounded wait of the chained top-level solve that ran out (checked after every solve)
+  int* d_wait_err = nullptr;
   ~pm_factor();
 };
 
@@ -647,8 +649,11 @@ void lu_batch(std::vector<LuProb<C>>& probs, Arena& scr, cudaStream_t st, const 
     if (h[i] != 0) fail(PM_ERR_SINGULAR, std::string(what) + ": exactly singular pivot in LU");
 }
 
+// wait_err (optional): lets one large matrix with few right-hand sides take
+// the chained triangular solves, whose bounded waits report there.
 template <class C>
-void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st) {
+void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st, int* wait_err = nullptr,
+                 bool debug_no_flag = false) {
   if (probs.empty()) return;
   int maxm = 0, maxr = 0;
   std::vector<int> hm, hr;
@@ -657,7 +662,9 @@ void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st) 
     hm.push_back(p.m); hr.push_back(p.nrhs);
   }
   auto* dp = upload(scr, probs, st);
-  la_getrs_batched<C>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st);
+  int* sync = wait_err ? scr.get<int>(la_getrs_sync_ints(maxm)) : nullptr;
+  la_getrs_batched<C>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st, sync, wait_err,
+                      debug_no_flag ? 1 : 0);
   CK(cudaGetLastError());
 }
 
@@ -1680,7 +1687,7 @@ void solve_down(pm_factor* F, int nrhs, SolveWork<C>& w, C* phi, Arena& ws, cuda
 void root_solve(pm_factor* F, double2* x, int ldx, int nrhs, Arena& ws, cudaStream_t st) {
   BoxF<double2>& rt = F->root;
   std::vector<SolveProb<double2>> sv{SolveProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, x, ldx, nrhs}};
-  solve_batch<double2>(sv, ws, st);
+  solve_batch<double2>(sv, ws, st, F->d_wait_err, (F->opts.debug_flags & PM_DEBUG_SOLVE_NO_FLAG) != 0);
 }
 
 // phi = M^{-1} rhs with the compressed factorization (FP64 levels).
@@ -1940,7 +1947,13 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     info->residual = res;
     for (size_t i = 0; i < hist.size() && i < 16; ++i) info->history[i] = hist[i];
   }
-  if (res > tolr) fail(PM_ERR_NOT_CONVERGED, "iterative refinement stopped at relative residual " + std::to_string(res));
+  if (res > tolr) {
+    int werr = 0;
+    CK(cudaMemcpyAsync(&werr, F->d_wait_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (werr) return;   // reported as PM_ERR_TIMEOUT by the caller
+    fail(PM_ERR_NOT_CONVERGED, "iterative refinement stopped at relative residual " + std::to_string(res));
+  }
 }
 
 pm_status run_guarded(const char* where, const std::function<void()>& fn);
@@ -2101,6 +2114,8 @@ double setup_factor(pm_factor* F, const pm_geometry* g, const pm_factor_opts* op
   F->profiling = (opts->flags & 1u) != 0;
   if (F->precision == PM_FP64) F->lev64.assign(F->L + 1, {});
   else F->lev32.assign(F->L + 1, {});
+  F->d_wait_err = F->arena.get<int>(1);
+  CK(cudaMemsetAsync(F->d_wait_err, 0, sizeof(int), F->st));
   return id_tol;
 }
 
@@ -2454,8 +2469,15 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
       solve_refined(F, drhs, nrhs, dphi, ws, st, info);
     }
     if (!on_device) CK(cudaMemcpyAsync(phi, dphi, bytes, cudaMemcpyDeviceToHost, st));
+    int werr = 0;
+    CK(cudaMemcpyAsync(&werr, F->d_wait_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (F->profiling) F->prof.collect();
+    if (werr) {
+      CK(cudaMemsetAsync(F->d_wait_err, 0, sizeof(int), st));
+      CK(cudaStreamSynchronize(st));
+      fail(PM_ERR_TIMEOUT, "a bounded wait of the chained top-level solve ran out");
+    }
   });
 }
 }  // namespace

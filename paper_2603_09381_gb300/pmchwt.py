@@ -86,6 +86,7 @@ PM_DEBUG_SINGULAR_BLOCK = 1
 PM_DEBUG_SINGULAR_COMPRESSED = 2
 PM_DEBUG_UNDERPREDICT = 4
 PM_DEBUG_TC_NO_ARRIVE = 8
+PM_DEBUG_SOLVE_NO_FLAG = 16
 _lib = None
 
 EXPORTS = {

@@ -2,8 +2,9 @@
 
 Every fault here is made on the host: a block overwritten with zeros before
 its LU (a plain memset), a changed host decision (the predicted ranks), a
-tensor-core wait on a barrier that nothing arrives at (bounded, before any
-work is issued), a non-finite right-hand side, a host pointer where device
+tensor-core wait on a barrier that nothing arrives at and a chained-solve
+wait on a flag that nothing sets (both bounded, before any work is issued),
+a non-finite right-hand side, a host pointer where device
 memory belongs.  None of them faults the GPU: after each the context stays
 usable, which the last step of every test checks by solving again.
 """
@@ -134,3 +135,20 @@ def test_host_pointer_for_a_device_solve_is_rejected(pm):
     assert e.value.status == 1 and "device memory" in str(e.value)
     assert not np.any(out != 0)
     assert _still_solves(pm, prob)
+
+
+def test_chained_solve_wait_that_runs_out_returns_timeout(pm):
+    """The chained top-level triangular solves (one launch per triangle, each
+    block waiting on the flags of the blocks it depends on) first wait, with
+    a 1 ms bound, on a flag that nothing sets: every block leaves, the host
+    reports PM_ERR_TIMEOUT, and the same geometry then factors and solves."""
+    prob = wl.star_grid(2, 2, n=64, seed=1)
+    g = pm.Geometry(prob)
+    f = pm.Factor(g, 1e-10, debug_flags=pm.PM_DEBUG_SOLVE_NO_FLAG)
+    assert f.stats()["K"] > 32
+    F = g.plane_wave([0.5, 1.0])
+    with pytest.raises(pm.PmError) as e:
+        f.solve(F)
+    assert e.value.status == 6
+    f2 = pm.Factor(g, 1e-10)
+    assert _rel(f2.solve(F), dense.solve(prob, [0.5, 1.0])) < 1e-9
