@@ -7,6 +7,7 @@
 #include "dense_la.cuh"
 #include "prof.cuh"
 #include <algorithm>
+#include <vector>
 #include <cooperative_groups.h>
 
 namespace {
@@ -586,20 +587,23 @@ __global__ void __launch_bounds__(128) k_getrs_update_thin(const SolveProb<C>* _
   *out = *out - (acc0 + acc1);
 }
 
-// One triangle of a single large LU solve with at most 8 right-hand sides as
-// ONE launch: a chain of RS_NB-row blocks, one CTA per block.  Each CTA
-// takes a ticket from a counter (so a CTA only ever waits on CTAs that took
-// a smaller ticket and are therefore already running: no co-residency is
-// assumed), maps it to its block (lower: top down; upper: bottom up), and
-// subtracts the products of the blocks it depends on in the same order and
-// with the same two-chain sums as k_getrs_update_thin, each as soon as that
-// block's flag is up; then it solves its diagonal block as k_getrs_diag
-// does, stores the result and raises its own flag.  Results are therefore
-// bit-identical to the launch-per-block sequence, without ~4 launches per
-// block on the critical path.  Every wait is bounded (TS_WAIT_NS); a wait
-// that runs out sets *err and the shared abort word, and every CTA then
-// leaves without writing.
-// sync: [0] ticket, [1] abort, [2, 2 + nblk) flags; zeroed before the launch.
+// One triangle of the LU solves of a batch of matrices, each with at most 8
+// right-hand sides, as ONE launch: every matrix is a chain of RS_NB-row
+// blocks, one CTA per block.  Each CTA takes a ticket from a counter and
+// reads its (matrix, block) from items[ticket]; the items are ordered so that
+// every block comes after the blocks it depends on (lower: by block index
+// from the top, upper: by distance from the bottom), hence a CTA only ever
+// waits on CTAs that took a smaller ticket and are already running: no
+// co-residency is assumed.  A CTA subtracts the products of the blocks it
+// depends on in the same order and with the same two-chain sums as
+// k_getrs_update_thin, each as soon as that block's flag is up, then solves
+// its diagonal block as k_getrs_diag does, stores the result and raises its
+// own flag.  In FP64 the results are bit-identical to the launch-per-block
+// sequence, without ~4 launches per block on the critical path.  Every wait
+// is bounded (TS_WAIT_NS); a wait that runs out sets *err and the shared
+// abort word, and every CTA then leaves without writing.
+// items[t] = (matrix, block, flag base of the matrix, 0); sync: [0] ticket,
+// [1] abort, [2, 2 + total blocks) flags; zeroed before the launch.
 // no_flag (failure-path tests): every CTA first waits, with a 1 ms bound, on
 // `never`, which nothing sets.
 constexpr long long TS_WAIT_NS = 2000000000ll;   // 2 s per wait
@@ -617,17 +621,16 @@ __device__ __forceinline__ void ts_store_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 template <typename C>
-__global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restrict__ P, int lower, int* sync,
-                                                    int* err, const int* never, int no_flag) {
+__global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restrict__ P, const int4* __restrict__ items,
+                                                    int nitems, int lower, int* sync, int* err, const int* never,
+                                                    int no_flag) {
   typedef typename real_of<C>::type R;
   constexpr int NB = 32;
   __shared__ C sl[NB][NB + 1];   // the off-diagonal block of the current dependency, [col][row]
   __shared__ C sx[NB][8];        // its solved rows
   __shared__ C sa[NB][NB + 1];   // the diagonal block
   __shared__ int s_t, s_stop;
-  const SolveProb<C> pr = P[0];
-  const int m = pr.m, nrhs = pr.nrhs;
-  const int nblk = (m + NB - 1) / NB;
+
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     s_t = atomicAdd(&sync[0], 1);
@@ -645,11 +648,15 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
   __syncthreads();
   if (s_stop) return;
   const int t = s_t;
-  if (t >= nblk) return;
-  const int b = lower ? t : nblk - 1 - t;
+  if (t >= nitems) return;
+  const int4 it = items[t];
+  const SolveProb<C> pr = P[it.x];
+  const int m = pr.m, nrhs = pr.nrhs;
+  const int nblk = (m + NB - 1) / NB;
+  const int b = it.y;
   const int r0 = b * NB, jb = min(NB, m - r0);
   const size_t ld = pr.ld;
-  int* flags = sync + 2;
+  int* flags = sync + 2 + it.z;
   for (int e = tid; e < jb * jb; e += 256) {
     const int r = e % jb, c = e / jb;
     sa[r][c] = pr.A[r0 + r + (size_t)(r0 + c) * ld];
@@ -788,7 +795,8 @@ void launch_panel_cluster(const LuProb<C>* d_prob, int nprob, int p, cudaStream_
   cudaLaunchKernelEx(&cfg, k_lu_panel_cluster<C, 256>, d_prob, p, LU_NB);
 }
 
-// A few large matrices (the top-level LU) with look-ahead: step p's update
+// A few large matrices (the top-level LU, the upper levels' blocks) with
+// look-ahead, each panel on a cluster of 8 CTAs: step p's update
 // of the next panel's LU_NB columns runs first, on a high-priority stream
 // with the panels, and the rest of the trailing update on a low-priority
 // stream, so that panel p+1 (latency-bound, on one 8-CTA cluster) overlaps
@@ -859,7 +867,7 @@ void la_getrf_lookahead(const LuProb<C>* d_prob, int nprob, int maxm, const int*
 template <typename C>
 void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st) {
   if (nprob <= 0 || maxm <= 0) return;
-  if (nprob <= 8 && maxm >= 2048) {
+  if (nprob <= 16 && maxm >= 512) {
     la_getrf_lookahead<C>(d_prob, nprob, maxm, h_m, st);
     return;
   }
@@ -887,11 +895,30 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
   }
 }
 
-int la_getrs_sync_ints(int maxm) { return 2 * (2 + (maxm + RS_NB - 1) / RS_NB) + 1; }
+int la_chain_items(const int* h_m, int nprob, std::vector<int4>& items) {
+  std::vector<int> nb(nprob), base(nprob);
+  int total = 0, maxb = 0;
+  for (int i = 0; i < nprob; ++i) {
+    nb[i] = std::max(0, (h_m[i] + RS_NB - 1) / RS_NB);
+    base[i] = total;
+    total += nb[i];
+    maxb = std::max(maxb, nb[i]);
+  }
+  items.clear();
+  items.reserve(2 * (size_t)total);
+  for (int d = 0; d < maxb; ++d)   // lower: block d of every matrix that has one
+    for (int i = 0; i < nprob; ++i)
+      if (d < nb[i]) items.push_back(make_int4(i, d, base[i], 0));
+  for (int d = 0; d < maxb; ++d)   // upper: block d from the bottom
+    for (int i = 0; i < nprob; ++i)
+      if (d < nb[i]) items.push_back(make_int4(i, nb[i] - 1 - d, base[i], 0));
+  return total;
+}
+int la_chain_sync_ints(int total) { return 2 * (2 + total) + 1; }
 
 template <typename C>
 void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
-                      const int* h_rhs, cudaStream_t st, int* d_sync, int* d_err, int debug_no_flag) {
+                      const int* h_rhs, cudaStream_t st, const ChainArgs* chain) {
   if (nprob <= 0 || maxm <= 0 || maxrhs <= 0) return;
   double fl = 0;
   if (g_kprof)
@@ -908,14 +935,18 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
     k_getrs_swap<C><<<gsw, 128, 0, st>>>(d_prob);
   }
   pm_launch_count_add(1);
-  if (d_sync && d_err && nprob == 1 && maxrhs <= 8 && maxm > RS_NB) {
-    // one large matrix, few right-hand sides: each triangle as one chained launch
-    const int nblk = (maxm + RS_NB - 1) / RS_NB;
-    cudaMemsetAsync(d_sync, 0, sizeof(int) * la_getrs_sync_ints(maxm), st);
-    const int* never = d_sync + 2 * (2 + nblk);
-    k_trsv_chain<C><<<nblk, 256, 0, st>>>(d_prob, 1, d_sync, d_err, never, debug_no_flag);
-    k_trsv_chain<C><<<nblk, 256, 0, st>>>(d_prob, 0, d_sync + 2 + nblk, d_err, never, debug_no_flag);
-    pm_launch_count_add(2);
+  if (chain && maxrhs <= 8) {
+    // few right-hand sides: each triangle of every matrix in one chained launch
+    const int T = chain->total_blocks;
+    cudaMemsetAsync(chain->sync, 0, sizeof(int) * la_chain_sync_ints(T), st);
+    const int* never = chain->sync + 2 * (2 + T);
+    if (T > 0) {
+      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items, T, 1, chain->sync, chain->err, never,
+                                         chain->no_flag);
+      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items + T, T, 0, chain->sync + 2 + T, chain->err, never,
+                                         chain->no_flag);
+      pm_launch_count_add(2);
+    }
     KPROF_END(st, kname<C>("getrs", "getrs32"), fl);
     return;
   }
@@ -959,6 +990,6 @@ template void la_gemm_batched<float2>(const GemmDesc<float2>*, const int*, int, 
 template void la_getrf_batched<double2>(const LuProb<double2>*, int, int, const int*, cudaStream_t);
 template void la_getrf_batched<float2>(const LuProb<float2>*, int, int, const int*, cudaStream_t);
 template void la_getrs_batched<double2>(const SolveProb<double2>*, int, int, int, const int*, const int*, cudaStream_t,
-                                        int*, int*, int);
+                                        const ChainArgs*);
 template void la_getrs_batched<float2>(const SolveProb<float2>*, int, int, int, const int*, const int*, cudaStream_t,
-                                       int*, int*, int);
+                                       const ChainArgs*);

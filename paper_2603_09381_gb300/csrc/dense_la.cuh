@@ -3,6 +3,7 @@
 // All matrices are column-major with interleaved complex entries.
 #pragma once
 #include <cuda_runtime.h>
+#include <vector>
 #include "pm_common.cuh"
 
 template <typename C>
@@ -36,17 +37,27 @@ void la_gemm_batched(const GemmDesc<C>* d_desc, const int* d_tile_off, int nprob
 // h_m: host copy of the matrix sizes (flop accounting for the optional profiler)
 template <typename C>
 void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st);
-// d_sync / d_err (optional, device): for one matrix with at most 8
-// right-hand sides each triangle runs as one chained launch (k_trsv_chain);
-// d_sync holds la_getrs_sync_ints(maxm) ints (zeroed by the call) and
-// *d_err is set to 1 if one of its bounded waits runs out (results invalid).
-// debug_no_flag (failure-path tests): the chained launches first wait, with
-// a 1 ms bound, on a flag that nothing sets.
-int la_getrs_sync_ints(int maxm);
+// Chained triangular solves (k_trsv_chain): with at most 8 right-hand sides
+// per matrix, each triangle of every matrix of the batch runs in ONE launch
+// whose blocks wait on one another through flags (bounded waits).
+// la_chain_items fills the 2 x total ticket items (lower, then upper) for the
+// matrix sizes h_m and returns the total number of RS_NB-row blocks;
+// the sync buffer holds la_chain_sync_ints(total) ints (zeroed by the call);
+// *err is set to 1 if a wait runs out (the results are then invalid).
+// no_flag (failure-path tests): every block first waits, with a 1 ms bound,
+// on a flag that nothing sets.
+struct ChainArgs {
+  const int4* items;
+  int total_blocks;
+  int* sync;
+  int* err;
+  int no_flag;
+};
+int la_chain_items(const int* h_m, int nprob, std::vector<int4>& items);
+int la_chain_sync_ints(int total);
 template <typename C>
 void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
-                      const int* h_rhs, cudaStream_t st, int* d_sync = nullptr, int* d_err = nullptr,
-                      int debug_no_flag = 0);
+                      const int* h_rhs, cudaStream_t st, const ChainArgs* chain = nullptr);
 
 // tiles of a GEMM problem for the 32 x 32 output tiling
 inline int gemm_tiles(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }

@@ -649,8 +649,9 @@ void lu_batch(std::vector<LuProb<C>>& probs, Arena& scr, cudaStream_t st, const 
     if (h[i] != 0) fail(PM_ERR_SINGULAR, std::string(what) + ": exactly singular pivot in LU");
 }
 
-// wait_err (optional): lets one large matrix with few right-hand sides take
-// the chained triangular solves, whose bounded waits report there.
+// wait_err (optional): lets batches with at most 8 right-hand sides take the
+// chained triangular solves (one launch per triangle for all matrices),
+// whose bounded waits report there.
 template <class C>
 void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st, int* wait_err = nullptr,
                  bool debug_no_flag = false) {
@@ -662,9 +663,18 @@ void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st, 
     hm.push_back(p.m); hr.push_back(p.nrhs);
   }
   auto* dp = upload(scr, probs, st);
-  int* sync = wait_err ? scr.get<int>(la_getrs_sync_ints(maxm)) : nullptr;
-  la_getrs_batched<C>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st, sync, wait_err,
-                      debug_no_flag ? 1 : 0);
+  if (wait_err && maxr <= 8) {
+    std::vector<int4> items;
+    ChainArgs ch;
+    ch.total_blocks = la_chain_items(hm.data(), (int)probs.size(), items);
+    ch.items = items.empty() ? nullptr : upload(scr, items, st);
+    ch.sync = scr.get<int>(la_chain_sync_ints(ch.total_blocks));
+    ch.err = wait_err;
+    ch.no_flag = debug_no_flag ? 1 : 0;
+    la_getrs_batched<C>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st, &ch);
+  } else {
+    la_getrs_batched<C>(dp, (int)probs.size(), maxm, maxr, hm.data(), hr.data(), st);
+  }
   CK(cudaGetLastError());
 }
 
@@ -1607,7 +1617,7 @@ void solve_up(pm_factor* F, const C* rhs, int nrhs, SolveWork<C>& w, Arena& ws, 
     std::vector<SolveProb<C>> sv;
     for (size_t b = 0; b < BF.size(); ++b)
       sv.push_back(SolveProb<C>{BF[b].D, BF[b].mb, BF[b].mb, BF[b].ipiv, w.fin[l][b], BF[b].mb, nrhs});
-    solve_batch<C>(sv, ws, st);  // g_b = D_b^{-1} f_b
+    solve_batch<C>(sv, ws, st, F->d_wait_err, (F->opts.debug_flags & PM_DEBUG_SOLVE_NO_FLAG) != 0);  // g_b = D_b^{-1} f_b
     std::vector<C*> t(BF.size());
     GemmBatch<C> g1, g2;
     for (size_t b = 0; b < BF.size(); ++b) {
