@@ -795,8 +795,8 @@ void launch_panel_cluster(const LuProb<C>* d_prob, int nprob, int p, cudaStream_
   cudaLaunchKernelEx(&cfg, k_lu_panel_cluster<C, 256>, d_prob, p, LU_NB);
 }
 
-// A few large matrices (the top-level LU, the upper levels' blocks) with
-// look-ahead, each panel on a cluster of 8 CTAs: step p's update
+// A few large matrices (the top-level LU) with look-ahead, each panel on a
+// cluster of 8 CTAs: step p's update
 // of the next panel's LU_NB columns runs first, on a high-priority stream
 // with the panels, and the rest of the trailing update on a low-priority
 // stream, so that panel p+1 (latency-bound, on one 8-CTA cluster) overlaps
@@ -867,7 +867,7 @@ void la_getrf_lookahead(const LuProb<C>* d_prob, int nprob, int maxm, const int*
 template <typename C>
 void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h_m, cudaStream_t st) {
   if (nprob <= 0 || maxm <= 0) return;
-  if (nprob <= 16 && maxm >= 512) {
+  if (nprob <= 8 && maxm >= 2048) {
     la_getrf_lookahead<C>(d_prob, nprob, maxm, h_m, st);
     return;
   }

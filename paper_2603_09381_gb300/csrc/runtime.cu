@@ -51,20 +51,139 @@ void ck(cudaError_t e, const char* what) {
 
 void fail(pm_status s, const std::string& m) { throw PmError{s, m}; }
 
-// Bump allocator over large cudaMalloc blocks; reset() keeps the blocks for reuse.
+// Process-wide cache of freed device blocks.  Returning a large block with
+// cudaFree unmaps it (25 ms for the 69 GB operator of a 65,536-unknown
+// problem, 6 ms for 16 GB on GB300) and synchronises the device, and the next
+// factorization of the same problem asks for the same sizes again.  A freed
+// block is kept with an event recorded on the stream that last used it (or
+// after a device synchronisation when that stream is not known) and handed
+// out again, best fit within 1.5x of the request, once that event has
+// completed.  At most 45% of the device's memory stays cached; a cudaMalloc
+// that fails releases this device's cached blocks and retries;
+// pm_release_cached_memory releases them all.
+struct PoolBlk {
+  void* p;
+  size_t size;
+  int dev;
+  cudaEvent_t ev;   // null: idle when cached
+};
+std::mutex g_pool_mu;
+std::multimap<size_t, PoolBlk> g_pool;   // by size
+size_t g_pool_bytes[64] = {};            // cached bytes per device
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d < 0 || d >= 64 ? 0 : d;
+}
+
+size_t pool_cached_bytes(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  return g_pool_bytes[dev];
+}
+
+// Frees every cached block of device dev (all devices: dev < 0); returns the bytes freed.
+size_t pool_trim(int dev) {
+  std::vector<PoolBlk> out;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto it = g_pool.begin(); it != g_pool.end();) {
+      if (dev < 0 || it->second.dev == dev) {
+        out.push_back(it->second);
+        g_pool_bytes[it->second.dev] -= it->second.size;
+        it = g_pool.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  size_t n = 0;
+  const int cur = current_device();
+  for (auto& b : out) {
+    if (b.dev != cur) cudaSetDevice(b.dev);
+    if (b.ev) { cudaEventSynchronize(b.ev); cudaEventDestroy(b.ev); }
+    cudaFree(b.p);
+    if (b.dev != cur) cudaSetDevice(cur);
+    n += b.size;
+  }
+  return n;
+}
+
+void* pool_malloc(size_t bytes) {
+  const int dev = current_device();
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto it = g_pool.lower_bound(bytes); it != g_pool.end() && it->first <= bytes + bytes / 2; ++it) {
+      const PoolBlk& b = it->second;
+      if (b.dev != dev) continue;
+      if (b.ev && cudaEventQuery(b.ev) != cudaSuccess) { cudaGetLastError(); continue; }
+      void* p = b.p;
+      if (b.ev) cudaEventDestroy(b.ev);
+      g_pool_bytes[dev] -= it->first;
+      g_pool.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) == cudaSuccess) return p;
+  cudaGetLastError();
+  if (pool_trim(dev) == 0) return nullptr;
+  if (cudaMalloc(&p, bytes) == cudaSuccess) return p;
+  cudaGetLastError();
+  return nullptr;
+}
+
+// st: the stream whose work last used the block (nullptr: unknown).
+void pool_free(void* p, size_t bytes, const cudaStream_t* st) {
+  if (!p) return;
+  const int dev = current_device();
+  cudaEvent_t ev = nullptr;
+  if (st && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+    if (cudaEventRecord(ev, *st) != cudaSuccess) { cudaEventDestroy(ev); ev = nullptr; cudaDeviceSynchronize(); }
+  } else {
+    cudaDeviceSynchronize();
+  }
+  cudaGetLastError();
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  std::vector<PoolBlk> evict;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    g_pool.emplace(bytes, PoolBlk{p, bytes, dev, ev});
+    g_pool_bytes[dev] += bytes;
+    // over the cap: the largest other blocks of this device go first
+    for (auto it = g_pool.end(); g_pool_bytes[dev] > tot / 100 * 45 && it != g_pool.begin();) {
+      --it;
+      if (it->second.dev != dev || it->second.p == p) continue;
+      evict.push_back(it->second);
+      g_pool_bytes[dev] -= it->first;
+      it = g_pool.erase(it);
+    }
+  }
+  for (auto& b : evict) {
+    if (b.ev) { cudaEventSynchronize(b.ev); cudaEventDestroy(b.ev); }
+    cudaFree(b.p);
+  }
+}
+
+// Bump allocator over large device blocks (from the pool above); reset()
+// keeps the blocks for reuse.  `stream`, when set, is the stream its users
+// run on (the pool then waits for that stream's work instead of the device).
 struct Arena {
   struct Blk { char* p; size_t size; };
   std::vector<Blk> blks;
   size_t cur = 0, off = 0;
   size_t min_block = (size_t)64 << 20;
+  cudaStream_t stream = nullptr;
+  bool stream_known = false;
   void* alloc(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
     while (cur < blks.size() && off + bytes > blks[cur].size) { ++cur; off = 0; }
     if (cur == blks.size()) {
       size_t sz = std::max(bytes, min_block);
-      void* p = nullptr;
-      CK(cudaMalloc(&p, sz));
+      void* p = pool_malloc(sz);
+      if (!p) fail(PM_ERR_OOM, "device memory: " + std::to_string(sz) + " bytes");
       blks.push_back({(char*)p, sz});
       off = 0;
     }
@@ -74,8 +193,9 @@ struct Arena {
   }
   template <class T> T* get(size_t n) { return (T*)alloc(n * sizeof(T)); }
   void reset() { cur = 0; off = 0; }
+  void on_stream(cudaStream_t st) { stream = st; stream_known = true; }
   void release() {
-    for (auto& b : blks) cudaFree(b.p);
+    for (auto& b : blks) pool_free(b.p, b.size, stream_known ? &stream : nullptr);
     blks.clear();
     cur = off = 0;
   }
@@ -248,7 +368,7 @@ size_t g_dense_held = 0;
 
 pm_factor::~pm_factor() {
   if (dense64) {
-    cudaFree(dense64);
+    pool_free(dense64, dense_bytes, st ? &st : nullptr);
     std::lock_guard<std::mutex> lk(g_dense_mu);
     g_dense_held -= dense_bytes;
   }
@@ -1754,6 +1874,8 @@ void run_planned(pm_factor* F, int kind, const double2* rhs, int nrhs, double2* 
   auto& up = F->plans[std::make_pair(kind, nrhs)];
   if (!up) up.reset(new SolvePlan());
   SolvePlan& P = *up;
+  P.io.on_stream(st);
+  P.ws.on_stream(st);
   P.uses++;
   const size_t bytes = sizeof(double2) * (size_t)N * nrhs;
   if (!P.in) {
@@ -2124,6 +2246,8 @@ double setup_factor(pm_factor* F, const pm_geometry* g, const pm_factor_opts* op
   F->profiling = (opts->flags & 1u) != 0;
   if (F->precision == PM_FP64) F->lev64.assign(F->L + 1, {});
   else F->lev32.assign(F->L + 1, {});
+  F->arena.on_stream(F->st);
+  F->scratch.on_stream(F->st);
   F->d_wait_err = F->arena.get<int>(1);
   CK(cudaMemsetAsync(F->d_wait_err, 0, sizeof(int), F->st));
   return id_tol;
@@ -2193,7 +2317,7 @@ void factor_group_t(std::vector<pm_factor*>& Fs, double id_tol, Arena& scr, cuda
     if (!(budget > 0)) {
       size_t fr = 0, tot = 0;
       CK(cudaMemGetInfo(&fr, &tot));
-      budget = 0.35 * (double)fr;
+      budget = 0.35 * (double)(fr + pool_cached_bytes(current_device()));
     }
     const auto chunks = plan_chunks<C>(level_jobs, budget);
     for (const auto& jobs : chunks) {
@@ -2267,13 +2391,12 @@ void finish_mixed(pm_factor* F) {
     std::lock_guard<std::mutex> lk(g_dense_mu);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
+    fr += pool_cached_bytes(current_device());   // cached blocks are free for this purpose
     if (need <= fr / 10 * 6 && g_dense_held + need <= tot / 10 * 4) {
-      if (cudaMalloc(&F->dense64, need) == cudaSuccess) {
+      F->dense64 = (float4*)pool_malloc(need);
+      if (F->dense64) {
         F->dense_bytes = need;
         g_dense_held += need;
-      } else {
-        F->dense64 = nullptr;
-        cudaGetLastError();   // clear the failed allocation's error
       }
     }
   }
@@ -2299,6 +2422,12 @@ void finish_mixed(pm_factor* F) {
 extern "C" {
 
 const char* pm_last_error(void) { return g_err.c_str(); }
+
+pm_status pm_release_cached_memory(int64_t* bytes) {
+  const size_t n = pool_trim(-1);
+  if (bytes) *bytes = (int64_t)n;
+  return PM_OK;
+}
 
 pm_status pm_build_geometry(const pm_problem* prob, pm_geometry** out) {
   if (!prob || !out) { g_err = "pm_build_geometry: NULL argument"; return PM_ERR_INVALID_ARG; }
@@ -2436,6 +2565,7 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
     TuneScope ts((F->opts.flags & PM_FLAG_NO_AUTOTUNE) != 0);
     Arena ws;
     ws.min_block = 1 << 20;
+    ws.on_stream(st);
     const size_t bytes = sizeof(Cd) * (size_t)F->g->N * nrhs;
     if (on_device) {
       require_current_device(F->g->device, "pm_solve");
@@ -2571,6 +2701,7 @@ pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_f
       }
       Timer tt(st);
       Arena scr;
+      scr.on_stream(st);
       factor_group(Fs, id_tol, scr, st);
       scr.release();
       for (pm_factor* F : Fs)
@@ -2579,6 +2710,7 @@ pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_f
       for (pm_factor* F : Fs) {
         F->stats.ms_total = ms;
         F->st = nullptr;   // the worker streams end with the batch
+        F->arena.stream_known = F->scratch.stream_known = false;
       }
     });
   });

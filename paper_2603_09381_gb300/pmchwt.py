@@ -127,6 +127,7 @@ EXPORTS = {
                                ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_float),
                                ct.POINTER(ct.c_float), ct.c_void_p]),
     "pm_measure_peak": (ct.c_int, [ct.c_int32, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+    "pm_release_cached_memory": (ct.c_int, [ct.POINTER(ct.c_int64)]),
     "pm_factor_free": (None, [ct.c_void_p]),
     "pm_geometry_free": (None, [ct.c_void_p]),
     "pm_last_error": (ct.c_char_p, []),
@@ -185,6 +186,13 @@ def measure_peak(which, ms_target=200.0):
     v, mhz = ct.c_double(), ct.c_double()
     _check(load().pm_measure_peak(int(which), float(ms_target), ct.byref(v), ct.byref(mhz)))
     return v.value, mhz.value
+
+
+def release_cached_memory():
+    """Free the device blocks the library keeps for reuse; returns the bytes freed."""
+    n = ct.c_int64()
+    _check(load().pm_release_cached_memory(ct.byref(n)))
+    return n.value
 
 
 def autotune_table():

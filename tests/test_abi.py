@@ -38,6 +38,11 @@ def test_calls_fail_loudly_without_gpu():
     assert e.value.status == 3  # PM_ERR_CUDA: no CPU fallback
 
 
+def test_release_cached_memory_without_gpu_is_a_no_op():
+    from paper_2603_09381_gb300 import pmchwt as pm
+    assert pm.release_cached_memory() == 0
+
+
 def test_invalid_arguments_rejected_before_device_use():
     from paper_2603_09381_gb300 import pmchwt as pm
     from paper_2603_09381_gb300 import workloads as wl
