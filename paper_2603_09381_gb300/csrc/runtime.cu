@@ -55,10 +55,11 @@ void fail(pm_status s, const std::string& m) { throw PmError{s, m}; }
 // cudaFree unmaps it (25 ms for the 69 GB operator of a 65,536-unknown
 // problem, 6 ms for 16 GB on GB300) and synchronises the device, and the next
 // factorization of the same problem asks for the same sizes again.  A freed
-// block is kept with an event recorded on the stream that last used it (or
-// after a device synchronisation when that stream is not known) and handed
-// out again, best fit within 1.5x of the request, once that event has
-// completed.  At most 45% of the device's memory stays cached; a cudaMalloc
+// block is kept with an event recorded on the stream that last used it (only
+// while the caller knows that stream to be alive), as idle when the caller has
+// synchronised, or else after a device synchronisation (as cudaFree would
+// do), and handed out again, best fit within 1.5x of the request, once that
+// event has completed.  At most 45% of the device's memory stays cached; a cudaMalloc
 // that fails releases this device's cached blocks and retries;
 // pm_release_cached_memory releases them all.
 struct PoolBlk {
@@ -133,14 +134,18 @@ void* pool_malloc(size_t bytes) {
   return nullptr;
 }
 
-// st: the stream whose work last used the block (nullptr: unknown).
-void pool_free(void* p, size_t bytes, const cudaStream_t* st) {
+// How the caller knows that the work using a block has finished.
+enum class Done { Unknown, Idle, Stream };
+// Done::Stream: st is a live stream whose work last used the block (an event
+// is recorded on it); Done::Idle: the caller has synchronised; Done::Unknown:
+// the device is synchronised here.
+void pool_free(void* p, size_t bytes, Done how, cudaStream_t st = nullptr) {
   if (!p) return;
   const int dev = current_device();
   cudaEvent_t ev = nullptr;
-  if (st && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
-    if (cudaEventRecord(ev, *st) != cudaSuccess) { cudaEventDestroy(ev); ev = nullptr; cudaDeviceSynchronize(); }
-  } else {
+  if (how == Done::Stream && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+    if (cudaEventRecord(ev, st) != cudaSuccess) { cudaEventDestroy(ev); ev = nullptr; cudaDeviceSynchronize(); }
+  } else if (how != Done::Idle) {
     cudaDeviceSynchronize();
   }
   cudaGetLastError();
@@ -167,15 +172,13 @@ void pool_free(void* p, size_t bytes, const cudaStream_t* st) {
 }
 
 // Bump allocator over large device blocks (from the pool above); reset()
-// keeps the blocks for reuse.  `stream`, when set, is the stream its users
-// run on (the pool then waits for that stream's work instead of the device).
+// keeps the blocks for reuse.  release() tells the pool how the blocks' work
+// ends (the destructor: not known, so the device is synchronised).
 struct Arena {
   struct Blk { char* p; size_t size; };
   std::vector<Blk> blks;
   size_t cur = 0, off = 0;
   size_t min_block = (size_t)64 << 20;
-  cudaStream_t stream = nullptr;
-  bool stream_known = false;
   void* alloc(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
@@ -193,9 +196,11 @@ struct Arena {
   }
   template <class T> T* get(size_t n) { return (T*)alloc(n * sizeof(T)); }
   void reset() { cur = 0; off = 0; }
-  void on_stream(cudaStream_t st) { stream = st; stream_known = true; }
-  void release() {
-    for (auto& b : blks) pool_free(b.p, b.size, stream_known ? &stream : nullptr);
+  void release(Done how = Done::Unknown, cudaStream_t st = nullptr) {
+    for (auto& b : blks) {
+      pool_free(b.p, b.size, how, st);
+      if (how == Done::Unknown) how = Done::Idle;   // one device synchronisation covers the rest
+    }
     blks.clear();
     cur = off = 0;
   }
@@ -368,7 +373,7 @@ size_t g_dense_held = 0;
 
 pm_factor::~pm_factor() {
   if (dense64) {
-    pool_free(dense64, dense_bytes, st ? &st : nullptr);
+    pool_free(dense64, dense_bytes, Done::Unknown);   // the caller's stream may be gone
     std::lock_guard<std::mutex> lk(g_dense_mu);
     g_dense_held -= dense_bytes;
   }
@@ -1874,8 +1879,6 @@ void run_planned(pm_factor* F, int kind, const double2* rhs, int nrhs, double2* 
   auto& up = F->plans[std::make_pair(kind, nrhs)];
   if (!up) up.reset(new SolvePlan());
   SolvePlan& P = *up;
-  P.io.on_stream(st);
-  P.ws.on_stream(st);
   P.uses++;
   const size_t bytes = sizeof(double2) * (size_t)N * nrhs;
   if (!P.in) {
@@ -2246,8 +2249,6 @@ double setup_factor(pm_factor* F, const pm_geometry* g, const pm_factor_opts* op
   F->profiling = (opts->flags & 1u) != 0;
   if (F->precision == PM_FP64) F->lev64.assign(F->L + 1, {});
   else F->lev32.assign(F->L + 1, {});
-  F->arena.on_stream(F->st);
-  F->scratch.on_stream(F->st);
   F->d_wait_err = F->arena.get<int>(1);
   CK(cudaMemsetAsync(F->d_wait_err, 0, sizeof(int), F->st));
   return id_tol;
@@ -2311,7 +2312,7 @@ void factor_group_t(std::vector<pm_factor*>& Fs, double id_tol, Arena& scr, cuda
     // next level's boxes need.
     if (s > 0) {
       CK(cudaStreamSynchronize(st));
-      scr.release();
+      scr.release(Done::Idle);
     }
     double budget = Fs[0]->opts.scratch_gb * 1e9;
     if (!(budget > 0)) {
@@ -2545,7 +2546,7 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
     if (F->precision == PM_MIXED) finish_mixed(F);
     F->stats.ms_total = tt.stop();
     if (F->profiling) F->prof.collect();
-    F->scratch.release();
+    F->scratch.release(Done::Idle);   // tt.stop() waited for the stream
   });
   if (s != PM_OK) { delete F; return s; }
   *out = F;
@@ -2565,7 +2566,6 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
     TuneScope ts((F->opts.flags & PM_FLAG_NO_AUTOTUNE) != 0);
     Arena ws;
     ws.min_block = 1 << 20;
-    ws.on_stream(st);
     const size_t bytes = sizeof(Cd) * (size_t)F->g->N * nrhs;
     if (on_device) {
       require_current_device(F->g->device, "pm_solve");
@@ -2612,6 +2612,7 @@ pm_status solve_impl(const pm_factor* Fc, const pm_c64* rhs, int32_t nrhs, pm_c6
     int werr = 0;
     CK(cudaMemcpyAsync(&werr, F->d_wait_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    ws.release(Done::Idle);
     if (F->profiling) F->prof.collect();
     if (werr) {
       CK(cudaMemsetAsync(F->d_wait_err, 0, sizeof(int), st));
@@ -2701,16 +2702,14 @@ pm_status pm_factor_batch(const pm_geometry* const* g, int32_t count, const pm_f
       }
       Timer tt(st);
       Arena scr;
-      scr.on_stream(st);
       factor_group(Fs, id_tol, scr, st);
-      scr.release();
+      scr.release(Done::Stream, st);
       for (pm_factor* F : Fs)
-        if (F->precision == PM_MIXED) { finish_mixed(F); F->scratch.release(); }
+        if (F->precision == PM_MIXED) { finish_mixed(F); F->scratch.release(Done::Stream, st); }
       const double ms = tt.stop();
       for (pm_factor* F : Fs) {
         F->stats.ms_total = ms;
         F->st = nullptr;   // the worker streams end with the batch
-        F->arena.stream_known = F->scratch.stream_known = false;
       }
     });
   });
