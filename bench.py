@@ -227,7 +227,7 @@ def _traffic_for(kernel):
 FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",
                 "apply_offdiag64", "dense_matvec64", "dense_offdiag64"}        # FP64 flops
 FP32_FLOP_KERNELS = {"lu_update32", "lu_panel32", "lu_swap_trsm32", "getrs32", "gemm_batched32", "interp_solve32",
-                     "qr_update32", "tc_gemm32"}
+                     "qr_update32", "qr_update_tc32", "tc_gemm32"}
 BYTE_KERNELS = {"cpqr_step32"}     # memory-bound FP32 CPQR: algorithmic bytes
 
 

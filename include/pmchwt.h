@@ -102,11 +102,15 @@ typedef struct pm_factor pm_factor;
  *      PM_FLAG_NO_DENSE_OPERATOR, the operator is applied on the fly).  PM_MIXED reduces every complex64 ID
  *      input with at least twice as many rows as candidate columns to its
  *      triangular factor (unpivoted Householder QR) before the pivoted QR;
- *      PM_FLAG_NO_QR_FIRST pivots on the full input instead.  The trailing
- *      updates of that QR run on the FP32 CUDA cores; PM_FLAG_TENSOR_CORES
- *      moves them to the tensor cores (pm_gemm_c32's kernel), which is
- *      slower today and, over the long row reductions, adds enough rounding
- *      error to raise the ranks at the complex64 threshold.
+ *      PM_FLAG_NO_QR_FIRST pivots on the full input instead.  Each trailing
+ *      update of that QR, Q^H C = C - V (T^H (V^H C)), forms V^H C per block
+ *      of 256 rows on the FP32 CUDA cores, sums the blocks in a fixed order,
+ *      and applies C -= V Y on the tensor cores (3xTF32, FP32 accuracy; a
+ *      64-term real accumulation per tile); PM_FLAG_QR_CUDA_CORES applies it
+ *      on the CUDA cores instead.  PM_FLAG_TENSOR_CORES moves the whole
+ *      update to pm_gemm_c32's kernel, whose FP32 accumulation over the full
+ *      row count adds enough rounding error to raise the ranks at the
+ *      complex64 threshold.
  *      Confirming residual (PM_MIXED with the dense operator): by default the
  *      residual that ends the refinement comes from a float-float product of
  *      the stored operator whose sums are folded into FP64 every 16 columns
@@ -176,9 +180,10 @@ typedef struct pm_factor pm_factor;
  *      PM_DEBUG_UNDERPREDICT replaces every predicted rank by 1 (with a
  *        rank_model): every ID falls back to the adaptive checks, and the
  *        factorization is unchanged;
- *      PM_DEBUG_TC_NO_ARRIVE makes the tensor-core kernels (PM_FLAG_TENSOR_CORES)
- *        wait, with a short bound, on a barrier that nothing arrives at
- *        before they issue any work (-> PM_ERR_TIMEOUT);
+ *      PM_DEBUG_TC_NO_ARRIVE makes the tensor-core kernels (the QR update's
+ *        C -= V Y by default, pm_gemm_c32's with PM_FLAG_TENSOR_CORES) wait,
+ *        with a short bound, on a barrier that nothing arrives at before
+ *        they issue any work (-> PM_ERR_TIMEOUT);
  *      PM_DEBUG_SOLVE_NO_FLAG makes the chained top-level triangular solves
  *        (one launch per triangle, used for at most 8 right-hand sides) wait,
  *        with a 1 ms bound, on a flag that nothing sets before any work
@@ -371,7 +376,8 @@ enum {
   PM_FLAG_FP64_CONFIRM = 32,
   PM_FLAG_NO_AUTOTUNE = 64,
   PM_FLAG_NO_GRAPHS = 128,
-  PM_FLAG_PROXY_CHECK = 256
+  PM_FLAG_PROXY_CHECK = 256,
+  PM_FLAG_QR_CUDA_CORES = 512
 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 

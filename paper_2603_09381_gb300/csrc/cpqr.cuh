@@ -60,9 +60,14 @@ struct QrProb {
 // 32-column tiles right of a panel in any matrix.
 template <typename C>
 void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st);
-// max_rb: the most QR_RB-row blocks of rows j0..W-1 in any matrix.
+// max_rb: the most QR_RB-row blocks of rows j0..W-1 in any matrix.  With
+// tc_err (complex64 only) the last step, C -= V Y, runs on the tensor cores
+// (k_qr_apply_tc; max_w = the largest W), which set *tc_err if a bounded wait
+// runs out; without it, on the CUDA cores.  no_arrive: see k_qr_apply_tc
+// (tests of the timeout path).
 template <typename C>
-void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, int max_rb, cudaStream_t st);
+void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, int max_rb, cudaStream_t st,
+               int* tc_err = nullptr, int max_w = 0, bool no_arrive = false);
 template <typename C>
 void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t st);
 

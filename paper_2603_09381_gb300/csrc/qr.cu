@@ -17,7 +17,9 @@
 // (tile, block), so that the rows of a tall matrix spread over many CTAs.
 #include "cpqr.cuh"
 #include "prof.cuh"
+#include "tc_common.cuh"
 #include <cooperative_groups.h>
+#include <type_traits>
 
 namespace cg = cooperative_groups;
 
@@ -357,6 +359,160 @@ __global__ void __launch_bounds__(UT) k_qr_apply(const QrProb<C>* __restrict__ P
   }
 }
 
+// C_b -= V_b Y on the fifth-generation tensor cores (complex64, the default
+// path): one CTA per 64-row block of a matrix walks all 32-column tiles of
+// its trailing block.  The complex product is a real one of twice the size,
+// [Re D; Im D] = [[Re V, -Im V], [Im V, Re V]] [Re Y; Im Y], i.e. an
+// M = 128, N = 32, K = 64 real MMA; every FP32 operand is split into tf32
+// parts x = hi + lo and hi*hi + hi*lo + lo*hi are accumulated in FP32 (the
+// 3xTF32 scheme, FP32 accuracy), and each tile's accumulation is only 64
+// real terms long.  V_b is split into shared memory once; per tile the CTA
+// stages Y (from the row-block reduction) into one of two buffers, one
+// thread issues the 24 MMAs into one of two TMEM accumulators and commits
+// them to that buffer's mbarrier, and the epilogue of the previous tile
+// (tcgen05.ld, then C -= D with coalesced loads and stores) overlaps them.
+// Every wait is bounded; a wait that runs out sets *err and the CTA stops
+// writing.
+namespace tcq {
+constexpr int T = 128;                         // threads: warp w reads TMEM lanes [32w, 32w + 32)
+constexpr int ROWS = 64;                       // complex rows per CTA
+constexpr int KR = 2 * QR_NB;                  // real k: real and imaginary parts of the reflectors
+constexpr uint32_t A_BYTES = 2 * ROWS * KR * 4;    // one of hi / lo: 128 x 64 tf32
+constexpr uint32_t B_BYTES = 32 * KR * 4;          // one of hi / lo: 32 x 64 tf32
+constexpr uint32_t OFF_B = 2 * A_BYTES;            // two buffers of (hi, lo)
+constexpr uint32_t OFF_BAR = OFF_B + 4 * B_BYTES;
+constexpr int SMEM = OFF_BAR + 64;
+constexpr uint32_t IDESC = tcx::idesc_tf32(2 * ROWS, 32);
+constexpr uint32_t TMEM_COLS = 64;             // two 32-column accumulators
+constexpr int WAIT = 1 << 20;                  // x ~1 us suspend hint: about a second
+static_assert(B_BYTES * 2 >= 2 * ROWS * 32 * 4, "epilogue stage fits a (hi, lo) buffer");
+}  // namespace tcq
+
+// no_arrive (tests of the timeout path): every CTA first waits, with a bound
+// of about a millisecond, on a barrier that nothing arrives at, then issues
+// nothing, frees its tensor memory and sets *err.
+__global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __restrict__ P, int j0, int* err,
+                                                        int no_arrive) {
+  using namespace tcq;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const QrProb<float2> p = P[blockIdx.y];
+  if (j0 >= p.n) return;
+  const int jb = min(QR_NB, p.n - j0);
+  const int cfirst = j0 + jb;
+  const int ntiles = (p.n - cfirst + 31) / 32;
+  const int rbeg = j0 + (int)blockIdx.x * ROWS;
+  if (ntiles <= 0 || rbeg >= p.W) return;
+  const int rend = min(p.W, rbeg + ROWS);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* Ahi = sm;
+  unsigned char* Alo = sm + A_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 24);
+  if (tid == 0) {
+    tcx::mbar_init(&mbar[0]);
+    tcx::mbar_init(&mbar[1]);
+    tcx::mbar_init(&mbar[2]);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tcx::smem_u32(s_taddr)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // A: the block's reflector rows (unit diagonal, zeros above it and past W)
+#pragma unroll 4
+  for (int i = 0; i < 16; ++i) {
+    const int mm = tid & 63, kk = (tid >> 6) + 2 * i;
+    const float2 v = v_entry(p, j0, jb, rbeg + mm, kk);
+    tcx::put_split(Ahi, Alo, tcx::core_off<KR>(mm, kk), v.x);
+    tcx::put_split(Ahi, Alo, tcx::core_off<KR>(mm, QR_NB + kk), -v.y);
+    tcx::put_split(Ahi, Alo, tcx::core_off<KR>(ROWS + mm, kk), v.y);
+    tcx::put_split(Ahi, Alo, tcx::core_off<KR>(ROWS + mm, QR_NB + kk), v.x);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *s_taddr;
+  bool ok = true;
+  if (no_arrive) ok = tcx::mbar_wait(&mbar[2], 0, 1 << 10);
+  const int nt = __syncthreads_and(ok ? 1 : 0) ? ntiles : -1;
+  for (int t = 0; t <= nt; ++t) {
+    if (t < nt) {
+      const int b = t & 1;
+      unsigned char* Bhi = sm + OFF_B + b * 2 * B_BYTES;
+      unsigned char* Blo = Bhi + B_BYTES;
+      // Y of tile t (rows: reflectors, columns: the tile's columns), stored transposed
+      const float2* yp = p.Yp + (size_t)t * p.mrb * (QR_NB * 32);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int kk = tid & 31, nn = (tid >> 5) + 4 * i;
+        const float2 y = yp[kk + QR_NB * nn];
+        tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, kk), y.x);
+        tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, QR_NB + kk), y.y);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t acc = tmem + (uint32_t)(b * 32);
+        const uint32_t ah = tcx::smem_u32(Ahi), al = tcx::smem_u32(Alo);
+        const uint32_t bh = tcx::smem_u32(Bhi), bl = tcx::smem_u32(Blo);
+#pragma unroll
+        for (int s = 0; s < KR / 8; ++s) {
+          const uint32_t o = s * 2 * tcx::LBO;   // 8 tf32 along k = two core matrices
+          tcx::mma_tf32<IDESC>(acc, tcx::sdesc<KR>(ah + o), tcx::sdesc<KR>(bh + o), s > 0 ? 1u : 0u);
+          tcx::mma_tf32<IDESC>(acc, tcx::sdesc<KR>(ah + o), tcx::sdesc<KR>(bl + o), 1u);
+          tcx::mma_tf32<IDESC>(acc, tcx::sdesc<KR>(al + o), tcx::sdesc<KR>(bh + o), 1u);
+        }
+        tcx::mma_commit(&mbar[b]);
+      }
+    }
+    if (t >= 1) {   // epilogue of tile u = t - 1
+      const int u = t - 1, b = u & 1;
+      ok = ok && tcx::mbar_wait(&mbar[b], (uint32_t)((u >> 1) & 1), WAIT);   // after a failure: no more waits
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float d[32];
+      if (__all_sync(0xffffffffu, ok ? 1 : 0)) {
+        tcx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 32), d);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) d[j] = 0.f;
+      }
+      // tile u's operand buffer is free (its MMAs are done): stage D there,
+      // 128 rows x 32 columns, columns permuted by row (conflict-free)
+      float* sD = reinterpret_cast<float*>(sm + OFF_B + b * 2 * B_BYTES);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) sD[tid * 32 + (j ^ (tid & 31))] = d[j];
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      const int all_ok = __syncthreads_and(ok ? 1 : 0);
+      const int r = tid & 63, h = tid >> 6, row = rbeg + r;
+      const int c0 = cfirst + u * 32, nc = min(32, p.n - c0);
+      if (all_ok && row < rend) {
+#pragma unroll 4
+        for (int j = 0; j < 16; ++j) {
+          const int col = h * 16 + j;
+          if (col < nc) {
+            const float re = sD[r * 32 + (col ^ (r & 31))], im = sD[(ROWS + r) * 32 + (col ^ (r & 31))];
+            float2* pz = p.Z + row + (size_t)(c0 + col) * p.ld;
+            float2 z = *pz;
+            z.x -= re;
+            z.y -= im;
+            *pz = z;
+          }
+        }
+      }
+      if (!all_ok) ok = false;
+      __syncthreads();   // sD is tile t + 1's operand buffer
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  const int all_ok = __syncthreads_and(ok ? 1 : 0);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  if (!all_ok && tid == 0) atomicExch(err, 1);
+}
+
 // Zeros below the diagonal of the top n x n block (the reflectors' storage).
 template <typename C>
 __global__ void k_qr_zero_lower(const QrProb<C>* __restrict__ P) {
@@ -396,14 +552,26 @@ void qr_panel(const QrProb<C>* d_prob, int nprob, int j0, cudaStream_t st) {
   KPROF_END(st, kname<C>("qr_panel", "qr_panel32"), 0.0);
 }
 template <typename C>
-void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, int max_rb, cudaStream_t st) {
+void qr_update(const QrProb<C>* d_prob, int nprob, int j0, int max_tiles, int max_rb, cudaStream_t st,
+               int* tc_err, int max_w, bool no_arrive) {
   if (nprob <= 0 || max_tiles <= 0 || max_rb <= 0) return;
   KPROF_BEGIN(st);
   k_qr_ypart<C><<<dim3(max_tiles, max_rb, nprob), UT, 0, st>>>(d_prob, j0);
   k_qr_yreduce<C><<<dim3(max_tiles, nprob), UT, 0, st>>>(d_prob, j0);
-  k_qr_apply<C><<<dim3(max_tiles, max_rb, nprob), UT, 0, st>>>(d_prob, j0);
+  bool on_tc = false;
+  if constexpr (std::is_same<C, float2>::value) {
+    if (tc_err) {
+      // the same value every time: idempotent across threads and devices
+      cudaFuncSetAttribute(k_qr_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcq::SMEM);
+      const int rblocks = (max_w - j0 + tcq::ROWS - 1) / tcq::ROWS;
+      if (rblocks > 0) k_qr_apply_tc<<<dim3(rblocks, nprob), tcq::T, tcq::SMEM, st>>>(d_prob, j0, tc_err,
+                                                                                       no_arrive ? 1 : 0);
+      on_tc = true;
+    }
+  }
+  if (!on_tc) k_qr_apply<C><<<dim3(max_tiles, max_rb, nprob), UT, 0, st>>>(d_prob, j0);
   pm_launch_count_add(3);
-  KPROF_END(st, kname<C>("qr_update", "qr_update32"), 0.0);
+  KPROF_END(st, on_tc ? "qr_update_tc32" : kname<C>("qr_update", "qr_update32"), 0.0);
 }
 template <typename C>
 void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t st) {
@@ -413,5 +581,5 @@ void qr_zero_lower(const QrProb<C>* d_prob, int nprob, int max_n, cudaStream_t s
 }
 
 template void qr_panel<float2>(const QrProb<float2>*, int, int, cudaStream_t);
-template void qr_update<float2>(const QrProb<float2>*, int, int, int, int, cudaStream_t);
+template void qr_update<float2>(const QrProb<float2>*, int, int, int, int, cudaStream_t, int*, int, bool);
 template void qr_zero_lower<float2>(const QrProb<float2>*, int, int, cudaStream_t);

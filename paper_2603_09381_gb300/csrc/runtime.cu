@@ -1258,14 +1258,27 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
             maxW = std::max(maxW, qp[q].W);
           }
           auto* dqp = upload(scr, qp, st);
+          // C -= V Y on the tensor cores unless PM_FLAG_QR_CUDA_CORES
+          int* terr = nullptr;
+          if (!(O.flags & PM_FLAG_QR_CUDA_CORES)) {
+            terr = scr.get<int>(1);
+            CK(cudaMemsetAsync(terr, 0, sizeof(int), st));
+          }
           for (int j0 = 0; j0 < maxn; j0 += QR_NB) {
             qr_panel<C>(dqp, nq, j0, st);
             const int tiles = (maxn - j0 - QR_NB + 31) / 32;
             const int rbs = (maxW - j0 + QR_RB - 1) / QR_RB;
-            if (tiles > 0) qr_update<C>(dqp, nq, j0, tiles, rbs, st);
+            if (tiles > 0)
+              qr_update<C>(dqp, nq, j0, tiles, rbs, st, terr, maxW, (O.debug_flags & PM_DEBUG_TC_NO_ARRIVE) != 0);
           }
           qr_zero_lower<C>(dqp, nq, maxn, st);
-          if (g_kprof) g_kprof->add_flops("qr_update32", fl);
+          if (terr) {
+            int herr = 0;
+            CK(cudaMemcpyAsync(&herr, terr, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (herr) fail(PM_ERR_TIMEOUT, "a wait on the tensor cores ran out (QR update)");
+          }
+          if (g_kprof) g_kprof->add_flops(terr ? "qr_update_tc32" : "qr_update32", fl);
         } else {
           // Trailing update of every panel on the tensor cores: with V the
           // panel's reflectors (unit diagonal) and C its trailing block,

@@ -18,6 +18,7 @@
 // CTA owns TMEM lane i = real row i) and writes alpha D + beta C.  Every
 // mbarrier wait is bounded; a wait that runs out sets the caller's error flag.
 #include "tc_gemm.cuh"
+#include "tc_common.cuh"
 #include "prof.cuh"
 #include <cstdint>
 
@@ -31,64 +32,21 @@ constexpr int B_ROWS = TC_TN;             // 32
 constexpr uint32_t A_BYTES = A_ROWS * KR * 4;
 constexpr uint32_t B_BYTES = B_ROWS * KR * 4;
 constexpr uint32_t BUF = 2 * A_BYTES + 2 * B_BYTES;   // hi and lo of both operands
-constexpr uint32_t LBO = 128;             // next core matrix along k
-constexpr uint32_t SBO = (KR / 4) * 128;  // next 8-row group
 constexpr uint32_t TMEM_COLS = 32;
 constexpr int WAIT_LIMIT = 1 << 20;       // x ~1 us suspend hint: about a second
 constexpr int SMEM_BYTES = 2 * BUF + 64;
+constexpr uint32_t IDESC = tcx::idesc_tf32(A_ROWS, TC_TN);
+constexpr uint32_t LBO = tcx::LBO;
 
-// kind::tf32: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12 = 2), both
-// K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_TN >> 3) << 17) |
-                           ((uint32_t)(A_ROWS >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4);
-}
-
-// Shared-memory matrix descriptor: start address, leading (k) and stride
-// (8-row) byte offsets, each >> 4; version 1 at bit 46; no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((LBO >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((SBO >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, uint32_t off, float x) {
-  const float h = to_tf32(x);
-  *reinterpret_cast<float*>(hi + off) = h;
-  *reinterpret_cast<float*>(lo + off) = to_tf32(x - h);
-}
-
+using tcx::smem_u32;
+using tcx::put_split;
+__device__ __forceinline__ uint32_t core_off(int row, int k) { return tcx::core_off<KR>(row, k); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return tcx::sdesc<KR>(saddr); }
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = WAIT_LIMIT) {
-  const uint32_t a = smem_u32(bar);
-  for (int i = 0; i < limit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return tcx::mbar_wait(bar, parity, limit);
 }
-
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem),
-      "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate));
+  tcx::mma_tf32<IDESC>(tmem, ad, bd, accumulate);
 }
 
 __global__ void __launch_bounds__(TC_T) k_tc_gemm(const TcGemmProb* __restrict__ P, const int* __restrict__ tile_off,
@@ -205,15 +163,7 @@ __global__ void __launch_bounds__(TC_T) k_tc_gemm(const TcGemmProb* __restrict__
     // tcgen05.ld is warp-collective: the whole warp takes the same branch
     if (__all_sync(0xffffffffu, ok ? 1 : 0)) {
       const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
-          "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]), "=f"(d[6]), "=f"(d[7]),
-            "=f"(d[8]), "=f"(d[9]), "=f"(d[10]), "=f"(d[11]), "=f"(d[12]), "=f"(d[13]), "=f"(d[14]), "=f"(d[15]),
-            "=f"(d[16]), "=f"(d[17]), "=f"(d[18]), "=f"(d[19]), "=f"(d[20]), "=f"(d[21]), "=f"(d[22]), "=f"(d[23]),
-            "=f"(d[24]), "=f"(d[25]), "=f"(d[26]), "=f"(d[27]), "=f"(d[28]), "=f"(d[29]), "=f"(d[30]), "=f"(d[31])
-          : "r"(ta));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tcx::tmem_ld32(ta, d);
     }
   }
   // ok is per thread: make the CTA agree before branching on it

@@ -77,6 +77,18 @@ def test_tensor_core_wait_that_runs_out_returns_timeout(pm):
     assert _rel(f.solve(F), dense.solve(prob, [0.5])) < 1e-8
 
 
+def test_default_tensor_core_update_wait_that_runs_out_returns_timeout(pm):
+    """The default QR-first update applies C -= V Y on the tensor cores; with
+    the injected wait on a barrier that nothing arrives at, every CTA frees
+    its tensor memory and flags the error before issuing any work."""
+    prob = wl.star_grid(2, 2, n=64, seed=1)
+    g = pm.Geometry(prob)
+    with pytest.raises(pm.PmError) as e:
+        pm.Factor(g, 1e-10, precision=pm.PM_MIXED, debug_flags=pm.PM_DEBUG_TC_NO_ARRIVE)
+    assert e.value.status == 6
+    assert _still_solves(pm, prob)
+
+
 def test_forced_underprediction_falls_back_to_the_adaptive_rank(pm):
     """Every predicted rank forced to 1: each ID exceeds its prediction and
     falls back to the adaptive CPQR, which stays the judge of the rank, so the
