@@ -370,9 +370,9 @@ __global__ void __launch_bounds__(UT) k_qr_apply(const QrProb<C>* __restrict__ P
 // stages Y (from the row-block reduction) into one of two buffers, one
 // thread issues the 24 MMAs into one of two TMEM accumulators and commits
 // them to that buffer's mbarrier, and the epilogue of the previous tile
-// (tcgen05.ld, then C -= D with coalesced loads and stores) overlaps them.
-// Every wait is bounded; a wait that runs out sets *err and the CTA stops
-// writing.
+// (tcgen05.ld, then each thread's component of C -= D, with C loaded one
+// tile ahead) overlaps them.  Every wait is bounded; a wait that runs out
+// sets *err and the CTA stops writing.
 namespace tcq {
 constexpr int T = 128;                         // threads: warp w reads TMEM lanes [32w, 32w + 32)
 constexpr int ROWS = 64;                       // complex rows per CTA
@@ -385,7 +385,6 @@ constexpr int SMEM = OFF_BAR + 64;
 constexpr uint32_t IDESC = tcx::idesc_tf32(2 * ROWS, 32);
 constexpr uint32_t TMEM_COLS = 64;             // two 32-column accumulators
 constexpr int WAIT = 1 << 20;                  // x ~1 us suspend hint: about a second
-static_assert(B_BYTES * 2 >= 2 * ROWS * 32 * 4, "epilogue stage fits a (hi, lo) buffer");
 }  // namespace tcq
 
 // no_arrive (tests of the timeout path): every CTA first waits, with a bound
@@ -436,19 +435,35 @@ __global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __
   bool ok = true;
   if (no_arrive) ok = tcx::mbar_wait(&mbar[2], 0, 1 << 10);
   const int nt = __syncthreads_and(ok ? 1 : 0) ? ntiles : -1;
+  // Epilogue work split: thread tid owns TMEM lane tid = real row tid of D,
+  // i.e. the real (tid < 64) or imaginary (tid >= 64) part of complex row
+  // rbeg + (tid & 63), and updates that component of C itself (no exchange).
+  // C of tile t is loaded at iteration t and updated at iteration t + 1, and
+  // Y of tile t + 1 is loaded at iteration t, so their latency overlaps the
+  // MMAs and the previous epilogue.
+  const int r = tid & 63, comp = tid >> 6;
+  const int row = rbeg + r;
+  const bool row_ok = row < rend;
+  float cnext[32], ccur[32];
+  float2 ynext[8];
+  auto load_y = [&](int t) {
+    const float2* yp = p.Yp + (size_t)t * p.mrb * (QR_NB * 32);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ynext[i] = yp[(tid & 31) + QR_NB * ((tid >> 5) + 4 * i)];
+  };
+  if (nt > 0) load_y(0);
   for (int t = 0; t <= nt; ++t) {
     if (t < nt) {
       const int b = t & 1;
       unsigned char* Bhi = sm + OFF_B + b * 2 * B_BYTES;
       unsigned char* Blo = Bhi + B_BYTES;
-      // Y of tile t (rows: reflectors, columns: the tile's columns), stored transposed
-      const float2* yp = p.Yp + (size_t)t * p.mrb * (QR_NB * 32);
+      // Y of tile t (rows: reflectors, columns: the tile's columns), stored transposed;
+      // buffer b was last read by the MMAs of tile t - 2, waited for at iteration t - 1
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int kk = tid & 31, nn = (tid >> 5) + 4 * i;
-        const float2 y = yp[kk + QR_NB * nn];
-        tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, kk), y.x);
-        tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, QR_NB + kk), y.y);
+        tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, kk), ynext[i].x);
+        tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, QR_NB + kk), ynext[i].y);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -467,44 +482,33 @@ __global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __
         }
         tcx::mma_commit(&mbar[b]);
       }
+      if (t + 1 < nt) load_y(t + 1);
+      // this thread's component of C, tile t
+      const int c0 = cfirst + t * 32, nc = min(32, p.n - c0);
+      const float* cz = reinterpret_cast<const float*>(p.Z + row + (size_t)c0 * p.ld) + comp;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) cnext[j] = (row_ok && j < nc) ? cz[(size_t)j * 2 * p.ld] : 0.f;
     }
     if (t >= 1) {   // epilogue of tile u = t - 1
       const int u = t - 1, b = u & 1;
       ok = ok && tcx::mbar_wait(&mbar[b], (uint32_t)((u >> 1) & 1), WAIT);   // after a failure: no more waits
       asm volatile("tcgen05.fence::after_thread_sync;");
       float d[32];
-      if (__all_sync(0xffffffffu, ok ? 1 : 0)) {
+      const bool wok = __all_sync(0xffffffffu, ok ? 1 : 0);
+      if (wok) {
         tcx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 32), d);
-      } else {
+        const int c0 = cfirst + u * 32, nc = min(32, p.n - c0);
+        float* cz = reinterpret_cast<float*>(p.Z + row + (size_t)c0 * p.ld) + comp;
+        if (row_ok) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) d[j] = 0.f;
-      }
-      // tile u's operand buffer is free (its MMAs are done): stage D there,
-      // 128 rows x 32 columns, columns permuted by row (conflict-free)
-      float* sD = reinterpret_cast<float*>(sm + OFF_B + b * 2 * B_BYTES);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) sD[tid * 32 + (j ^ (tid & 31))] = d[j];
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      const int all_ok = __syncthreads_and(ok ? 1 : 0);
-      const int r = tid & 63, h = tid >> 6, row = rbeg + r;
-      const int c0 = cfirst + u * 32, nc = min(32, p.n - c0);
-      if (all_ok && row < rend) {
-#pragma unroll 4
-        for (int j = 0; j < 16; ++j) {
-          const int col = h * 16 + j;
-          if (col < nc) {
-            const float re = sD[r * 32 + (col ^ (r & 31))], im = sD[(ROWS + r) * 32 + (col ^ (r & 31))];
-            float2* pz = p.Z + row + (size_t)(c0 + col) * p.ld;
-            float2 z = *pz;
-            z.x -= re;
-            z.y -= im;
-            *pz = z;
-          }
+          for (int j = 0; j < 32; ++j)
+            if (j < nc) cz[(size_t)j * 2 * p.ld] = ccur[j] - d[j];
         }
       }
-      if (!all_ok) ok = false;
-      __syncthreads();   // sD is tile t + 1's operand buffer
+      asm volatile("tcgen05.fence::before_thread_sync;");
     }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ccur[j] = cnext[j];
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   const int all_ok = __syncthreads_and(ok ? 1 : 0);
