@@ -149,11 +149,16 @@ __device__ __forceinline__ float4 split4(double re, double im) {
 }
 
 // Dense off-diagonal operator: thread = (node t, node s) with t < s, nodes t
-// fastest.  One Hankel evaluation fills both 2 x 2 blocks of the pair:
-// with d = x_t - x_s, a = n_t.d/r, b = n_s.d/r and c = (ik/4) H1,
-//   (t <- s): -eps+S w_s,  D = c b w_s,  -D* = c a w_s,  N = (ik/4)[..] w_s
-//   (s <- t): -eps+S w_t,  D = -c a w_t, -D* = -c b w_t, N = (ik/4)[..] w_t
-// (the bracket of N is symmetric in the pair).
+// fastest.  One Hankel evaluation fills both 2 x 2 blocks of the pair.  The
+// operator is stored column-scaled, A = As diag(cs), with cs = w/4 for a
+// u-column (the density of -eps+ S and of the D-type block) and cs = k w/4
+// for a q-column, so the quadrature weight and the factors 1/4 and k/4 of
+// the kernels leave the per-pair arithmetic (the products scale X by cs
+// first).  With d = x_t - x_s, a = n_t.d/r, b = n_s.d/r:
+//   (t <- s): u-col (Y0 - i J0, -k a (Y1 - i J1)), q-col (-b (Y1 - i J1), N)
+//   (s <- t): u-col (Y0 - i J0, k b (Y1 - i J1)),  q-col (a (Y1 - i J1), N)
+// with N = -(c0 Y0 + c1 Y1) + i (c0 J0 + c1 J1), c0 = k a b,
+// c1 = (n_t.n_s - 2 a b)/r, symmetric in the pair.
 __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double ik,
                                                        float4* __restrict__ A, size_t lda) {
   const int s = blockIdx.y;
@@ -168,28 +173,43 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
   const double z = k * r;
   double J0, Y0, J1, Y1;
   hankel01_inv(z, ir * ik, J0, Y0, J1, Y1);
-  const double ws = nd.w[s], wt = nd.w[t];
   const double tnx = nd.nx[t], tny = nd.ny[t], snx = nd.nx[s], sny = nd.ny[s];
   const double a = (tnx * dx + tny * dy) * ir, b = (snx * dx + sny * dy) * ir;
-  const double nn = tnx * snx + tny * sny;
-  const double q = 0.25 * k;
-  const double c0 = k * a * b, c1 = (nn - 2 * a * b) * ir;
-  const double Nre = -(c0 * Y0 + c1 * Y1) * q, Nim = (c0 * J0 + c1 * J1) * q;   // (ik/4)[..]
-  // common factors, formed once (the FP64 pipe bounds this kernel)
-  const double s0r = 0.25 * Y0, s0i = -0.25 * J0;          // -eps+ S / w
-  const double y1q = Y1 * q, j1q = J1 * q;
-  const double ya = y1q * a, ja = j1q * a, yb = y1q * b, jb = j1q * b;
+  const double ab = a * b;
+  const double c0 = k * ab, c1 = fma(-2.0, ab, tnx * snx + tny * sny) * ir;
+  const double Nre = -fma(c0, Y0, c1 * Y1), Nim = fma(c0, J0, c1 * J1);
+  const double ka = k * a, kb = k * b;
   const size_t ut = nd.iu[t], qt = nd.iq[t], us = nd.iu[s], qs = nd.iq[s];
-  // rows of t, columns of s (column index: q density at the u-equation index, u density at the q index)
-  A[ut + us * lda] = split4t(s0r * ws, s0i * ws);
-  A[ut + qs * lda] = split4t(-yb * ws, jb * ws);
-  A[qt + us * lda] = split4t(-ya * ws, ja * ws);
-  A[qt + qs * lda] = split4t(Nre * ws, Nim * ws);
+  // rows of t, columns of s
+  A[ut + us * lda] = split4t(Y0, -J0);
+  A[qt + us * lda] = split4t(-ka * Y1, ka * J1);
+  A[ut + qs * lda] = split4t(-b * Y1, b * J1);
+  A[qt + qs * lda] = split4t(Nre, Nim);
   // rows of s, columns of t
-  A[us + ut * lda] = split4t(s0r * wt, s0i * wt);
-  A[us + qt * lda] = split4t(ya * wt, -ja * wt);
-  A[qs + ut * lda] = split4t(yb * wt, -jb * wt);
-  A[qs + qt * lda] = split4t(Nre * wt, Nim * wt);
+  A[us + ut * lda] = split4t(Y0, -J0);
+  A[qs + ut * lda] = split4t(kb * Y1, -kb * J1);
+  A[us + qt * lda] = split4t(a * Y1, -a * J1);
+  A[qs + qt * lda] = split4t(Nre, Nim);
+}
+
+// Column scales of the stored operator: cs[u index] = w/4, cs[q index] = k w/4.
+__global__ void k_dense_colscale(const double* __restrict__ w, const int* __restrict__ iu, const int* __restrict__ iq,
+                                 int total, double k, double* __restrict__ cs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  cs[iu[t]] = 0.25 * w[t];
+  cs[iq[t]] = 0.25 * k * w[t];
+}
+
+// Xs = diag(cs) X (the right-hand operand of a product with the stored operator).
+__global__ void k_scale_rows(const double* __restrict__ cs, const double2* __restrict__ X, int ldx,
+                             double2* __restrict__ Xs, int ldxs, int N) {
+  const int q = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double c = cs[i];
+  const double2 v = X[i + (size_t)q * ldx];
+  Xs[i + (size_t)q * ldxs] = make_double2(c * v.x, c * v.y);
 }
 
 // Skinny product Y = A X: a CTA owns 128 rows and one segment of the columns of
@@ -401,13 +421,15 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __re
   }
 }
 
+// dst = split(src diag(1 / cs)): a self block into the column-scaled operator.
 __global__ void k_split_copy(const double2* __restrict__ src, int lds, float4* __restrict__ dst, size_t ldd, int m,
-                             int n) {
+                             int n, const double* __restrict__ cs) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * n) return;
   const int i = e % m, j = e / m;
   const double2 v = src[i + (size_t)j * lds];
-  dst[i + (size_t)j * ldd] = split4t(v.x, v.y);
+  const double c = 1.0 / cs[j];
+  dst[i + (size_t)j * ldd] = split4t(v.x * c, v.y * c);
 }
 
 __global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,
@@ -486,9 +508,24 @@ void apply_offdiag64(OpNodes nd, int total, double k0, const double2* X, int ldx
   KPROF_END(st, "apply_offdiag64", 0.0);
 }
 
-void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, cudaStream_t st) {
+void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, const double* cs,
+                cudaStream_t st) {
   if (m <= 0 || n <= 0) return;
-  k_split_copy<<<(m * n + 255) / 256, 256, 0, st>>>(src, lds, dst, ldd, m, n);
+  k_split_copy<<<(m * n + 255) / 256, 256, 0, st>>>(src, lds, dst, ldd, m, n, cs);
+  pm_launch_count_add(1);
+}
+
+void dense_colscale(const double* w, const int* iu, const int* iq, int total_nodes, double k0, double* cs,
+                    cudaStream_t st) {
+  if (total_nodes <= 0) return;
+  k_dense_colscale<<<(total_nodes + 255) / 256, 256, 0, st>>>(w, iu, iq, total_nodes, k0, cs);
+  pm_launch_count_add(1);
+}
+
+void scale_rows(const double* cs, const double2* X, int ldx, double2* Xs, int ldxs, int N, int nrhs,
+                cudaStream_t st) {
+  if (N <= 0 || nrhs <= 0) return;
+  k_scale_rows<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(cs, X, ldx, Xs, ldxs, N);
   pm_launch_count_add(1);
 }
 

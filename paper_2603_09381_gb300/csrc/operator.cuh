@@ -20,12 +20,21 @@ void apply_offdiag64(OpNodes nd, int total_nodes, double k0, const double2* X, i
 // {hi(re), hi(im), lo(re), lo(im)} with hi = a truncated to 24 significant
 // bits and lo the next 24 bits, so hi + lo is exact in FP64 and within 2^-47
 // of the entry, in 16 bytes.
+// The stored operator is column-scaled: As = A diag(1 / cs) with cs[u index]
+// = w/4 and cs[q index] = k0 w/4 (dense_colscale), so that A X = As (cs X):
+// every product below takes cs X (scale_rows) as its right-hand operand.
 // Off-diagonal part written out densely (column-major, leading dimension lda);
 // same-inclusion pairs untouched (the caller copies the self blocks in).  One
 // Hankel evaluation per node pair fills the pair's 2 x 2 entries.
 void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, float4* A, size_t lda, cudaStream_t st);
-// dst (split) <- src (FP64) for an m x n block.
-void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, cudaStream_t st);
+void dense_colscale(const double* w, const int* iu, const int* iq, int total_nodes, double k0, double* cs,
+                    cudaStream_t st);
+// Xs = diag(cs) X, N x nrhs.
+void scale_rows(const double* cs, const double2* X, int ldx, double2* Xs, int ldxs, int N, int nrhs,
+                cudaStream_t st);
+// dst (split) <- src diag(1 / cs) (FP64) for an m x n block (cs: its n column scales).
+void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, const double* cs,
+                cudaStream_t st);
 // Y (N x nrhs) = A X in FP64 arithmetic (entries hi + lo); Y overwritten.
 void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st);

@@ -335,6 +335,7 @@ struct pm_factor {
   int* d_iu = nullptr;
   int* d_iq = nullptr;
   float4* dense64 = nullptr;    // the whole FP64 operator, N x N, split hi/lo, when it fits the memory budget
+  double* d_colscale = nullptr; // its column scales: A = dense64 diag(d_colscale)
   size_t dense_bytes = 0;
   // CUDA graphs of the compressed inverse (FP64) or the mixed preconditioner,
   // one per right-hand-side count; solves of one factor are serialised by plan_mu
@@ -1947,7 +1948,9 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
   const pm_geometry* g = F->g;
   const int N = g->N;
   if (F->dense64) {
-    dense_matvec64(F->dense64, (size_t)N, N, X, N, Y, N, nrhs, st);
+    double2* Xs = ws.get<double2>((size_t)N * nrhs);
+    scale_rows(F->d_colscale, X, N, Xs, N, N, nrhs, st);
+    dense_matvec64(F->dense64, (size_t)N, N, Xs, N, Y, N, nrhs, st);
     if (g_kprof) g_kprof->add_flops("dense_matvec64", 8.0 * (double)N * N * nrhs);
     CK(cudaGetLastError());
     return;
@@ -2001,9 +2004,15 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   // sequential FP64 sum, on the FP32 pipes), or with PM_FLAG_FP64_CONFIRM the
   // FP64 product.
   const bool ff_confirm = F->dense64 && !(F->opts.flags & PM_FLAG_FP64_CONFIRM);
+  // the stored operator is column-scaled: its products take diag(cs) x
+  double2* Xs = F->dense64 ? ws.get<double2>((size_t)N * nrhs) : nullptr;
+  auto scaled = [&](const double2* x) -> const double2* {
+    scale_rows(F->d_colscale, x, N, Xs, N, N, nrhs, st);
+    return Xs;
+  };
   auto residual = [&](const double2* x) {
     if (ff_confirm) {
-      dense_matvec_ffc(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
+      dense_matvec_ffc(F->dense64, (size_t)N, N, scaled(x), N, Y, N, nrhs, st);
       CK(cudaGetLastError());
     } else {
       apply_operator64(F, x, nrhs, Y, ws, st);
@@ -2011,12 +2020,12 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     return finish();
   };
   auto residual_low = [&](const double2* x) {
-    dense_matvec_ff(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
+    dense_matvec_ff(F->dense64, (size_t)N, N, scaled(x), N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     return finish();
   };
   auto residual_f32 = [&](const double2* x) {
-    dense_matvec32(F->dense64, (size_t)N, N, x, N, Y, N, nrhs, st);
+    dense_matvec32(F->dense64, (size_t)N, N, scaled(x), N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     return finish();
   };
@@ -2026,7 +2035,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   // so it is used only while 1e-6 |r| is far below refine_tol; the new
   // residual goes to dx's buffer and the two buffers swap.
   auto residual_update32 = [&]() {
-    dense_matvec32(F->dense64, (size_t)N, N, dX, N, Y, N, nrhs, st);
+    dense_matvec32(F->dense64, (size_t)N, N, scaled(dX), N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
     residual64(R, Y, dX, N, nrhs, norms, st);
@@ -2416,16 +2425,18 @@ void finish_mixed(pm_factor* F) {
   }
   if (F->dense64) {
     OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
+    F->d_colscale = F->arena.get<double>((size_t)g->N);
+    dense_colscale(g->nodes.w, F->d_iu, F->d_iq, g->total_nodes, g->k0, F->d_colscale, F->st);
     assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense64, (size_t)g->N, F->st);
     if (g_kprof) {
       double pairs = (double)g->total_nodes * g->total_nodes;
       for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
-      g_kprof->add_flops("dense_offdiag64", pairs * 164.0);
+      g_kprof->add_flops("dense_offdiag64", pairs * 146.0);
     }
     for (int j = 0; j < g->m; ++j) {
       const int m2 = 2 * g->inc[j].n_nodes;
       split_copy(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, (size_t)g->N, m2,
-                 m2, F->st);
+                 m2, F->d_colscale + g->row_off[j], F->st);
     }
     CK(cudaGetLastError());
   }
