@@ -1,16 +1,20 @@
 // Bessel functions J0, J1, Y0, Y1 of a positive real argument in FP64, for the
 // Hankel functions H_nu = J_nu + i Y_nu of the Helmholtz kernels.
 //
-// z >= HK_ZA: Hankel's asymptotic expansion (DLMF 10.17.3-10.17.4;
-//   Abramowitz & Stegun 9.2.5-9.2.10)
+// z >= 8: Hankel's modulus-phase form (DLMF 10.17.3-10.17.4; Abramowitz &
+//   Stegun 9.2.5-9.2.10)
 //     H_nu(z) = sqrt(2/(pi z)) e^{i w} (P_nu(z) + i Q_nu(z)),  w = z - nu pi/2 - pi/4,
-//     P = sum_k (-1)^k a_{2k}(nu) z^{-2k},  Q = sum_k (-1)^k a_{2k+1}(nu) z^{-2k-1},
-//     a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (k! 8^k).
-//   For real z the remainder is bounded by the first omitted term (DLMF
-//   10.17(iii)): below 1e-17 with 27 terms for z >= 20, 17 terms for z >= 30
-//   and 12 terms for z >= 60.  One sincos(z) serves both orders:
-//   w_1 = w_0 - pi/2.
-// z < HK_ZA: CUDA's j0 / y0 / j1 / y1.
+//   with P_nu and Q_nu from
+//   - z >= 60: the asymptotic expansion in 1/z^2,
+//       P = sum_k (-1)^k a_{2k}(nu) z^{-2k},  Q = sum_k (-1)^k a_{2k+1}(nu) z^{-2k-1},
+//       a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (k! 8^k),
+//     12 terms (remainder below 1e-17: for real z it is bounded by the first
+//     omitted term, DLMF 10.17(iii));
+//   - 8 <= z < 60: polynomial fits of P_nu - 1 and z Q_nu in 1/z^2 on
+//     [8, 12), [12, 20), [20, 30), [30, 60) (hankel_fit.h, written by
+//     gen_hankel_fit.py from 40-digit values; within 2e-17 of P_nu and Q_nu).
+//   One sincos(z) serves both orders: w_1 = w_0 - pi/2.
+// z < 8: CUDA's j0 / y0 / j1 / y1.
 // Complex z (lossy interiors, self blocks): Miller's backward recurrence
 //   J_{n-1} = (2n/z) J_n - J_{n+1} from an even start M > |z| + 25 + 3 sqrt|z|,
 //   normalised by 1 = J0 + 2 sum J_2k (A&S 9.1.27, 9.1.46), and Neumann's
@@ -20,9 +24,11 @@
 //     (pi/2) Y1 = -J0/z + (ln(z/2) + gamma) J1 + sum_{k>=1} (-1)^k (J_{2k-1} - J_{2k+1})/k.
 #pragma once
 #include <cuda_runtime.h>
+#include "hankel_fit.h"
 
-constexpr double HK_ZA = 20.0;
-constexpr int HK_TERMS = 27;   // a_0 .. a_26
+constexpr double HK_ZA = 8.0;    // modulus-phase form from here up
+constexpr double HK_ZS = 60.0;   // asymptotic series from here up
+constexpr int HK_TERMS = 12;     // a_0 .. a_11
 
 // a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (8 j), with the (-1)^floor(k/2)
 // sign of the series folded in (evaluated at compile time).
@@ -33,21 +39,28 @@ constexpr double hk_coef(int nu, int k) {
 }
 #define HK_ROW(nu) \
   {hk_coef(nu, 0), hk_coef(nu, 1), hk_coef(nu, 2), hk_coef(nu, 3), hk_coef(nu, 4), hk_coef(nu, 5), hk_coef(nu, 6), \
-   hk_coef(nu, 7), hk_coef(nu, 8), hk_coef(nu, 9), hk_coef(nu, 10), hk_coef(nu, 11), hk_coef(nu, 12),             \
-   hk_coef(nu, 13), hk_coef(nu, 14), hk_coef(nu, 15), hk_coef(nu, 16), hk_coef(nu, 17), hk_coef(nu, 18),          \
-   hk_coef(nu, 19), hk_coef(nu, 20), hk_coef(nu, 21), hk_coef(nu, 22), hk_coef(nu, 23), hk_coef(nu, 24),          \
-   hk_coef(nu, 25), hk_coef(nu, 26)}
+   hk_coef(nu, 7), hk_coef(nu, 8), hk_coef(nu, 9), hk_coef(nu, 10), hk_coef(nu, 11)}
 static __constant__ double c_hk_a0[HK_TERMS] = HK_ROW(0);
 static __constant__ double c_hk_a1[HK_TERMS] = HK_ROW(1);
 #undef HK_ROW
 
-// Expansion with the first T terms a_0 .. a_{T-1}: P from the even, Q from
-// the odd indices.  Terms needed for a remainder below 1e-17: 27 at z >= 20,
-// 17 at z >= 30, 12 at z >= 60.
-template <int T>
-__device__ __forceinline__ void hankel_asym_t(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
-  constexpr int PE = (T - 1) - ((T - 1) & 1);   // highest even index < T
-  constexpr int QO = (T - 1) - (T & 1);         // highest odd index < T
+// J and Y of orders 0 and 1 from P_nu, Q_nu (iz = 1/z).
+__device__ __forceinline__ void hankel_combine(double z, double iz, double P0, double Q0, double P1, double Q1,
+                                               double& J0, double& Y0, double& J1, double& Y1) {
+  double sn, cs;
+  sincos(z, &sn, &cs);
+  const double s = sqrt(0.63661977236758134308 * iz);          // sqrt(2/(pi z))
+  const double c = (cs + sn) * 0.70710678118654752440;         // cos(z - pi/4)
+  const double d = (sn - cs) * 0.70710678118654752440;         // sin(z - pi/4)
+  J0 = s * (P0 * c - Q0 * d);
+  Y0 = s * (P0 * d + Q0 * c);
+  J1 = s * (P1 * d + Q1 * c);
+  Y1 = s * (Q1 * d - P1 * c);
+}
+
+// z >= 60: the expansion's 12 terms (P from the even, Q from the odd indices).
+__device__ __forceinline__ void hankel_series(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
+  constexpr int PE = 10, QO = 11;
   const double u = iz * iz;
   double P0 = c_hk_a0[PE], P1 = c_hk_a1[PE];
   double Q0 = c_hk_a0[QO], Q1 = c_hk_a1[QO];
@@ -61,27 +74,26 @@ __device__ __forceinline__ void hankel_asym_t(double z, double iz, double& J0, d
     Q0 = fma(Q0, u, c_hk_a0[k]);
     Q1 = fma(Q1, u, c_hk_a1[k]);
   }
-  Q0 *= iz;
-  Q1 *= iz;
-  double sn, cs;
-  sincos(z, &sn, &cs);
-  const double s = sqrt(0.63661977236758134308 * iz);          // sqrt(2/(pi z))
-  const double c = (cs + sn) * 0.70710678118654752440;         // cos(z - pi/4)
-  const double d = (sn - cs) * 0.70710678118654752440;         // sin(z - pi/4)
-  J0 = s * (P0 * c - Q0 * d);
-  Y0 = s * (P0 * d + Q0 * c);
-  J1 = s * (P1 * d + Q1 * c);
-  Y1 = s * (Q1 * d - P1 * c);
+  hankel_combine(z, iz, P0, Q0 * iz, P1, Q1 * iz, J0, Y0, J1, Y1);
 }
 
+// z >= 8 (iz = 1/z)
 __device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
-  if (z >= 60.0) hankel_asym_t<12>(z, iz, J0, Y0, J1, Y1);
-  else if (z >= 30.0) hankel_asym_t<17>(z, iz, J0, Y0, J1, Y1);
-  else hankel_asym_t<HK_TERMS>(z, iz, J0, Y0, J1, Y1);
+  if (z >= HK_ZS) {
+    hankel_series(z, iz, J0, Y0, J1, Y1);
+    return;
+  }
+  const double v = iz * iz;
+  double P0, zQ0, P1, zQ1;
+  if (z >= 30.0) hankel_fit3(v, P0, zQ0, P1, zQ1);
+  else if (z >= 20.0) hankel_fit2(v, P0, zQ0, P1, zQ1);
+  else if (z >= 12.0) hankel_fit1(v, P0, zQ0, P1, zQ1);
+  else hankel_fit0(v, P0, zQ0, P1, zQ1);
+  hankel_combine(z, iz, P0, zQ0 * iz, P1, zQ1 * iz, J0, Y0, J1, Y1);
 }
 
-// Below z = 20 CUDA's j0/y0/j1/y1 (~1e-15 absolute below 8, ~2e-13 up to
-// 30, measured against scipy on GB300) are much cheaper than a recurrence.
+// Below z = 8 CUDA's j0/y0/j1/y1 (~1e-15 absolute, measured against scipy
+// on GB300).
 __device__ __forceinline__ void hankel01(double z, double& J0, double& Y0, double& J1, double& Y1) {
   if (z >= HK_ZA) hankel_asym(z, 1.0 / z, J0, Y0, J1, Y1);
   else { J0 = j0(z); Y0 = y0(z); J1 = j1(z); Y1 = y1(z); }
