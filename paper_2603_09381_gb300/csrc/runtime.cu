@@ -1943,6 +1943,8 @@ void run_planned(pm_factor* F, int kind, const double2* rhs, int nrhs, double2* 
   CK(cudaMemcpyAsync(phi, P.out, bytes, cudaMemcpyDeviceToDevice, st));
 }
 
+double hankel_flops_per_pair(const pm_geometry* g);
+
 // Y = A X with the FP64 operator (self blocks + on-the-fly off-diagonal kernels).
 void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Arena& ws, cudaStream_t st) {
   const pm_geometry* g = F->g;
@@ -1964,12 +1966,12 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
   OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
   apply_offdiag64(nd, g->total_nodes, g->k0, X, N, Y, N, nrhs, st);
   if (g_kprof) {
-    // algorithmic FP64 flops per node pair: 164 for geometry, Hankel expansion and
-    // kernels + 32 per right-hand side (4 complex multiply-adds); special
-    // functions (rsqrt, sincos, sqrt) not counted
+    // algorithmic FP64 flops per ordered node pair: 47 for the geometry and
+    // the four weighted entries, the Hankel pair, 32 per right-hand side (4
+    // complex multiply-adds); special functions not counted
     double pairs = (double)g->total_nodes * g->total_nodes;
     for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
-    g_kprof->add_flops("apply_offdiag64", pairs * (164.0 + 32.0 * nrhs));
+    g_kprof->add_flops("apply_offdiag64", pairs * (47.0 + hankel_flops_per_pair(g) + 32.0 * nrhs));
   }
   CK(cudaGetLastError());
 }
@@ -2383,6 +2385,39 @@ void factor_group(std::vector<pm_factor*>& Fs, double id_tol, Arena& scr, cudaSt
 
 // Mixed mode, after the complex64 levels: the FP64 self blocks, index maps and
 // (when it fits) the dense FP64 operator of the refinement residual.
+// Average algorithmic FP64 flops of one Hankel pair (H0, H1) over the node
+// pairs of a geometry (the square root, reciprocal square root, sincos and,
+// below z = 8, CUDA's Bessel functions not counted): 64 for the 12-term
+// expansion (z >= 60), 28 + 8 d for a degree-d fit (d = 5 on [20, 60), 7 on
+// [12, 20), 8 on [8, 12)), none below 8; averaged over 65,536 pairs of
+// nodes of different inclusions drawn with a fixed seed.  Used for the
+// profiler's counts of the operator kernels.
+double hankel_flops_per_pair(const pm_geometry* g) {
+  const int T = g->total_nodes;
+  if (T < 2 || g->m < 2) return 0.0;
+  auto incl_of = [&](int q) {
+    return (int)(std::upper_bound(g->node_off.begin(), g->node_off.begin() + g->m, q) - g->node_off.begin()) - 1;
+  };
+  uint64_t st = 0x9E3779B97F4A7C15ull;
+  auto next = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (int)((st >> 33) % (uint64_t)T);
+  };
+  double sum = 0;
+  int n = 0;
+  while (n < 65536) {
+    const int t = next(), q = next();
+    if (incl_of(t) == incl_of(q)) continue;
+    const double z = g->k0 * std::hypot(g->hx[t] - g->hx[q], g->hy[t] - g->hy[q]);
+    if (z >= 60) sum += 64;
+    else if (z >= 20) sum += 28 + 8 * 5;
+    else if (z >= 12) sum += 28 + 8 * 7;
+    else if (z >= 8) sum += 28 + 8 * 8;
+    ++n;
+  }
+  return sum / n;
+}
+
 void finish_mixed(pm_factor* F) {
   const pm_geometry* g = F->g;
   const pm_factor_opts* opts = &F->opts;
@@ -2431,7 +2466,9 @@ void finish_mixed(pm_factor* F) {
     if (g_kprof) {
       double pairs = (double)g->total_nodes * g->total_nodes;
       for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
-      g_kprof->add_flops("dense_offdiag64", pairs * 146.0);
+      // per unordered pair: 40 for the geometry and the eight entries of both
+      // 2 x 2 blocks, plus the Hankel pair
+      g_kprof->add_flops("dense_offdiag64", 0.5 * pairs * (40.0 + hankel_flops_per_pair(g)));
     }
     for (int j = 0; j < g->m; ++j) {
       const int m2 = 2 * g->inc[j].n_nodes;
