@@ -86,39 +86,29 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const GemmDesc<C>* __restr
 // order), so all tile shapes give bit-identical results; the autotuner picks
 // among them by speed alone.
 template <typename C, int TM, int TN, int MR, int NR>
-__global__ void __launch_bounds__(256) k_gemm_batched_t(const GemmDesc<C>* __restrict__ d,
-                                                        const int* __restrict__ tile_off, int nprob) {
+__device__ __forceinline__ void gemm_tile_t(int m, int n, int k, const C* __restrict__ A, int lda,
+                                            const C* __restrict__ B, int ldb, C* Cm, int ldc, C alpha, C beta,
+                                            int beta_zero, int r0, int c0) {
   constexpr int TX = TM / MR, TY = TN / NR;
   static_assert(TX * TY == 256, "256 threads per tile");
   __shared__ C As[TK][TM + 1];
   __shared__ C Bs[TK][TN + 1];
-  const int t = blockIdx.x;
-  int lo = 0, hi = nprob;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (tile_off[mid] <= t) lo = mid; else hi = mid;
-  }
-  const GemmDesc<C> g = d[lo];
-  if (g.m <= 0 || g.n <= 0) return;
-  const int local = t - tile_off[lo];
-  const int tiles_m = (g.m + TM - 1) / TM;
-  const int r0 = (local % tiles_m) * TM, c0 = (local / tiles_m) * TN;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   C acc[MR][NR];
 #pragma unroll
   for (int a = 0; a < MR; ++a)
 #pragma unroll
     for (int b = 0; b < NR; ++b) acc[a][b] = czero<C>();
-  for (int l0 = 0; l0 < g.k; l0 += TK) {
+  for (int l0 = 0; l0 < k; l0 += TK) {
     for (int e = tid; e < TM * TK; e += 256) {
       const int i = e % TM, l = e / TM;
       const int gi = r0 + i, gl = l0 + l;
-      As[l][i] = (gi < g.m && gl < g.k) ? g.A[gi + (size_t)gl * g.lda] : czero<C>();
+      As[l][i] = (gi < m && gl < k) ? A[gi + (size_t)gl * lda] : czero<C>();
     }
     for (int e = tid; e < TN * TK; e += 256) {
       const int l = e % TK, j = e / TK;
       const int gl = l0 + l, gj = c0 + j;
-      Bs[l][j] = (gl < g.k && gj < g.n) ? g.B[gl + (size_t)gj * g.ldb] : czero<C>();
+      Bs[l][j] = (gl < k && gj < n) ? B[gl + (size_t)gj * ldb] : czero<C>();
     }
     __syncthreads();
 #pragma unroll
@@ -140,13 +130,30 @@ __global__ void __launch_bounds__(256) k_gemm_batched_t(const GemmDesc<C>* __res
 #pragma unroll
     for (int b = 0; b < NR; ++b) {
       const int gi = r0 + tx + TX * a, gj = c0 + ty + TY * b;
-      if (gi < g.m && gj < g.n) {
-        C* p = g.Cm + gi + (size_t)gj * g.ldc;
-        C v = g.alpha * acc[a][b];
-        if (!g.beta_zero) v = v + g.beta * (*p);
+      if (gi < m && gj < n) {
+        C* p = Cm + gi + (size_t)gj * ldc;
+        C v = alpha * acc[a][b];
+        if (!beta_zero) v = v + beta * (*p);
         *p = v;
       }
     }
+}
+
+template <typename C, int TM, int TN, int MR, int NR>
+__global__ void __launch_bounds__(256) k_gemm_batched_t(const GemmDesc<C>* __restrict__ d,
+                                                        const int* __restrict__ tile_off, int nprob) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = nprob;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_off[mid] <= t) lo = mid; else hi = mid;
+  }
+  const GemmDesc<C> g = d[lo];
+  if (g.m <= 0 || g.n <= 0) return;
+  const int local = t - tile_off[lo];
+  const int tiles_m = (g.m + TM - 1) / TM;
+  gemm_tile_t<C, TM, TN, MR, NR>(g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, g.Cm, g.ldc, g.alpha, g.beta, g.beta_zero,
+                                 (local % tiles_m) * TM, (local / tiles_m) * TN);
 }
 
 // ---- LU with partial pivoting (blocked, right-looking) ---------------------------------
@@ -450,6 +457,30 @@ __global__ void __launch_bounds__(256) k_lu_update(const LuProb<C>* __restrict__
   gemm_tile<C>(mt, c1 - c0, jb, A + (p + jb) + p * ld, pr.ld, A + p + c0 * ld, pr.ld,
                A + (p + jb) + c0 * ld, pr.ld, mone, mk((typename real_of<C>::type)1, (typename real_of<C>::type)0),
                0, t % tiles_m, t / tiles_m);
+}
+
+// The same trailing update with 64 x 64 output tiles (4 x 4 outputs per
+// thread: four times the multiply-adds per shared-memory load of the 32 x 32
+// tile); each entry is the same sum, so the bits do not change.
+template <typename C>
+__global__ void __launch_bounds__(256) k_lu_update64(const LuProb<C>* __restrict__ P, int p, int nb, int lo, int hi) {
+  const LuProb<C> pr = P[blockIdx.y];
+  const int m = pr.m;
+  if (p >= m) return;
+  const int jb = min(nb, m - p);
+  const int mt = m - p - jb;
+  if (mt <= 0) return;
+  const int c0 = p + jb + lo, c1 = p + jb + min(hi, mt);
+  if (c1 <= c0) return;
+  const int tiles_m = (mt + 63) / 64, tiles_n = (c1 - c0 + 63) / 64;
+  const int t = blockIdx.x;
+  if (t >= tiles_m * tiles_n) return;
+  C* A = pr.A;
+  const size_t ld = pr.ld;
+  typedef typename real_of<C>::type R;
+  gemm_tile_t<C, 64, 64, 4, 4>(mt, c1 - c0, jb, A + (p + jb) + p * ld, pr.ld, A + p + c0 * ld, pr.ld,
+                               A + (p + jb) + c0 * ld, pr.ld, mk((R)-1, (R)0), mk((R)1, (R)0), 0,
+                               (t % tiles_m) * 64, (t / tiles_m) * 64);
 }
 
 // ---- LU solve ----------------------------------------------------------------------
@@ -844,9 +875,14 @@ void la_getrf_lookahead(const LuProb<C>* d_prob, int nprob, int maxm, const int*
     KPROF_END(sp, kname<C>("lu_update", "lu_update32"), fn);
     if (nrest > 0) {
       cudaStreamWaitEvent(su, e_next, 0);
-      dim3 g2(tiles_m * ((nrest + TB - 1) / TB), nprob);
       KPROF_BEGIN(su);
-      k_lu_update<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
+      if (nrest >= 512) {   // large trailing blocks: the 64 x 64 tile
+        dim3 g2(((mt + 63) / 64) * ((nrest + 63) / 64), nprob);
+        k_lu_update64<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
+      } else {
+        dim3 g2(tiles_m * ((nrest + TB - 1) / TB), nprob);
+        k_lu_update<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
+      }
       pm_launch_count_add(1);
       KPROF_END(su, kname<C>("lu_update", "lu_update32"), fu - fn);
       cudaEventRecord(e_rest, su);

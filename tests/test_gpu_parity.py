@@ -226,6 +226,25 @@ def test_offdiagonal_entries_large_arguments(pm):
     assert np.max(err / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))) < 1e-11
 
 
+@pytest.mark.parametrize("k_out", [3.0, 6.0, 12.0, 20.0])
+def test_offdiagonal_entries_across_the_hankel_intervals(pm, k_out):
+    # two disks 3 apart: k r spans [2.2 k, 3.8 k], across z = 8, 12, 20, 30 and
+    # 60, where the GPU's H0 / H1 change from CUDA's Bessel functions to the
+    # four polynomial fits and to the asymptotic expansion
+    prob = wl.circle_grid(2, 1, radius=0.4, spacing=3.0, k_out=k_out, k_in=2 * k_out, n=96)
+    g = pm.Geometry(prob)
+    n = 96
+    rows = np.arange(0, 2 * n)                 # both equation groups of disk 0
+    cols = np.arange(2 * n, 4 * n)             # both density groups of disk 1
+    got = g.matrix_entries(rows, cols)
+    nds = geometry.all_nodes(prob)
+    ix = proxy._Index(prob, nds)
+    ref = proxy.entries(ix, prob["k_out"], rows, cols)
+    err = np.abs(got - ref)
+    assert np.max(err) < 2e-14 * np.max(np.abs(ref))
+    assert np.max(err / np.maximum(np.abs(ref), 1e-6 * np.max(np.abs(ref)))) < 1e-12
+
+
 # ---- lossy interiors (complex k-), FP64 and mixed ---------------------------------
 
 def test_lossy_small_circles_fp64_and_mixed(pm):
