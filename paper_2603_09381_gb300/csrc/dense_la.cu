@@ -459,30 +459,6 @@ __global__ void __launch_bounds__(256) k_lu_update(const LuProb<C>* __restrict__
                0, t % tiles_m, t / tiles_m);
 }
 
-// The same trailing update with 64 x 64 output tiles (4 x 4 outputs per
-// thread: four times the multiply-adds per shared-memory load of the 32 x 32
-// tile); each entry is the same sum, so the bits do not change.
-template <typename C>
-__global__ void __launch_bounds__(256) k_lu_update64(const LuProb<C>* __restrict__ P, int p, int nb, int lo, int hi) {
-  const LuProb<C> pr = P[blockIdx.y];
-  const int m = pr.m;
-  if (p >= m) return;
-  const int jb = min(nb, m - p);
-  const int mt = m - p - jb;
-  if (mt <= 0) return;
-  const int c0 = p + jb + lo, c1 = p + jb + min(hi, mt);
-  if (c1 <= c0) return;
-  const int tiles_m = (mt + 63) / 64, tiles_n = (c1 - c0 + 63) / 64;
-  const int t = blockIdx.x;
-  if (t >= tiles_m * tiles_n) return;
-  C* A = pr.A;
-  const size_t ld = pr.ld;
-  typedef typename real_of<C>::type R;
-  gemm_tile_t<C, 64, 64, 4, 4>(mt, c1 - c0, jb, A + (p + jb) + p * ld, pr.ld, A + p + c0 * ld, pr.ld,
-                               A + (p + jb) + c0 * ld, pr.ld, mk((R)-1, (R)0), mk((R)1, (R)0), 0,
-                               (t % tiles_m) * 64, (t / tiles_m) * 64);
-}
-
 // ---- LU solve ----------------------------------------------------------------------
 
 template <typename C>
@@ -875,14 +851,9 @@ void la_getrf_lookahead(const LuProb<C>* d_prob, int nprob, int maxm, const int*
     KPROF_END(sp, kname<C>("lu_update", "lu_update32"), fn);
     if (nrest > 0) {
       cudaStreamWaitEvent(su, e_next, 0);
+      dim3 g2(tiles_m * ((nrest + TB - 1) / TB), nprob);
       KPROF_BEGIN(su);
-      if (nrest >= 512) {   // large trailing blocks: the 64 x 64 tile
-        dim3 g2(((mt + 63) / 64) * ((nrest + 63) / 64), nprob);
-        k_lu_update64<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
-      } else {
-        dim3 g2(tiles_m * ((nrest + TB - 1) / TB), nprob);
-        k_lu_update<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
-      }
+      k_lu_update<C><<<g2, 256, 0, su>>>(d_prob, p, LU_NB, LU_NB, 1 << 30);
       pm_launch_count_add(1);
       KPROF_END(su, kname<C>("lu_update", "lu_update32"), fu - fn);
       cudaEventRecord(e_rest, su);
