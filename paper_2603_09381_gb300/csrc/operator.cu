@@ -383,7 +383,7 @@ __device__ __forceinline__ void ff_acc(float& h, float& l, float xh, float xl) {
   l += e + xl;
 }
 template <int NR>
-__global__ void __launch_bounds__(MV_ROWS, 5) k_dense_matvec_ffc(const float4* __restrict__ A, size_t lda, int N,
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __restrict__ A, size_t lda, int N,
                                                               const double2* __restrict__ X, int ldx,
                                                               double2* __restrict__ Y, int ldy, int seg) {
   __shared__ float4 xs[NR][MV_KT];   // {hi(re), hi(im), lo(re), lo(im)} of x
