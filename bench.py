@@ -511,7 +511,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "c64+c128" if precision == pm.PM_MIXED else "c128",
             "data": "synthetic",
             "config": _workload_config(WORKLOADS[args.workload], N, st["levels"], args.precision, ws, args.workload),
-            "refinement_confirm": "fp64" if args.fp64_confirm else "float-float, sums restarted every 16 columns and folded into FP64 every 64",
+            "refinement_confirm": "fp64" if args.fp64_confirm else "float-float folded into FP64 every 16 columns",
             "solve_ms": solve, "factor_ms": ms - solve, "K": st["K"], "skeleton_per_level": st["skeleton"],
             "refinement": info,
             "rank_predictor": {"used": model_ptr is not None, "cpqr_launches": st["cpqr_launches"],

@@ -113,9 +113,8 @@ typedef struct pm_factor pm_factor;
  *      complex64 threshold.
  *      Confirming residual (PM_MIXED with the dense operator): by default the
  *      residual that ends the refinement comes from a float-float product of
- *      the stored operator whose sums restart every 16 columns and are folded
- *      into FP64 every 64
- *      (worst-case error ~1.2e-12 of sum_j |a_ij| |x_j| per row, below that of
+ *      the stored operator whose sums are folded into FP64 every 16 columns
+ *      (worst-case error ~9e-13 of sum_j |a_ij| |x_j| per row, below that of
  *      a sequential FP64 sum); PM_FLAG_FP64_CONFIRM forms it with the FP64
  *      product instead.  PM_FLAG_FF_CONFIRM names the default and changes
  *      nothing.  PM_FLAG_NO_AUTOTUNE: the call tunes no batched-GEMM tile

@@ -362,26 +362,12 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float4* __res
 }
 
 // The float-float product with its (hi, lo) sums restarted every FFC_FOLD
-// columns.  Within a group of m terms lo's own rounding is at most
-// ~(m^2/2 + 7m) u^2 sum |a||x| (u = 2^-24): with m = 16 about 9e-13 of
-// sum_j |a_ij||x_j| per row.  The group sums go into a float-float
-// accumulator (exact TwoSum of the high parts, the low parts added: at most
-// 4 G^2 u^2 sum |a||x| over G groups, 2.3e-13 for G = FFC_GROUPS = 4), which
-// is folded into FP64 every G groups (64 columns): about 1.2e-12 of
-// sum_j |a_ij||x_j| per row in all, below the n 2^-53 worst case of a
-// sequential FP64 sum over a ~20,000-term segment, so this product can end
-// the refinement in place of the FP64 one.  Folding every group into FP64
-// instead took four FP64 operations per group and component, which the
-// FP64 pipe (1/64 of the FP32 rate) turned into a fifth of the kernel's time.
+// columns and folded into FP64.  Within a group of m terms lo's own rounding
+// is at most ~(m^2/2 + 7m) u^2 sum |a||x| (u = 2^-24): with m = 16 about 9e-13
+// of sum_j |a_ij||x_j| per row, below the n 2^-53 worst case of a sequential
+// FP64 sum over a ~20,000-term segment, so this product can end the
+// refinement in place of the FP64 one.
 constexpr int FFC_FOLD = 16;
-constexpr int FFC_GROUPS = 4;
-static_assert(MV_KT == FFC_GROUPS * FFC_FOLD, "one FP64 fold per staged block of columns");
-__device__ __forceinline__ void ff_acc(float& h, float& l, float xh, float xl) {
-  float s, e;
-  two_sum(h, xh, s, e);
-  h = s;
-  l += e + xl;
-}
 template <int NR>
 __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __restrict__ A, size_t lda, int N,
                                                               const double2* __restrict__ X, int ldx,
@@ -403,10 +389,6 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __re
     if (row < N) {
       const int cnt = min(MV_KT, k1 - kb);
       const float4* col = A + row + (size_t)kb * lda;
-      // MV_KT = FFC_GROUPS * FFC_FOLD: one FP64 fold per staged block of columns
-      float ah[NR], al[NR], bh[NR], bl[NR];
-#pragma unroll
-      for (int q = 0; q < NR; ++q) { ah[q] = al[q] = bh[q] = bl[q] = 0.f; }
       for (int kf = 0; kf < cnt; kf += FFC_FOLD) {
         const int kend = min(cnt, kf + FFC_FOLD);
         float rh[NR], rl[NR], ih[NR], il[NR];
@@ -425,14 +407,9 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __re
         }
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-          ff_acc(ah[q], al[q], rh[q], rl[q]);
-          ff_acc(bh[q], bl[q], ih[q], il[q]);
+          accd[q].x += (double)rh[q] + (double)rl[q];
+          accd[q].y += (double)ih[q] + (double)il[q];
         }
-      }
-#pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        accd[q].x += (double)ah[q] + (double)al[q];
-        accd[q].y += (double)bh[q] + (double)bl[q];
       }
     }
   }

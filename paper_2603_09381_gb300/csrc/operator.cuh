@@ -43,9 +43,8 @@ void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ld
 // sums; ~1e-13 relative, for refinement residuals.
 void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                      cudaStream_t st);
-// The float-float product with its sums restarted every 16 columns (float-float
-// group sums, folded into FP64 every 64 columns):
-// worst-case error ~1.2e-12 of sum_j |a_ij||x_j| per row, so it may decide the
+// The float-float product with its sums folded into FP64 every 16 columns:
+// worst-case error ~9e-13 of sum_j |a_ij||x_j| per row, so it may decide the
 // convergence of the refinement (PM_FLAG_FF_CONFIRM).
 void dense_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                       cudaStream_t st);

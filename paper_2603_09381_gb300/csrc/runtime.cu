@@ -2002,7 +2002,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     return worst;
   };
   // The residual that can end the refinement: the float-float product folded
-  // into FP64 every 64 columns, restarted every 16 (a smaller worst-case error bound than a
+  // into FP64 every 16 columns (a smaller worst-case error bound than a
   // sequential FP64 sum, on the FP32 pipes), or with PM_FLAG_FP64_CONFIRM the
   // FP64 product.
   const bool ff_confirm = F->dense64 && !(F->opts.flags & PM_FLAG_FP64_CONFIRM);
