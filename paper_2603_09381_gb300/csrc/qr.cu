@@ -370,11 +370,12 @@ __global__ void __launch_bounds__(UT) k_qr_apply(const QrProb<C>* __restrict__ P
 // stages Y (from the row-block reduction) into one of two buffers, one
 // thread issues the 24 MMAs into one of two TMEM accumulators and commits
 // them to that buffer's mbarrier, and the epilogue of the previous tile
-// (tcgen05.ld, then each thread's component of C -= D, with C loaded one
+// (tcgen05.ld by all eight warps, each with a quarter of the rows and half
+// of the columns, then each thread's component of C -= D, with C loaded one
 // tile ahead) overlaps them.  Every wait is bounded; a wait that runs out
 // sets *err and the CTA stops writing.
 namespace tcq {
-constexpr int T = 128;                         // threads: warp w reads TMEM lanes [32w, 32w + 32)
+constexpr int T = 256;                         // threads: warp w reads TMEM lanes [32 (w % 4), + 32), columns 16 (w / 4) ..
 constexpr int ROWS = 64;                       // complex rows per CTA
 constexpr int KR = 2 * QR_NB;                  // real k: real and imaginary parts of the reflectors
 constexpr uint32_t A_BYTES = 2 * ROWS * KR * 4;    // one of hi / lo: 128 x 64 tf32
@@ -420,8 +421,8 @@ __global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __
   }
   // A: the block's reflector rows (unit diagonal, zeros above it and past W)
 #pragma unroll 4
-  for (int i = 0; i < 16; ++i) {
-    const int mm = tid & 63, kk = (tid >> 6) + 2 * i;
+  for (int i = 0; i < 8; ++i) {
+    const int mm = tid & 63, kk = (tid >> 6) + 4 * i;
     const float2 v = v_entry(p, j0, jb, rbeg + mm, kk);
     tcx::put_split(Ahi, Alo, tcx::core_off<KR>(mm, kk), v.x);
     tcx::put_split(Ahi, Alo, tcx::core_off<KR>(mm, QR_NB + kk), -v.y);
@@ -435,21 +436,23 @@ __global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __
   bool ok = true;
   if (no_arrive) ok = tcx::mbar_wait(&mbar[2], 0, 1 << 10);
   const int nt = __syncthreads_and(ok ? 1 : 0) ? ntiles : -1;
-  // Epilogue work split: thread tid owns TMEM lane tid = real row tid of D,
-  // i.e. the real (tid < 64) or imaginary (tid >= 64) part of complex row
-  // rbeg + (tid & 63), and updates that component of C itself (no exchange).
-  // C of tile t is loaded at iteration t and updated at iteration t + 1, and
-  // Y of tile t + 1 is loaded at iteration t, so their latency overlaps the
-  // MMAs and the previous epilogue.
-  const int r = tid & 63, comp = tid >> 6;
+  // Epilogue work split: warp w reads TMEM lanes 32 (w % 4) .. + 32, i.e.
+  // D's real row lane = 32 (w % 4) + (tid & 31): the real (lane < 64) or
+  // imaginary (lane >= 64) part of complex row rbeg + (lane & 63), columns
+  // 16 (w / 4) .. + 16 of the tile; each thread updates that component of C
+  // itself (no exchange).  C of tile t is loaded at iteration t and updated
+  // at iteration t + 1, and Y of tile t + 1 is loaded at iteration t, so
+  // their latency overlaps the MMAs and the previous epilogue.
+  const int lane_row = 32 * (warp & 3) + (tid & 31), hcol = 16 * (warp >> 2);
+  const int r = lane_row & 63, comp = lane_row >> 6;
   const int row = rbeg + r;
   const bool row_ok = row < rend;
-  float cnext[32], ccur[32];
-  float2 ynext[8];
+  float cnext[16], ccur[16];
+  float2 ynext[4];
   auto load_y = [&](int t) {
     const float2* yp = p.Yp + (size_t)t * p.mrb * (QR_NB * 32);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) ynext[i] = yp[(tid & 31) + QR_NB * ((tid >> 5) + 4 * i)];
+    for (int i = 0; i < 4; ++i) ynext[i] = yp[(tid & 31) + QR_NB * ((tid >> 5) + 8 * i)];
   };
   if (nt > 0) load_y(0);
   for (int t = 0; t <= nt; ++t) {
@@ -460,8 +463,8 @@ __global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __
       // Y of tile t (rows: reflectors, columns: the tile's columns), stored transposed;
       // buffer b was last read by the MMAs of tile t - 2, waited for at iteration t - 1
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int kk = tid & 31, nn = (tid >> 5) + 4 * i;
+      for (int i = 0; i < 4; ++i) {
+        const int kk = tid & 31, nn = (tid >> 5) + 8 * i;
         tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, kk), ynext[i].x);
         tcx::put_split(Bhi, Blo, tcx::core_off<KR>(nn, QR_NB + kk), ynext[i].y);
       }
@@ -483,32 +486,32 @@ __global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __
         tcx::mma_commit(&mbar[b]);
       }
       if (t + 1 < nt) load_y(t + 1);
-      // this thread's component of C, tile t
-      const int c0 = cfirst + t * 32, nc = min(32, p.n - c0);
+      // this thread's component of C, tile t, its 16 columns
+      const int c0 = cfirst + t * 32 + hcol, nc = min(16, p.n - c0);
       const float* cz = reinterpret_cast<const float*>(p.Z + row + (size_t)c0 * p.ld) + comp;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) cnext[j] = (row_ok && j < nc) ? cz[(size_t)j * 2 * p.ld] : 0.f;
+      for (int j = 0; j < 16; ++j) cnext[j] = (row_ok && j < nc) ? cz[(size_t)j * 2 * p.ld] : 0.f;
     }
     if (t >= 1) {   // epilogue of tile u = t - 1
       const int u = t - 1, b = u & 1;
       ok = ok && tcx::mbar_wait(&mbar[b], (uint32_t)((u >> 1) & 1), WAIT);   // after a failure: no more waits
       asm volatile("tcgen05.fence::after_thread_sync;");
-      float d[32];
+      float d[16];
       const bool wok = __all_sync(0xffffffffu, ok ? 1 : 0);
       if (wok) {
-        tcx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 32), d);
-        const int c0 = cfirst + u * 32, nc = min(32, p.n - c0);
+        tcx::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * 32 + hcol), d);
+        const int c0 = cfirst + u * 32 + hcol, nc = min(16, p.n - c0);
         float* cz = reinterpret_cast<float*>(p.Z + row + (size_t)c0 * p.ld) + comp;
         if (row_ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
+          for (int j = 0; j < 16; ++j)
             if (j < nc) cz[(size_t)j * 2 * p.ld] = ccur[j] - d[j];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
     }
 #pragma unroll
-    for (int j = 0; j < 32; ++j) ccur[j] = cnext[j];
+    for (int j = 0; j < 16; ++j) ccur[j] = cnext[j];
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   const int all_ok = __syncthreads_and(ok ? 1 : 0);
