@@ -204,9 +204,9 @@ def _kernel_source_sha(src_text, anchors):
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
-def _traffic_for(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, while the captured
-    kernel's source (and its helpers') is unchanged; else None."""
+def _ncu_record(kernel):
+    """The committed ncu record of a kernel while its source (and its helpers')
+    is unchanged; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(p))
@@ -221,7 +221,22 @@ def _traffic_for(kernel):
     except OSError:
         return None
     sha = _kernel_source_sha(text, ent["anchors"])
-    return ent["bytes_per_launch"] if sha is not None and sha == ent["source_sha"] else None
+    return ent if sha is not None and sha == ent["source_sha"] else None
+
+
+def _traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, while the captured
+    kernel's source (and its helpers') is unchanged; else None."""
+    ent = _ncu_record(kernel)
+    return ent["bytes_per_launch"] if ent else None
+
+
+def _pipe_busy_for(kernel):
+    """The captured kernel's busiest-pipe utilisation from the committed ncu
+    summary (context for an ALU roofline whose count leaves out special
+    functions), while its source is unchanged; else None."""
+    ent = _ncu_record(kernel)
+    return ent.get("pipe_busy") if ent else None
 
 
 FLOP_KERNELS = {"cpqr_step", "lu_update", "lu_panel", "lu_swap_trsm", "getrs", "gemm_batched", "interp_solve",
@@ -340,6 +355,9 @@ def _roofline(prof_tot, steps, peaks=None):
         peak, src = _alu_peak("fp64", peaks)
         roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "peak_source": src, "traffic": _traffic_for(name)})
+        busy = _pipe_busy_for(name)
+        if busy:
+            roof["ncu_pipe_busy"] = busy
     elif name in FP32_FLOP_KERNELS and d["ms"] > 0:
         achieved = d["work"] / (d["ms"] / 1e3) / 1e12
         peak, src = _alu_peak("fp32", peaks)
