@@ -248,19 +248,18 @@ __global__ void __launch_bounds__(256) k_cpqr_step(const CpqrProb<C>* __restrict
   }
 }
 
+// R11 (k x k, upper, diagonal from rdiag, zero below) and R12 (into T) in
+// pivot order, both with leading dimension k.
 template <typename C>
-__global__ void k_interp(const InterpProb<C>* __restrict__ P) {
+__global__ void k_interp_gather(const InterpProb<C>* __restrict__ P) {
   const InterpProb<C> p = P[blockIdx.y];
-  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = p.k;
-  if (cc >= p.n - k || k <= 0) return;
-  const C* r12 = p.Z + (size_t)p.perm[k + cc] * p.ld;
-  C* t = p.T + (size_t)cc * p.ldt;
-  for (int i = k - 1; i >= 0; --i) {
-    C acc = r12[i];
-    for (int j = i + 1; j < k; ++j) cfms(acc, p.Z[i + (size_t)p.perm[j] * p.ld], t[j]);
-    t[i] = cdiv(acc, p.rdiag[i]);
-  }
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k <= 0 || e >= (size_t)k * p.n) return;
+  const int i = (int)(e % k), j = (int)(e / k);
+  const C v = p.Z[i + (size_t)p.perm[j] * p.ld];
+  if (j < k) p.R11[i + (size_t)j * k] = i < j ? v : (i == j ? p.rdiag[i] : czero<C>());
+  else p.T[i + (size_t)(j - k) * p.ldt] = v;
 }
 
 template <typename C>
@@ -353,13 +352,11 @@ void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, 
   KPROF_END(st, kname<C>("cpqr_step", "cpqr_step32"), 0.0);   // work is added per level from the steps performed
 }
 template <typename C>
-void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st) {
-  if (nprob <= 0 || max_cols <= 0) return;
-  dim3 g((max_cols + 63) / 64, nprob);
-  KPROF_BEGIN(st);
-  k_interp<C><<<g, 64, 0, st>>>(d_prob);
+void interp_gather(const InterpProb<C>* d_prob, int nprob, size_t max_elems, cudaStream_t st) {
+  if (nprob <= 0 || max_elems == 0) return;
+  dim3 g((unsigned)((max_elems + 255) / 256), nprob);
+  k_interp_gather<C><<<g, 256, 0, st>>>(d_prob);
   pm_launch_count_add(1);
-  KPROF_END(st, kname<C>("interp_solve", "interp_solve32"), 0.0);
 }
 template <typename C>
 void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st) {
@@ -378,7 +375,7 @@ void copy_batched(const CopyProb<S, D>* d_prob, int nprob, int max_elems, cudaSt
 
 template void cpqr_init_norms<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, cudaStream_t);
 template void cpqr_step<double2>(const CpqrProb<double2>*, const CpqrChunk*, int, int, int*, cudaStream_t, bool);
-template void interp_solve<double2>(const InterpProb<double2>*, int, int, cudaStream_t);
+template void interp_gather<double2>(const InterpProb<double2>*, int, size_t, cudaStream_t);
 template void scatter_interp<double2>(const ScatterProb<double2>*, int, int, cudaStream_t);
 template void copy_batched<double2, double2>(const CopyProb<double2, double2>*, int, int, cudaStream_t);
 template void copy_batched<float2, float2>(const CopyProb<float2, float2>*, int, int, cudaStream_t);
@@ -386,5 +383,5 @@ template void copy_batched<float2, double2>(const CopyProb<float2, double2>*, in
 template void copy_batched<double2, float2>(const CopyProb<double2, float2>*, int, int, cudaStream_t);
 template void cpqr_init_norms<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, cudaStream_t);
 template void cpqr_step<float2>(const CpqrProb<float2>*, const CpqrChunk*, int, int, int*, cudaStream_t, bool);
-template void interp_solve<float2>(const InterpProb<float2>*, int, int, cudaStream_t);
+template void interp_gather<float2>(const InterpProb<float2>*, int, size_t, cudaStream_t);
 template void scatter_interp<float2>(const ScatterProb<float2>*, int, int, cudaStream_t);

@@ -27,6 +27,7 @@ struct InterpProb {              // T (k x (n-k)) = R11^{-1} R12 in pivot order
   const C* Z; int ld; int n; int k;
   const int* perm; const C* rdiag;
   C* T; int ldt;
+  C* R11;                        // k x k workspace (leading dimension k): R11 in pivot order
 };
 
 template <typename C>
@@ -81,8 +82,11 @@ void cpqr_init_norms(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nc
 template <typename C>
 void cpqr_step(const CpqrProb<C>* d_prob, const CpqrChunk* d_chunk, int nchunk, int t, int* d_counter,
                cudaStream_t st, bool tall);
+// R11 (upper triangular, diagonal from rdiag) and R12 of every problem gathered
+// in pivot order into R11 and T (ldt = k), for a blocked triangular solve
+// T <- R11^{-1} T; max_elems = the largest k * n.
 template <typename C>
-void interp_solve(const InterpProb<C>* d_prob, int nprob, int max_cols, cudaStream_t st);
+void interp_gather(const InterpProb<C>* d_prob, int nprob, size_t max_elems, cudaStream_t st);
 template <typename C>
 void scatter_interp(const ScatterProb<C>* d_prob, int nprob, int max_elems, cudaStream_t st);
 template <typename S, typename D>

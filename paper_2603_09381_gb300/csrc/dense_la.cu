@@ -998,6 +998,30 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
   KPROF_END(st, kname<C>("getrs", "getrs32"), fl);
 }
 
+template <typename C>
+void la_trsm_upper_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const char* name,
+                           double flops, cudaStream_t st) {
+  if (nprob <= 0 || maxm <= 0 || maxrhs <= 0) return;
+  KPROF_BEGIN(st);
+  dim3 gs((maxrhs + DG_RHS - 1) / DG_RHS, nprob);
+  const int tiles_n = (maxrhs + TB - 1) / TB;
+  int last = ((maxm - 1) / RS_NB) * RS_NB;
+  for (int p = last; p >= 0; p -= RS_NB) {
+    k_getrs_diag<C><<<gs, 256, 0, st>>>(d_prob, p, RS_NB, 0);
+    pm_launch_count_add(1);
+    if (p > 0) {
+      dim3 g2(((p + TB - 1) / TB) * tiles_n, nprob);
+      k_getrs_update<C><<<g2, 256, 0, st>>>(d_prob, p, RS_NB, 0);
+      pm_launch_count_add(1);
+    }
+  }
+  KPROF_END(st, name, flops);
+}
+
+template void la_trsm_upper_batched<double2>(const SolveProb<double2>*, int, int, int, const char*, double,
+                                             cudaStream_t);
+template void la_trsm_upper_batched<float2>(const SolveProb<float2>*, int, int, int, const char*, double,
+                                            cudaStream_t);
 template void la_gemm_batched_shape<double2>(int, const GemmDesc<double2>*, const int*, int, int, cudaStream_t);
 template void la_gemm_batched_shape<float2>(int, const GemmDesc<float2>*, const int*, int, int, cudaStream_t);
 template void la_gemm_batched<double2>(const GemmDesc<double2>*, const int*, int, int, cudaStream_t);

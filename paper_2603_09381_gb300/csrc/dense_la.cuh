@@ -59,6 +59,13 @@ template <typename C>
 void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,
                       const int* h_rhs, cudaStream_t st, const ChainArgs* chain = nullptr);
 
+// B (m x nrhs) <- U^{-1} B for the upper triangle U (diagonal included) of A,
+// blocked (diagonal blocks of 32, then GEMM updates of the rows above);
+// `name` and `flops` label the launches for the optional profiler.
+template <typename C>
+void la_trsm_upper_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const char* name,
+                           double flops, cudaStream_t st);
+
 // tiles of a GEMM problem for the 32 x 32 output tiling
 inline int gemm_tiles(int m, int n) { return ((m + 31) / 32) * ((n + 31) / 32); }
 

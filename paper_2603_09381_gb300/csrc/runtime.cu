@@ -1487,20 +1487,29 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
   std::vector<int> hperm(std::max(total_n, 1));
   CK(cudaMemcpyAsync(hperm.data(), perm, std::max(total_n, 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  // 5. interpolation matrices T = R11^{-1} R12
+  // 5. interpolation matrices T = R11^{-1} R12: R11 and R12 gathered in pivot
+  // order, then one blocked upper-triangular solve for all IDs
   std::vector<InterpProb<C>> ip;
+  std::vector<SolveProb<C>> ts;
   std::vector<C*> T(nid, nullptr);
-  int maxcols = 0;
+  int maxcols = 0, maxk = 0;
+  size_t maxel = 0;
   for (int i = 0; i < nid; ++i) {
     int k = kk[i], n = nn[i];
     if (k <= 0 || n - k <= 0 || zero_in[i]) continue;
     T[i] = scr.get<C>((size_t)k * (n - k));
-    ip.push_back(InterpProb<C>{Z[i], W[i], n, k, perm + noff[i], rdiag + noff[i], T[i], k});
+    C* r11 = scr.get<C>((size_t)k * k);
+    ip.push_back(InterpProb<C>{Z[i], W[i], n, k, perm + noff[i], rdiag + noff[i], T[i], k, r11});
+    ts.push_back(SolveProb<C>{r11, k, k, nullptr, T[i], k, n - k});
     maxcols = std::max(maxcols, n - k);
+    maxk = std::max(maxk, k);
+    maxel = std::max(maxel, (size_t)k * n);
   }
   if (!ip.empty()) {
     auto* dip = upload(scr, ip, st);
-    interp_solve<C>(dip, (int)ip.size(), maxcols, st);
+    interp_gather<C>(dip, (int)ip.size(), maxel, st);
+    auto* dts = upload(scr, ts, st);
+    la_trsm_upper_batched<C>(dts, (int)ts.size(), maxk, maxcols, kname<C>("interp_solve", "interp_solve32"), 0.0, st);
     CK(cudaGetLastError());
   }
   // 5b. held-out proxy check: each ID's candidates against its box's held-out
