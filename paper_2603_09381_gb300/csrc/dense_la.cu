@@ -391,12 +391,17 @@ __global__ void __launch_bounds__(NT) k_lu_panel_cluster(const LuProb<C>* __rest
 
 // Row interchanges of the panel applied to every other column, then the unit
 // lower triangular solve U12 = L11^{-1} A12 on the columns right of the panel.
-// Thread 0 composes the panel's jb interchanges into one map over the rows
-// they touch (the jb panel rows first, then at most jb rows below), so each
-// column does independent gathers instead of a chain of dependent swaps.
+// Thread 0 of each CTA composes the panel's jb interchanges into one map over
+// the rows they touch (the jb panel rows first, then at most jb rows below).
+// One warp per column: lane i gathers the column's entry for position i (the
+// panel rows are contiguous, so the first half of the warp reads one
+// coalesced segment), the swapped-in rows below are written back, and the
+// triangular solve runs across the lanes, each lane's row taking its
+// subtractions in the same (ascending) order as a row-by-row substitution.
 template <typename C>
 __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuProb<C>* __restrict__ P, int p, int nb) {
   constexpr int MB = MAXNB;
+  static_assert(2 * MB <= 32, "one lane per touched row");
   const LuProb<C> pr = P[blockIdx.y];
   const int m = pr.m;
   if (p >= m) return;
@@ -423,24 +428,21 @@ __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuProb<C>* __restric
   }
   for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) s_l[e % jb][e / jb] = A[p + e % jb + (size_t)(p + e / jb) * ld];
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m || (j >= p && j < p + jb)) return;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= m || (j >= p && j < p + jb)) return;   // whole warps leave together
   C* col = A + (size_t)j * ld;
   const int cnt = s_cnt;
-  C v[2 * MB];
-#pragma unroll
-  for (int i = 0; i < 2 * MB; ++i) v[i] = i < cnt ? col[s_org[i]] : czero<C>();
-#pragma unroll
-  for (int i = 0; i < 2 * MB; ++i) if (i >= jb && i < cnt) col[s_row[i]] = v[i];   // rows below the panel
+  C v = lane < cnt ? col[s_org[lane]] : czero<C>();
+  __syncwarp();                                    // every read before any write
+  if (lane >= jb && lane < cnt) col[s_row[lane]] = v;   // rows below the panel
   if (j >= p + jb) {
-#pragma unroll
-    for (int r = 1; r < MB; ++r)
-#pragma unroll
-      for (int q = 0; q < r; ++q)
-        if (r < jb) cfms(v[r], s_l[r][q], v[q]);
+    for (int q = 0; q < jb - 1; ++q) {
+      const C vq = shfl_c(v, q);
+      if (lane > q && lane < jb) cfms(v, s_l[lane][q], vq);
+    }
   }
-#pragma unroll
-  for (int i = 0; i < MB; ++i) if (i < jb) col[p + i] = v[i];
+  if (lane < jb) col[p + lane] = v;
 }
 
 // Trailing update A22 -= L21 * U12 on the trailing columns [p+jb+lo, p+jb+hi)
@@ -841,7 +843,7 @@ void la_getrf_lookahead(const LuProb<C>* d_prob, int nprob, int maxm, const int*
     pm_launch_count_add(1);
     KPROF_END(sp, kname<C>("lu_panel", "lu_panel32"), fp);
     if (rest_pending) cudaStreamWaitEvent(sp, e_rest, 0);
-    dim3 g1((maxm + 255) / 256, nprob);
+    dim3 g1((maxm + 7) / 8, nprob);   // a warp per column
     KPROF_BEGIN(sp);
     k_lu_swap_trsm<C><<<g1, 256, 0, sp>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
@@ -893,7 +895,7 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
     k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
     KPROF_END(st, kname<C>("lu_panel", "lu_panel32"), fp);
-    dim3 g1((maxm + 255) / 256, nprob);
+    dim3 g1((maxm + 7) / 8, nprob);   // a warp per column
     KPROF_BEGIN(st);
     k_lu_swap_trsm<C><<<g1, 256, 0, st>>>(d_prob, p, LU_NB);
     pm_launch_count_add(1);
