@@ -274,6 +274,103 @@ __global__ void __launch_bounds__(NT) k_lu_panel(const LuProb<C>* __restrict__ P
   }
 }
 
+// The same panel with its rows p..m-1 held in shared memory for the whole
+// panel (dynamic, (m - p) x jb, leading dimension m - p): loaded once,
+// factored there (the lazy updates read the L entries from shared memory
+// instead of L2), stored once; the same operations in the same order as
+// k_lu_panel, so the same bits.
+template <typename C, int NT>
+__global__ void __launch_bounds__(NT) k_lu_panel_smem(const LuProb<C>* __restrict__ P, int p, int nb) {
+  typedef typename real_of<C>::type R;
+  extern __shared__ __align__(16) unsigned char lu_sm[];
+  C* pan = reinterpret_cast<C*>(lu_sm);
+  const LuProb<C> pr = P[blockIdx.x];
+  const int m = pr.m;
+  if (p >= m) return;
+  const int jb = min(nb, m - p);
+  const int mr = m - p;
+  C* A = pr.A;
+  const size_t ld = pr.ld;
+  __shared__ R sval[NT / 32];
+  __shared__ int sidx[NT / 32];
+  __shared__ C s_l[MAXNB][MAXNB + 1];
+  __shared__ C s_u[MAXNB];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < mr * jb; e += NT) pan[e] = A[p + e % mr + (size_t)(p + e / mr) * ld];
+  __syncthreads();
+  for (int jj = 0; jj < jb; ++jj) {
+    C* colc = pan + (size_t)jj * mr;   // local row i = global row p + i
+    if (jj > 0) {
+      for (int e = tid; e < jj * jj; e += NT) s_l[e % jj][e / jj] = pan[e % jj + (size_t)(e / jj) * mr];
+      __syncthreads();
+      if (warp == 0) {
+        C x = lane < jj ? colc[lane] : czero<C>();
+        for (int l = 0; l < jj - 1; ++l) {
+          const C xl = shfl_c(x, l);
+          if (lane > l && lane < jj) cfms(x, s_l[lane][l], xl);
+        }
+        if (lane < jj) {
+          s_u[lane] = x;
+          colc[lane] = x;
+        }
+      }
+      __syncthreads();
+    }
+    R best = -1;
+    int bi = m;
+    for (int r = jj + tid; r < mr; r += NT) {
+      C lr[MAXNB];
+#pragma unroll
+      for (int l = 0; l < MAXNB; ++l) if (l < jj) lr[l] = pan[r + (size_t)l * mr];
+      C a0 = colc[r], a1 = czero<C>(), a2 = czero<C>(), a3 = czero<C>();
+#pragma unroll
+      for (int l = 0; l < MAXNB; l += 4) {
+        if (l < jj) cfms(a0, lr[l], s_u[l]);
+        if (l + 1 < jj) cfms(a1, lr[l + 1], s_u[l + 1]);
+        if (l + 2 < jj) cfms(a2, lr[l + 2], s_u[l + 2]);
+        if (l + 3 < jj) cfms(a3, lr[l + 3], s_u[l + 3]);
+      }
+      const C a = (a0 + a1) + (a2 + a3);
+      if (jj > 0) colc[r] = a;
+      const R v = abs2(a);
+      if (v > best) { best = v; bi = p + r; }   // rows ascend: the first of equal values stays
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+    }
+    if (lane == 0) { sval[warp] = best; sidx[warp] = bi; }
+    __syncthreads();
+    const int c = p + jj;
+    if (tid == 0) {
+      R bv = sval[0];
+      int piv = sidx[0];
+      for (int w = 1; w < NT / 32; ++w)
+        if (sval[w] > bv || (sval[w] == bv && sidx[w] < piv)) { bv = sval[w]; piv = sidx[w]; }
+      if (!(bv > 0)) { piv = c; if (*pr.info == 0) *pr.info = c + 1; }
+      s_piv = piv;
+      pr.ipiv[c] = piv;
+    }
+    __syncthreads();
+    const int piv = s_piv - p;
+    if (piv != jj && tid < jb) {
+      C* a = pan + jj + (size_t)tid * mr;
+      C* b = pan + piv + (size_t)tid * mr;
+      const C t = *a; *a = *b; *b = t;
+    }
+    __syncthreads();
+    const C d = colc[jj];
+    if (abs2(d) > 0) {
+      const C inv = cdiv(mk((R)1, (R)0), d);
+      for (int r = jj + 1 + tid; r < mr; r += NT) colc[r] = colc[r] * inv;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < mr * jb; e += NT) A[p + e % mr + (size_t)(p + e / mr) * ld] = pan[e];
+}
+
 // The same left-looking panel for one large matrix on a cluster of CTAs
 // (the top-level LU): the CTAs split the rows, so the lazy column updates
 // (FP64-bound on one SM) spread over the cluster's SMs.  Per column: every
@@ -779,6 +876,7 @@ void la_gemm_batched_shape(int shape, const GemmDesc<C>* d_desc, const int* d_ti
 }
 
 constexpr int LU_NB = 16;
+constexpr size_t LU_PANEL_SMEM = 216 * 1024;   // panels up to this size stay in shared memory
 static_assert(LU_NB <= MAXNB, "LU panel wider than the kernels' shared tiles");
 constexpr int RS_NB = 32;
 
@@ -892,7 +990,14 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
     double fp = 0, fs = 0, fu = 0;
     if (g_kprof) lu_step_flops(h_m, nprob, p, fp, fs, fu);
     KPROF_BEGIN(st);
-    k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
+    const size_t pan_bytes = (size_t)(maxm - p) * std::min(LU_NB, maxm - p) * sizeof(C);
+    if (pan_bytes <= LU_PANEL_SMEM) {
+      // the same value every time: idempotent across threads and devices
+      cudaFuncSetAttribute(k_lu_panel_smem<C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_PANEL_SMEM);
+      k_lu_panel_smem<C, 256><<<nprob, 256, pan_bytes, st>>>(d_prob, p, LU_NB);
+    } else {
+      k_lu_panel<C, 256><<<nprob, 256, 0, st>>>(d_prob, p, LU_NB);
+    }
     pm_launch_count_add(1);
     KPROF_END(st, kname<C>("lu_panel", "lu_panel32"), fp);
     dim3 g1((maxm + 7) / 8, nprob);   // a warp per column
