@@ -703,7 +703,10 @@ __global__ void __launch_bounds__(128) k_getrs_update_thin(const SolveProb<C>* _
 
 // One triangle of the LU solves of a batch of matrices, each with at most 8
 // right-hand sides, as ONE launch: every matrix is a chain of RS_NB-row
-// blocks, one CTA per block.  Each CTA takes a ticket from a counter and
+// blocks, one CTA per block and group of rg right-hand sides (the columns
+// are independent chains; in FP64 a CTA's products and diagonal solve are
+// bound by its SM's FP64 rate, so fewer columns per CTA shorten every link
+// of the chain).  Each CTA takes a ticket from a counter and
 // reads its (matrix, block) from items[ticket]; the items are ordered so that
 // every block comes after the blocks it depends on (lower: by block index
 // from the top, upper: by distance from the bottom), hence a CTA only ever
@@ -713,11 +716,13 @@ __global__ void __launch_bounds__(128) k_getrs_update_thin(const SolveProb<C>* _
 // k_getrs_update_thin, each as soon as that block's flag is up, then solves
 // its diagonal block as k_getrs_diag does, stores the result and raises its
 // own flag.  In FP64 the results are bit-identical to the launch-per-block
-// sequence, without ~4 launches per block on the critical path.  Every wait
+// sequence, without ~4 launches per block on the critical path.  With rg <= 4
+// the two sums of a product (even and odd terms) are taken by two threads
+// and joined in the same order, so the bits do not depend on rg.  Every wait
 // is bounded (TS_WAIT_NS); a wait that runs out sets *err and the shared
 // abort word, and every CTA then leaves without writing.
-// items[t] = (matrix, block, flag base of the matrix, 0); sync: [0] ticket,
-// [1] abort, [2, 2 + total blocks) flags; zeroed before the launch.
+// items[t] = (matrix, block, flag base of the matrix and group, group);
+// sync: [0] ticket, [1] abort, [2, 2 + items) flags; zeroed before the launch.
 // no_flag (failure-path tests): every CTA first waits, with a 1 ms bound, on
 // `never`, which nothing sets.
 constexpr long long TS_WAIT_NS = 2000000000ll;   // 2 s per wait
@@ -736,13 +741,14 @@ __device__ __forceinline__ void ts_store_release(int* p, int v) {
 }
 template <typename C>
 __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restrict__ P, const int4* __restrict__ items,
-                                                    int nitems, int lower, int* sync, int* err, const int* never,
-                                                    int no_flag) {
+                                                    int nitems, int lower, int rg, int* sync, int* err,
+                                                    const int* never, int no_flag) {
   typedef typename real_of<C>::type R;
   constexpr int NB = 32;
   __shared__ C sl[NB][NB + 1];   // the off-diagonal block of the current dependency, [col][row]
-  __shared__ C sx[NB][8];        // its solved rows
+  __shared__ C sx[NB][8];        // its solved rows (this CTA's right-hand sides)
   __shared__ C sa[NB][NB + 1];   // the diagonal block
+  __shared__ C s_odd[4][NB];     // rg <= 4: the odd-term sums
   __shared__ int s_t, s_stop;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -765,7 +771,9 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
   if (t >= nitems) return;
   const int4 it = items[t];
   const SolveProb<C> pr = P[it.x];
-  const int m = pr.m, nrhs = pr.nrhs;
+  const int m = pr.m;
+  const int q0 = it.w * rg, nrhs = min(rg, pr.nrhs - q0);   // this CTA's columns q0 .. q0 + nrhs - 1
+  if (nrhs <= 0) return;   // the whole (matrix, group) is empty: nobody waits on its flags
   const int nblk = (m + NB - 1) / NB;
   const int b = it.y;
   const int r0 = b * NB, jb = min(NB, m - r0);
@@ -775,10 +783,13 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
     const int r = e % jb, c = e / jb;
     sa[r][c] = pr.A[r0 + r + (size_t)(r0 + c) * ld];
   }
-  // this thread's entry (row i, right-hand side q) of the block being solved
-  const int i = tid & 31, q = tid >> 5;
-  const bool mine = i < jb && q < nrhs;
-  C x = mine ? pr.B[r0 + i + (size_t)q * pr.ldb] : czero<C>();
+  // this thread's entry (row i, right-hand side q) of the block being solved;
+  // with rg <= 4 thread h = 1 of (i, q) takes the odd-term sums for h = 0
+  const bool split = rg <= 4;
+  const int i = tid & 31, q = split ? (tid >> 5) % rg : tid >> 5, h = split ? (tid >> 5) / rg : 0;
+  const bool mine = i < jb && q < nrhs && h == 0;
+  const bool odd = split && i < jb && q < nrhs && h == 1;
+  C x = mine ? pr.B[r0 + i + (size_t)(q0 + q) * pr.ldb] : czero<C>();
   const int ndep = lower ? b : nblk - 1 - b;
   for (int d = 0; d < ndep; ++d) {
     const int j = lower ? d : nblk - 1 - d;
@@ -805,10 +816,18 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
     if (s_stop) return;
     for (int e = tid; e < jbj * nrhs; e += 256) {
       const int l = e % jbj, qq = e / jbj;
-      sx[l][qq] = __ldcg(pr.B + c0 + l + (size_t)qq * pr.ldb);
+      sx[l][qq] = __ldcg(pr.B + c0 + l + (size_t)(q0 + qq) * pr.ldb);
     }
     __syncthreads();
-    if (mine) {
+    if (split) {
+      // acc0 over the even terms, acc1 over the odd ones, each in order
+      C acc = czero<C>();
+      if (mine || odd)
+        for (int l = h; l < jbj; l += 2) cfma(acc, sl[l][i], sx[l][q]);
+      if (odd) s_odd[q][i] = acc;
+      __syncthreads();
+      if (mine) x = x - (acc + s_odd[q][i]);
+    } else if (mine) {
       C acc0 = czero<C>(), acc1 = czero<C>();
       int l = 0;
       for (; l + 1 < jbj; l += 2) {
@@ -818,7 +837,7 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
       if (l < jbj) cfma(acc0, sl[l][i], sx[l][q]);
       x = x - (acc0 + acc1);
     }
-    __syncthreads();   // sl and sx are refilled next
+    __syncthreads();   // sl, sx and s_odd are refilled next
   }
   // the diagonal block: warp q solves right-hand side q, lane r holds row r
   if (mine) sx[i][q] = x;
@@ -838,7 +857,7 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
         if (lane < c) cfms(y, sa[lane][c], yc);
       }
     }
-    if (lane < jb) pr.B[r0 + lane + (size_t)warp * pr.ldb] = y;
+    if (lane < jb) pr.B[r0 + lane + (size_t)(q0 + warp) * pr.ldb] = y;
   }
   __threadfence();
   __syncthreads();
@@ -1017,7 +1036,7 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
   }
 }
 
-int la_chain_items(const int* h_m, int nprob, std::vector<int4>& items) {
+int la_chain_items(const int* h_m, int nprob, int groups, std::vector<int4>& items) {
   std::vector<int> nb(nprob), base(nprob);
   int total = 0, maxb = 0;
   for (int i = 0; i < nprob; ++i) {
@@ -1027,14 +1046,17 @@ int la_chain_items(const int* h_m, int nprob, std::vector<int4>& items) {
     maxb = std::max(maxb, nb[i]);
   }
   items.clear();
-  items.reserve(2 * (size_t)total);
+  items.reserve(2 * (size_t)total * groups);
+  // flags of (matrix i, group g): groups * base[i] + g * nb[i] + block
   for (int d = 0; d < maxb; ++d)   // lower: block d of every matrix that has one
     for (int i = 0; i < nprob; ++i)
-      if (d < nb[i]) items.push_back(make_int4(i, d, base[i], 0));
+      for (int g = 0; g < groups; ++g)
+        if (d < nb[i]) items.push_back(make_int4(i, d, groups * base[i] + g * nb[i], g));
   for (int d = 0; d < maxb; ++d)   // upper: block d from the bottom
     for (int i = 0; i < nprob; ++i)
-      if (d < nb[i]) items.push_back(make_int4(i, nb[i] - 1 - d, base[i], 0));
-  return total;
+      for (int g = 0; g < groups; ++g)
+        if (d < nb[i]) items.push_back(make_int4(i, nb[i] - 1 - d, groups * base[i] + g * nb[i], g));
+  return total * groups;
 }
 int la_chain_sync_ints(int total) { return 2 * (2 + total) + 1; }
 
@@ -1063,10 +1085,10 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
     cudaMemsetAsync(chain->sync, 0, sizeof(int) * la_chain_sync_ints(T), st);
     const int* never = chain->sync + 2 * (2 + T);
     if (T > 0) {
-      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items, T, 1, chain->sync, chain->err, never,
-                                         chain->no_flag);
-      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items + T, T, 0, chain->sync + 2 + T, chain->err, never,
-                                         chain->no_flag);
+      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items, T, 1, chain->rhs_per_cta, chain->sync, chain->err,
+                                         never, chain->no_flag);
+      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items + T, T, 0, chain->rhs_per_cta, chain->sync + 2 + T,
+                                         chain->err, never, chain->no_flag);
       pm_launch_count_add(2);
     }
     KPROF_END(st, kname<C>("getrs", "getrs32"), fl);

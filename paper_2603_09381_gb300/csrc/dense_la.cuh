@@ -41,19 +41,22 @@ void la_getrf_batched(const LuProb<C>* d_prob, int nprob, int maxm, const int* h
 // per matrix, each triangle of every matrix of the batch runs in ONE launch
 // whose blocks wait on one another through flags (bounded waits).
 // la_chain_items fills the 2 x total ticket items (lower, then upper) for the
-// matrix sizes h_m and returns the total number of RS_NB-row blocks;
+// matrix sizes h_m and `groups` groups of right-hand sides, and returns total
+// = the number of (RS_NB-row block, group) pairs; a group holds rhs_per_cta
+// columns (groups * rhs_per_cta >= the most right-hand sides of a matrix);
 // the sync buffer holds la_chain_sync_ints(total) ints (zeroed by the call);
 // *err is set to 1 if a wait runs out (the results are then invalid).
 // no_flag (failure-path tests): every block first waits, with a 1 ms bound,
 // on a flag that nothing sets.
 struct ChainArgs {
   const int4* items;
-  int total_blocks;
+  int total_blocks;   // items per triangle
   int* sync;
   int* err;
   int no_flag;
+  int rhs_per_cta;    // 1 .. 8; at most 4 splits each product's two sums over two threads
 };
-int la_chain_items(const int* h_m, int nprob, std::vector<int4>& items);
+int la_chain_items(const int* h_m, int nprob, int groups, std::vector<int4>& items);
 int la_chain_sync_ints(int total);
 template <typename C>
 void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrhs, const int* h_m,

@@ -136,11 +136,13 @@ __device__ __forceinline__ double join_trunc(float hi, float lo) {
                                           ((unsigned long long)(eh - 127 + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull)));
 }
 
-__device__ __forceinline__ float4 split4t(double re, double im) {
-  float4 v;
-  split_trunc(re, v.x, v.z);
-  split_trunc(im, v.y, v.w);
-  return v;
+// Entry idx of the split operator: hi and lo planes.
+__device__ __forceinline__ void store_split(const SplitOp& A, size_t idx, double re, double im) {
+  float2 h, l;
+  split_trunc(re, h.x, l.x);
+  split_trunc(im, h.y, l.y);
+  A.hi[idx] = h;
+  A.lo[idx] = l;
 }
 
 __device__ __forceinline__ float4 split4(double re, double im) {
@@ -148,8 +150,11 @@ __device__ __forceinline__ float4 split4(double re, double im) {
   return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
 }
 
-// Dense off-diagonal operator: thread = (node t, node s) with t < s, nodes t
-// fastest.  One Hankel evaluation fills both 2 x 2 blocks of the pair.  The
+// Dense off-diagonal operator: thread = (node t, node s) with t < s; a block
+// covers 64 t by 4 s (s fastest), so that the writes of both halves fill
+// whole 32-byte sectors of each plane: the (t <- s) entries of 8 consecutive
+// t per column, the mirrored (s <- t) entries of 4 consecutive s per column.
+// One Hankel evaluation fills both 2 x 2 blocks of the pair.  The
 // operator is stored column-scaled, A = As diag(cs), with cs = w/4 for a
 // u-column (the density of -eps+ S and of the D-type block) and cs = k w/4
 // for a q-column, so the quadrature weight and the factors 1/4 and k/4 of
@@ -159,12 +164,11 @@ __device__ __forceinline__ float4 split4(double re, double im) {
 //   (s <- t): u-col (Y0 - i J0, k b (Y1 - i J1)),  q-col (a (Y1 - i J1), N)
 // with N = -(c0 Y0 + c1 Y1) + i (c0 J0 + c1 J1), c0 = k a b,
 // c1 = (n_t.n_s - 2 a b)/r, symmetric in the pair.
-__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double ik,
-                                                       float4* __restrict__ A, size_t lda) {
-  const int s = blockIdx.y;
-  if (blockIdx.x * 256 >= s) return;          // whole block on or below the diagonal
-  const int t = blockIdx.x * 256 + threadIdx.x;
-  if (t >= s) return;
+__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double ik, SplitOp A) {
+  if (blockIdx.x * 64 >= blockIdx.y * 4 + 3) return;   // whole block on or below the diagonal
+  const int s = blockIdx.y * 4 + (threadIdx.x & 3);
+  const int t = blockIdx.x * 64 + (threadIdx.x >> 2);
+  if (s >= total || t >= s) return;
   const int ti = nd.incl[t], si = nd.incl[s];
   if (ti == si) return;
   const double dx = nd.x[t] - nd.x[s], dy = nd.y[t] - nd.y[s];
@@ -180,16 +184,17 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
   const double Nre = -fma(c0, Y0, c1 * Y1), Nim = fma(c0, J0, c1 * J1);
   const double ka = k * a, kb = k * b;
   const size_t ut = nd.iu[t], qt = nd.iq[t], us = nd.iu[s], qs = nd.iq[s];
+  const size_t lda = A.ld;
   // rows of t, columns of s
-  A[ut + us * lda] = split4t(Y0, -J0);
-  A[qt + us * lda] = split4t(-ka * Y1, ka * J1);
-  A[ut + qs * lda] = split4t(-b * Y1, b * J1);
-  A[qt + qs * lda] = split4t(Nre, Nim);
+  store_split(A, ut + us * lda, Y0, -J0);
+  store_split(A, qt + us * lda, -ka * Y1, ka * J1);
+  store_split(A, ut + qs * lda, -b * Y1, b * J1);
+  store_split(A, qt + qs * lda, Nre, Nim);
   // rows of s, columns of t
-  A[us + ut * lda] = split4t(Y0, -J0);
-  A[qs + ut * lda] = split4t(kb * Y1, -kb * J1);
-  A[us + qt * lda] = split4t(a * Y1, -a * J1);
-  A[qs + qt * lda] = split4t(Nre, Nim);
+  store_split(A, us + ut * lda, Y0, -J0);
+  store_split(A, qs + ut * lda, kb * Y1, -kb * J1);
+  store_split(A, us + qt * lda, a * Y1, -a * J1);
+  store_split(A, qs + qt * lda, Nre, Nim);
 }
 
 // Column scales of the stored operator: cs[u index] = w/4, cs[q index] = k w/4.
@@ -217,7 +222,8 @@ __global__ void k_scale_rows(const double* __restrict__ cs, const double2* __res
 // FP64 atomics.  Every A entry is read once and feeds NR complex FMAs.
 constexpr int MV_ROWS = 128, MV_KT = 64;
 template <int NR>
-__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restrict__ A, size_t lda, int N,
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float2* __restrict__ Ah, const float2* __restrict__ Al,
+                                                          size_t lda, int N,
                                                           const double2* __restrict__ X, int ldx, double2* __restrict__ Y,
                                                           int ldy, int seg) {
   __shared__ double2 xs[NR][MV_KT];
@@ -235,10 +241,11 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restri
     __syncthreads();
     if (row < N) {
       const int cnt = min(MV_KT, k1 - kb);
-      const float4* col = A + row + (size_t)kb * lda;
+      const float2* colh = Ah + row + (size_t)kb * lda;
+      const float2* coll = Al + row + (size_t)kb * lda;
       for (int kk = 0; kk < cnt; ++kk) {
-        const float4 s4 = __ldg(col + (size_t)kk * lda);
-        const double2 a = make_double2(join_trunc(s4.x, s4.z), join_trunc(s4.y, s4.w));
+        const float2 h = __ldg(colh + (size_t)kk * lda), l = __ldg(coll + (size_t)kk * lda);
+        const double2 a = make_double2(join_trunc(h.x, l.x), join_trunc(h.y, l.y));
 #pragma unroll
         for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
       }
@@ -252,49 +259,82 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec(const float4* __restri
   }
 }
 
-// The same product with the hi parts only, in FP32 arithmetic over runs of
-// MV_KT columns whose sums are folded into FP64 accumulators (~1e-7 relative
-// to |A| |X|, not growing with N): for the first refinement residual, which
-// is ~1e-3 of the right-hand side.  Bound by the one read of A.
+// The same product with the hi parts only (one read of the hi plane, 8
+// bytes per entry), in FP32 arithmetic over runs of MV32_KT columns whose
+// sums are folded into FP64 accumulators (~1e-7 relative to |A| |X|
+// typically, not growing with N): for the first refinement residual, which
+// is ~1e-3 of the right-hand side, and for residual updates r - A dx.  The
+// column loads are software-pipelined (the next MV32_G entries of the row
+// are in flight while the current ones are multiplied), the next run's X
+// values are fetched into registers during the current run, and the FP64
+// accumulators live in shared memory (touched once per run).
+constexpr int MV32_KT = 128, MV32_G = 8;
+static_assert(MV32_KT == MV_ROWS, "one staged column of X per thread and right-hand side");
+static_assert(MV32_KT % MV32_G == 0, "runs hold whole load groups");
 template <int NR>
-__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec32(const float4* __restrict__ A, size_t lda, int N,
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec32(const float2* __restrict__ Ah, size_t lda, int N,
                                                             const double2* __restrict__ X, int ldx,
                                                             double2* __restrict__ Y, int ldy, int seg) {
-  __shared__ float2 xs[NR][MV_KT];
+  __shared__ float2 xs[MV32_KT][NR];
+  __shared__ double2 accd[NR][MV_ROWS];   // this thread's FP64 sums: accd[q][threadIdx.x]
   const int row = blockIdx.x * MV_ROWS + threadIdx.x;
   const int k0 = blockIdx.y * seg, k1 = min(N, k0 + seg);
-  double2 accd[NR];
+  float2 pre[NR];   // X[kb + threadIdx.x, q] of the next run, in FP32
 #pragma unroll
-  for (int q = 0; q < NR; ++q) accd[q] = make_double2(0.0, 0.0);
-  for (int kb = k0; kb < k1; kb += MV_KT) {
-    float2 acc[NR];
+  for (int q = 0; q < NR; ++q) accd[q][threadIdx.x] = make_double2(0.0, 0.0);
+  auto fetch = [&](int kb) {
+    const int kk = kb + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < NR; ++q) acc[q] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int e = threadIdx.x; e < NR * MV_KT; e += MV_ROWS) {
-      const int q = e / MV_KT, kk = e % MV_KT;
-      const double2 v = (kb + kk < k1) ? X[kb + kk + (size_t)q * ldx] : make_double2(0, 0);
-      xs[q][kk] = make_float2((float)v.x, (float)v.y);
+    for (int q = 0; q < NR; ++q) {
+      const double2 v = kk < k1 ? X[kk + (size_t)q * ldx] : make_double2(0, 0);
+      pre[q] = make_float2((float)v.x, (float)v.y);
     }
+  };
+  if (k0 < k1) fetch(k0);
+  for (int kb = k0; kb < k1; kb += MV32_KT) {
     __syncthreads();
-    if (row < N) {
-      const int cnt = min(MV_KT, k1 - kb);
-      const float4* col = A + row + (size_t)kb * lda;
-      for (int kk = 0; kk < cnt; ++kk) {
-        const float4 s4 = __ldg(col + (size_t)kk * lda);
-        const float2 a = make_float2(s4.x, s4.y);
 #pragma unroll
-        for (int q = 0; q < NR; ++q) cfma(acc[q], a, xs[q][kk]);
+    for (int q = 0; q < NR; ++q) xs[threadIdx.x][q] = pre[q];
+    __syncthreads();
+    if (kb + MV32_KT < k1) fetch(kb + MV32_KT);
+    if (row < N) {
+      // columns at or past cnt load as zero and meet zero X entries: they add 0
+      const int cnt = min(MV32_KT, k1 - kb);
+      const float2* col = Ah + row + (size_t)kb * lda;
+      float2 acc[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = make_float2(0.f, 0.f);
+      float2 nxt[MV32_G];
+#pragma unroll
+      for (int g = 0; g < MV32_G; ++g) nxt[g] = g < cnt ? __ldg(col + (size_t)g * lda) : make_float2(0.f, 0.f);
+      for (int kk = 0; kk < cnt; kk += MV32_G) {
+        float2 cur[MV32_G];
+#pragma unroll
+        for (int g = 0; g < MV32_G; ++g) cur[g] = nxt[g];
+#pragma unroll
+        for (int g = 0; g < MV32_G; ++g) {
+          const int kn = kk + MV32_G + g;
+          nxt[g] = kn < cnt ? __ldg(col + (size_t)kn * lda) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int g = 0; g < MV32_G; ++g)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) cfma(acc[q], cur[g], xs[kk + g][q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        double2 d = accd[q][threadIdx.x];
+        d.x += (double)acc[q].x;
+        d.y += (double)acc[q].y;
+        accd[q][threadIdx.x] = d;
       }
     }
-#pragma unroll
-    for (int q = 0; q < NR; ++q) { accd[q].x += (double)acc[q].x; accd[q].y += (double)acc[q].y; }
   }
   if (row >= N) return;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
-    atomicAdd(&Y[row + (size_t)q * ldy].x, accd[q].x);
-    atomicAdd(&Y[row + (size_t)q * ldy].y, accd[q].y);
+    atomicAdd(&Y[row + (size_t)q * ldy].x, accd[q][threadIdx.x].x);
+    atomicAdd(&Y[row + (size_t)q * ldy].y, accd[q][threadIdx.x].y);
   }
 }
 
@@ -319,7 +359,8 @@ __device__ __forceinline__ void ff_mac(float& hi, float& lo, float ah, float al,
 }
 
 template <int NR>
-__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float4* __restrict__ A, size_t lda, int N,
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float2* __restrict__ Ah,
+                                                             const float2* __restrict__ Al, size_t lda, int N,
                                                              const double2* __restrict__ X, int ldx,
                                                              double2* __restrict__ Y, int ldy, int seg) {
   __shared__ float4 xs[NR][MV_KT];   // {hi(re), hi(im), lo(re), lo(im)} of x
@@ -338,9 +379,11 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float4* __res
     __syncthreads();
     if (row < N) {
       const int cnt = min(MV_KT, k1 - kb);
-      const float4* col = A + row + (size_t)kb * lda;
+      const float2* colh = Ah + row + (size_t)kb * lda;
+      const float2* coll = Al + row + (size_t)kb * lda;
       for (int kk = 0; kk < cnt; ++kk) {
-        const float4 a = __ldg(col + (size_t)kk * lda);
+        const float2 h = __ldg(colh + (size_t)kk * lda), l = __ldg(coll + (size_t)kk * lda);
+        const float4 a = make_float4(h.x, h.y, l.x, l.y);
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
           const float4 x = xs[q][kk];
@@ -369,7 +412,8 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ff(const float4* __res
 // refinement in place of the FP64 one.
 constexpr int FFC_FOLD = 16;
 template <int NR>
-__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __restrict__ A, size_t lda, int N,
+__global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float2* __restrict__ Ah,
+                                                              const float2* __restrict__ Al, size_t lda, int N,
                                                               const double2* __restrict__ X, int ldx,
                                                               double2* __restrict__ Y, int ldy, int seg) {
   __shared__ float4 xs[NR][MV_KT];   // {hi(re), hi(im), lo(re), lo(im)} of x
@@ -388,14 +432,16 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __re
     __syncthreads();
     if (row < N) {
       const int cnt = min(MV_KT, k1 - kb);
-      const float4* col = A + row + (size_t)kb * lda;
+      const float2* colh = Ah + row + (size_t)kb * lda;
+      const float2* coll = Al + row + (size_t)kb * lda;
       for (int kf = 0; kf < cnt; kf += FFC_FOLD) {
         const int kend = min(cnt, kf + FFC_FOLD);
         float rh[NR], rl[NR], ih[NR], il[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) { rh[q] = rl[q] = ih[q] = il[q] = 0.f; }
         for (int kk = kf; kk < kend; ++kk) {
-          const float4 a = __ldg(col + (size_t)kk * lda);
+          const float2 h = __ldg(colh + (size_t)kk * lda), l = __ldg(coll + (size_t)kk * lda);
+          const float4 a = make_float4(h.x, h.y, l.x, l.y);
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
             const float4 x = xs[q][kk];
@@ -422,14 +468,14 @@ __global__ void __launch_bounds__(MV_ROWS) k_dense_matvec_ffc(const float4* __re
 }
 
 // dst = split(src diag(1 / cs)): a self block into the column-scaled operator.
-__global__ void k_split_copy(const double2* __restrict__ src, int lds, float4* __restrict__ dst, size_t ldd, int m,
-                             int n, const double* __restrict__ cs) {
+__global__ void k_split_copy(const double2* __restrict__ src, int lds, SplitOp dst, int m, int n,
+                             const double* __restrict__ cs) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * n) return;
   const int i = e % m, j = e / m;
   const double2 v = src[i + (size_t)j * lds];
   const double c = 1.0 / cs[j];
-  dst[i + (size_t)j * ldd] = split4t(v.x * c, v.y * c);
+  store_split(dst, i + (size_t)j * dst.ld, v.x * c, v.y * c);
 }
 
 __global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,
@@ -508,10 +554,9 @@ void apply_offdiag64(OpNodes nd, int total, double k0, const double2* X, int ldx
   KPROF_END(st, "apply_offdiag64", 0.0);
 }
 
-void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, const double* cs,
-                cudaStream_t st) {
+void split_copy(const double2* src, int lds, SplitOp dst, int m, int n, const double* cs, cudaStream_t st) {
   if (m <= 0 || n <= 0) return;
-  k_split_copy<<<(m * n + 255) / 256, 256, 0, st>>>(src, lds, dst, ldd, m, n, cs);
+  k_split_copy<<<(m * n + 255) / 256, 256, 0, st>>>(src, lds, dst, m, n, cs);
   pm_launch_count_add(1);
 }
 
@@ -529,17 +574,17 @@ void scale_rows(const double* cs, const double2* X, int ldx, double2* Xs, int ld
   pm_launch_count_add(1);
 }
 
-void assemble_dense_offdiag64(OpNodes nd, int total, double k0, float4* A, size_t lda, cudaStream_t st) {
+void assemble_dense_offdiag64(OpNodes nd, int total, double k0, SplitOp A, cudaStream_t st) {
   if (total <= 0) return;
-  dim3 g((total + 255) / 256, total);
+  dim3 g((total + 63) / 64, (total + 3) / 4);
   KPROF_BEGIN(st);
-  k_dense_offdiag<<<g, 256, 0, st>>>(nd, total, k0, 1.0 / k0, A, lda);
+  k_dense_offdiag<<<g, 256, 0, st>>>(nd, total, k0, 1.0 / k0, A);
   pm_launch_count_add(1);
   KPROF_END(st, "dense_offdiag64", 0.0);
 }
 
 template <int NR>
-void launch_matvec(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, cudaStream_t st) {
+void launch_matvec(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -549,11 +594,11 @@ void launch_matvec(const float4* A, size_t lda, int N, const double2* X, int ldx
   seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
   segs = (N + seg - 1) / seg;
   dim3 g(rb, segs);
-  k_dense_matvec<NR><<<g, MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  k_dense_matvec<NR><<<g, MV_ROWS, 0, st>>>(A.hi, A.lo, A.ld, N, X, ldx, Y, ldy, seg);
   pm_launch_count_add(1);
 }
 
-void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec64(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st) {
   if (N <= 0 || nrhs <= 0) return;
   for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
@@ -562,16 +607,16 @@ void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ld
     const int left = nrhs - r0;
     const double2* Xr = X + (size_t)r0 * ldx;
     double2* Yr = Y + (size_t)r0 * ldy;
-    if (left >= 8) { launch_matvec<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
-    else if (left >= 4) { launch_matvec<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
-    else if (left >= 2) { launch_matvec<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
-    else { launch_matvec<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+    if (left >= 8) { launch_matvec<8>(A, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec<4>(A, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec<2>(A, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec<1>(A, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "dense_matvec64", 0.0);
 }
 
 template <int NR>
-void launch_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy,
+void launch_matvec_ff(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy,
                       cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -582,12 +627,12 @@ void launch_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int 
   seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
   segs = (N + seg - 1) / seg;
   dim3 g(rb, segs);
-  k_dense_matvec_ff<NR><<<g, MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  k_dense_matvec_ff<NR><<<g, MV_ROWS, 0, st>>>(A.hi, A.lo, A.ld, N, X, ldx, Y, ldy, seg);
   pm_launch_count_add(1);
 }
 
 template <int NR>
-void launch_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy,
+void launch_matvec32(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy,
                      cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -595,13 +640,13 @@ void launch_matvec32(const float4* A, size_t lda, int N, const double2* X, int l
   const int rb = (N + MV_ROWS - 1) / MV_ROWS;
   int segs = std::max(1, (sms * 12 + rb - 1) / rb);
   int seg = (N + segs - 1) / segs;
-  seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
+  seg = ((seg + MV32_KT - 1) / MV32_KT) * MV32_KT;
   segs = (N + seg - 1) / seg;
-  k_dense_matvec32<NR><<<dim3(rb, segs), MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  k_dense_matvec32<NR><<<dim3(rb, segs), MV_ROWS, 0, st>>>(A.hi, A.ld, N, X, ldx, Y, ldy, seg);
   pm_launch_count_add(1);
 }
 
-void dense_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec32(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st) {
   if (N <= 0 || nrhs <= 0) return;
   for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
@@ -610,15 +655,15 @@ void dense_matvec32(const float4* A, size_t lda, int N, const double2* X, int ld
     const int left = nrhs - r0;
     const double2* Xr = X + (size_t)r0 * ldx;
     double2* Yr = Y + (size_t)r0 * ldy;
-    if (left >= 8) { launch_matvec32<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
-    else if (left >= 4) { launch_matvec32<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
-    else if (left >= 2) { launch_matvec32<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
-    else { launch_matvec32<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+    if (left >= 8) { launch_matvec32<8>(A, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec32<4>(A, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec32<2>(A, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec32<1>(A, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "dense_matvec32", 0.0);
 }
 
-void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec_ff(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                      cudaStream_t st) {
   if (N <= 0 || nrhs <= 0) return;
   for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
@@ -627,16 +672,16 @@ void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int l
     const int left = nrhs - r0;
     const double2* Xr = X + (size_t)r0 * ldx;
     double2* Yr = Y + (size_t)r0 * ldy;
-    if (left >= 8) { launch_matvec_ff<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
-    else if (left >= 4) { launch_matvec_ff<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
-    else if (left >= 2) { launch_matvec_ff<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
-    else { launch_matvec_ff<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+    if (left >= 8) { launch_matvec_ff<8>(A, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec_ff<4>(A, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec_ff<2>(A, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec_ff<1>(A, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "dense_matvec_ff", 0.0);
 }
 
 template <int NR>
-void launch_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy,
+void launch_matvec_ffc(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy,
                        cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -646,11 +691,11 @@ void launch_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int
   int seg = (N + segs - 1) / segs;
   seg = ((seg + MV_KT - 1) / MV_KT) * MV_KT;
   segs = (N + seg - 1) / seg;
-  k_dense_matvec_ffc<NR><<<dim3(rb, segs), MV_ROWS, 0, st>>>(A, lda, N, X, ldx, Y, ldy, seg);
+  k_dense_matvec_ffc<NR><<<dim3(rb, segs), MV_ROWS, 0, st>>>(A.hi, A.lo, A.ld, N, X, ldx, Y, ldy, seg);
   pm_launch_count_add(1);
 }
 
-void dense_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec_ffc(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                       cudaStream_t st) {
   if (N <= 0 || nrhs <= 0) return;
   for (int q = 0; q < nrhs; ++q) cudaMemsetAsync(Y + (size_t)q * ldy, 0, sizeof(double2) * N, st);
@@ -659,10 +704,10 @@ void dense_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int 
     const int left = nrhs - r0;
     const double2* Xr = X + (size_t)r0 * ldx;
     double2* Yr = Y + (size_t)r0 * ldy;
-    if (left >= 8) { launch_matvec_ffc<8>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
-    else if (left >= 4) { launch_matvec_ffc<4>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
-    else if (left >= 2) { launch_matvec_ffc<2>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
-    else { launch_matvec_ffc<1>(A, lda, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
+    if (left >= 8) { launch_matvec_ffc<8>(A, N, Xr, ldx, Yr, ldy, st); r0 += 8; }
+    else if (left >= 4) { launch_matvec_ffc<4>(A, N, Xr, ldx, Yr, ldy, st); r0 += 4; }
+    else if (left >= 2) { launch_matvec_ffc<2>(A, N, Xr, ldx, Yr, ldy, st); r0 += 2; }
+    else { launch_matvec_ffc<1>(A, N, Xr, ldx, Yr, ldy, st); r0 += 1; }
   }
   KPROF_END(st, "dense_matvec_ffc", 0.0);
 }

@@ -16,41 +16,49 @@ struct OpNodes {
 // different inclusions; same-inclusion pairs are skipped).
 void apply_offdiag64(OpNodes nd, int total_nodes, double k0, const double2* X, int ldx, double2* Y, int ldy,
                      int nrhs, cudaStream_t st);
-// The dense operator is stored split: each complex entry a as float4
-// {hi(re), hi(im), lo(re), lo(im)} with hi = a truncated to 24 significant
-// bits and lo the next 24 bits, so hi + lo is exact in FP64 and within 2^-47
-// of the entry, in 16 bytes.
+// The dense operator is stored split, in two planes of float2 with the same
+// column-major layout: each complex entry a as hi = a truncated to 24
+// significant bits (per part) and lo = the next 24 bits, so hi + lo is exact
+// in FP64 and within 2^-47 of the entry, in 16 bytes; a product that needs
+// only the hi parts reads half of them.
+struct SplitOp {
+  float2* hi;
+  float2* lo;
+  size_t ld;
+  __host__ __device__ SplitOp at(size_t row, size_t col) const {
+    return SplitOp{hi + row + col * ld, lo + row + col * ld, ld};
+  }
+};
 // The stored operator is column-scaled: As = A diag(1 / cs) with cs[u index]
 // = w/4 and cs[q index] = k0 w/4 (dense_colscale), so that A X = As (cs X):
 // every product below takes cs X (scale_rows) as its right-hand operand.
-// Off-diagonal part written out densely (column-major, leading dimension lda);
-// same-inclusion pairs untouched (the caller copies the self blocks in).  One
-// Hankel evaluation per node pair fills the pair's 2 x 2 entries.
-void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, float4* A, size_t lda, cudaStream_t st);
+// Off-diagonal part written out densely; same-inclusion pairs untouched (the
+// caller copies the self blocks in).  One Hankel evaluation per node pair
+// fills the pair's 2 x 2 entries.
+void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, SplitOp A, cudaStream_t st);
 void dense_colscale(const double* w, const int* iu, const int* iq, int total_nodes, double k0, double* cs,
                     cudaStream_t st);
 // Xs = diag(cs) X, N x nrhs.
 void scale_rows(const double* cs, const double2* X, int ldx, double2* Xs, int ldxs, int N, int nrhs,
                 cudaStream_t st);
 // dst (split) <- src diag(1 / cs) (FP64) for an m x n block (cs: its n column scales).
-void split_copy(const double2* src, int lds, float4* dst, size_t ldd, int m, int n, const double* cs,
-                cudaStream_t st);
+void split_copy(const double2* src, int lds, SplitOp dst, int m, int n, const double* cs, cudaStream_t st);
 // Y (N x nrhs) = A X in FP64 arithmetic (entries hi + lo); Y overwritten.
-void dense_matvec64(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec64(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st);
 // The same product in float-float arithmetic on the FP32 pipes: error-free
 // FP32 products of the hi parts (FMA), first-order cross terms, compensated
 // sums; ~1e-13 relative, for refinement residuals.
-void dense_matvec_ff(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec_ff(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                      cudaStream_t st);
 // The float-float product with its sums folded into FP64 every 16 columns:
 // worst-case error ~9e-13 of sum_j |a_ij||x_j| per row, so it may decide the
 // convergence of the refinement (PM_FLAG_FF_CONFIRM).
-void dense_matvec_ffc(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec_ffc(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                       cudaStream_t st);
 // The same product with the hi parts in FP32 arithmetic (~1e-7 relative to
 // |A| |X|): the first refinement residual only.
-void dense_matvec32(const float4* A, size_t lda, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
+void dense_matvec32(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,
                     cudaStream_t st);
 // R = B - Y, and norms2[2 r] += |R[:, r]|^2, norms2[2 r + 1] += |B[:, r]|^2 (norms2 zeroed by caller)
 void residual64(const double2* B, const double2* Y, double2* R, int N, int nrhs, double* norms2, cudaStream_t st);

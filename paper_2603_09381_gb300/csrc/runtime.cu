@@ -334,7 +334,8 @@ struct pm_factor {
   std::vector<double2*> self64;
   int* d_iu = nullptr;
   int* d_iq = nullptr;
-  float4* dense64 = nullptr;    // the whole FP64 operator, N x N, split hi/lo, when it fits the memory budget
+  float2* dense64 = nullptr;    // the whole FP64 operator, N x N, split: hi plane then lo plane, when it fits
+  SplitOp dense_op{};           // its two planes
   double* d_colscale = nullptr; // its column scales: A = dense64 diag(d_colscale)
   size_t dense_bytes = 0;
   // CUDA graphs of the compressed inverse (FP64) or the mixed preconditioner,
@@ -792,7 +793,10 @@ void solve_batch(std::vector<SolveProb<C>>& probs, Arena& scr, cudaStream_t st, 
   if (wait_err && maxr <= 8) {
     std::vector<int4> items;
     ChainArgs ch;
-    ch.total_blocks = la_chain_items(hm.data(), (int)probs.size(), items);
+    // FP64: two columns per CTA (the links of the chain are bound by one SM's
+    // FP64 rate); complex64: all columns in one CTA
+    ch.rhs_per_cta = sizeof(C) == sizeof(double2) ? 2 : 8;
+    ch.total_blocks = la_chain_items(hm.data(), (int)probs.size(), (maxr + ch.rhs_per_cta - 1) / ch.rhs_per_cta, items);
     ch.items = items.empty() ? nullptr : upload(scr, items, st);
     ch.sync = scr.get<int>(la_chain_sync_ints(ch.total_blocks));
     ch.err = wait_err;
@@ -1961,7 +1965,7 @@ void apply_operator64(pm_factor* F, const double2* X, int nrhs, double2* Y, Aren
   if (F->dense64) {
     double2* Xs = ws.get<double2>((size_t)N * nrhs);
     scale_rows(F->d_colscale, X, N, Xs, N, N, nrhs, st);
-    dense_matvec64(F->dense64, (size_t)N, N, Xs, N, Y, N, nrhs, st);
+    dense_matvec64(F->dense_op, N, Xs, N, Y, N, nrhs, st);
     if (g_kprof) g_kprof->add_flops("dense_matvec64", 8.0 * (double)N * N * nrhs);
     CK(cudaGetLastError());
     return;
@@ -2023,7 +2027,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   };
   auto residual = [&](const double2* x) {
     if (ff_confirm) {
-      dense_matvec_ffc(F->dense64, (size_t)N, N, scaled(x), N, Y, N, nrhs, st);
+      dense_matvec_ffc(F->dense_op, N, scaled(x), N, Y, N, nrhs, st);
       CK(cudaGetLastError());
     } else {
       apply_operator64(F, x, nrhs, Y, ws, st);
@@ -2031,12 +2035,12 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
     return finish();
   };
   auto residual_low = [&](const double2* x) {
-    dense_matvec_ff(F->dense64, (size_t)N, N, scaled(x), N, Y, N, nrhs, st);
+    dense_matvec_ff(F->dense_op, N, scaled(x), N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     return finish();
   };
   auto residual_f32 = [&](const double2* x) {
-    dense_matvec32(F->dense64, (size_t)N, N, scaled(x), N, Y, N, nrhs, st);
+    dense_matvec32(F->dense_op, N, scaled(x), N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     return finish();
   };
@@ -2046,7 +2050,7 @@ void solve_refined(pm_factor* F, const double2* B, int nrhs, double2* X, Arena& 
   // so it is used only while 1e-6 |r| is far below refine_tol; the new
   // residual goes to dx's buffer and the two buffers swap.
   auto residual_update32 = [&]() {
-    dense_matvec32(F->dense64, (size_t)N, N, scaled(dX), N, Y, N, nrhs, st);
+    dense_matvec32(F->dense_op, N, scaled(dX), N, Y, N, nrhs, st);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
     residual64(R, Y, dX, N, nrhs, norms, st);
@@ -2453,15 +2457,16 @@ void finish_mixed(pm_factor* F) {
   // Budget: 60% of the free memory, and all dense operators held in the
   // process at most 40% of the device; otherwise (or if the allocation
   // fails) the refinement applies the operator on the fly.
-  const size_t need = sizeof(float4) * (size_t)g->N * g->N;
+  const size_t need = 2 * sizeof(float2) * (size_t)g->N * g->N;
   if (!(opts->flags & PM_FLAG_NO_DENSE_OPERATOR) && g->total_nodes <= 65535) {
     std::lock_guard<std::mutex> lk(g_dense_mu);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     fr += pool_cached_bytes(current_device());   // cached blocks are free for this purpose
     if (need <= fr / 10 * 6 && g_dense_held + need <= tot / 10 * 4) {
-      F->dense64 = (float4*)pool_malloc(need);
+      F->dense64 = (float2*)pool_malloc(need);
       if (F->dense64) {
+        F->dense_op = SplitOp{F->dense64, F->dense64 + (size_t)g->N * g->N, (size_t)g->N};
         F->dense_bytes = need;
         g_dense_held += need;
       }
@@ -2471,7 +2476,7 @@ void finish_mixed(pm_factor* F) {
     OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
     F->d_colscale = F->arena.get<double>((size_t)g->N);
     dense_colscale(g->nodes.w, F->d_iu, F->d_iq, g->total_nodes, g->k0, F->d_colscale, F->st);
-    assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense64, (size_t)g->N, F->st);
+    assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense_op, F->st);
     if (g_kprof) {
       double pairs = (double)g->total_nodes * g->total_nodes;
       for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
@@ -2481,8 +2486,8 @@ void finish_mixed(pm_factor* F) {
     }
     for (int j = 0; j < g->m; ++j) {
       const int m2 = 2 * g->inc[j].n_nodes;
-      split_copy(F->self64[j], m2, F->dense64 + g->row_off[j] + (size_t)g->row_off[j] * g->N, (size_t)g->N, m2,
-                 m2, F->d_colscale + g->row_off[j], F->st);
+      split_copy(F->self64[j], m2, F->dense_op.at(g->row_off[j], g->row_off[j]), m2, m2, F->d_colscale + g->row_off[j],
+                 F->st);
     }
     CK(cudaGetLastError());
   }
