@@ -451,6 +451,22 @@ void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, doubl
   KPROF_END(st, kname<C>("self_pointwise", "self_pointwise32"), 0.0);
 }
 
+__global__ void k_round_blocks(const double2* const* __restrict__ src, float2* const* __restrict__ dst,
+                               const int* __restrict__ n) {
+  const int b = blockIdx.y, m = n[b];
+  const double2* sb = src[b];
+  float2* db = dst[b];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x)
+    db[e] = make_float2((float)sb[e].x, (float)sb[e].y);
+}
+
+void round_blocks(const double2* const* d_src, float2* const* d_dst, const int* d_n, int nblk, int maxn,
+                  cudaStream_t st) {
+  if (nblk <= 0 || maxn <= 0) return;
+  k_round_blocks<<<dim3(std::min(64, (maxn * maxn + 255) / 256), nblk), 256, 0, st>>>(d_src, d_dst, d_n);
+  pm_launch_count_add(1);
+}
+
 template <typename C>
 void diff_matrices(int n, C* Dt, cudaStream_t st) {
   k_diff_matrix<C><<<(n * n + 255) / 256, 256, 0, st>>>(n, Dt);

@@ -69,6 +69,10 @@ void self_pointwise(const InclDev* d_inc, int m, int maxn, NodesDev nodes, doubl
 // Trigonometric differentiation matrix Dt (n x n) and diag(1/|x'|) Dt for an inclusion.
 template <typename C>
 void diff_matrices(int n, C* Dt, cudaStream_t st);
+// dst[b] = src[b] rounded to complex64, for nblk square blocks of order n[b]
+// (leading dimension n[b] on both sides); maxn: the largest order.
+void round_blocks(const double2* const* d_src, float2* const* d_dst, const int* d_n, int nblk, int maxn,
+                  cudaStream_t st);
 template <typename C>
 void scaled_diff(const InclDev* d_inc, int m, int maxn, NodesDev nodes, C* const* d_DtS, cudaStream_t st);
 template <typename C>

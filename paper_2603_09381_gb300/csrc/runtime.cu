@@ -1074,7 +1074,23 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
           bf.D = F->arena.get<C>((size_t)bf.mb * bf.mb);
           incl.push_back(boxes[b].leaves[0]); A.push_back(bf.D); lda.push_back(bf.mb);
         }
-        assemble_self<C>(g, incl, A, lda, scr, st, F->opts.formulation >= PM_FORM_BM);
+        if constexpr (std::is_same<C, float2>::value) {
+          // mixed mode: the FP64 self blocks (kept for the refinement's operator)
+          // rounded to complex64, instead of a second assembly in complex64
+          if (F->self64.size() != (size_t)g->m) F->self64.assign(g->m, nullptr);
+          std::vector<double2*> A64;
+          for (size_t i = 0; i < incl.size(); ++i) {
+            double2*& d = F->self64[incl[i]];
+            if (!d) d = F->arena.get<double2>((size_t)lda[i] * lda[i]);
+            A64.push_back(d);
+          }
+          assemble_self<double2>(g, incl, A64, lda, scr, st, F->opts.formulation >= PM_FORM_BM);
+          const int maxn = *std::max_element(lda.begin(), lda.end());
+          round_blocks(upload(scr, A64, st), upload(scr, A, st), upload(scr, lda, st), (int)incl.size(), maxn, st);
+          CK(cudaGetLastError());
+        } else {
+          assemble_self<C>(g, incl, A, lda, scr, st, F->opts.formulation >= PM_FORM_BM);
+        }
       } else {
         if (jb0[j] == 0)
           for (int b = 0; b < nbj; ++b) active_sets<C, C>(LV[lev + 1], boxes[b], BF[b]);
@@ -2435,15 +2451,18 @@ void finish_mixed(pm_factor* F) {
   const pm_geometry* g = F->g;
   const pm_factor_opts* opts = &F->opts;
   // FP64 self blocks and index maps for the refinement residual
+  // (those of the leaves' inclusions were assembled with the leaf level)
   F->scratch.reset();
-  std::vector<int> incl(g->m), lda(g->m);
-  F->self64.resize(g->m);
+  std::vector<int> incl, lda;
+  std::vector<double2*> A64;
+  if (F->self64.size() != (size_t)g->m) F->self64.assign(g->m, nullptr);
   for (int j = 0; j < g->m; ++j) {
-    incl[j] = j;
-    lda[j] = 2 * g->inc[j].n_nodes;
-    F->self64[j] = F->arena.get<double2>((size_t)lda[j] * lda[j]);
+    if (F->self64[j]) continue;
+    const int m2 = 2 * g->inc[j].n_nodes;
+    F->self64[j] = F->arena.get<double2>((size_t)m2 * m2);
+    incl.push_back(j); lda.push_back(m2); A64.push_back(F->self64[j]);
   }
-  assemble_self<double2>(g, incl, F->self64, lda, F->scratch, F->st);
+  if (!incl.empty()) assemble_self<double2>(g, incl, A64, lda, F->scratch, F->st);
   std::vector<int> iu(g->total_nodes), iq(g->total_nodes);
   for (int j = 0; j < g->m; ++j)
     for (int l = 0; l < g->inc[j].n_nodes; ++l) {
