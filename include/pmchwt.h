@@ -90,9 +90,11 @@ typedef struct pm_factor pm_factor;
  *      p = max(32, 8 ceil((2 k^+ R_p + ceil(ln(1/tol)/ln(proxy_factor)))/8)).
  * precision: PM_FP64 (everything complex128), or PM_MIXED: the levels are
  *      factored in complex64 with ID threshold max(tol, low_tol) and serve as a
- *      preconditioner; the top-level LU stays complex128 and pm_solve refines
- *      the solution against the complex128 operator (no counterpart in the
- *      paper).
+ *      preconditioner, and pm_solve refines the solution against the
+ *      complex128 operator (no counterpart in the paper).  The top-level
+ *      system is assembled in complex128 and factored in complex64 (its
+ *      rounding stays far below the levels' ID threshold); PM_FLAG_TOP_FP64
+ *      factors it in complex128.
  * stream: cudaStream_t to run on, or NULL for the default stream.
  * flags: PM_FLAG_PROFILE records per-kernel timings.  PM_MIXED writes the
  *      complex128 operator out densely (N^2 x 16 bytes) when it fits in 60% of
@@ -377,7 +379,8 @@ enum {
   PM_FLAG_NO_AUTOTUNE = 64,
   PM_FLAG_NO_GRAPHS = 128,
   PM_FLAG_PROXY_CHECK = 256,
-  PM_FLAG_QR_CUDA_CORES = 512
+  PM_FLAG_QR_CUDA_CORES = 512,
+  PM_FLAG_TOP_FP64 = 1024
 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 

@@ -739,17 +739,23 @@ __device__ __forceinline__ int ts_load_acquire(const int* p) {
 __device__ __forceinline__ void ts_store_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-template <typename C>
+// G: dependencies taken per round.  A round loads the coefficient blocks of
+// the next G dependencies together, waits for the first one's flag, adds
+// the later ones whose flags are already up, loads their solved rows
+// together and subtracts their products one by one in dependency order: a
+// block that is behind the chain's front catches up with one pair of
+// memory round trips per round instead of per dependency.
+template <typename C, int G>
 __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restrict__ P, const int4* __restrict__ items,
                                                     int nitems, int lower, int rg, int* sync, int* err,
                                                     const int* never, int no_flag) {
   typedef typename real_of<C>::type R;
   constexpr int NB = 32;
-  __shared__ C sl[NB][NB + 1];   // the off-diagonal block of the current dependency, [col][row]
-  __shared__ C sx[NB][8];        // its solved rows (this CTA's right-hand sides)
-  __shared__ C sa[NB][NB + 1];   // the diagonal block
-  __shared__ C s_odd[4][NB];     // rg <= 4: the odd-term sums
-  __shared__ int s_t, s_stop;
+  __shared__ C sl[G][NB][NB + 1];   // the off-diagonal blocks of this round's dependencies, [col][row]
+  __shared__ C sx[G][NB][8];        // their solved rows (this CTA's right-hand sides)
+  __shared__ C sa[NB][NB + 1];      // the diagonal block
+  __shared__ C s_odd[G][4][NB];     // rg <= 4: the odd-term sums
+  __shared__ int s_t, s_stop, s_cnt;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -791,17 +797,20 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
   const bool odd = split && i < jb && q < nrhs && h == 1;
   C x = mine ? pr.B[r0 + i + (size_t)(q0 + q) * pr.ldb] : czero<C>();
   const int ndep = lower ? b : nblk - 1 - b;
-  for (int d = 0; d < ndep; ++d) {
-    const int j = lower ? d : nblk - 1 - d;
-    const int c0 = j * NB, jbj = min(NB, m - c0);
-    // the coefficients do not depend on the flag: load them first
-    for (int e = tid; e < jb * jbj; e += 256) {
-      const int r = e % jb, c = e / jb;
-      sl[c][r] = pr.A[r0 + r + (size_t)(c0 + c) * ld];
+  auto dep = [&](int d) { return lower ? d : nblk - 1 - d; };   // the d-th block this one depends on
+  for (int d0 = 0; d0 < ndep;) {
+    const int gmax = min(G, ndep - d0);
+    // the coefficients do not depend on the flags: load them first
+    for (int g = 0; g < gmax; ++g) {
+      const int c0 = dep(d0 + g) * NB, jbj = min(NB, m - c0);
+      for (int e = tid; e < jb * jbj; e += 256) {
+        const int r = e % jb, c = e / jb;
+        sl[g][c][r] = pr.A[r0 + r + (size_t)(c0 + c) * ld];
+      }
     }
     if (tid == 0) {
       const unsigned long long t0 = ts_now();
-      while (ts_load_acquire(&flags[j]) == 0) {
+      while (ts_load_acquire(&flags[dep(d0)]) == 0) {
         if (ts_load_acquire(&sync[1]) != 0) { s_stop = 1; break; }
         if ((long long)(ts_now() - t0) > TS_WAIT_NS) {
           atomicExch(err, 1);
@@ -811,40 +820,51 @@ __global__ void __launch_bounds__(256) k_trsv_chain(const SolveProb<C>* __restri
         }
         __nanosleep(64);
       }
+      int cnt = 1;
+      while (cnt < gmax && ts_load_acquire(&flags[dep(d0 + cnt)]) != 0) ++cnt;
+      s_cnt = cnt;
     }
     __syncthreads();
     if (s_stop) return;
-    for (int e = tid; e < jbj * nrhs; e += 256) {
-      const int l = e % jbj, qq = e / jbj;
-      sx[l][qq] = __ldcg(pr.B + c0 + l + (size_t)(q0 + qq) * pr.ldb);
+    const int cnt = s_cnt;
+    for (int g = 0; g < cnt; ++g) {
+      const int c0 = dep(d0 + g) * NB, jbj = min(NB, m - c0);
+      for (int e = tid; e < jbj * nrhs; e += 256) {
+        const int l = e % jbj, qq = e / jbj;
+        sx[g][l][qq] = __ldcg(pr.B + c0 + l + (size_t)(q0 + qq) * pr.ldb);
+      }
     }
     __syncthreads();
-    if (split) {
-      // acc0 over the even terms, acc1 over the odd ones, each in order
-      C acc = czero<C>();
-      if (mine || odd)
-        for (int l = h; l < jbj; l += 2) cfma(acc, sl[l][i], sx[l][q]);
-      if (odd) s_odd[q][i] = acc;
-      __syncthreads();
-      if (mine) x = x - (acc + s_odd[q][i]);
-    } else if (mine) {
-      C acc0 = czero<C>(), acc1 = czero<C>();
-      int l = 0;
-      for (; l + 1 < jbj; l += 2) {
-        cfma(acc0, sl[l][i], sx[l][q]);
-        cfma(acc1, sl[l + 1][i], sx[l + 1][q]);
+    for (int g = 0; g < cnt; ++g) {
+      const int jbj = min(NB, m - dep(d0 + g) * NB);
+      if (split) {
+        // acc0 over the even terms, acc1 over the odd ones, each in order
+        C acc = czero<C>();
+        if (mine || odd)
+          for (int l = h; l < jbj; l += 2) cfma(acc, sl[g][l][i], sx[g][l][q]);
+        if (odd) s_odd[g][q][i] = acc;
+        __syncthreads();
+        if (mine) x = x - (acc + s_odd[g][q][i]);
+      } else if (mine) {
+        C acc0 = czero<C>(), acc1 = czero<C>();
+        int l = 0;
+        for (; l + 1 < jbj; l += 2) {
+          cfma(acc0, sl[g][l][i], sx[g][l][q]);
+          cfma(acc1, sl[g][l + 1][i], sx[g][l + 1][q]);
+        }
+        if (l < jbj) cfma(acc0, sl[g][l][i], sx[g][l][q]);
+        x = x - (acc0 + acc1);
       }
-      if (l < jbj) cfma(acc0, sl[l][i], sx[l][q]);
-      x = x - (acc0 + acc1);
     }
     __syncthreads();   // sl, sx and s_odd are refilled next
+    d0 += cnt;
   }
   // the diagonal block: warp q solves right-hand side q, lane r holds row r
-  if (mine) sx[i][q] = x;
+  if (mine) sx[0][i][q] = x;
   __syncthreads();
   if (warp < nrhs) {
     const C dinv = (!lower && lane < jb) ? cdiv(mk((R)1, (R)0), sa[lane][lane]) : czero<C>();
-    C y = lane < jb ? sx[lane][warp] : czero<C>();
+    C y = lane < jb ? sx[0][lane][warp] : czero<C>();
     if (lower) {
       for (int c = 0; c < jb - 1; ++c) {
         const C yc = shfl_c(y, c);
@@ -1085,10 +1105,13 @@ void la_getrs_batched(const SolveProb<C>* d_prob, int nprob, int maxm, int maxrh
     cudaMemsetAsync(chain->sync, 0, sizeof(int) * la_chain_sync_ints(T), st);
     const int* never = chain->sync + 2 * (2 + T);
     if (T > 0) {
-      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items, T, 1, chain->rhs_per_cta, chain->sync, chain->err,
-                                         never, chain->no_flag);
-      k_trsv_chain<C><<<T, 256, 0, st>>>(d_prob, chain->items + T, T, 0, chain->rhs_per_cta, chain->sync + 2 + T,
-                                         chain->err, never, chain->no_flag);
+      // complex64: three dependencies per round; FP64: one (its products are
+      // bound by the SM's FP64 rate, not by the round trips)
+      constexpr int G = sizeof(C) == sizeof(double2) ? 1 : 3;
+      k_trsv_chain<C, G><<<T, 256, 0, st>>>(d_prob, chain->items, T, 1, chain->rhs_per_cta, chain->sync, chain->err,
+                                            never, chain->no_flag);
+      k_trsv_chain<C, G><<<T, 256, 0, st>>>(d_prob, chain->items + T, T, 0, chain->rhs_per_cta, chain->sync + 2 + T,
+                                            chain->err, never, chain->no_flag);
       pm_launch_count_add(2);
     }
     KPROF_END(st, kname<C>("getrs", "getrs32"), fl);

@@ -474,8 +474,12 @@ __global__ void k_split_copy(const double2* __restrict__ src, int lds, SplitOp d
   if (e >= m * n) return;
   const int i = e % m, j = e / m;
   const double2 v = src[i + (size_t)j * lds];
-  const double c = 1.0 / cs[j];
-  store_split(dst, i + (size_t)j * dst.ld, v.x * c, v.y * c);
+  if (cs) {
+    const double c = 1.0 / cs[j];
+    store_split(dst, i + (size_t)j * dst.ld, v.x * c, v.y * c);
+  } else {
+    store_split(dst, i + (size_t)j * dst.ld, v.x, v.y);
+  }
 }
 
 __global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ Y, double2* __restrict__ R, int N,

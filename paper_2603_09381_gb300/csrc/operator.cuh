@@ -41,7 +41,8 @@ void dense_colscale(const double* w, const int* iu, const int* iq, int total_nod
 // Xs = diag(cs) X, N x nrhs.
 void scale_rows(const double* cs, const double2* X, int ldx, double2* Xs, int ldxs, int N, int nrhs,
                 cudaStream_t st);
-// dst (split) <- src diag(1 / cs) (FP64) for an m x n block (cs: its n column scales).
+// dst (split) <- src diag(1 / cs) (FP64) for an m x n block (cs: its n column
+// scales, or nullptr for none).
 void split_copy(const double2* src, int lds, SplitOp dst, int m, int n, const double* cs, cudaStream_t st);
 // Y (N x nrhs) = A X in FP64 arithmetic (entries hi + lo); Y overwritten.
 void dense_matvec64(SplitOp A, int N, const double2* X, int ldx, double2* Y, int ldy, int nrhs,

@@ -319,7 +319,10 @@ struct pm_factor {
   int precision = PM_FP64;
   std::vector<std::vector<BoxF<double2>>> lev64;   // FP64 mode
   std::vector<std::vector<BoxF<float2>>> lev32;    // mixed mode (FP32 factorization)
-  BoxF<double2> root;                              // top-level system, always FP64
+  BoxF<double2> root;                              // top-level system, assembled in FP64
+  float2* root32 = nullptr;                        // mixed mode: its complex64 LU factors
+  int* ipiv32 = nullptr;
+  SplitOp root_op{};                               // and the FP64 system (hi / lo planes) for one correction
   Arena arena, scratch;
   pm_stats stats{};
   std::vector<std::vector<Box>> tree;  // the geometry's quadtree with this factorization's proxies
@@ -1714,6 +1717,10 @@ void factor_tops(const std::vector<pm_factor*>& Fs, Arena& scr, cudaStream_t st)
   GatherBatch<double2> gb;
   CopyBatch<Cc, double2> cb;
   std::vector<LuProb<double2>> lu;
+  std::vector<LuProb<float2>> lu32;
+  std::vector<const double2*> r64;
+  std::vector<float2*> r32;
+  std::vector<int> rn;
   for (size_t i = 0; i < Fs.size(); ++i) {
     pm_factor* F = Fs[i];
     const pm_geometry* g = F->g;
@@ -1730,11 +1737,33 @@ void factor_tops(const std::vector<pm_factor*>& Fs, Arena& scr, cudaStream_t st)
       set_form(gb, F);
       merge_children<Cc, double2>(F, levels_of<Cc>(F)[1], F->tree[0][0], rt, gb, cb, 2 * base[i]);
     }
+    if (F->precision == PM_MIXED && !(F->opts.flags & PM_FLAG_TOP_FP64)) {
+      // mixed mode: a preconditioner whose levels carry ID errors of ~5e-6;
+      // the top system is factored in complex64 from its FP64 assembly
+      F->root32 = F->arena.get<float2>((size_t)std::max(rt.mb, 1) * rt.mb);
+      F->ipiv32 = F->arena.get<int>(std::max(rt.mb, 1));
+      lu32.push_back(LuProb<float2>{F->root32, rt.mb, rt.mb, F->ipiv32, nullptr});
+      r64.push_back(rt.D); r32.push_back(F->root32); rn.push_back(rt.mb);
+      continue;
+    }
     rt.ipiv = F->arena.get<int>(std::max(rt.mb, 1));
     lu.push_back(LuProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, nullptr});
   }
   gb.run(scr, P, 0.0, st);
   cb.run(scr, st);
+  if (!r64.empty()) {
+    const int maxn = *std::max_element(rn.begin(), rn.end());
+    round_blocks(upload(scr, r64, st), upload(scr, r32, st), upload(scr, rn, st), (int)rn.size(), maxn, st);
+    for (pm_factor* F : Fs)
+      if (F->root32) {
+        const int mb = F->root.mb;
+        float2* planes = F->arena.get<float2>(2 * (size_t)std::max(mb, 1) * mb);
+        F->root_op = SplitOp{planes, planes + (size_t)mb * mb, (size_t)std::max(mb, 1)};
+        split_copy(F->root.D, mb, F->root_op, mb, mb, nullptr, st);
+      }
+    CK(cudaGetLastError());
+    lu_batch<float2>(lu32, scr, st, "top-level system");
+  }
   lu_batch<double2>(lu, scr, st, "top-level system");
   const double ms = t.stop();
   for (pm_factor* F : Fs) {
@@ -1864,8 +1893,45 @@ void solve_down(pm_factor* F, int nrhs, SolveWork<C>& w, C* phi, Arena& ws, cuda
 
 void root_solve(pm_factor* F, double2* x, int ldx, int nrhs, Arena& ws, cudaStream_t st) {
   BoxF<double2>& rt = F->root;
+  const bool no_flag = (F->opts.debug_flags & PM_DEBUG_SOLVE_NO_FLAG) != 0;
+  if (F->root32) {
+    // complex64 top LU with one correction from the FP64 residual:
+    // x0 = S(b), x = x0 + S(b - A x0), S = the complex64 LU solve (the
+    // correction takes the top solve's error from ~kappa u32 to ~(kappa u32)^2)
+    const int mb = rt.mb;
+    const size_t len = (size_t)std::max(mb, 1) * nrhs;
+    float2* x32 = ws.get<float2>(len);
+    double2* b = ws.get<double2>(len);
+    double2* y = ws.get<double2>(len);
+    double* norms = ws.get<double>(2 * (size_t)nrhs);
+    auto solve32 = [&](const double2* src, int lds, double2* dst, int ldd) {
+      CopyBatch<double2, float2> down;
+      down.add(src, lds, x32, mb, mb, nrhs);
+      down.run(ws, st);
+      std::vector<SolveProb<float2>> sv{SolveProb<float2>{F->root32, mb, mb, F->ipiv32, x32, mb, nrhs}};
+      solve_batch<float2>(sv, ws, st, F->d_wait_err, no_flag);
+      CopyBatch<float2, double2> up;
+      up.add(x32, mb, dst, ldd, mb, nrhs);
+      up.run(ws, st);
+    };
+    CopyBatch<double2, double2> keep;                         // b: the right-hand sides, leading dimension mb
+    keep.add(x, ldx, b, mb, mb, nrhs);
+    keep.run(ws, st);
+    double2* x0 = ws.get<double2>(len);
+    solve32(b, mb, x0, mb);                                  // x0 = S(b)
+    dense_matvec64(F->root_op, mb, x0, mb, y, mb, nrhs, st);  // y = A x0
+    CK(cudaMemsetAsync(norms, 0, 2 * nrhs * sizeof(double), st));
+    residual64(b, y, b, mb, nrhs, norms, st);                // b = b - A x0
+    solve32(b, mb, y, mb);                                   // y = S(b - A x0)
+    axpy64(x0, y, mb, nrhs, st);                             // x0 += y
+    CopyBatch<double2, double2> back;
+    back.add(x0, mb, x, ldx, mb, nrhs);
+    back.run(ws, st);
+    CK(cudaGetLastError());
+    return;
+  }
   std::vector<SolveProb<double2>> sv{SolveProb<double2>{rt.D, rt.mb, rt.mb, rt.ipiv, x, ldx, nrhs}};
-  solve_batch<double2>(sv, ws, st, F->d_wait_err, (F->opts.debug_flags & PM_DEBUG_SOLVE_NO_FLAG) != 0);
+  solve_batch<double2>(sv, ws, st, F->d_wait_err, no_flag);
 }
 
 // phi = M^{-1} rhs with the compressed factorization (FP64 levels).
