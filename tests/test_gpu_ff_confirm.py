@@ -34,3 +34,27 @@ def test_confirming_residual_matches_the_oracle(pm, ff_confirm):
     res = max(np.linalg.norm(F[:, r] - A @ phi[:, r]) / np.linalg.norm(F[:, r]) for r in range(len(angs)))
     assert res <= 2e-10
     assert abs(res - info["residual"]) <= 5e-12
+
+
+@pytest.mark.parametrize("top_fp64", [False, True])
+def test_top_level_precision_matches_the_oracle(pm, top_fp64):
+    """The mixed preconditioner's top-level system factored in complex64 with
+    one FP64-residual correction per solve (default) or in complex128
+    (PM_FLAG_TOP_FP64): the refined solution agrees with the dense oracle
+    either way, and the complex64 top takes no more refinement steps than
+    the complex128 one plus one."""
+    prob = wl.star_grid(4, 4, n=64, seed=1)
+    angs = [0.3, 1.9, 4.4]
+    g = pm.Geometry(prob)
+    F = g.plane_wave(angs)
+    f = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, top_fp64=top_fp64)
+    phi = f.solve(F)
+    info = f.last_info
+    assert info["residual"] <= 1e-10
+    A = dense.assemble(prob)
+    ref = np.linalg.solve(A, F)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-8
+    if not top_fp64:
+        f64 = pm.Factor(g, 1e-10, precision=pm.PM_MIXED, top_fp64=True)
+        f64.solve(F)
+        assert info["iterations"] <= f64.last_info["iterations"] + 1
