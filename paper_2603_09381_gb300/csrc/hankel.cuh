@@ -13,7 +13,10 @@
 //   - 8 <= z < 60: polynomial fits of P_nu - 1 and z Q_nu in 1/z^2 on
 //     [8, 12), [12, 20), [20, 30), [30, 60) (hankel_fit.h, written by
 //     gen_hankel_fit.py from 40-digit values; within 2e-17 of P_nu and Q_nu).
-//   One sincos(z) serves both orders: w_1 = w_0 - pi/2.
+//   One sincos of w_0 = z - pi/4 serves both orders (w_1 = w_0 - pi/2); the
+//   subtraction adds at most half an ulp of z to the phase.
+// The interval of z is chosen on z rounded to FP32 (comparisons on the FP32
+// pipes): next to a boundary either neighbouring form is within its bound.
 // z < 8: CUDA's j0 / y0 / j1 / y1.
 // Complex z (lossy interiors, self blocks): Miller's backward recurrence
 //   J_{n-1} = (2n/z) J_n - J_{n+1} from an even start M > |z| + 25 + 3 sqrt|z|,
@@ -47,11 +50,9 @@ static __constant__ double c_hk_a1[HK_TERMS] = HK_ROW(1);
 // J and Y of orders 0 and 1 from P_nu, Q_nu (iz = 1/z).
 __device__ __forceinline__ void hankel_combine(double z, double iz, double P0, double Q0, double P1, double Q1,
                                                double& J0, double& Y0, double& J1, double& Y1) {
-  double sn, cs;
-  sincos(z, &sn, &cs);
+  double c, d;
+  sincos(z - 0.78539816339744830962, &d, &c);                  // sin, cos of z - pi/4
   const double s = sqrt(0.63661977236758134308 * iz);          // sqrt(2/(pi z))
-  const double c = (cs + sn) * 0.70710678118654752440;         // cos(z - pi/4)
-  const double d = (sn - cs) * 0.70710678118654752440;         // sin(z - pi/4)
   J0 = s * (P0 * c - Q0 * d);
   Y0 = s * (P0 * d + Q0 * c);
   J1 = s * (P1 * d + Q1 * c);
@@ -79,15 +80,16 @@ __device__ __forceinline__ void hankel_series(double z, double iz, double& J0, d
 
 // z >= 8 (iz = 1/z)
 __device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
-  if (z >= HK_ZS) {
+  const float zf = (float)z;
+  if (zf >= (float)HK_ZS) {
     hankel_series(z, iz, J0, Y0, J1, Y1);
     return;
   }
   const double v = iz * iz;
   double P0, zQ0, P1, zQ1;
-  if (z >= 30.0) hankel_fit3(v, P0, zQ0, P1, zQ1);
-  else if (z >= 20.0) hankel_fit2(v, P0, zQ0, P1, zQ1);
-  else if (z >= 12.0) hankel_fit1(v, P0, zQ0, P1, zQ1);
+  if (zf >= 30.f) hankel_fit3(v, P0, zQ0, P1, zQ1);
+  else if (zf >= 20.f) hankel_fit2(v, P0, zQ0, P1, zQ1);
+  else if (zf >= 12.f) hankel_fit1(v, P0, zQ0, P1, zQ1);
   else hankel_fit0(v, P0, zQ0, P1, zQ1);
   hankel_combine(z, iz, P0, zQ0 * iz, P1, zQ1 * iz, J0, Y0, J1, Y1);
 }
@@ -95,13 +97,13 @@ __device__ __forceinline__ void hankel_asym(double z, double iz, double& J0, dou
 // Below z = 8 CUDA's j0/y0/j1/y1 (~1e-15 absolute, measured against scipy
 // on GB300).
 __device__ __forceinline__ void hankel01(double z, double& J0, double& Y0, double& J1, double& Y1) {
-  if (z >= HK_ZA) hankel_asym(z, 1.0 / z, J0, Y0, J1, Y1);
+  if ((float)z >= (float)HK_ZA) hankel_asym(z, 1.0 / z, J0, Y0, J1, Y1);
   else { J0 = j0(z); Y0 = y0(z); J1 = j1(z); Y1 = y1(z); }
 }
 
 // Same, with 1/z supplied by the caller.
 __device__ __forceinline__ void hankel01_inv(double z, double iz, double& J0, double& Y0, double& J1, double& Y1) {
-  if (z >= HK_ZA) hankel_asym(z, iz, J0, Y0, J1, Y1);
+  if ((float)z >= (float)HK_ZA) hankel_asym(z, iz, J0, Y0, J1, Y1);
   else { J0 = j0(z); Y0 = y0(z); J1 = j1(z); Y1 = y1(z); }
 }
 
