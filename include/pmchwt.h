@@ -94,7 +94,11 @@ typedef struct pm_factor pm_factor;
  *      complex128 operator (no counterpart in the paper).  The top-level
  *      system is assembled in complex128 and factored in complex64 (its
  *      rounding stays far below the levels' ID threshold); PM_FLAG_TOP_FP64
- *      factors it in complex128.
+ *      factors it in complex128.  pm_factorize assembles the dense
+ *      complex128 operator on a low-priority stream concurrently with the
+ *      complex64 factorization (one persistent CTA of 128 threads per SM);
+ *      PM_FLAG_OPERATOR_AFTER assembles it after the factorization instead
+ *      (pm_factor_batch always does).
  * stream: cudaStream_t to run on, or NULL for the default stream.
  * flags: PM_FLAG_PROFILE records per-kernel timings.  PM_MIXED writes the
  *      complex128 operator out densely (N^2 x 16 bytes) when it fits in 60% of
@@ -380,7 +384,8 @@ enum {
   PM_FLAG_NO_GRAPHS = 128,
   PM_FLAG_PROXY_CHECK = 256,
   PM_FLAG_QR_CUDA_CORES = 512,
-  PM_FLAG_TOP_FP64 = 1024
+  PM_FLAG_TOP_FP64 = 1024,
+  PM_FLAG_OPERATOR_AFTER = 2048
 };
 pm_status pm_factor_profile(const pm_factor* f, pm_kernel_stat* out, int32_t cap, int32_t* count);
 

@@ -164,11 +164,8 @@ __device__ __forceinline__ float4 split4(double re, double im) {
 //   (s <- t): u-col (Y0 - i J0, k b (Y1 - i J1)),  q-col (a (Y1 - i J1), N)
 // with N = -(c0 Y0 + c1 Y1) + i (c0 J0 + c1 J1), c0 = k a b,
 // c1 = (n_t.n_s - 2 a b)/r, symmetric in the pair.
-__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double ik, SplitOp A) {
-  if (blockIdx.x * 64 >= blockIdx.y * 4 + 3) return;   // whole block on or below the diagonal
-  const int s = blockIdx.y * 4 + (threadIdx.x & 3);
-  const int t = blockIdx.x * 64 + (threadIdx.x >> 2);
-  if (s >= total || t >= s) return;
+// The pair (t, s), t < s, of different inclusions: both 2 x 2 entry blocks.
+__device__ __forceinline__ void offdiag_pair(const OpNodes& nd, int t, int s, double k, double ik, const SplitOp& A) {
   const int ti = nd.incl[t], si = nd.incl[s];
   if (ti == si) return;
   const double dx = nd.x[t] - nd.x[s], dy = nd.y[t] - nd.y[s];
@@ -195,6 +192,37 @@ __global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, do
   store_split(A, qs + ut * lda, kb * Y1, -kb * J1);
   store_split(A, us + qt * lda, a * Y1, -a * J1);
   store_split(A, qs + qt * lda, Nre, Nim);
+}
+
+__global__ void __launch_bounds__(256) k_dense_offdiag(OpNodes nd, int total, double k, double ik, SplitOp A) {
+  if (blockIdx.x * 64 >= blockIdx.y * 4 + 3) return;   // whole block on or below the diagonal
+  const int s = blockIdx.y * 4 + (threadIdx.x & 3);
+  const int t = blockIdx.x * 64 + (threadIdx.x >> 2);
+  if (s >= total || t >= s) return;
+  offdiag_pair(nd, t, s, k, ik, A);
+}
+
+// Persistent form, for a run beside other kernels with a small footprint
+// (one CTA of 128 threads per SM): each CTA takes rows of 4 nodes s from a
+// counter (longest rows first) and fills their pairs with every t < s in
+// passes of 32 t x 4 s (s fastest: whole-sector writes in both halves).
+// At most 64 registers: 128 x 64 = 8,192 of the SM's 65,536 (a 512-thread
+// CTA of 112 registers still fits beside it).
+__global__ void __maxnreg__(64) k_dense_offdiag_rows(OpNodes nd, int total, double k, double ik, SplitOp A,
+                                                           int* __restrict__ counter) {
+  __shared__ int s_item;
+  const int rows = (total + 3) / 4;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();   // s_item is rewritten next round
+    if (item >= rows) return;
+    const int s0 = (rows - 1 - item) * 4;
+    const int s = s0 + (threadIdx.x & 3);
+    for (int t = threadIdx.x >> 2; t < s0 + 3; t += 32)
+      if (s < total && t < s) offdiag_pair(nd, t, s, k, ik, A);
+  }
 }
 
 // Column scales of the stored operator: cs[u index] = w/4, cs[q index] = k w/4.
@@ -583,6 +611,23 @@ void assemble_dense_offdiag64(OpNodes nd, int total, double k0, SplitOp A, cudaS
   dim3 g((total + 63) / 64, (total + 3) / 4);
   KPROF_BEGIN(st);
   k_dense_offdiag<<<g, 256, 0, st>>>(nd, total, k0, 1.0 / k0, A);
+  pm_launch_count_add(1);
+  KPROF_END(st, "dense_offdiag64", 0.0);
+}
+
+void assemble_dense_offdiag64_rows(OpNodes nd, int total, double k0, SplitOp A, int* counter, cudaStream_t st) {
+  if (total <= 0) return;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaMemsetAsync(counter, 0, sizeof(int), st);
+  // an SM changes its shared-memory carveout only when it is empty: the
+  // persistent CTAs keep it at the maximum so that other kernels' shared
+  // memory still fits beside them (the same value every time)
+  cudaFuncSetAttribute(k_dense_offdiag_rows, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  KPROF_BEGIN(st);
+  k_dense_offdiag_rows<<<sms, 128, 0, st>>>(nd, total, k0, 1.0 / k0, A, counter);
   pm_launch_count_add(1);
   KPROF_END(st, "dense_offdiag64", 0.0);
 }

@@ -36,6 +36,11 @@ struct SplitOp {
 // caller copies the self blocks in).  One Hankel evaluation per node pair
 // fills the pair's 2 x 2 entries.
 void assemble_dense_offdiag64(OpNodes nd, int total_nodes, double k0, SplitOp A, cudaStream_t st);
+// The same entries from one persistent CTA of 128 threads per SM taking rows
+// from *counter (zeroed here), so that the assembly can run beside other
+// kernels on a low-priority stream.
+void assemble_dense_offdiag64_rows(OpNodes nd, int total_nodes, double k0, SplitOp A, int* counter,
+                                   cudaStream_t st);
 void dense_colscale(const double* w, const int* iu, const int* iq, int total_nodes, double k0, double* cs,
                     cudaStream_t st);
 // Xs = diag(cs) X, N x nrhs.

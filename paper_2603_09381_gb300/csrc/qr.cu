@@ -101,7 +101,9 @@ __device__ __forceinline__ void panel_pass(const QrProb<C>& p, int j0, int jb, i
 }
 
 template <typename C>
-__global__ void __launch_bounds__(PT) k_qr_panel(const QrProb<C>* __restrict__ P, int j0) {
+// At most 104 registers: 512 x 104 leaves room on the SM for one CTA of the
+// operator assembly that may run beside the factorization.
+__global__ void __maxnreg__(104) k_qr_panel(const QrProb<C>* __restrict__ P, int j0) {
   typedef typename real_of<C>::type R;
   cg::cluster_group cluster = cg::this_cluster();
   const int csize = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
@@ -391,7 +393,8 @@ constexpr int WAIT = 1 << 20;                  // x ~1 us suspend hint: about a 
 // no_arrive (tests of the timeout path): every CTA first waits, with a bound
 // of about a millisecond, on a barrier that nothing arrives at, then issues
 // nothing, frees its tensor memory and sets *err.
-__global__ void __launch_bounds__(tcq::T) k_qr_apply_tc(const QrProb<float2>* __restrict__ P, int j0, int* err,
+// At most 112 registers: two CTAs per SM beside one CTA of the operator assembly.
+__global__ void __maxnreg__(112) k_qr_apply_tc(const QrProb<float2>* __restrict__ P, int j0, int* err,
                                                         int no_arrive) {
   using namespace tcq;
   extern __shared__ __align__(1024) unsigned char sm[];

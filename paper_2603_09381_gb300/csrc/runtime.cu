@@ -339,6 +339,10 @@ struct pm_factor {
   int* d_iq = nullptr;
   float2* dense64 = nullptr;    // the whole FP64 operator, N x N, split: hi plane then lo plane, when it fits
   SplitOp dense_op{};           // its two planes
+  bool op_started = false;      // index maps, column scales and the operator's assembly are enqueued
+  bool op_pending = false;      // start the assembly beside the factorization once the leaves are assembled
+  cudaStream_t op_st = nullptr; // the operator's assembly beside the factorization (low priority)
+  cudaEvent_t op_done = nullptr;
   double* d_colscale = nullptr; // its column scales: A = dense64 diag(d_colscale)
   size_t dense_bytes = 0;
   // CUDA graphs of the compressed inverse (FP64) or the mixed preconditioner,
@@ -377,6 +381,11 @@ size_t g_dense_held = 0;
 }  // namespace
 
 pm_factor::~pm_factor() {
+  if (op_st) {
+    cudaStreamSynchronize(op_st);
+    cudaStreamDestroy(op_st);
+  }
+  if (op_done) cudaEventDestroy(op_done);
   if (dense64) {
     pool_free(dense64, dense_bytes, Done::Unknown);   // the caller's stream may be gone
     std::lock_guard<std::mutex> lk(g_dense_mu);
@@ -385,6 +394,9 @@ pm_factor::~pm_factor() {
 }
 
 template <class C> std::vector<std::vector<BoxF<C>>>& levels_of(pm_factor* F);
+namespace {
+void start_mixed_operator(pm_factor* F, bool beside);
+}
 template <> std::vector<std::vector<BoxF<double2>>>& levels_of<double2>(pm_factor* F) { return F->lev64; }
 template <> std::vector<std::vector<BoxF<float2>>>& levels_of<float2>(pm_factor* F) { return F->lev32; }
 
@@ -1251,6 +1263,13 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
   for (int i = 0; i < nid; ++i) jobs[job_of[i / 4]].F->stats.id_rows += W[i];
   const double ms_asm = t_asm.stop();
   for (const auto& J : jobs) J.F->stats.ms_assemble += ms_asm;
+  // the operator's FP64 assembly starts beside the factorization once the
+  // leaf level's FP64 work (self blocks, Maue products) is done
+  for (const auto& J : jobs)
+    if (J.F->op_pending) {
+      J.F->op_pending = false;
+      start_mixed_operator(J.F, true);
+    }
   Timer t_id(st);
   // 3a. complex64: tall inputs reduced to their triangular factor first, so
   // that the pivoted steps stream n instead of W rows
@@ -2513,22 +2532,16 @@ double hankel_flops_per_pair(const pm_geometry* g) {
   return sum / n;
 }
 
-void finish_mixed(pm_factor* F) {
+// Index maps, column scales and, when it fits, the dense FP64 operator of a
+// mixed factorization (its self blocks are copied in by finish_mixed).
+// beside: the assembly runs on a low-priority stream as the persistent
+// kernel (one CTA of 128 threads per SM), concurrently with the
+// factorization that follows: it is FP64-bound and the complex64
+// factorization leaves the FP64 pipes idle; finish_mixed joins it.
+void start_mixed_operator(pm_factor* F, bool beside) {
   const pm_geometry* g = F->g;
   const pm_factor_opts* opts = &F->opts;
-  // FP64 self blocks and index maps for the refinement residual
-  // (those of the leaves' inclusions were assembled with the leaf level)
-  F->scratch.reset();
-  std::vector<int> incl, lda;
-  std::vector<double2*> A64;
-  if (F->self64.size() != (size_t)g->m) F->self64.assign(g->m, nullptr);
-  for (int j = 0; j < g->m; ++j) {
-    if (F->self64[j]) continue;
-    const int m2 = 2 * g->inc[j].n_nodes;
-    F->self64[j] = F->arena.get<double2>((size_t)m2 * m2);
-    incl.push_back(j); lda.push_back(m2); A64.push_back(F->self64[j]);
-  }
-  if (!incl.empty()) assemble_self<double2>(g, incl, A64, lda, F->scratch, F->st);
+  F->op_started = true;
   std::vector<int> iu(g->total_nodes), iq(g->total_nodes);
   for (int j = 0; j < g->m; ++j)
     for (int l = 0; l < g->inc[j].n_nodes; ++l) {
@@ -2557,18 +2570,51 @@ void finish_mixed(pm_factor* F) {
       }
     }
   }
-  if (F->dense64) {
-    OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
-    F->d_colscale = F->arena.get<double>((size_t)g->N);
-    dense_colscale(g->nodes.w, F->d_iu, F->d_iq, g->total_nodes, g->k0, F->d_colscale, F->st);
+  if (!F->dense64) return;
+  OpNodes nd{g->nodes.x, g->nodes.y, g->nodes.nx, g->nodes.ny, g->nodes.w, g->nodes.incl, F->d_iu, F->d_iq};
+  F->d_colscale = F->arena.get<double>((size_t)g->N);
+  dense_colscale(g->nodes.w, F->d_iu, F->d_iq, g->total_nodes, g->k0, F->d_colscale, F->st);
+  if (beside) {
+    int pr_lo = 0, pr_hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&pr_lo, &pr_hi));
+    CK(cudaStreamCreateWithPriority(&F->op_st, cudaStreamNonBlocking, pr_lo));
+    CK(cudaEventCreateWithFlags(&F->op_done, cudaEventDisableTiming));
+    CK(cudaEventRecord(F->op_done, F->st));   // the index maps are on the device
+    CK(cudaStreamWaitEvent(F->op_st, F->op_done, 0));
+    int* counter = F->arena.get<int>(1);
+    assemble_dense_offdiag64_rows(nd, g->total_nodes, g->k0, F->dense_op, counter, F->op_st);
+    CK(cudaEventRecord(F->op_done, F->op_st));
+  } else {
     assemble_dense_offdiag64(nd, g->total_nodes, g->k0, F->dense_op, F->st);
-    if (g_kprof) {
-      double pairs = (double)g->total_nodes * g->total_nodes;
-      for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
-      // per unordered pair: 40 for the geometry and the eight entries of both
-      // 2 x 2 blocks, plus the Hankel pair
-      g_kprof->add_flops("dense_offdiag64", 0.5 * pairs * (40.0 + hankel_flops_per_pair(g)));
-    }
+  }
+  if (g_kprof) {
+    double pairs = (double)g->total_nodes * g->total_nodes;
+    for (int j = 0; j < g->m; ++j) pairs -= (double)g->inc[j].n_nodes * g->inc[j].n_nodes;
+    // per unordered pair: 40 for the geometry and the eight entries of both
+    // 2 x 2 blocks, plus the Hankel pair
+    g_kprof->add_flops("dense_offdiag64", 0.5 * pairs * (40.0 + hankel_flops_per_pair(g)));
+  }
+  CK(cudaGetLastError());
+}
+
+void finish_mixed(pm_factor* F) {
+  const pm_geometry* g = F->g;
+  // FP64 self blocks and index maps for the refinement residual
+  // (those of the leaves' inclusions were assembled with the leaf level)
+  F->scratch.reset();
+  std::vector<int> incl, lda;
+  std::vector<double2*> A64;
+  if (F->self64.size() != (size_t)g->m) F->self64.assign(g->m, nullptr);
+  for (int j = 0; j < g->m; ++j) {
+    if (F->self64[j]) continue;
+    const int m2 = 2 * g->inc[j].n_nodes;
+    F->self64[j] = F->arena.get<double2>((size_t)m2 * m2);
+    incl.push_back(j); lda.push_back(m2); A64.push_back(F->self64[j]);
+  }
+  if (!incl.empty()) assemble_self<double2>(g, incl, A64, lda, F->scratch, F->st);
+  if (!F->op_started) start_mixed_operator(F, false);
+  if (F->dense64) {
+    if (F->op_done) CK(cudaStreamWaitEvent(F->st, F->op_done, 0));
     for (int j = 0; j < g->m; ++j) {
       const int m2 = 2 * g->inc[j].n_nodes;
       split_copy(F->self64[j], m2, F->dense_op.at(g->row_off[j], g->row_off[j]), m2, m2, F->d_colscale + g->row_off[j],
@@ -2701,6 +2747,7 @@ pm_status pm_factorize(const pm_geometry* g, const pm_factor_opts* opts, pm_fact
       ~ProfScope() { g_kprof = nullptr; }
     } scope(F->profiling ? &F->prof : nullptr);
     Timer tt(F->st);
+    F->op_pending = F->precision == PM_MIXED && !(F->opts.flags & PM_FLAG_OPERATOR_AFTER);
     std::vector<pm_factor*> one{F};
     factor_group(one, id_tol, F->scratch, F->st);
     if (F->precision == PM_MIXED) finish_mixed(F);

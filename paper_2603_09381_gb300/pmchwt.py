@@ -84,6 +84,7 @@ PM_FLAG_NO_GRAPHS = 128
 PM_FLAG_PROXY_CHECK = 256
 PM_FLAG_QR_CUDA_CORES = 512
 PM_FLAG_TOP_FP64 = 1024
+PM_FLAG_OPERATOR_AFTER = 2048
 PM_DEBUG_SINGULAR_BLOCK = 1
 PM_DEBUG_SINGULAR_COMPRESSED = 2
 PM_DEBUG_UNDERPREDICT = 4
@@ -288,12 +289,14 @@ class Factor:
                  profile=False, refine_tol=0.0, max_refine=0, low_tol=0.0, rank_model=None, dense_operator=True,
                  qr_first=True, tensor_cores=False, ff_confirm=True, debug_flags=0, autotune=True, graphs=True,
                  proxy_scale=0.0, proxy_check=False, formulation=PM_FORM_OMIT, scratch_gb=0.0,
-                 qr_tensor_cores=True, top_fp64=False):
+                 qr_tensor_cores=True, top_fp64=False, operator_after=False):
         """rank_model: device pointer (int) of a trained predictor, or None;
         qr_tensor_cores: the QR-first update's C -= V Y on the tensor cores (default) or,
         with False, on the CUDA cores (PM_FLAG_QR_CUDA_CORES);
         top_fp64: PM_MIXED factors the top-level system in complex128 (PM_FLAG_TOP_FP64)
         instead of complex64;
+        operator_after: PM_MIXED assembles the dense operator after the factorization
+        (PM_FLAG_OPERATOR_AFTER) instead of beside it;
         ff_confirm: the refinement ends on the folded float-float product (default) or,
         with False, on the FP64 product (PM_FLAG_FP64_CONFIRM);
         debug_flags: PM_DEBUG_* fault injection for failure-path tests (0 in normal use)."""
@@ -307,7 +310,8 @@ class Factor:
                            | (0 if ff_confirm else PM_FLAG_FP64_CONFIRM) | (0 if autotune else PM_FLAG_NO_AUTOTUNE)
                            | (0 if graphs else PM_FLAG_NO_GRAPHS) | (PM_FLAG_PROXY_CHECK if proxy_check else 0)
                            | (0 if qr_tensor_cores else PM_FLAG_QR_CUDA_CORES)
-                           | (PM_FLAG_TOP_FP64 if top_fp64 else 0),
+                           | (PM_FLAG_TOP_FP64 if top_fp64 else 0)
+                           | (PM_FLAG_OPERATOR_AFTER if operator_after else 0),
                            float(refine_tol), int(max_refine), float(low_tol),
                            ct.c_void_p(rank_model) if rank_model else None, int(debug_flags), float(proxy_scale),
                            int(formulation), float(scratch_gb))
