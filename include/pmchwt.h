@@ -96,7 +96,8 @@ typedef struct pm_factor pm_factor;
  *      rounding stays far below the levels' ID threshold); PM_FLAG_TOP_FP64
  *      factors it in complex128.  pm_factorize assembles the dense
  *      complex128 operator on a low-priority stream concurrently with the
- *      complex64 factorization (one persistent CTA of 128 threads per SM);
+ *      complex64 factorization, from the end of the leaf level's assembly
+ *      (one persistent CTA of 128 threads per SM);
  *      PM_FLAG_OPERATOR_AFTER assembles it after the factorization instead
  *      (pm_factor_batch always does).
  * stream: cudaStream_t to run on, or NULL for the default stream.
