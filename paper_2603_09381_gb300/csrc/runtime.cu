@@ -1192,7 +1192,7 @@ void process_levels(const std::vector<LevelJob>& jobs, Arena& scr, cudaStream_t 
     }
     if (O.debug_flags & PM_DEBUG_UNDERPREDICT) std::fill(khat.begin(), khat.end(), 1);   // injected
   }
-  // the held-out proxy check: asked for, or the judge of lowered counts in FP64
+  // the held-out proxy check: asked for, or what decides lowered counts in FP64
   const bool check_on = O.formulation == PM_FORM_OMIT &&
                         ((O.flags & PM_FLAG_PROXY_CHECK) ||
                          (lowered && O.rank_model && O.precision == PM_FP64 && O.proxy_points == 0));

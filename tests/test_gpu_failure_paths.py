@@ -91,7 +91,7 @@ def test_default_tensor_core_update_wait_that_runs_out_returns_timeout(pm):
 
 def test_forced_underprediction_falls_back_to_the_adaptive_rank(pm):
     """Every predicted rank forced to 1: each ID exceeds its prediction and
-    falls back to the adaptive CPQR, which stays the judge of the rank, so the
+    falls back to the adaptive CPQR, which still decides the rank, so the
     factorization and the solution are those of the run without a predictor."""
     from paper_2603_09381_gb300 import rank_predictor as rp
     mdl = rp.load_model()

@@ -92,7 +92,7 @@ def test_simplified_burton_miller_is_singular(pm):
     with pytest.raises(pm.PmError) as e:
         pm.Factor(g, 1e-10, formulation=pm.PM_FORM_BM_SIMPLIFIED)
     assert e.value.status == 4 and "R A^-1 L" in str(e.value)
-    # the oracle reaches the same verdict
+    # the oracle reaches the same conclusion
     with pytest.raises(proxy.SingularError):
         proxy.factor(wl.circle_grid(2, 2), {"tol": 1e-10, "formulation": "bm_simplified"})
 
