@@ -375,15 +375,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // acc (hi, lo) += a * x for split a = (ah, al), x = (xh, xl): the hi products
-// are split exactly (fmaf), the cross terms and all errors go to lo.
+// are split exactly (fmaf); their error and the cross terms are gathered in
+// one FMA chain, which goes to lo with the TwoSum error (12 FP32 operations).
 __device__ __forceinline__ void ff_mac(float& hi, float& lo, float ah, float al, float xh, float xl, float sgn) {
   const float p = ah * xh;
-  const float pe = fmaf(ah, xh, -p);
-  const float cross = fmaf(ah, xl, al * xh);
+  float t = fmaf(ah, xh, -p);   // the exact error of ah xh
+  t = fmaf(ah, xl, t);
+  t = fmaf(al, xh, t);
   float s, e;
   two_sum(hi, sgn * p, s, e);
   hi = s;
-  lo += e + sgn * (pe + cross);
+  lo += e + sgn * t;
 }
 
 template <int NR>

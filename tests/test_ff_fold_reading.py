@@ -4,7 +4,7 @@ The CUDA product behind PM_FLAG_FF_CONFIRM works as follows.
   * The operator entry a = a_hi + a_lo is a 24+24-bit split.
   * x = x_hi + x_lo is rounded to nearest.
   * For each term, the FMA-exact error of a_hi x_hi and the first-order
-    cross terms a_hi x_lo + a_lo x_hi go to lo.
+    cross terms a_hi x_lo and a_lo x_hi, gathered by one FMA chain, go to lo.
   * The TwoSum error of hi + a_hi x_hi also goes to lo.
   * (hi, lo) is folded into an FP64 sum every 16 terms.
 This restatement checks that the folded sum stays within the bound the
@@ -33,10 +33,11 @@ def _ff_dot(ah, al, xh, xl, fold):
     acc, hi, lo = 0.0, f32(0), f32(0)
     for j in range(len(ah)):
         p = f32(ah[j] * xh[j])
-        pe = f32(f64(ah[j]) * f64(xh[j]) - f64(p))                   # exact product error (FMA)
-        cross = f32(f64(ah[j]) * f64(xl[j]) + f64(f32(al[j] * xh[j])))
+        t = f32(f64(ah[j]) * f64(xh[j]) - f64(p))                    # exact product error (FMA)
+        t = f32(f64(ah[j]) * f64(xl[j]) + f64(t))                    # FMA chain of the cross terms
+        t = f32(f64(al[j]) * f64(xh[j]) + f64(t))
         hi, e = _two_sum(hi, p)
-        lo = f32(lo + f32(e + f32(pe + cross)))
+        lo = f32(lo + f32(e + t))
         if fold and (j + 1) % fold == 0:
             acc += f64(hi) + f64(lo)
             hi, lo = f32(0), f32(0)
