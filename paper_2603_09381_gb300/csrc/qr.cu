@@ -101,9 +101,9 @@ __device__ __forceinline__ void panel_pass(const QrProb<C>& p, int j0, int jb, i
 }
 
 template <typename C>
-// At most 104 registers: 512 x 104 leaves room on the SM for one CTA of the
+// At most 112 registers: 512 x 112 leaves room on the SM for one CTA of the
 // operator assembly that may run beside the factorization.
-__global__ void __maxnreg__(104) k_qr_panel(const QrProb<C>* __restrict__ P, int j0) {
+__global__ void __maxnreg__(112) k_qr_panel(const QrProb<C>* __restrict__ P, int j0) {
   typedef typename real_of<C>::type R;
   cg::cluster_group cluster = cg::this_cluster();
   const int csize = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
